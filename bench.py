@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the FEM harmonic-inpainting data optimisation on GB300.
+
+One step = the whole hot path on one seeded 1025 x 1025 image: create the
+two-triangle mesh, spatial optimisation (top-k 1 % of triangles per round,
+newest-vertex bisection, FP32 CG inside FP64 refinement, until 3 % of the
+pixels are vertices), g = f at the mask vertices, tonal optimisation (CG on
+the normal equations through forward and adjoint solves).  value = image
+Mpixel per second of whole-step time, inputs resident in HBM; e2e = the same
+through the public API with the image copied from pinned host memory and the
+result (mesh + g) copied back inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank optimises its own image (seed + rank):
+replicas, no collective on the data path; the barrier and the max over
+ranks of the timed region are the only communication.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s FEM inpaint+tonal opt at 1e-6 rel err vs FP64"
+UNIT = "Mpixel/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1025)
+    ap.add_argument("--density", type=float, default=0.03)
+    ap.add_argument("--frac", type=float, default=0.01)
+    ap.add_argument("--tonal-tol", type=float, default=1e-8)
+    ap.add_argument("--precision", default="fp32ir", choices=["fp32ir", "fp64"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check after timing")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"{a.n}x{a.n} seeded image: spatial optimisation (top-k {a.frac:.0%} of triangles per round, NVB, "
+            f"to {a.density:.0%} vertex density) + tonal optimisation (CG on B^T B g = B^T f, tol {a.tonal_tol:g})")
+
+
+def config(a, world):
+    return {"workload": workload_name(a), "image": f"{a.n}x{a.n}", "density": a.density, "topk_frac": a.frac,
+            "tonal_tol": a.tonal_tol, "precision": a.precision, "seed": a.seed, "l2_flush": True,
+            "parallelism": f"replicas{world}" if world > 1 else "single"}
+
+
+# ------------------------------------------------------------------ helpers
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.lines = []
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(family):
+    """Per-launch DRAM bytes of the dominant kernel from a committed ncu
+    summary, used only while the kernel source it was taken from is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    import hashlib
+    with open(p) as fh:
+        rec = json.load(fh).get(family)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2105_01586_gb300", "csrc", rec["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.exists(src) else None
+    return rec["dram_bytes_per_launch"] if h == rec.get("source_sha256_16") else None
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(a, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2105_01586_gb300 as fem
+    import seeded_inputs
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = a.n
+    P = n * n
+    f_np = seeded_inputs.make_image(n, a.seed + rank)
+    f = torch.from_numpy(f_np).to(dev)
+    prec = fem.FEM_PREC_FP64 if a.precision == "fp64" else fem.FEM_PREC_FP32_IR
+    p = fem.params(topk_frac=a.frac, tonal_tol=a.tonal_tol, precision=prec)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(f_dev, keep=False):
+        mesh = fem.Mesh(n)
+        mesh.spatial_refine(f_dev, a.density, p)
+        g = mesh.g_from_f(f_dev)
+        fem.fem_tonal_opt(mesh.h, f_dev, g, p)
+        if keep:
+            return mesh, g
+        mesh.close()
+        return None
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(a.warmup):
+        step(f)
+    # which kernel family dominates (one profiled step, all families)
+    fem.fem_profile_enable(True)
+    step(f)
+    prof_all = fem.fem_profile_read()
+    fem.fem_profile_enable(False)
+    dom = max(prof_all, key=lambda k: prof_all[k]["ms"])
+
+    # timed region: K steps, L2 flushed between steps (outside the events);
+    # the dominant family's launches are bracketed by events on the launching stream
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    fem.fem_profile_enable(dom)
+    launches0 = fem.fem_launch_count()
+    times = []
+    for _ in range(a.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(f)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = fem.fem_launch_count() - launches0
+    prof = fem.fem_profile_read()[dom]
+    fem.fem_profile_enable(False)
+    clocks = clk.stop()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    barrier()
+    ms_per_step = total_ms / a.steps
+    value = world * P / 1e6 / (ms_per_step / 1e3)
+
+    # end to end through the public API: pinned host image in, mesh + g out
+    f_host = torch.from_numpy(f_np).pin_memory()
+    e2e_times = []
+    h2d = d2h = 0
+    for _ in range(max(1, min(a.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        f_dev = f_host.to(dev, non_blocking=True)
+        mesh, g = step(f_dev, keep=True)
+        g_host = g.cpu()
+        xy, tri, mk = mesh.export()
+        torch.cuda.synchronize(dev)
+        e2e_times.append((time.perf_counter() - t0) * 1e3)
+        h2d = f_host.numel() * 4
+        d2h = g_host.numel() * 4 + xy.nbytes + tri.nbytes + mk.nbytes
+        mesh.close()
+    e2e_ms = statistics.mean(e2e_times)
+    e2e = {"value": round(world * P / 1e6 / (e2e_ms / 1e3), 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)}
+
+    # accuracy vs the plain FP64 GPU path at tight tolerance (outside the timed region)
+    mesh, g = step(f, keep=True)
+    st = mesh.stats()
+    info = mesh.info
+    extra = {"V": info[0], "T": info[1], "nmask": info[2], "tonal_iters": st["tonal_iters"],
+             "tonal_relres": st["tonal_relres"]}
+    s2 = fem.Mesh(n)
+    s2.spatial_refine(f, a.density, fem.params(topk_frac=a.frac, precision=fem.FEM_PREC_FP64))
+    extra["rounds"] = s2.stats()["rounds"]
+    extra["min_topk_margin"] = s2.stats()["min_margin"]
+    if not a.no_check:
+        same = all(np.array_equal(x, y) for x, y in zip(mesh.export(), s2.export()))
+        g64 = s2.g_from_f(f)
+        fem.fem_tonal_opt(s2.h, f, g64, fem.params(tonal_tol=1e-12, precision=fem.FEM_PREC_FP64, inner_tol=1e-13,
+                                                   tonal_maxit=20000))
+        rel = float(torch.linalg.vector_norm((g.double() - g64.double())) / torch.linalg.vector_norm(g64.double()))
+        extra["mesh_equal_fp64"] = bool(same)
+        extra["rel_err_vs_fp64"] = rel
+    mesh.close()
+    s2.close()
+
+    peak, peak_kind = measured_peaks()
+    per_launch_bytes = prof["bytes"] / max(1, prof["launches"])
+    per_launch_ms = prof["ms"] / max(1, prof["launches"])
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel_family": dom, "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic_record(dom), "peak_kind": peak_kind,
+                "launches_in_timed_region": prof["launches"], "ms_in_timed_region": round(prof["ms"], 3),
+                "share_of_step": round(prof["ms"] / total_ms, 4) if world == 1 else None,
+                "family_ms_one_step": {k: round(v["ms"], 3) for k, v in prof_all.items()}}
+
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32+fp64", "data": "synthetic",
+            "config": config(a, world), "roofline": roofline, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(launches)}
+    line.update(extra)
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a, f_np)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------- the oracle on CPU
+def oracle_job(a, f_np, tonal_iters=None):
+    """The oracle on the same workload; tonal_iters caps the outer iterations
+    (None: run to the tolerance).  Returns (spatial s, tonal s, outer iterations)."""
+    import oracle
+    t0 = time.perf_counter()
+    om, log = oracle.spatial(f_np, a.density, a.frac)
+    t1 = time.perf_counter()
+    g, st = oracle.tonal(om, f_np, tol=a.tonal_tol, maxit=tonal_iters or 100000, inner_tol=1e-11,
+                         allow_not_converged=True)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, st["iters"], len(log)
+
+
+def cpu_baseline(a, f_np):
+    ts, tt, it, rounds = oracle_job(a, f_np)
+    P = a.n * a.n
+    return {"value": round(P / 1e6 / (ts + tt), 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full run of the workload by the FP64 C oracle (single thread): spatial {rounds} rounds "
+                      f"{ts:.1f} s + tonal {it} outer iterations {tt:.1f} s"}
+
+
+def run_reference(a, world, rank):
+    """The oracle as the reference arm: each step runs the full spatial
+    optimisation and 10 tonal outer iterations; the tonal time is scaled to
+    the outer-iteration count of a full tonal run taken in the first warm-up."""
+    if rank != 0:
+        return
+    import seeded_inputs
+    f_np = seeded_inputs.make_image(a.n, a.seed)
+    P = a.n * a.n
+    cap = 10
+    full_iters = None
+    for w in range(a.warmup):
+        if w == 0:
+            _, _, full_iters, _ = oracle_job(a, f_np)
+        else:
+            oracle_job(a, f_np, cap)
+    times = []
+    for _ in range(a.steps):
+        ts, tt, it, rounds = oracle_job(a, f_np, cap)
+        times.append(ts + tt * (full_iters / max(1, it)))
+    ms = 1e3 * statistics.mean(times)
+    value = P / 1e6 / (ms / 1e3)
+    sample = (f"per step: oracle spatial optimisation in full ({rounds} rounds) + {cap} tonal outer iterations, "
+              f"tonal time scaled to the {full_iters} iterations of a full tonal run (first warm-up step)")
+    line = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(a, 1), "impl": "reference",
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    world, rank, local = dist_setup()
+    if a.warmup < 3:
+        a.warmup = 3
+    if a.impl == "reference":
+        run_reference(a, world, rank)
+    else:
+        run_ours(a, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

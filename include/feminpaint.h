@@ -1,0 +1,197 @@
+/*
+ * feminpaint.h -- C ABI of the GB300 (sm_103a) library for FEM harmonic
+ * inpainting with spatial and tonal data optimisation, after Chizhov &
+ * Weickert, "Efficient Data Optimisation for Harmonic Inpainting with Finite
+ * Elements" (arXiv 2105.01586).
+ *
+ * Conventions shared by every call
+ *  - Images are width x height float32, row-major, y pointing down; pixel
+ *    (x, y) is at offset y*width + x.  width == height == 2^L + 1 (L >= 1), so
+ *    that every edge midpoint created by bisection is a pixel.
+ *  - A mesh has V vertices (integer pixel positions) and T triangles.  A
+ *    triangle is stored as (a, b, c): (a, b) is its refinement edge and c its
+ *    newest vertex (the right-angle corner).  Vertices are either mask
+ *    vertices (the Dirichlet set K of eqs. 1-3, "stored pixels") or unknown
+ *    vertices (U), whose values the Laplace solve provides (Sec. 2.2).
+ *  - g, the grey values at the mask vertices, is ordered by ascending vertex
+ *    id among the mask vertices (nmask entries).
+ *  - "_dev" pointers are device pointers on the current CUDA device; the
+ *    caller owns them.  Host pointers are named "_host" or documented as host
+ *    buffers.  The library owns the mesh and all its scratch memory, which it
+ *    allocates with the stream-ordered allocator on the stream it is given.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call enqueues its work on that stream; calls that return
+ *    sizes or convergence results synchronise that stream before returning.
+ *  - Every call returns a fem_status and never aborts or traps; on failure
+ *    fem_last_error() gives a message.  A solve that reaches its iteration
+ *    cap returns FEM_E_NOT_CONVERGED with the last iterate written.  Waits
+ *    inside persistent kernels are bounded; when one runs out the call
+ *    returns FEM_E_TIMEOUT and the CUDA context stays usable.
+ */
+#ifndef FEMINPAINT_H
+#define FEMINPAINT_H
+
+#if defined(__GNUC__)
+#define FEM_API __attribute__((visibility("default")))
+#else
+#define FEM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fem_mesh fem_mesh;
+
+typedef enum {
+    FEM_OK = 0,
+    FEM_E_INVALID = 1,       /* bad argument or malformed mesh */
+    FEM_E_SHAPE = 2,         /* image side is not 2^L + 1, or width != height */
+    FEM_E_OOM = 3,           /* device allocation failed */
+    FEM_E_NOT_CONVERGED = 4, /* iteration cap reached; last iterate written */
+    FEM_E_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+    FEM_E_CUDA = 6           /* a CUDA runtime error (message in fem_last_error) */
+} fem_status;
+
+enum {
+    FEM_PREC_FP32_IR = 0, /* FP32 preconditioned CG inside FP64 iterative refinement */
+    FEM_PREC_FP64 = 1     /* plain FP64 preconditioned CG */
+};
+
+/* Solver and optimisation parameters.  fem_params_default() fills:
+ * tol 1e-12, maxit 20000, precision FP32_IR, topk_frac 0.01, max_rounds 0,
+ * tonal_tol 1e-8, tonal_maxit 2000, inner_tol 1e-11. */
+typedef struct {
+    double tol;         /* Laplace solve: stop at ||b - A x|| <= tol ||b|| (FP64 residual) */
+    int maxit;          /* Laplace solve: cap on CG iterations summed over refinement steps */
+    int precision;      /* FEM_PREC_FP32_IR or FEM_PREC_FP64 */
+    double topk_frac;   /* spatial: k = max(1, ceil(topk_frac * T)) triangles per round */
+    int max_rounds;     /* spatial: stop after this many rounds (0 = only the density rule) */
+    double tonal_tol;   /* tonal: stop at ||B^T (f - B g)|| <= tonal_tol ||B^T f|| */
+    int tonal_maxit;    /* tonal: cap on outer CG iterations */
+    double inner_tol;   /* tonal and adjoint: relative tolerance of the inner Laplace solves */
+} fem_params;
+
+/* Counters of the last call on a mesh (host copy). */
+typedef struct {
+    int rounds;            /* spatial: refinement rounds run */
+    long long cg_iters;    /* CG iterations, all solves of the call */
+    int solves;            /* Laplace solves run */
+    double relres;         /* last Laplace solve's FP64 relative residual */
+    int tonal_iters;       /* tonal: outer iterations */
+    double tonal_relres;   /* tonal: ||B^T r|| / ||B^T f|| at exit */
+    double min_margin;     /* spatial: smallest relative gap between the k-th and (k+1)-th key */
+} fem_stats;
+
+FEM_API void fem_params_default(fem_params *p);
+
+/* Create the initial mesh for a width x height image (Sec. 2.2's mesh,
+ * replaced by the two triangles of the image square split along the diagonal
+ * (0,0)-(N-1,N-1)): vertices 0..3 at the corners (0,0), (N-1,0), (0,N-1),
+ * (N-1,N-1), all mask vertices, and triangles (v0,v3,v2), (v3,v0,v1).
+ * *out receives a library-owned handle.  FEM_E_SHAPE unless width == height
+ * == 2^L + 1 with 2 <= 2^L <= 2^15. */
+FEM_API fem_status fem_mesh_create(int width, int height, void *stream, fem_mesh **out);
+
+/* Free the mesh and its device memory (after the work on its streams ends). */
+FEM_API fem_status fem_mesh_destroy(fem_mesh *m);
+
+/* Sizes of the mesh: vertices, triangles, mask vertices (any pointer may be NULL). */
+FEM_API fem_status fem_mesh_info(const fem_mesh *m, int *V, int *T, int *nmask);
+
+/* Copy the mesh to host buffers: xy (2V ints: x0,y0,x1,y1,...), tri (3T ints:
+ * a,b,c per triangle), is_mask (V bytes, 1 = mask vertex).  Any may be NULL.
+ * Synchronises the mesh's last stream. */
+FEM_API fem_status fem_mesh_export(fem_mesh *m, int *xy, int *tri, unsigned char *is_mask);
+
+/* Replace the mesh by host arrays of the same layout (checkpoint/resume).
+ * The arrays are checked: vertices on the grid, triangles positively
+ * oriented and right-isosceles with c at the right angle, areas summing to
+ * the image.  Conformity is the caller's contract.  FEM_E_INVALID otherwise. */
+FEM_API fem_status fem_mesh_import(fem_mesh *m, int V, const int *xy, int T, const int *tri,
+                           const unsigned char *is_mask);
+
+/* Harmonic inpainting on the mesh (Sec. 2.2, eqs. 1-3): the linear FEM
+ * system A_UU x_U = -A_UK g is solved by preconditioned CG and the solution
+ * is interpolated linearly inside each triangle (u = B g of Sec. 4).
+ *   g_dev   in : nmask float32 mask-vertex values
+ *   u_dev   out: width*height float32 image, or NULL
+ *   uv_dev  out: V float64 vertex values (g at K, solution at U), or NULL
+ * Each pixel takes its value from exactly one owning triangle. */
+FEM_API fem_status fem_inpaint(fem_mesh *m, const float *g_dev, float *u_dev, double *uv_dev,
+                       const fem_params *p, void *stream);
+
+/* Dirichlet data taken from the image: g_dev[k] = f at the pixel of the k-th
+ * mask vertex (the stored grey values before tonal optimisation, Sec. 3).
+ *   f_dev in : width*height float32;  g_dev out: nmask float32 */
+FEM_API fem_status fem_gather_mask(fem_mesh *m, const float *f_dev, float *g_dev, void *stream);
+
+/* Per-triangle squared L2 error of Sec. 3: err[t] = sum over the pixels owned
+ * by t of (u - f)^2, with u the linear interpolant of the vertex values.
+ *   uv_dev  in : V float64 vertex values
+ *   f_dev   in : width*height float32 image
+ *   err_dev out: T float64 errors (interpolation and sums in FP64) */
+FEM_API fem_status fem_triangle_errors(fem_mesh *m, const double *uv_dev, const float *f_dev, double *err_dev,
+                               void *stream);
+
+/* Linear interpolation of vertex values to every pixel (end of Sec. 2.2).
+ *   uv_dev    in : V float64 vertex values
+ *   u_dev     out: width*height float32 image, or NULL
+ *   owner_dev out: width*height int32 owning triangle per pixel, or NULL */
+FEM_API fem_status fem_rasterize(fem_mesh *m, const double *uv_dev, float *u_dev, int *owner_dev, void *stream);
+
+/* Spatial optimisation (Sec. 3, with bisection instead of insertion): until
+ * V >= ceil(density * width*height) (or p->max_rounds rounds), each round
+ * sets g = f at the mask vertices, solves (warm-started), computes the
+ * per-triangle errors, selects the top k = max(1, ceil(topk_frac*T))
+ * eligible triangles (error descending, id ascending; eligible = refinement
+ * edge midpoint is a pixel; k capped by the vertex target) and refines them
+ * by newest-vertex bisection.  Midpoints of selected refinement edges become
+ * mask vertices; midpoints created only to keep the mesh conforming become
+ * unknown vertices.  New vertices are numbered by ascending pixel index, new
+ * triangles by ascending (generation, parent id).
+ *   f_dev in: width*height float32 image */
+FEM_API fem_status fem_spatial_refine(fem_mesh *m, const float *f_dev, double density, const fem_params *p,
+                              void *stream);
+
+/* Tonal optimisation (Sec. 4, eqs. 4-5): g* = argmin ||B g - f||^2 by CG on
+ * the normal equations B^T B g = B^T f, applying B and B^T through inner
+ * Laplace solves; B is never formed.
+ *   f_dev in : width*height float32 image
+ *   g_dev in : nmask float32 start values; out: the optimised values */
+FEM_API fem_status fem_tonal_opt(fem_mesh *m, const float *f_dev, float *g_dev, const fem_params *p, void *stream);
+
+/* Adjoint of u = B g (Sec. 4): gbar = B^T r = (P^T r)_K - A_KU A_UU^{-1} (P^T r)_U,
+ * with P the pixel interpolation matrix.  This is the gradient of
+ * <r, B g> with respect to g.
+ *   r_dev    in : width*height float32 pixel co-vector
+ *   gbar_dev out: nmask float32 */
+FEM_API fem_status fem_adjoint(fem_mesh *m, const float *r_dev, float *gbar_dev, const fem_params *p, void *stream);
+
+/* Counters of the last inpaint / refine / tonal / adjoint call on m. */
+FEM_API fem_status fem_mesh_stats(const fem_mesh *m, fem_stats *out);
+
+/* Message of the last failure on the calling thread ("" if none). */
+FEM_API const char *fem_last_error(void);
+
+/* Instrumentation, off by default.  family_mask bit f turns on family f
+ * (0 turns everything off).  For an enabled family the library records a
+ * CUDA event pair around every launch on the launching stream and adds up
+ * the algorithmic bytes of the work (bytes the operation must move at
+ * least once: inputs read, outputs written; counted on the host from the
+ * sizes and iteration counts).  fem_profile_read() synchronises, returns
+ * per family the launches, summed device time in ms and algorithmic bytes,
+ * and clears the records.  Families: 0 raster/error, 1 CG, 2 assembly,
+ * 3 top-k, 4 refinement, 5 tonal vector work, 6 other.  name receives a
+ * static label.  Returns 0, or -1 for an unknown family. */
+FEM_API void fem_profile_enable(int family_mask);
+FEM_API int fem_profile_read(int family, long long *launches, double *ms, double *bytes, const char **name);
+
+/* Number of kernels this library has launched in the process so far. */
+FEM_API long long fem_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEMINPAINT_H */

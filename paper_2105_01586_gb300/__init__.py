@@ -1,0 +1,347 @@
+"""GB300 (sm_103a) FEM harmonic inpainting with spatial and tonal data
+optimisation, after Chizhov & Weickert, "Efficient Data Optimisation for
+Harmonic Inpainting with Finite Elements" (arXiv 2105.01586).
+
+This module is a thin binding over the C ABI of ``libfeminpaint.so``
+(declared in ``include/feminpaint.h``): it checks and marshals torch tensors
+(device pointers and the current CUDA stream) and converts status codes to
+exceptions.  Every step of the computation runs in the library's CUDA
+kernels; there is no CPU fallback.  Importing this package raises if the
+library has not been built (``python -m paper_2105_01586_gb300._build``).
+
+Functions keep the C names (``fem_inpaint``, ``fem_triangle_errors``,
+``fem_spatial_refine``, ``fem_tonal_opt``, ``fem_adjoint``, ...).  ``Mesh``
+wraps a handle; ``FemInpaint`` / ``TonalLoss`` (in ``.autograd``) expose the
+forward map u = B g and its adjoint to torch autograd.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfeminpaint.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: the CUDA library must be built first "
+        "(python -m paper_2105_01586_gb300._build); there is no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+FEM_OK = 0
+FEM_E_INVALID = 1
+FEM_E_SHAPE = 2
+FEM_E_OOM = 3
+FEM_E_NOT_CONVERGED = 4
+FEM_E_TIMEOUT = 5
+FEM_E_CUDA = 6
+FEM_PREC_FP32_IR = 0
+FEM_PREC_FP64 = 1
+_STATUS = {0: "FEM_OK", 1: "FEM_E_INVALID", 2: "FEM_E_SHAPE", 3: "FEM_E_OOM", 4: "FEM_E_NOT_CONVERGED",
+           5: "FEM_E_TIMEOUT", 6: "FEM_E_CUDA"}
+
+EXPORTED = ["fem_params_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_info", "fem_mesh_export",
+            "fem_mesh_import", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_rasterize", "fem_spatial_refine",
+            "fem_tonal_opt", "fem_adjoint", "fem_mesh_stats", "fem_last_error", "fem_profile_enable",
+            "fem_profile_read", "fem_launch_count"]
+
+
+class fem_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
+                ("topk_frac", ctypes.c_double), ("max_rounds", ctypes.c_int), ("tonal_tol", ctypes.c_double),
+                ("tonal_maxit", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+
+
+class fem_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int), ("cg_iters", ctypes.c_longlong), ("solves", ctypes.c_int),
+                ("relres", ctypes.c_double), ("tonal_iters", ctypes.c_int), ("tonal_relres", ctypes.c_double),
+                ("min_margin", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_ip = ctypes.POINTER(ctypes.c_int)
+_pp = ctypes.POINTER(fem_params)
+_sig = {
+    "fem_params_default": (None, [_pp]),
+    "fem_mesh_create": (_i, [_i, _i, _vp, ctypes.POINTER(_vp)]),
+    "fem_mesh_destroy": (_i, [_vp]),
+    "fem_mesh_info": (_i, [_vp, _ip, _ip, _ip]),
+    "fem_mesh_export": (_i, [_vp, _vp, _vp, _vp]),
+    "fem_mesh_import": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
+    "fem_gather_mask": (_i, [_vp, _vp, _vp, _vp]),
+    "fem_inpaint": (_i, [_vp, _vp, _vp, _vp, _pp, _vp]),
+    "fem_triangle_errors": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "fem_rasterize": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "fem_spatial_refine": (_i, [_vp, _vp, ctypes.c_double, _pp, _vp]),
+    "fem_tonal_opt": (_i, [_vp, _vp, _vp, _pp, _vp]),
+    "fem_adjoint": (_i, [_vp, _vp, _vp, _pp, _vp]),
+    "fem_mesh_stats": (_i, [_vp, ctypes.POINTER(fem_stats)]),
+    "fem_last_error": (ctypes.c_char_p, []),
+    "fem_profile_enable": (None, [_i]),
+    "fem_profile_read": (_i, [_i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_char_p)]),
+    "fem_launch_count": (ctypes.c_longlong, []),
+}
+for _n, (_r, _a) in _sig.items():
+    _f = getattr(_lib, _n)
+    _f.restype = _r
+    _f.argtypes = _a
+
+
+class FemError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.fem_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+
+
+def _check(st: int, where: str, allow=()):
+    if st != FEM_OK and st not in allow:
+        raise FemError(st, where)
+    return st
+
+
+def params(**kw) -> fem_params:
+    """Default parameters (fem_params_default) with keyword overrides."""
+    p = fem_params()
+    _lib.fem_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None) -> int:
+    torch = _torch()
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev_ptr(t, dtype, numel=None, name="tensor"):
+    torch = _torch()
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+# ------------------------------------------------------------------ C names
+def fem_mesh_create(width: int, height: int, stream=None) -> int:
+    h = _vp()
+    _check(_lib.fem_mesh_create(width, height, _stream(stream), ctypes.byref(h)), "fem_mesh_create")
+    return h.value
+
+
+def fem_mesh_destroy(h: int) -> None:
+    _lib.fem_mesh_destroy(h)
+
+
+def fem_mesh_info(h: int) -> tuple[int, int, int]:
+    V, T, K = _i(), _i(), _i()
+    _check(_lib.fem_mesh_info(h, ctypes.byref(V), ctypes.byref(T), ctypes.byref(K)), "fem_mesh_info")
+    return V.value, T.value, K.value
+
+
+def fem_mesh_export(h: int):
+    V, T, _ = fem_mesh_info(h)
+    xy = np.zeros((V, 2), np.int32)
+    tri = np.zeros((T, 3), np.int32)
+    mk = np.zeros(V, np.uint8)
+    _check(_lib.fem_mesh_export(h, xy.ctypes.data, tri.ctypes.data, mk.ctypes.data), "fem_mesh_export")
+    return xy, tri, mk
+
+
+def fem_mesh_import(h: int, xy, tri, is_mask) -> None:
+    xy = np.ascontiguousarray(xy, np.int32).reshape(-1, 2)
+    tri = np.ascontiguousarray(tri, np.int32).reshape(-1, 3)
+    mk = np.ascontiguousarray(is_mask, np.uint8).reshape(-1)
+    _check(_lib.fem_mesh_import(h, len(xy), xy.ctypes.data, len(tri), tri.ctypes.data, mk.ctypes.data),
+           "fem_mesh_import")
+
+
+def fem_gather_mask(h: int, f, g, stream=None):
+    V, T, K = fem_mesh_info(h)
+    torch = _torch()
+    _check(_lib.fem_gather_mask(h, _dev_ptr(f, torch.float32, None, "f"), _dev_ptr(g, torch.float32, K, "g"),
+                                _stream(stream)), "fem_gather_mask")
+
+
+def fem_inpaint(h: int, g, u=None, uv=None, p: fem_params | None = None, stream=None, allow_not_converged=False):
+    V, T, K = fem_mesh_info(h)
+    st = _lib.fem_inpaint(h, _dev_ptr(g, _torch().float32, K, "g"), _dev_ptr(u, _torch().float32, None, "u"),
+                          _dev_ptr(uv, _torch().float64, V, "uv"), ctypes.byref(p or params()), _stream(stream))
+    return _check(st, "fem_inpaint", (FEM_E_NOT_CONVERGED,) if allow_not_converged else ())
+
+
+def fem_triangle_errors(h: int, uv, f, err, stream=None):
+    V, T, K = fem_mesh_info(h)
+    torch = _torch()
+    _check(_lib.fem_triangle_errors(h, _dev_ptr(uv, torch.float64, V, "uv"), _dev_ptr(f, torch.float32, None, "f"),
+                                    _dev_ptr(err, torch.float64, T, "err"), _stream(stream)), "fem_triangle_errors")
+
+
+def fem_rasterize(h: int, uv, u=None, owner=None, stream=None):
+    V, T, K = fem_mesh_info(h)
+    torch = _torch()
+    _check(_lib.fem_rasterize(h, _dev_ptr(uv, torch.float64, V, "uv"), _dev_ptr(u, torch.float32, None, "u"),
+                              _dev_ptr(owner, torch.int32, None, "owner"), _stream(stream)), "fem_rasterize")
+
+
+def fem_spatial_refine(h: int, f, density: float, p: fem_params | None = None, stream=None):
+    _check(_lib.fem_spatial_refine(h, _dev_ptr(f, _torch().float32, None, "f"), float(density),
+                                   ctypes.byref(p or params()), _stream(stream)), "fem_spatial_refine")
+
+
+def fem_tonal_opt(h: int, f, g, p: fem_params | None = None, stream=None, allow_not_converged=False):
+    V, T, K = fem_mesh_info(h)
+    torch = _torch()
+    st = _lib.fem_tonal_opt(h, _dev_ptr(f, torch.float32, None, "f"), _dev_ptr(g, torch.float32, K, "g"),
+                            ctypes.byref(p or params()), _stream(stream))
+    return _check(st, "fem_tonal_opt", (FEM_E_NOT_CONVERGED,) if allow_not_converged else ())
+
+
+def fem_adjoint(h: int, r, gbar, p: fem_params | None = None, stream=None):
+    V, T, K = fem_mesh_info(h)
+    torch = _torch()
+    _check(_lib.fem_adjoint(h, _dev_ptr(r, torch.float32, None, "r"), _dev_ptr(gbar, torch.float32, K, "gbar"),
+                            ctypes.byref(p or params()), _stream(stream)), "fem_adjoint")
+
+
+def fem_mesh_stats(h: int) -> dict:
+    s = fem_stats()
+    _check(_lib.fem_mesh_stats(h, ctypes.byref(s)), "fem_mesh_stats")
+    return {k: getattr(s, k) for k, _ in fem_stats._fields_}
+
+
+FAMILIES = ["raster", "cg", "assembly", "topk", "refine", "tonal", "other"]
+
+
+def fem_profile_enable(mask) -> None:
+    """mask: int bitmask, True (all families), False/0 (off) or a family name."""
+    if isinstance(mask, str):
+        mask = 1 << FAMILIES.index(mask)
+    elif mask is True:
+        mask = (1 << len(FAMILIES)) - 1
+    _lib.fem_profile_enable(int(mask))
+
+
+def fem_profile_read() -> dict:
+    out = {}
+    for fam in range(len(FAMILIES)):
+        n = ctypes.c_longlong()
+        ms = ctypes.c_double()
+        by = ctypes.c_double()
+        name = ctypes.c_char_p()
+        _lib.fem_profile_read(fam, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(name))
+        out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "bytes": by.value}
+    return out
+
+
+def fem_launch_count() -> int:
+    return int(_lib.fem_launch_count())
+
+
+# ------------------------------------------------------------- convenience
+class Mesh:
+    """Owning wrapper of a mesh handle for an N x N image (N = 2^L + 1)."""
+
+    def __init__(self, n: int, stream=None):
+        self.n = n
+        self.h = fem_mesh_create(n, n, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fem_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self):
+        return fem_mesh_info(self.h)
+
+    @property
+    def V(self):
+        return self.info[0]
+
+    @property
+    def T(self):
+        return self.info[1]
+
+    @property
+    def nmask(self):
+        return self.info[2]
+
+    def export(self):
+        return fem_mesh_export(self.h)
+
+    def import_(self, xy, tri, is_mask):
+        fem_mesh_import(self.h, xy, tri, is_mask)
+
+    def stats(self):
+        return fem_mesh_stats(self.h)
+
+    def inpaint(self, g, p=None, want_uv=False, stream=None, allow_not_converged=False):
+        torch = _torch()
+        u = torch.empty((self.n, self.n), dtype=torch.float32, device=g.device)
+        uv = torch.empty(self.V, dtype=torch.float64, device=g.device) if want_uv else None
+        fem_inpaint(self.h, g, u, uv, p, stream, allow_not_converged)
+        return (u, uv) if want_uv else u
+
+    def triangle_errors(self, uv, f, stream=None):
+        torch = _torch()
+        err = torch.empty(self.T, dtype=torch.float64, device=f.device)
+        fem_triangle_errors(self.h, uv, f, err, stream)
+        return err
+
+    def rasterize(self, uv, want_owner=False, stream=None):
+        torch = _torch()
+        u = torch.empty((self.n, self.n), dtype=torch.float32, device=uv.device)
+        own = torch.empty((self.n, self.n), dtype=torch.int32, device=uv.device) if want_owner else None
+        fem_rasterize(self.h, uv, u, own, stream)
+        return (u, own) if want_owner else u
+
+    def spatial_refine(self, f, density, p=None, stream=None):
+        fem_spatial_refine(self.h, f, density, p, stream)
+
+    def g_from_f(self, f, stream=None):
+        """g = f at the mask vertices (fem_gather_mask)."""
+        torch = _torch()
+        g = torch.empty(self.nmask, dtype=torch.float32, device=f.device)
+        fem_gather_mask(self.h, f, g, stream)
+        return g
+
+    def tonal_opt(self, f, g0=None, p=None, stream=None, allow_not_converged=False):
+        g = (self.g_from_f(f) if g0 is None else g0).clone()
+        fem_tonal_opt(self.h, f, g, p, stream, allow_not_converged)
+        return g
+
+    def adjoint(self, r, p=None, stream=None):
+        torch = _torch()
+        gbar = torch.empty(self.nmask, dtype=torch.float32, device=r.device)
+        fem_adjoint(self.h, r, gbar, p, stream)
+        return gbar

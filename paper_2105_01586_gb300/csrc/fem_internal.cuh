@@ -1,0 +1,250 @@
+// fem_internal.cuh -- internal declarations of the GB300 FEM inpainting library.
+//
+// Device data layout (all arrays live in HBM, owned by the mesh handle):
+//   vxy[V]   int2   vertex pixel positions (x, y)
+//   mask[V]  uint8  1 = mask vertex (Dirichlet set K), 0 = unknown vertex (U)
+//   tri[T]   int4   (a, b, c, 0): refinement edge (a, b), newest vertex c
+//   uv[V]    double vertex values (g at K, Laplace solution at U), kept
+//                   between rounds as the warm start
+// Per-round scratch is sized by capacity and reused.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/feminpaint.h"
+
+namespace fem {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+fem_status cuda_fail(cudaError_t e, const char* what);
+
+#define FEM_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return ::fem::cuda_fail(e_, #call);  \
+    } while (0)
+
+#define FEM_TRY(expr)                        \
+    do {                                     \
+        fem_status s_ = (expr);              \
+        if (s_ != FEM_OK) return s_;         \
+    } while (0)
+
+// ------------------------------------------------------ launch accounting
+enum Family { F_RASTER = 0, F_CG = 1, F_ASSEMBLY = 2, F_TOPK = 3, F_REFINE = 4, F_TONAL = 5, F_OTHER = 6, F_COUNT = 7 };
+void note_launch_begin(int family, cudaStream_t s);
+bool profiling(int family);
+// algorithmic bytes moved by work of a family (counted only while profiling)
+void note_bytes(int family, double bytes);
+void note_launch_end(int family, cudaStream_t s);
+
+// Launch a kernel with accounting; returns FEM_E_CUDA on a launch error.
+#define FEM_LAUNCH(family, stream, kernel, grid, block, smem, ...)                   \
+    do {                                                                             \
+        ::fem::note_launch_begin((family), (stream));                                \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                  \
+        cudaError_t e_ = cudaGetLastError();                                         \
+        ::fem::note_launch_end((family), (stream));                                  \
+        if (e_ != cudaSuccess) return ::fem::cuda_fail(e_, #kernel);                 \
+    } while (0)
+
+// Cooperative launch (all blocks co-resident; used by kernels with grid barriers).
+fem_status launch_coop(int family, const void* func, int grid, int block, size_t smem, cudaStream_t s,
+                       void** args, const char* name);
+
+// ------------------------------------------------------------ device utils
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+    return *(const volatile int*)p;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Bounded grid-wide barrier for cooperatively launched kernels.  bar[0] is
+// the arrival counter, bar[1] the generation.  A block that waits longer
+// than `limit_ns` records FEM_E_TIMEOUT in *err and stops waiting; once *err
+// is set every later barrier returns at once, so the kernel winds down.
+// Returns false when the kernel must stop.
+constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+        unsigned gen = ld_acquire_u32(bar + 1);
+        __threadfence();
+        unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == nb) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long t0 = globaltimer_ns();
+            while (ld_acquire_u32(bar + 1) == gen) {
+                if (ld_volatile_i32(err) != 0) { ok = 0; break; }
+                if (globaltimer_ns() - t0 > kBarrierLimitNs) {
+                    atomicCAS(err, 0, (int)FEM_E_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (ld_volatile_i32(err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Direction index (0..7) of a nonzero lattice step whose components are each
+// -1, 0 or +1 after taking signs: E, NE(+x,+y), N(+y), NW, W, SW, S, SE.
+__host__ __device__ __forceinline__ int dir_index(int dx, int dy) {
+    int sx = (dx > 0) - (dx < 0), sy = (dy > 0) - (dy < 0);
+    // table over (sx+1)*3 + (sy+1)
+    const int tab[9] = {5, 4, 3, 6, -1, 2, 7, 0, 1};
+    return tab[(sx + 1) * 3 + (sy + 1)];
+}
+
+// ------------------------------------------------------------ device arrays
+template <class T>
+struct DArr {
+    T* p = nullptr;
+    size_t n = 0;  // capacity in elements
+};
+
+fem_status dalloc_raw(void** p, size_t bytes, cudaStream_t s);
+void dfree_raw(void* p, cudaStream_t s);
+
+// Ensure capacity >= need; keep_n leading elements are preserved when growing.
+template <class T>
+fem_status ensure(DArr<T>& a, size_t need, cudaStream_t s, size_t keep_n = 0) {
+    if (need <= a.n && a.p) return FEM_OK;
+    size_t cap = a.n ? a.n : 64;
+    while (cap < need) cap *= 2;
+    void* np = nullptr;
+    FEM_TRY(dalloc_raw(&np, cap * sizeof(T), s));
+    if (keep_n && a.p) {
+        cudaError_t e = cudaMemcpyAsync(np, a.p, keep_n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) { dfree_raw(np, s); return cuda_fail(e, "cudaMemcpyAsync(grow)"); }
+    }
+    if (a.p) dfree_raw(a.p, s);
+    a.p = (T*)np;
+    a.n = cap;
+    return FEM_OK;
+}
+
+template <class T>
+void release(DArr<T>& a, cudaStream_t s) {
+    if (a.p) dfree_raw(a.p, s);
+    a.p = nullptr;
+    a.n = 0;
+}
+
+}  // namespace fem
+
+// ------------------------------------------------------------------ mesh
+struct fem_mesh {
+    int N = 0;          // image side (2^L + 1)
+    long long P = 0;    // pixels
+    int V = 0, T = 0, nK = 0, nU = 0;
+    int dev = 0, num_sms = 0;
+    cudaStream_t last_stream = nullptr;
+
+    // mesh proper
+    fem::DArr<int2> vxy;
+    fem::DArr<unsigned char> mask;
+    fem::DArr<int4> tri;
+    fem::DArr<double> uv;
+
+    // rasterisation plan (valid for plan_T triangles of plan_version)
+    fem::DArr<int> item_cnt, item_off, item_tri;
+    fem::DArr<double> partial;
+    fem::DArr<double> keys;
+    long long plan_version = -1, mesh_version = 0;
+    int n_items = 0;
+
+    // refinement
+    fem::DArr<unsigned> bmM, bmS, wpre;
+    fem::DArr<int> flags, fscan, wcnt;
+    fem::DArr<unsigned> topk_hist;
+
+    // Laplace system on U
+    long long sys_version = -1;
+    fem::DArr<int> uidx;            // vertex -> U row or -1
+    fem::DArr<int> kidx;            // vertex -> K index or -1
+    fem::DArr<int> nbr;             // 8*V neighbour per direction (-1 none)
+    fem::DArr<float> coefA;         // 8*V stiffness entry per direction
+    fem::DArr<float> diagA;         // V stiffness diagonal
+    fem::DArr<int> ucol;            // 8*nU ELL columns (slot-major), padded with own row
+    fem::DArr<float> uval32;        // 8*nU ELL values (0 in padding)
+    fem::DArr<double> uval64;
+    fem::DArr<float> dinv32;        // nU inverse diagonal
+    fem::DArr<double> dinv64;
+    fem::DArr<int> urow_vertex;     // nU: vertex of each U row
+    fem::DArr<int> kvert;           // nK: vertex of each K index
+    // CG work
+    fem::DArr<double> x64, b64, r64, p64, q64, z64;
+    fem::DArr<float> r32, p32, q32, z32, d32;
+    fem::DArr<double> red;          // grid-reduction partials
+    fem::DArr<unsigned> bar;        // grid barrier words
+    fem::DArr<int> dflag;           // device status/flags
+    fem::DArr<double> dscal;        // device scalars
+    fem::DArr<int> dcount;          // device counters
+
+    // tonal (pixel mass matrix M = P^T P, incidence by sector)
+    long long tonal_version = -1;
+    fem::DArr<int> inc;             // 8*V triangle per sector (-1 none)
+    fem::DArr<double> loc;          // 6*T local pixel-mass or 3*T scatter sums
+    fem::DArr<double> Moff;         // 8*V pixel-mass off-diagonal per direction
+    fem::DArr<double> Mdiag;        // V
+    fem::DArr<double> tv, ty, tz, tg, tr, tp, tw, tc;  // tonal work vectors
+
+    // host staging (pinned)
+    void* host_stage = nullptr;
+
+    fem_stats stats{};
+};
+
+namespace fem {
+// helpers implemented in the .cu files
+fem_status exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, int* total_dev);
+fem_status build_system(fem_mesh* m, cudaStream_t s);
+fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cudaStream_t s,
+                         int* iters_out, double* relres_out);
+fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, double tol, int maxit, cudaStream_t s,
+                     int* iters_out, double* relres_out);
+fem_status set_uv_from_g(fem_mesh* m, const float* g_dev, cudaStream_t s);
+fem_status set_uv_from_f(fem_mesh* m, const float* f_dev, cudaStream_t s);
+fem_status raster_plan(fem_mesh* m, cudaStream_t s);
+fem_status raster_errors(fem_mesh* m, const double* uv, const float* f, double* err, cudaStream_t s);
+fem_status raster_image(fem_mesh* m, const double* uv, float* u, int* owner, cudaStream_t s);
+fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s);
+fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vstar, cudaStream_t s,
+                        double* margin_out, int* k_out);
+fem_status sync_counts(fem_mesh* m, cudaStream_t s);
+fem_status ensure_mesh_capacity(fem_mesh* m, int needV, int needT, cudaStream_t s);
+int sm_count();
+}  // namespace fem

@@ -1,0 +1,463 @@
+// mesh.cu -- mesh handle, import/export, errors, launch accounting, scans.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "fem_internal.cuh"
+
+namespace fem {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+fem_status cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return FEM_E_OOM;
+    return FEM_E_CUDA;
+}
+
+// ------------------------------------------------------ launch accounting
+static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_prof_on{0};
+static std::mutex g_prof_mu;
+struct ProfRec {
+    cudaEvent_t a, b;
+};
+static std::vector<ProfRec> g_prof_open[F_COUNT];
+static long long g_prof_launches[F_COUNT];
+static double g_prof_bytes[F_COUNT];
+static std::vector<cudaEvent_t> g_event_pool;
+static thread_local cudaEvent_t t_begin_ev = nullptr;
+
+static cudaEvent_t pool_get() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+bool profiling(int family) { return (g_prof_on.load(std::memory_order_relaxed) >> family) & 1; }
+
+void note_bytes(int family, double bytes) {
+    if (!profiling(family)) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_bytes[family] += bytes;
+}
+
+void note_launch_begin(int family, cudaStream_t s) {
+    if (!profiling(family)) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    t_begin_ev = pool_get();
+    cudaEventRecord(t_begin_ev, s);
+}
+
+void note_launch_end(int family, cudaStream_t s) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!profiling(family) || !t_begin_ev) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t e = pool_get();
+    cudaEventRecord(e, s);
+    g_prof_open[family].push_back({t_begin_ev, e});
+    g_prof_launches[family]++;
+    t_begin_ev = nullptr;
+}
+
+fem_status launch_coop(int family, const void* func, int grid, int block, size_t smem, cudaStream_t s,
+                       void** args, const char* name) {
+    note_launch_begin(family, s);
+    cudaError_t e = cudaLaunchCooperativeKernel(func, dim3(grid), dim3(block), args, smem, s);
+    note_launch_end(family, s);
+    if (e != cudaSuccess) return cuda_fail(e, name);
+    return FEM_OK;
+}
+
+// ------------------------------------------------------------------ memory
+fem_status dalloc_raw(void** p, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        set_error("device allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+        return FEM_E_OOM;
+    }
+    return FEM_OK;
+}
+
+void dfree_raw(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// ------------------------------------------------------------------- scans
+constexpr int SCAN_BT = 256;
+constexpr int SCAN_IPT = 8;
+constexpr int SCAN_TILE = SCAN_BT * SCAN_IPT;
+
+// exclusive scan of v[] within the block; returns the block total
+__device__ int block_exclusive_scan(int (&v)[SCAN_IPT]) {
+    __shared__ int s_warp[SCAN_BT / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int sum = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_IPT; ++i) {
+        int t = v[i];
+        v[i] = sum;
+        sum += t;
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < SCAN_BT / 32 ? s_warp[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < SCAN_BT / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
+    }
+    __syncthreads();
+    int base = s_warp[wid] + incl - sum;
+#pragma unroll
+    for (int i = 0; i < SCAN_IPT; ++i) v[i] += base;
+    __shared__ int s_total;
+    if (threadIdx.x == SCAN_BT - 1) s_total = base + sum;
+    __syncthreads();
+    int tot = s_total;
+    __syncthreads();
+    return tot;
+}
+
+__global__ void k_scan_tiles(const int* __restrict__ in, int* __restrict__ out, int n, int* __restrict__ tile_sums) {
+    int v[SCAN_IPT];
+    long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
+#pragma unroll
+    for (int i = 0; i < SCAN_IPT; ++i) v[i] = (base + i < n) ? in[base + i] : 0;
+    int tot = block_exclusive_scan(v);
+#pragma unroll
+    for (int i = 0; i < SCAN_IPT; ++i)
+        if (base + i < n) out[base + i] = v[i];
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ tile_off) {
+    long long base = (long long)blockIdx.x * SCAN_TILE;
+    int add = tile_off[blockIdx.x];
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_BT)
+        if (base + i < n) out[base + i] += add;
+}
+
+__global__ void k_scan_total(const int* in, const int* out, int n, int* total) {
+    *total = n > 0 ? out[n - 1] + in[n - 1] : 0;
+}
+
+// out[i] = sum of in[0..i-1]; *total_dev (if non-null) = sum of all.  out may alias in? no.
+fem_status exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, int* total_dev) {
+    if (n <= 0) {
+        if (total_dev) FEM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int), s));
+        return FEM_OK;
+    }
+    int tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    int* sums = nullptr;
+    FEM_TRY(dalloc_raw((void**)&sums, sizeof(int) * (size_t)(2 * tiles + 2), s));
+    int* sums_off = sums + tiles + 1;
+    fem_status st = FEM_OK;
+    do {
+        note_launch_begin(F_OTHER, s);
+        k_scan_tiles<<<tiles, SCAN_BT, 0, s>>>(in, out, n, sums);
+        cudaError_t e = cudaGetLastError();
+        note_launch_end(F_OTHER, s);
+        if (e != cudaSuccess) { st = cuda_fail(e, "k_scan_tiles"); break; }
+        if (tiles > 1) {
+            st = exclusive_scan_i32(sums, sums_off, tiles, s, nullptr);
+            if (st != FEM_OK) break;
+            note_launch_begin(F_OTHER, s);
+            k_scan_add<<<tiles, SCAN_BT, 0, s>>>(out, n, sums_off);
+            e = cudaGetLastError();
+            note_launch_end(F_OTHER, s);
+            if (e != cudaSuccess) { st = cuda_fail(e, "k_scan_add"); break; }
+        }
+        if (total_dev) {
+            note_launch_begin(F_OTHER, s);
+            k_scan_total<<<1, 1, 0, s>>>(in, out, n, total_dev);
+            e = cudaGetLastError();
+            note_launch_end(F_OTHER, s);
+            if (e != cudaSuccess) { st = cuda_fail(e, "k_scan_total"); break; }
+        }
+    } while (0);
+    dfree_raw(sums, s);
+    return st;
+}
+
+// ------------------------------------------------------------- capacities
+fem_status ensure_mesh_capacity(fem_mesh* m, int needV, int needT, cudaStream_t s) {
+    long long maxV = m->P, maxT = 2LL * (m->N - 1) * (m->N - 1);
+    size_t nv = (size_t)std::min<long long>(std::max(needV, 4), maxV);
+    size_t nt = (size_t)std::min<long long>(std::max(needT, 2), maxT);
+    if (needV > maxV) nv = (size_t)needV;
+    if (needT > maxT) nt = (size_t)needT;
+    FEM_TRY(ensure(m->vxy, nv, s, m->V));
+    FEM_TRY(ensure(m->mask, nv, s, m->V));
+    FEM_TRY(ensure(m->uv, nv, s, m->V));
+    FEM_TRY(ensure(m->tri, nt, s, m->T));
+    return FEM_OK;
+}
+
+fem_status sync_counts(fem_mesh* m, cudaStream_t s) {
+    FEM_CUDA(cudaStreamSynchronize(s));
+    return FEM_OK;
+}
+
+}  // namespace fem
+
+using namespace fem;
+
+static fem_status check_mesh(const fem_mesh* m) {
+    if (!m) {
+        set_error("null mesh handle");
+        return FEM_E_INVALID;
+    }
+    return FEM_OK;
+}
+
+extern "C" {
+
+void fem_params_default(fem_params* p) {
+    if (!p) return;
+    p->tol = 1e-12;
+    p->maxit = 20000;
+    p->precision = FEM_PREC_FP32_IR;
+    p->topk_frac = 0.01;
+    p->max_rounds = 0;
+    p->tonal_tol = 1e-8;
+    p->tonal_maxit = 2000;
+    p->inner_tol = 1e-11;
+}
+
+const char* fem_last_error(void) { return g_last_error.c_str(); }
+
+long long fem_launch_count(void) { return g_launches.load(); }
+
+void fem_profile_enable(int family_mask) { g_prof_on.store(family_mask); }
+
+int fem_profile_read(int family, long long* launches, double* ms, double* bytes, const char** name) {
+    static const char* names[F_COUNT] = {"raster", "cg", "assembly", "topk", "refine", "tonal", "other"};
+    if (family < 0 || family >= F_COUNT) return -1;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    double tot = 0.0;
+    for (auto& r : g_prof_open[family]) {
+        cudaEventSynchronize(r.b);
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) tot += t;
+        g_event_pool.push_back(r.a);
+        g_event_pool.push_back(r.b);
+    }
+    cudaGetLastError();
+    g_prof_open[family].clear();
+    if (launches) *launches = g_prof_launches[family];
+    if (ms) *ms = tot;
+    if (name) *name = names[family];
+    if (bytes) *bytes = g_prof_bytes[family];
+    g_prof_launches[family] = 0;
+    g_prof_bytes[family] = 0.0;
+    return 0;
+}
+
+fem_status fem_mesh_create(int width, int height, void* stream, fem_mesh** out) {
+    if (!out) {
+        set_error("fem_mesh_create: out is NULL");
+        return FEM_E_INVALID;
+    }
+    *out = nullptr;
+    int L = width - 1;
+    if (width != height || width < 3 || width > 32769 || (L & (L - 1)) != 0) {
+        set_error("fem_mesh_create: width == height == 2^L + 1 (3..32769) required");
+        return FEM_E_SHAPE;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    fem_mesh* m = new fem_mesh();
+    m->N = width;
+    m->P = (long long)width * width;
+    cudaGetDevice(&m->dev);
+    m->num_sms = sm_count();
+    m->last_stream = s;
+    fem_status st = FEM_OK;
+    do {
+        st = ensure_mesh_capacity(m, 64, 64, s);
+        if (st) break;
+        st = ensure(m->red, (size_t)8 * 4096, s);
+        if (st) break;
+        st = ensure(m->bar, 64, s);
+        if (st) break;
+        st = ensure(m->dflag, 64, s);
+        if (st) break;
+        st = ensure(m->dscal, 256, s);
+        if (st) break;
+        st = ensure(m->dcount, 64, s);
+        if (st) break;
+        cudaError_t e = cudaMallocHost(&m->host_stage, 1 << 16);
+        if (e != cudaSuccess) { st = cuda_fail(e, "cudaMallocHost"); break; }
+        e = cudaMemsetAsync(m->bar.p, 0, 64 * sizeof(unsigned), s);
+        if (e != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
+        int n1 = width - 1;
+        int2 xy[4] = {{0, 0}, {n1, 0}, {0, n1}, {n1, n1}};
+        unsigned char mk[4] = {1, 1, 1, 1};
+        int4 tr[2] = {{0, 3, 2, 0}, {3, 0, 1, 0}};
+        double uv0[4] = {0, 0, 0, 0};
+        e = cudaMemcpyAsync(m->vxy.p, xy, sizeof(xy), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(m->mask.p, mk, sizeof(mk), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(m->tri.p, tr, sizeof(tr), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(m->uv.p, uv0, sizeof(uv0), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { st = cuda_fail(e, "fem_mesh_create upload"); break; }
+        m->V = 4;
+        m->T = 2;
+        m->nK = 4;
+        m->nU = 0;
+    } while (0);
+    if (st != FEM_OK) {
+        fem_mesh_destroy(m);
+        return st;
+    }
+    *out = m;
+    return FEM_OK;
+}
+
+fem_status fem_mesh_destroy(fem_mesh* m) {
+    if (!m) return FEM_OK;
+    cudaStream_t s = m->last_stream;
+    cudaStreamSynchronize(s);
+    release(m->vxy, s); release(m->mask, s); release(m->tri, s); release(m->uv, s);
+    release(m->item_cnt, s); release(m->item_off, s); release(m->item_tri, s); release(m->partial, s);
+    release(m->keys, s);
+    release(m->bmM, s); release(m->bmS, s); release(m->wpre, s);
+    release(m->flags, s); release(m->fscan, s); release(m->wcnt, s); release(m->topk_hist, s);
+    release(m->uidx, s); release(m->kidx, s); release(m->nbr, s); release(m->coefA, s); release(m->diagA, s);
+    release(m->ucol, s); release(m->uval32, s); release(m->uval64, s); release(m->dinv32, s); release(m->dinv64, s);
+    release(m->urow_vertex, s); release(m->kvert, s);
+    release(m->x64, s); release(m->b64, s); release(m->r64, s); release(m->p64, s); release(m->q64, s); release(m->z64, s);
+    release(m->r32, s); release(m->p32, s); release(m->q32, s); release(m->z32, s); release(m->d32, s);
+    release(m->red, s); release(m->bar, s); release(m->dflag, s); release(m->dscal, s); release(m->dcount, s);
+    release(m->inc, s); release(m->loc, s); release(m->Moff, s); release(m->Mdiag, s);
+    release(m->tv, s); release(m->ty, s); release(m->tz, s); release(m->tg, s);
+    release(m->tr, s); release(m->tp, s); release(m->tw, s); release(m->tc, s);
+    cudaStreamSynchronize(s);
+    if (m->host_stage) cudaFreeHost(m->host_stage);
+    cudaGetLastError();
+    delete m;
+    return FEM_OK;
+}
+
+fem_status fem_mesh_info(const fem_mesh* m, int* V, int* T, int* nmask) {
+    FEM_TRY(check_mesh(m));
+    if (V) *V = m->V;
+    if (T) *T = m->T;
+    if (nmask) *nmask = m->nK;
+    return FEM_OK;
+}
+
+fem_status fem_mesh_stats(const fem_mesh* m, fem_stats* out) {
+    FEM_TRY(check_mesh(m));
+    if (out) *out = m->stats;
+    return FEM_OK;
+}
+
+fem_status fem_mesh_export(fem_mesh* m, int* xy, int* tri, unsigned char* is_mask) {
+    FEM_TRY(check_mesh(m));
+    cudaStream_t s = m->last_stream;
+    FEM_CUDA(cudaStreamSynchronize(s));
+    if (xy) FEM_CUDA(cudaMemcpy(xy, m->vxy.p, sizeof(int2) * m->V, cudaMemcpyDeviceToHost));
+    if (is_mask) FEM_CUDA(cudaMemcpy(is_mask, m->mask.p, m->V, cudaMemcpyDeviceToHost));
+    if (tri) {
+        std::vector<int4> t4(m->T);
+        FEM_CUDA(cudaMemcpy(t4.data(), m->tri.p, sizeof(int4) * m->T, cudaMemcpyDeviceToHost));
+        for (int t = 0; t < m->T; ++t) {
+            tri[3 * t] = t4[t].x;
+            tri[3 * t + 1] = t4[t].y;
+            tri[3 * t + 2] = t4[t].z;
+        }
+    }
+    return FEM_OK;
+}
+
+fem_status fem_mesh_import(fem_mesh* m, int V, const int* xy, int T, const int* tri, const unsigned char* is_mask) {
+    FEM_TRY(check_mesh(m));
+    if (V < 3 || T < 1 || !xy || !tri || !is_mask || (long long)V > m->P || (long long)T > 2LL * (m->N - 1) * (m->N - 1)) {
+        set_error("fem_mesh_import: bad sizes or null arrays");
+        return FEM_E_INVALID;
+    }
+    int N = m->N;
+    for (int i = 0; i < V; ++i) {
+        if (xy[2 * i] < 0 || xy[2 * i] >= N || xy[2 * i + 1] < 0 || xy[2 * i + 1] >= N) {
+            set_error("fem_mesh_import: vertex off the pixel grid");
+            return FEM_E_INVALID;
+        }
+    }
+    long long area2 = 0;
+    std::vector<int4> t4(T);
+    for (int t = 0; t < T; ++t) {
+        int a = tri[3 * t], b = tri[3 * t + 1], c = tri[3 * t + 2];
+        if (a < 0 || b < 0 || c < 0 || a >= V || b >= V || c >= V) {
+            set_error("fem_mesh_import: triangle index out of range");
+            return FEM_E_INVALID;
+        }
+        long long ax = xy[2 * a], ay = xy[2 * a + 1], bx = xy[2 * b], by = xy[2 * b + 1], cx = xy[2 * c], cy = xy[2 * c + 1];
+        long long cr = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+        long long d1x = ax - cx, d1y = ay - cy, d2x = bx - cx, d2y = by - cy;
+        bool right = (d1x * d2x + d1y * d2y == 0) && (d1x * d1x + d1y * d1y == d2x * d2x + d2y * d2y);
+        bool axial = (d1x == 0 || d1y == 0 || d1x == d1y || d1x == -d1y);
+        if (cr <= 0 || !right || !axial) {
+            set_error("fem_mesh_import: triangle " + std::to_string(t) + " is not a positively oriented right-isosceles lattice triangle with c at the right angle");
+            return FEM_E_INVALID;
+        }
+        area2 += cr;
+        t4[t] = make_int4(a, b, c, 0);
+    }
+    if (area2 != 2LL * (N - 1) * (N - 1)) {
+        set_error("fem_mesh_import: triangle areas do not add up to the image");
+        return FEM_E_INVALID;
+    }
+    cudaStream_t s = m->last_stream;
+    FEM_TRY(ensure_mesh_capacity(m, V, T, s));
+    FEM_CUDA(cudaMemcpyAsync(m->vxy.p, xy, sizeof(int2) * V, cudaMemcpyHostToDevice, s));
+    FEM_CUDA(cudaMemcpyAsync(m->mask.p, is_mask, V, cudaMemcpyHostToDevice, s));
+    FEM_CUDA(cudaMemcpyAsync(m->tri.p, t4.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, s));
+    FEM_CUDA(cudaMemsetAsync(m->uv.p, 0, sizeof(double) * V, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    int nk = 0;
+    for (int i = 0; i < V; ++i) nk += is_mask[i] ? 1 : 0;
+    m->V = V;
+    m->T = T;
+    m->nK = nk;
+    m->nU = V - nk;
+    m->mesh_version++;
+    return FEM_OK;
+}
+
+}  // extern "C"

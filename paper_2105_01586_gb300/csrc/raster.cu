@@ -1,0 +1,314 @@
+// raster.cu -- pixel ownership, linear interpolation and per-triangle
+// reductions on the pixel grid (Sec. 2.2 interpolation, Sec. 3 error map).
+//
+// Ownership: pixel (x, y) belongs to the triangle whose interior contains
+// (x, y) + eps*(sx, delta*sy), 0 < delta << 1, eps -> 0+, sx = sy = +1 except
+// -1 on the last column / row.  For a lattice triangle with edges of slope
+// 0, +-1 or infinity this is: rows [ytop, ybot) (plus ybot on the last image
+// row), and in row y the columns [L(y), R(y)) (plus R on the last image
+// column when L < R), where [L, R] is the triangle's intersection with the row.
+//
+// Work decomposition: a triangle is cut into items of rpi consecutive rows
+// (rpi = clamp(1024 / bbox width, 1, 32)), so an item holds about a thousand
+// pixels at most.  One warp takes one item: lane i holds the span of the
+// item's row i, a warp scan turns the spans into offsets, and the warp walks
+// the item's pixels 32 at a time, each lane finding its row by a binary
+// search over the lanes.  Consecutive lanes read consecutive pixels of a row.
+// Per-item partial sums are added per triangle in item order, so results do
+// not depend on scheduling.
+#include <climits>
+
+#include "fem_internal.cuh"
+
+namespace fem {
+
+enum RasterMode { R_ERR = 0, R_IMG = 1, R_MASS = 2, R_SCAT = 3 };
+constexpr int kItemPixels = 1024;
+constexpr int kRasterThreads = 256;
+
+struct TriGeom {
+    int ax, ay, bx, by, cx, cy;
+    int ytop, yend;  // owned rows ytop..yend (inclusive)
+    int maxw;        // bounding-box width in pixels
+};
+
+__device__ __forceinline__ TriGeom tri_geom(int4 tr, const int2* __restrict__ vxy, int N) {
+    TriGeom g;
+    int2 a = vxy[tr.x], b = vxy[tr.y], c = vxy[tr.z];
+    g.ax = a.x; g.ay = a.y; g.bx = b.x; g.by = b.y; g.cx = c.x; g.cy = c.y;
+    int ytop = min(a.y, min(b.y, c.y)), ybot = max(a.y, max(b.y, c.y));
+    g.ytop = ytop;
+    g.yend = (ybot == N - 1) ? ybot : ybot - 1;
+    g.maxw = max(a.x, max(b.x, c.x)) - min(a.x, min(b.x, c.x)) + 1;
+    return g;
+}
+
+__device__ __forceinline__ int rows_per_item(int maxw) {
+    int r = kItemPixels / maxw;
+    return r < 1 ? 1 : (r > 32 ? 32 : r);
+}
+
+__device__ __forceinline__ void edge_x(int px, int py, int qx, int qy, int y, int& L, int& R) {
+    if (py == qy) return;
+    int lo = min(py, qy), hi = max(py, qy);
+    if (y < lo || y > hi) return;
+    int s = (qx == px) ? 0 : (((qx > px) == (qy > py)) ? 1 : -1);
+    int x = px + (y - py) * s;
+    L = min(L, x);
+    R = max(R, x);
+}
+
+// owned columns of row y: [L, L + len)
+__device__ __forceinline__ void row_span(const TriGeom& g, int y, int N, int& L, int& len) {
+    int l = INT_MAX, r = INT_MIN;
+    edge_x(g.ax, g.ay, g.bx, g.by, y, l, r);
+    edge_x(g.bx, g.by, g.cx, g.cy, y, l, r);
+    edge_x(g.cx, g.cy, g.ax, g.ay, y, l, r);
+    int n = r - l + ((r == N - 1 && l < r) ? 1 : 0);
+    L = l;
+    len = n > 0 ? n : 0;
+}
+
+__global__ void k_item_count(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int N,
+                             int* __restrict__ cnt) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    TriGeom g = tri_geom(tri[t], vxy, N);
+    int rows = g.yend - g.ytop + 1;
+    int rpi = rows_per_item(g.maxw);
+    cnt[t] = rows > 0 ? (rows + rpi - 1) / rpi : 0;
+}
+
+__global__ void k_item_expand(const int* __restrict__ cnt, const int* __restrict__ off, int T, int cap,
+                              int* __restrict__ item_tri, int* __restrict__ err) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    int o = off[t], n = cnt[t];
+    if (o + n > cap) {
+        atomicCAS(err, 0, (int)FEM_E_INVALID);
+        return;
+    }
+    for (int j = 0; j < n; ++j) item_tri[o + j] = t;
+}
+
+template <int MODE>
+struct NAcc {
+    static constexpr int n = MODE == R_ERR ? 1 : (MODE == R_MASS ? 6 : (MODE == R_SCAT ? 3 : 0));
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kRasterThreads) k_raster(
+    const int4* __restrict__ tri, const int2* __restrict__ vxy, const double* __restrict__ uv,
+    const float* __restrict__ img, int N, const int* __restrict__ item_tri, const int* __restrict__ item_off,
+    const int* __restrict__ n_items_dev, int item_cap, double* __restrict__ partial, float* __restrict__ u_out,
+    int* __restrict__ owner_out) {
+    constexpr int NA = NAcc<MODE>::n;
+    const unsigned FULL = 0xffffffffu;
+    int lane = threadIdx.x & 31;
+    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    int n_items = min(*n_items_dev, item_cap);  // never past the plan's capacity
+    for (long long it = warp; it < n_items; it += nwarps) {
+        int t = item_tri[it];
+        int j = (int)(it - item_off[t]);
+        int4 tr = tri[t];
+        TriGeom g = tri_geom(tr, vxy, N);
+        int rpi = rows_per_item(g.maxw);
+        int r0 = g.ytop + j * rpi;
+        int nr = min(rpi, g.yend + 1 - r0);
+        int L = 0, len = 0;
+        if (lane < nr) row_span(g, r0 + lane, N, L, len);
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int off = incl - len;
+        int total = __shfl_sync(FULL, incl, 31);
+
+        double va = 0, vb = 0, vc = 0;
+        if (MODE == R_ERR || MODE == R_IMG) {
+            va = uv[tr.x]; vb = uv[tr.y]; vc = uv[tr.z];
+        }
+        int dax = g.ax - g.cx, day = g.ay - g.cy, dbx = g.bx - g.cx, dby = g.by - g.cy;
+        // |a - c|^2 = |b - c|^2 is a power of two, so this reciprocal is exact
+        double inv_l2 = 1.0 / (double)((long long)dax * dax + (long long)day * day);
+        double acc[NA > 0 ? NA : 1];
+#pragma unroll
+        for (int q = 0; q < (NA > 0 ? NA : 1); ++q) acc[q] = 0.0;
+
+        for (int base = 0; base < total; base += 32) {
+            int jj = base + lane;
+            int k = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                int cand = k + step;
+                int oc = __shfl_sync(FULL, off, cand & 31);
+                if (cand < nr && oc <= jj) k = cand;
+            }
+            int Lk = __shfl_sync(FULL, L, k);
+            int ok = __shfl_sync(FULL, off, k);
+            if (jj < total) {
+                int x = Lk + (jj - ok), y = r0 + k;
+                long long dxp = x - g.cx, dyp = y - g.cy;
+                double la = (double)(dxp * dax + dyp * day) * inv_l2;
+                double lb = (double)(dxp * dbx + dyp * dby) * inv_l2;
+                double lc = 1.0 - la - lb;
+                long long p = (long long)y * N + x;
+                if (MODE == R_ERR) {
+                    double u = fma(la, va, fma(lb, vb, lc * vc));
+                    double d = u - (double)img[p];
+                    acc[0] = fma(d, d, acc[0]);
+                } else if (MODE == R_IMG) {
+                    double u = fma(la, va, fma(lb, vb, lc * vc));
+                    if (u_out) u_out[p] = (float)u;
+                    if (owner_out) owner_out[p] = t;
+                } else if (MODE == R_MASS) {
+                    acc[0] = fma(la, la, acc[0]);
+                    acc[1] = fma(lb, lb, acc[1]);
+                    acc[2] = fma(lc, lc, acc[2]);
+                    acc[3] = fma(la, lb, acc[3]);
+                    acc[4] = fma(lb, lc, acc[4]);
+                    acc[5] = fma(lc, la, acc[5]);
+                } else if (MODE == R_SCAT) {
+                    double r = (double)img[p];
+                    acc[0] = fma(la, r, acc[0]);
+                    acc[1] = fma(lb, r, acc[1]);
+                    acc[2] = fma(lc, r, acc[2]);
+                }
+            }
+        }
+        if (NA > 0) {
+#pragma unroll
+            for (int q = 0; q < (NA > 0 ? NA : 1); ++q) {
+                double v = warp_sum(acc[q]);
+                if (lane == 0) partial[it * NA + q] = v;
+            }
+        }
+    }
+}
+
+template <int NA>
+__global__ void k_finalize(const int* __restrict__ cnt, const int* __restrict__ off, const double* __restrict__ partial,
+                           int T, double* __restrict__ out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    int o = off[t], n = cnt[t];
+    double s[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) s[q] = 0.0;
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+        for (int q = 0; q < NA; ++q) s[q] += partial[(long long)(o + j) * NA + q];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) out[(long long)t * NA + q] = s[q];
+}
+
+static int raster_grid(fem_mesh* m) { return m->num_sms * (2048 / kRasterThreads); }
+
+fem_status raster_plan(fem_mesh* m, cudaStream_t s) {
+    if (m->plan_version == m->mesh_version) return FEM_OK;
+    int T = m->T;
+    size_t cap = (size_t)3 * T + (size_t)(m->P / 128) + 1024;
+    FEM_TRY(ensure(m->item_cnt, T + 1, s));
+    FEM_TRY(ensure(m->item_off, T + 1, s));
+    FEM_TRY(ensure(m->item_tri, cap, s));
+    FEM_TRY(ensure(m->partial, cap * 6, s));
+    int* n_items_dev = m->dcount.p + 0;
+    int* err = m->dflag.p + 0;
+    FEM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    int blocks = (T + 255) / 256;
+    FEM_LAUNCH(F_RASTER, s, k_item_count, blocks, 256, 0, m->tri.p, m->vxy.p, T, m->N, m->item_cnt.p);
+    FEM_TRY(exclusive_scan_i32(m->item_cnt.p, m->item_off.p, T, s, n_items_dev));
+    FEM_LAUNCH(F_RASTER, s, k_item_expand, blocks, 256, 0, m->item_cnt.p, m->item_off.p, T, (int)m->item_tri.n,
+               m->item_tri.p, err);
+    m->plan_version = m->mesh_version;
+    return FEM_OK;
+}
+
+// algorithmic bytes of one error pass: f once (4 B/px), triangles (16 B),
+// vertex positions and values (8 + 8 B), one key out (8 B per triangle)
+static double raster_err_bytes(const fem_mesh* m) {
+    return 4.0 * (double)m->P + 24.0 * m->T + 16.0 * m->V;
+}
+
+fem_status raster_errors(fem_mesh* m, const double* uv, const float* f, double* err_out, cudaStream_t s) {
+    FEM_TRY(raster_plan(m, s));
+    note_bytes(F_RASTER, raster_err_bytes(m));
+    FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, f, m->N,
+               m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p, (float*)nullptr, (int*)nullptr);
+    int blocks = (m->T + 255) / 256;
+    FEM_LAUNCH(F_RASTER, s, k_finalize<1>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T, err_out);
+    return FEM_OK;
+}
+
+fem_status raster_image(fem_mesh* m, const double* uv, float* u, int* owner, cudaStream_t s) {
+    FEM_TRY(raster_plan(m, s));
+    note_bytes(F_RASTER, (u ? 4.0 * (double)m->P : 0.0) + (owner ? 4.0 * (double)m->P : 0.0) + 16.0 * m->T +
+                             16.0 * m->V);
+    FEM_LAUNCH(F_RASTER, s, k_raster<R_IMG>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv,
+               (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p, u, owner);
+    return FEM_OK;
+}
+
+// mode R_MASS: loc[6t..6t+5] = sums of la^2, lb^2, lc^2, la lb, lb lc, lc la
+// mode R_SCAT: loc[3t..3t+2] = sums of la r, lb r, lc r
+fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s) {
+    FEM_TRY(raster_plan(m, s));
+    FEM_TRY(ensure(m->loc, (size_t)6 * m->T + 6, s));
+    int blocks = (m->T + 255) / 256;
+    note_bytes(F_RASTER, (mode == R_MASS ? 64.0 * m->T : 4.0 * (double)m->P + 40.0 * m->T) + 8.0 * m->V);
+    if (mode == R_MASS) {
+        FEM_LAUNCH(F_RASTER, s, k_raster<R_MASS>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
+                   (const double*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0,
+                   (int)m->item_tri.n, m->partial.p, (float*)nullptr, (int*)nullptr);
+        FEM_LAUNCH(F_RASTER, s, k_finalize<6>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
+                   m->loc.p);
+    } else {
+        FEM_LAUNCH(F_RASTER, s, k_raster<R_SCAT>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
+                   (const double*)nullptr, r, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p,
+                   (float*)nullptr, (int*)nullptr);
+        FEM_LAUNCH(F_RASTER, s, k_finalize<3>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
+                   m->loc.p);
+    }
+    return FEM_OK;
+}
+
+}  // namespace fem
+
+using namespace fem;
+
+extern "C" {
+
+fem_status fem_triangle_errors(fem_mesh* m, const double* uv_dev, const float* f_dev, double* err_dev, void* stream) {
+    if (!m || !uv_dev || !f_dev || !err_dev) {
+        set_error("fem_triangle_errors: null argument");
+        return FEM_E_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    m->last_stream = s;
+    FEM_TRY(raster_errors(m, uv_dev, f_dev, err_dev, s));
+    int e = 0;
+    FEM_CUDA(cudaMemcpyAsync(&e, m->dflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    if (e) {
+        set_error("fem_triangle_errors: rasterisation plan overflow");
+        return (fem_status)e;
+    }
+    return FEM_OK;
+}
+
+fem_status fem_rasterize(fem_mesh* m, const double* uv_dev, float* u_dev, int* owner_dev, void* stream) {
+    if (!m || !uv_dev) {
+        set_error("fem_rasterize: null argument");
+        return FEM_E_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    m->last_stream = s;
+    FEM_TRY(raster_image(m, uv_dev, u_dev, owner_dev, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    return FEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,435 @@
+// refine.cu -- spatial optimisation (Sec. 3, adapted): top-k selection of
+// the triangles with the largest squared error and their refinement by
+// newest-vertex bisection (NVB).
+//
+// Edge marks.  Every edge that can be bisected has a midpoint on the pixel
+// grid, and distinct edges have distinct midpoints, so a bitmap with one bit
+// per pixel is a collision-free set of marked edges (bmM) and of the
+// refinement edges of selected triangles (bmS).  No neighbour lists are kept.
+// Closure: a triangle with a marked leg marks its refinement edge; sweeps
+// repeat until nothing changes (marks only grow, so a sweep that adds none
+// saw the fixpoint).
+// Numbering.  The marked midpoints are exactly the new vertices; the id of
+// the midpoint at pixel p is V + (number of set bits before p), i.e. new
+// vertices are numbered by ascending pixel index.  One exclusive scan over
+// the flags [gen-1 bisections | gen-2 of kept children | gen-2 of new
+// children] gives every new triangle its id in (generation, parent id) order.
+#include <cmath>
+
+#include "fem_internal.cuh"
+
+namespace fem {
+
+constexpr int kTopkThreads = 256;
+
+__device__ __forceinline__ bool lattice_mid(int2 p, int2 q) { return (((p.x + q.x) | (p.y + q.y)) & 1) == 0; }
+
+__device__ __forceinline__ long long mid_pixel(int2 p, int2 q, int N) {
+    return (long long)((p.y + q.y) >> 1) * N + ((p.x + q.x) >> 1);
+}
+
+__device__ __forceinline__ bool test_bit(const unsigned* bm, long long p) {
+    return (__ldcg(&bm[p >> 5]) >> (p & 31)) & 1u;
+}
+
+// ------------------------------------------------------------------ top-k
+struct TopkArgs {
+    const double* keys;
+    const int4* tri;
+    const int2* vxy;
+    int T;
+    double frac;
+    long long vcap;          // V* - V
+    unsigned* hist;          // 12 * 256 counters, zeroed
+    unsigned long long* below_max;  // zeroed
+    unsigned* bar;
+    int* err;
+    int* out_k;              // k
+    unsigned long long* out_thr;    // [0] hi, [1] lo of the k-th composite key
+    double* red;
+    double* out_margin;
+};
+
+__device__ __forceinline__ unsigned long long comp_hi(const TopkArgs& A, int t) {
+    int4 tr = A.tri[t];
+    int2 a = A.vxy[tr.x], b = A.vxy[tr.y];
+    if (!lattice_mid(a, b)) return 0ull;
+    return (unsigned long long)__double_as_longlong(A.keys[t]) | (1ull << 63);
+}
+
+__device__ __forceinline__ unsigned digit_of(unsigned long long hi, unsigned lo, int d) {
+    return d < 8 ? (unsigned)(hi >> (56 - 8 * d)) & 255u : (lo >> (24 - 8 * (d - 8))) & 255u;
+}
+
+__global__ void __launch_bounds__(kTopkThreads) k_topk(TopkArgs A) {
+    __shared__ unsigned s_hist[256];
+    __shared__ unsigned long long s_pre_hi;
+    __shared__ unsigned s_pre_lo;
+    __shared__ long long s_krem;
+    int tid0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    int parity = 0;
+    (void)parity;
+    // eligible count -> k
+    __shared__ unsigned s_ne;
+    if (threadIdx.x == 0) s_ne = 0;
+    __syncthreads();
+    unsigned ne_loc = 0;
+    for (int t = tid0; t < A.T; t += stride) ne_loc += comp_hi(A, t) ? 1u : 0u;
+    ne_loc = warp_sum(ne_loc);
+    if ((threadIdx.x & 31) == 0 && ne_loc) atomicAdd(&s_ne, ne_loc);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_ne) atomicAdd(&A.hist[12 * 256], s_ne);  // slot after the histograms
+    if (!grid_barrier(A.bar, A.err)) return;
+    long long ne = (long long)__ldcg(&A.hist[12 * 256]);
+    long long k = (long long)ceil(A.frac * (double)A.T);
+    if (k < 1) k = 1;
+    if (k > ne) k = ne;
+    if (k > A.vcap) k = A.vcap;
+    if (k < 0) k = 0;
+    if (tid0 == 0) *A.out_k = (int)k;
+    if (k == 0) return;
+    if (threadIdx.x == 0) { s_pre_hi = 0; s_pre_lo = 0; s_krem = k; }
+    __syncthreads();
+    for (int d = 0; d < 12; ++d) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) s_hist[i] = 0;
+        __syncthreads();
+        unsigned long long pre_hi = s_pre_hi;
+        unsigned pre_lo = s_pre_lo;
+        // bits already decided: the top 8*d bits of the 96-bit composite
+        unsigned long long mhi = d >= 8 ? ~0ull : (d == 0 ? 0ull : (~0ull << (64 - 8 * d)));
+        unsigned mlo = d <= 8 ? 0u : (~0u << (32 - 8 * (d - 8)));
+        for (int t = tid0; t < A.T; t += stride) {
+            unsigned long long hi = comp_hi(A, t);
+            unsigned lo = ~(unsigned)t;
+            if ((hi & mhi) == pre_hi && (lo & mlo) == pre_lo) atomicAdd(&s_hist[digit_of(hi, lo, d)], 1u);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 256; i += blockDim.x)
+            if (s_hist[i]) atomicAdd(&A.hist[d * 256 + i], s_hist[i]);
+        if (!grid_barrier(A.bar, A.err)) return;
+        if (threadIdx.x == 0) {
+            long long krem = s_krem, cum = 0;
+            int chosen = 0;
+            for (int b = 255; b >= 0; --b) {
+                long long h = (long long)__ldcg(&A.hist[d * 256 + b]);
+                if (cum + h >= krem) { chosen = b; break; }
+                cum += h;
+            }
+            s_krem = krem - cum;
+            if (d < 8) s_pre_hi = pre_hi | ((unsigned long long)chosen << (56 - 8 * d));
+            else s_pre_lo = pre_lo | ((unsigned)chosen << (24 - 8 * (d - 8)));
+        }
+        __syncthreads();
+    }
+    unsigned long long thr_hi = s_pre_hi;
+    unsigned thr_lo = s_pre_lo;
+    if (tid0 == 0) { A.out_thr[0] = thr_hi; A.out_thr[1] = thr_lo; }
+    // largest composite strictly below the threshold (for the decision margin)
+    unsigned long long best = 0ull;
+    for (int t = tid0; t < A.T; t += stride) {
+        unsigned long long hi = comp_hi(A, t);
+        unsigned lo = ~(unsigned)t;
+        bool below = hi < thr_hi || (hi == thr_hi && lo < thr_lo);
+        if (below && hi > best) best = hi;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+        best = v > best ? v : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(A.below_max, best);
+    if (!grid_barrier(A.bar, A.err)) return;
+    if (tid0 == 0) {
+        unsigned long long bm = __ldcg(A.below_max);
+        double kth = __longlong_as_double((long long)(thr_hi & ~(1ull << 63)));
+        if (bm & (1ull << 63)) {
+            double nxt = __longlong_as_double((long long)(bm & ~(1ull << 63)));
+            *A.out_margin = kth > 0.0 ? (kth - nxt) / kth : 0.0;
+        } else {
+            *A.out_margin = INFINITY;
+        }
+    }
+}
+
+// mark the refinement edges of the selected triangles in bmM and bmS
+__global__ void k_mark_selected(const double* __restrict__ keys, const int4* __restrict__ tri,
+                                const int2* __restrict__ vxy, int T, int N, const unsigned long long* __restrict__ thr,
+                                const int* __restrict__ kdev, unsigned* __restrict__ bmM, unsigned* __restrict__ bmS) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T || *kdev == 0) return;
+    int4 tr = tri[t];
+    int2 a = vxy[tr.x], b = vxy[tr.y];
+    if (!lattice_mid(a, b)) return;
+    unsigned long long hi = (unsigned long long)__double_as_longlong(keys[t]) | (1ull << 63);
+    unsigned lo = ~(unsigned)t;
+    unsigned long long th = thr[0];
+    unsigned tl = (unsigned)thr[1];
+    if (hi > th || (hi == th && lo >= tl)) {
+        long long p = mid_pixel(a, b, N);
+        unsigned bit = 1u << (p & 31);
+        atomicOr(&bmM[p >> 5], bit);
+        atomicOr(&bmS[p >> 5], bit);
+    }
+}
+
+// closure sweeps until a sweep adds no mark (cooperative, bounded)
+__global__ void k_closure(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int N,
+                          unsigned* __restrict__ bmM, int* __restrict__ changed, int max_sweeps, unsigned* bar,
+                          int* err, int* out_sweeps) {
+    int tid0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+        int any = 0;
+        for (int t = tid0; t < T; t += stride) {
+            int4 tr = tri[t];
+            int2 a = vxy[tr.x], b = vxy[tr.y], c = vxy[tr.z];
+            if (!lattice_mid(a, b)) continue;  // unit triangles: never marked (no marked leg can exist)
+            long long pr = mid_pixel(a, b, N);
+            if (test_bit(bmM, pr)) continue;
+            bool leg = (lattice_mid(b, c) && test_bit(bmM, mid_pixel(b, c, N))) ||
+                       (lattice_mid(c, a) && test_bit(bmM, mid_pixel(c, a, N)));
+            if (leg) {
+                atomicOr(&bmM[pr >> 5], 1u << (pr & 31));
+                any = 1;
+            }
+        }
+        if (any) changed[sw] = 1;
+        if (!grid_barrier(bar, err)) return;
+        if (__ldcg(&changed[sw]) == 0) {
+            if (tid0 == 0) *out_sweeps = sw + 1;
+            return;
+        }
+    }
+    if (tid0 == 0) {
+        *out_sweeps = max_sweeps;
+        atomicCAS(err, 0, (int)FEM_E_INVALID);
+    }
+}
+
+__global__ void k_word_popc(const unsigned* __restrict__ bm, int W, int* __restrict__ cnt) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < W) cnt[w] = __popc(bm[w]);
+}
+
+__device__ __forceinline__ int midpoint_id(const unsigned* __restrict__ bm, const int* __restrict__ wpre, int V0,
+                                           long long p) {
+    unsigned w = bm[p >> 5];
+    unsigned below = w & ((1u << (p & 31)) - 1u);
+    return V0 + wpre[p >> 5] + __popc(below);
+}
+
+__global__ void k_new_vertices(const unsigned* __restrict__ bmM, const unsigned* __restrict__ bmS,
+                               const int* __restrict__ wpre, int W, int N, int V0, int2* __restrict__ vxy,
+                               unsigned char* __restrict__ mask, int* __restrict__ n_new_mask) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    unsigned bits = bmM[w], sbits = bmS[w];
+    if (sbits & bits) atomicAdd(n_new_mask, __popc(sbits & bits));
+    int id = V0 + wpre[w];
+    while (bits) {
+        int b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        long long p = (long long)w * 32 + b;
+        vxy[id] = make_int2((int)(p % N), (int)(p / N));
+        mask[id] = (unsigned char)((sbits >> b) & 1u);
+        id++;
+    }
+}
+
+__global__ void k_bisect_flags(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int N,
+                               const unsigned* __restrict__ bmM, int* __restrict__ flags) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    int4 tr = tri[t];
+    int2 a = vxy[tr.x], b = vxy[tr.y], c = vxy[tr.z];
+    int e0 = lattice_mid(a, b) && test_bit(bmM, mid_pixel(a, b, N));
+    int e1 = e0 && lattice_mid(b, c) && test_bit(bmM, mid_pixel(b, c, N));
+    int e2 = e0 && lattice_mid(c, a) && test_bit(bmM, mid_pixel(c, a, N));
+    flags[t] = e0;
+    flags[T + t] = e2;
+    flags[2 * T + t] = e1;
+}
+
+__global__ void k_bisect(int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int N,
+                         const unsigned* __restrict__ bmM, const int* __restrict__ wpre, int V0,
+                         const int* __restrict__ flags, const int* __restrict__ fscan, double* __restrict__ uv) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T || !flags[t]) return;
+    int4 tr = tri[t];
+    int a = tr.x, b = tr.y, c = tr.z;
+    int2 pa = vxy[a], pb = vxy[b], pc = vxy[c];
+    int m = midpoint_id(bmM, wpre, V0, mid_pixel(pa, pb, N));
+    uv[m] = 0.5 * (uv[a] + uv[b]);
+    int id1 = T + fscan[t];
+    int4 kept = make_int4(c, a, m, 0);   // (c, a, m) keeps id t
+    int4 fresh = make_int4(b, c, m, 0);  // (b, c, m) new id
+    if (flags[T + t]) {  // kept child's refinement edge (c, a) is marked
+        int m2 = midpoint_id(bmM, wpre, V0, mid_pixel(pc, pa, N));
+        uv[m2] = 0.5 * (uv[c] + uv[a]);
+        tri[T + fscan[T + t]] = make_int4(a, m, m2, 0);
+        kept = make_int4(m, c, m2, 0);
+    }
+    if (flags[2 * T + t]) {  // new child's refinement edge (b, c) is marked
+        int m1 = midpoint_id(bmM, wpre, V0, mid_pixel(pb, pc, N));
+        uv[m1] = 0.5 * (uv[b] + uv[c]);
+        tri[T + fscan[2 * T + t]] = make_int4(c, m, m1, 0);
+        fresh = make_int4(m, b, m1, 0);
+    }
+    tri[t] = kept;
+    tri[id1] = fresh;
+}
+
+static int coop_grid(const void* func, int threads, int work, int num_sms) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, 0);
+    if (nb < 1) nb = 1;
+    int maxb = nb * num_sms;
+    int want = (work + threads * 4 - 1) / (threads * 4);
+    if (want < 1) want = 1;
+    return want < maxb ? want : maxb;
+}
+
+// One refinement round on the current keys (m->keys).  Returns k via k_out.
+fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vstar, cudaStream_t s, double* margin_out,
+                        int* k_out) {
+    (void)f;
+    int T = m->T, V = m->V, N = m->N;
+    long long W = (m->P + 31) / 32;
+    FEM_TRY(ensure(m->bmM, (size_t)W, s));
+    FEM_TRY(ensure(m->bmS, (size_t)W, s));
+    FEM_TRY(ensure(m->wpre, (size_t)W + 1, s));
+    FEM_TRY(ensure(m->topk_hist, (size_t)12 * 256 + 8, s));
+    FEM_TRY(ensure(m->flags, (size_t)3 * T + 1, s));
+    FEM_TRY(ensure(m->fscan, (size_t)3 * T + 1, s));
+    FEM_TRY(ensure(m->wcnt, (size_t)W + 1, s));
+    // capacity: at most one new vertex per edge (E = V + T - 1), at most 4 children per triangle
+    FEM_TRY(ensure_mesh_capacity(m, V + T + V + 4, 4 * T, s));
+    unsigned* hist = m->topk_hist.p;
+    int* kdev = m->dcount.p + 2;
+    int* sweeps = m->dcount.p + 3;
+    int* nnew = m->dcount.p + 4;
+    int* ntri = m->dcount.p + 5;
+    int* nmask_new = m->dcount.p + 6;
+    int* changed = m->dcount.p + 16;  // 48 flags
+    unsigned long long* thr = (unsigned long long*)(m->dscal.p + 8);
+    unsigned long long* below = (unsigned long long*)(m->dscal.p + 10);
+    double* margin = m->dscal.p + 11;
+    int* err = m->dflag.p + 2;
+    FEM_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned) * (12 * 256 + 1), s));
+    FEM_CUDA(cudaMemsetAsync(below, 0, sizeof(unsigned long long), s));
+    FEM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    FEM_CUDA(cudaMemsetAsync(m->bmM.p, 0, sizeof(unsigned) * W, s));
+    FEM_CUDA(cudaMemsetAsync(m->bmS.p, 0, sizeof(unsigned) * W, s));
+    FEM_CUDA(cudaMemsetAsync(changed, 0, sizeof(int) * 48, s));
+    FEM_CUDA(cudaMemsetAsync(nmask_new, 0, sizeof(int), s));
+
+    TopkArgs A;
+    A.keys = m->keys.p;
+    A.tri = m->tri.p;
+    A.vxy = m->vxy.p;
+    A.T = T;
+    A.frac = frac;
+    A.vcap = vstar - V;
+    A.hist = hist;
+    A.below_max = below;
+    A.bar = m->bar.p;
+    A.err = err;
+    A.out_k = kdev;
+    A.out_thr = thr;
+    A.red = m->red.p;
+    A.out_margin = margin;
+    {
+        void* args[] = {&A};
+        int grid = coop_grid((const void*)k_topk, kTopkThreads, T, m->num_sms);
+        FEM_TRY(launch_coop(F_TOPK, (const void*)k_topk, grid, kTopkThreads, 0, s, args, "k_topk"));
+    }
+    int tb = (T + 255) / 256;
+    FEM_LAUNCH(F_REFINE, s, k_mark_selected, tb, 256, 0, m->keys.p, m->tri.p, m->vxy.p, T, N, thr, kdev, m->bmM.p,
+               m->bmS.p);
+    {
+        int max_sweeps = 48;
+        const unsigned* cbm = nullptr;
+        (void)cbm;
+        void* args[] = {(void*)&m->tri.p, (void*)&m->vxy.p, (void*)&T, (void*)&N, (void*)&m->bmM.p,
+                        (void*)&changed, (void*)&max_sweeps, (void*)&m->bar.p, (void*)&err, (void*)&sweeps};
+        int grid = coop_grid((const void*)k_closure, 256, T, m->num_sms);
+        FEM_TRY(launch_coop(F_REFINE, (const void*)k_closure, grid, 256, 0, s, args, "k_closure"));
+    }
+    int Wi = (int)W;
+    FEM_LAUNCH(F_REFINE, s, k_word_popc, (Wi + 255) / 256, 256, 0, m->bmM.p, Wi, m->wcnt.p);
+    FEM_TRY(exclusive_scan_i32(m->wcnt.p, (int*)m->wpre.p, Wi, s, nnew));
+    FEM_LAUNCH(F_REFINE, s, k_new_vertices, (Wi + 255) / 256, 256, 0, m->bmM.p, m->bmS.p, (const int*)m->wpre.p, Wi,
+               N, V, m->vxy.p, m->mask.p, nmask_new);
+    FEM_LAUNCH(F_REFINE, s, k_bisect_flags, tb, 256, 0, m->tri.p, m->vxy.p, T, N, m->bmM.p, m->flags.p);
+    FEM_TRY(exclusive_scan_i32(m->flags.p, m->fscan.p, 3 * T, s, ntri));
+    FEM_LAUNCH(F_REFINE, s, k_bisect, tb, 256, 0, m->tri.p, m->vxy.p, T, N, m->bmM.p, (const int*)m->wpre.p, V,
+               m->flags.p, m->fscan.p, m->uv.p);
+    // read back k, sweeps, new counts, margin, error
+    int* hs = (int*)m->host_stage;
+    FEM_CUDA(cudaMemcpyAsync(hs, m->dcount.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaMemcpyAsync(hs + 8, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaMemcpyAsync((double*)(hs + 16), margin, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    int k = hs[2], nn = hs[4], nt = hs[5], nkm = hs[6], e = hs[8];
+    double mg = *(double*)(hs + 16);
+    if (e) {
+        cudaMemsetAsync(m->bar.p, 0, 2 * sizeof(unsigned), s);
+        set_error(e == FEM_E_TIMEOUT ? "refinement: a grid barrier wait ran out" : "refinement: closure did not settle");
+        return (fem_status)e;
+    }
+    if (k > 0 && nn <= 0) {
+        set_error("refinement: selected triangles produced no new vertex");
+        return FEM_E_INVALID;
+    }
+    if (k_out) *k_out = k;
+    if (margin_out) *margin_out = mg;
+    if (k > 0) {
+        m->V = V + nn;
+        m->T = T + nt;
+        m->nK += nkm;
+        m->nU = m->V - m->nK;
+        m->mesh_version++;
+    }
+    return FEM_OK;
+}
+
+}  // namespace fem
+
+using namespace fem;
+
+extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double density, const fem_params* p,
+                                         void* stream) {
+    if (!m || !f_dev || !(density > 0.0) || density > 1.0) {
+        set_error("fem_spatial_refine: null argument or density outside (0, 1]");
+        return FEM_E_INVALID;
+    }
+    fem_params d;
+    fem_params_default(&d);
+    if (!p) p = &d;
+    cudaStream_t s = (cudaStream_t)stream;
+    m->last_stream = s;
+    m->stats = fem_stats{};
+    m->stats.min_margin = INFINITY;
+    long long vstar = (long long)ceil(density * (double)m->P);
+    int round = 0;
+    while ((long long)m->V < vstar && (p->max_rounds <= 0 || round < p->max_rounds)) {
+        FEM_TRY(build_system(m, s));
+        FEM_TRY(set_uv_from_f(m, f_dev, s));
+        int it = 0;
+        double rel = 0.0;
+        long long before = m->stats.cg_iters;
+        int solves = m->stats.solves;
+        fem_status st = solve_laplace(m, p->precision == FEM_PREC_FP64, p->tol, p->maxit, s, &it, &rel);
+        (void)before;
+        (void)solves;
+        if (st != FEM_OK) return st;
+        FEM_TRY(ensure(m->keys, (size_t)m->T, s));
+        FEM_TRY(raster_errors(m, m->uv.p, f_dev, m->keys.p, s));
+        double margin = 0.0;
+        int k = 0;
+        FEM_TRY(refine_round(m, f_dev, p->topk_frac, vstar, s, &margin, &k));
+        if (k == 0) break;
+        if (margin < m->stats.min_margin) m->stats.min_margin = margin;
+        round++;
+    }
+    m->stats.rounds = round;
+    return FEM_OK;
+}

@@ -1,0 +1,66 @@
+"""The C-ABI library loads and exports every symbol include/feminpaint.h
+declares; host-side argument checks work without a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fem():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2105_01586_gb300 as fem
+    return fem
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "feminpaint.h")).read()
+    return sorted(set(re.findall(r"FEM_API\s+[\w\s\*]*?\b(fem_\w+)\s*\(", src)))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ("fem_mesh_create", "fem_inpaint", "fem_triangle_errors", "fem_spatial_refine", "fem_tonal_opt",
+              "fem_adjoint"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(fem):
+    out = subprocess.run(["nm", "-D", "--defined-only", fem.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (fem_\w+)$", out, flags=re.M))
+    declared = set(_declared())
+    assert declared <= exported, declared - exported
+    for n in declared:
+        assert hasattr(fem._lib, n)
+    assert set(fem.EXPORTED) == declared
+
+
+def test_defaults_and_host_checks(fem):
+    p = fem.params()
+    assert p.tol == 1e-12 and p.precision == fem.FEM_PREC_FP32_IR and p.topk_frac == 0.01
+    # null handle and null arguments are rejected on the host, before any CUDA call
+    assert fem._lib.fem_mesh_info(None, None, None, None) == fem.FEM_E_INVALID
+    assert fem._lib.fem_inpaint(None, None, None, None, None, None) == fem.FEM_E_INVALID
+    assert fem._lib.fem_spatial_refine(None, None, ctypes.c_double(0.1), None, None) == fem.FEM_E_INVALID
+    assert fem._lib.fem_tonal_opt(None, None, None, None, None) == fem.FEM_E_INVALID
+    assert fem._lib.fem_adjoint(None, None, None, None, None) == fem.FEM_E_INVALID
+    assert b"null" in fem._lib.fem_last_error()
+    h = ctypes.c_void_p()
+    for bad in ((256, 256), (257, 129), (2, 2), (0, 0)):
+        assert fem._lib.fem_mesh_create(bad[0], bad[1], None, ctypes.byref(h)) == fem.FEM_E_SHAPE
+    assert fem.fem_launch_count() == 0
+
+
+def test_product_path_does_not_import_oracle():
+    """The binding, build and CUDA sources never reference the oracle."""
+    pkg = os.path.join(ROOT, "paper_2105_01586_gb300")
+    for dp, _, fns in os.walk(pkg):
+        for fn in fns:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dp, fn)).read()
+                assert "import oracle" not in txt and "oracle." not in txt, fn
