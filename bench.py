@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check after timing")
+    ap.add_argument("--ncu-step", action="store_true",
+                    help="for ncu launch lists: one warm-up step, then exactly one step, no timing output")
     return ap.parse_args()
 
 
@@ -189,6 +191,15 @@ def run_ours(a, world, rank, local):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
+
+    if a.ncu_step:
+        step(f)
+        torch.cuda.synchronize(dev)
+        n0 = fem.fem_launch_count()
+        step(f)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"ncu_step_launches": fem.fem_launch_count() - n0, "warmup_launches": n0}), flush=True)
+        return
 
     for _ in range(a.warmup):
         step(f)
