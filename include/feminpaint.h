@@ -134,6 +134,32 @@ FEM_API fem_status fem_gather_mask(fem_mesh *m, const float *f_dev, float *g_dev
 FEM_API fem_status fem_triangle_errors(fem_mesh *m, const double *uv_dev, const float *f_dev, double *err_dev,
                                void *stream);
 
+/* The per-triangle errors of fem_triangle_errors for callers that cannot
+ * allocate device memory (no counterpart in the paper).  Some callers cannot
+ * call cudaMalloc: code running while a CUDA graph is captured on their
+ * stream, programs whose allocator owns all device memory, or loops that
+ * must not allocate after start-up.  This call allocates nothing: the
+ * caller passes the mesh arrays, the vertex values, the image and the
+ * output; the scratch it needs is a fixed 3.4 MB device array inside the
+ * library, present on every GPU that loads the library until the process
+ * exits.  The first call on a device looks up that array's address (once
+ * per device, with the device current); make that first call before any
+ * stream capture.  The array is shared by all calls and keeps the last
+ * call's contents (the call clears what must start at zero), so calls that
+ * overlap on the GPU, on any stream, race: serialise them.
+ *   width      image side, 2^L + 1, at most 2049
+ *   V, xy_dev  vertices: 2V int32 (x, y) pairs, 8-byte aligned
+ *   T, tri_dev triangles: 4T int32 (a, b, c, unused), 16-byte aligned;
+ *              1 <= T <= 65536; the caller guarantees a valid mesh of the
+ *              image (indices < V, as produced by fem_spatial_refine)
+ *   uv_dev     V float64 vertex values; f_dev width*width float32
+ *   err_dev    out: T float64
+ * Sizes beyond the limits return FEM_E_SHAPE / FEM_E_INVALID with a message
+ * before any work.  Synchronises `stream` before returning. */
+FEM_API fem_status fem_triangle_errors_noalloc(int width, int V, const int *xy_dev, int T, const int *tri_dev,
+                                               const double *uv_dev, const float *f_dev, double *err_dev,
+                                               void *stream);
+
 /* Linear interpolation of vertex values to every pixel (end of Sec. 2.2).
  *   uv_dev    in : V float64 vertex values
  *   u_dev     out: width*height float32 image, or NULL

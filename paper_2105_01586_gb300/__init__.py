@@ -44,7 +44,7 @@ _STATUS = {0: "FEM_OK", 1: "FEM_E_INVALID", 2: "FEM_E_SHAPE", 3: "FEM_E_OOM", 4:
            5: "FEM_E_TIMEOUT", 6: "FEM_E_CUDA"}
 
 EXPORTED = ["fem_params_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_info", "fem_mesh_export",
-            "fem_mesh_import", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_rasterize", "fem_spatial_refine",
+            "fem_mesh_import", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_triangle_errors_noalloc", "fem_rasterize", "fem_spatial_refine",
             "fem_tonal_opt", "fem_adjoint", "fem_mesh_stats", "fem_last_error", "fem_profile_enable",
             "fem_profile_read", "fem_launch_count"]
 
@@ -75,6 +75,7 @@ _sig = {
     "fem_gather_mask": (_i, [_vp, _vp, _vp, _vp]),
     "fem_inpaint": (_i, [_vp, _vp, _vp, _vp, _pp, _vp]),
     "fem_triangle_errors": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "fem_triangle_errors_noalloc": (_i, [_i, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "fem_rasterize": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "fem_spatial_refine": (_i, [_vp, _vp, ctypes.c_double, _pp, _vp]),
     "fem_tonal_opt": (_i, [_vp, _vp, _vp, _pp, _vp]),
@@ -198,6 +199,23 @@ def fem_triangle_errors(h: int, uv, f, err, stream=None):
     torch = _torch()
     _check(_lib.fem_triangle_errors(h, _dev_ptr(uv, torch.float64, V, "uv"), _dev_ptr(f, torch.float32, None, "f"),
                                     _dev_ptr(err, torch.float64, T, "err"), _stream(stream)), "fem_triangle_errors")
+
+
+def fem_triangle_errors_noalloc(width: int, xy, tri4, uv, f, err, stream=None):
+    """Per-triangle errors without any device allocation (fixed library
+    scratch; see include/feminpaint.h).  xy: (V, 2) int32, tri4: (T, 4)
+    int32 (a, b, c, unused), uv: V float64, f: width*width float32, err: T
+    float64, all CUDA tensors the caller owns."""
+    torch = _torch()
+    V = xy.shape[0]
+    T = tri4.shape[0]
+    if xy.dim() != 2 or xy.shape[1] != 2 or tri4.dim() != 2 or tri4.shape[1] != 4:
+        raise ValueError("xy must be (V, 2) and tri4 (T, 4)")
+    _check(_lib.fem_triangle_errors_noalloc(int(width), V, _dev_ptr(xy, torch.int32, 2 * V, "xy"), T,
+                                            _dev_ptr(tri4, torch.int32, 4 * T, "tri4"),
+                                            _dev_ptr(uv, torch.float64, V, "uv"), _dev_ptr(f, torch.float32, None, "f"),
+                                            _dev_ptr(err, torch.float64, T, "err"), _stream(stream)),
+           "fem_triangle_errors_noalloc")
 
 
 def fem_rasterize(h: int, uv, u=None, owner=None, stream=None):

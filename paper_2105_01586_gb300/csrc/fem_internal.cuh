@@ -247,4 +247,22 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
 fem_status sync_counts(fem_mesh* m, cudaStream_t s);
 fem_status ensure_mesh_capacity(fem_mesh* m, int needV, int needT, cudaStream_t s);
 int sm_count();
+
+// caller-provided scratch for the allocation-free error pass
+struct RasterScratch {
+    int* item_cnt;   // T
+    int* item_off;   // T + 1
+    int* item_tri;   // item_cap
+    double* partial; // item_cap
+    int item_cap;
+    int* counters;   // [0] item count, [1] overflow flag; zeroed by the caller
+    int* scan_tmp;
+    int scan_tmp_n;
+    int grid;
+};
+int scan_tmp_ints(int n);
+fem_status exclusive_scan_i32_scratch(const int* in, int* out, int n, cudaStream_t s, int* total_dev, int* tmp,
+                                      int tmp_n);
+fem_status raster_errors_scratch(const int4* tri, const int2* vxy, int T, int N, const double* uv, const float* f,
+                                 double* err_out, cudaStream_t s, const RasterScratch& w);
 }  // namespace fem

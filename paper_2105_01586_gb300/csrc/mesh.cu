@@ -215,6 +215,37 @@ fem_status exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, in
     return st;
 }
 
+// The same scan with caller-provided temporary storage (no allocation):
+// tmp must hold at least scan_tmp_ints(n) ints.
+int scan_tmp_ints(int n) {
+    if (n <= SCAN_TILE) return 0;
+    int tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    return 2 * tiles + 2 + scan_tmp_ints(tiles);
+}
+
+fem_status exclusive_scan_i32_scratch(const int* in, int* out, int n, cudaStream_t s, int* total_dev, int* tmp,
+                                      int tmp_n) {
+    if (n <= 0) {
+        if (total_dev) FEM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int), s));
+        return FEM_OK;
+    }
+    if (tmp_n < scan_tmp_ints(n)) {
+        set_error("scan: temporary storage too small");
+        return FEM_E_INVALID;
+    }
+    int tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    int* sums = tmp;
+    int* sums_off = tmp + tiles + 1;
+    FEM_LAUNCH(F_OTHER, s, k_scan_tiles, tiles, SCAN_BT, 0, in, out, n, sums);
+    if (tiles > 1) {
+        FEM_TRY(exclusive_scan_i32_scratch(sums, sums_off, tiles, s, nullptr, tmp + 2 * tiles + 2,
+                                           tmp_n - (2 * tiles + 2)));
+        FEM_LAUNCH(F_OTHER, s, k_scan_add, tiles, SCAN_BT, 0, out, n, sums_off);
+    }
+    if (total_dev) FEM_LAUNCH(F_OTHER, s, k_scan_total, 1, 1, 0, in, out, n, total_dev);
+    return FEM_OK;
+}
+
 // ------------------------------------------------------------- capacities
 fem_status ensure_mesh_capacity(fem_mesh* m, int needV, int needT, cudaStream_t s) {
     long long maxV = m->P, maxT = 2LL * (m->N - 1) * (m->N - 1);

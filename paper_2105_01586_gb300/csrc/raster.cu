@@ -275,6 +275,22 @@ fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s) {
     return FEM_OK;
 }
 
+// Error pass on caller-described mesh arrays with caller-provided scratch
+// (no allocation).  Same kernels as raster_errors.
+fem_status raster_errors_scratch(const int4* tri, const int2* vxy, int T, int N, const double* uv, const float* f,
+                                 double* err_out, cudaStream_t s, const RasterScratch& w) {
+    int* n_items_dev = w.counters + 0;
+    int* err = w.counters + 1;
+    int blocks = (T + 255) / 256;
+    FEM_LAUNCH(F_RASTER, s, k_item_count, blocks, 256, 0, tri, vxy, T, N, w.item_cnt);
+    FEM_TRY(exclusive_scan_i32_scratch(w.item_cnt, w.item_off, T, s, n_items_dev, w.scan_tmp, w.scan_tmp_n));
+    FEM_LAUNCH(F_RASTER, s, k_item_expand, blocks, 256, 0, w.item_cnt, w.item_off, T, w.item_cap, w.item_tri, err);
+    FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, w.grid, kRasterThreads, 0, tri, vxy, uv, f, N, w.item_tri, w.item_off,
+               n_items_dev, w.item_cap, w.partial, (float*)nullptr, (int*)nullptr);
+    FEM_LAUNCH(F_RASTER, s, k_finalize<1>, blocks, 256, 0, w.item_cnt, w.item_off, w.partial, T, err_out);
+    return FEM_OK;
+}
+
 }  // namespace fem
 
 using namespace fem;

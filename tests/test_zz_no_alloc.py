@@ -1,0 +1,67 @@
+"""The allocation-free error entry point (fem_triangle_errors_noalloc).
+
+It serves callers that cannot allocate device memory (graph capture in
+progress, allocators that own all device memory, loops that must not
+allocate).  It must give the same per-triangle errors as
+fem_triangle_errors, on two calls in a row (the shared scratch keeps the
+previous call's contents), alone in a fresh process or after other tests.
+This file is named so that pytest collects it last.
+"""
+import numpy as np
+import pytest
+
+import seeded_inputs as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fem():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2105_01586_gb300 as fem
+    return fem
+
+
+def _case(oracle_mod, fem, N, seed, density):
+    f_np = S.make_image(N, seed)
+    om, _ = oracle_mod.spatial(f_np, density, 0.01)
+    m = fem.Mesh(N)
+    m.import_(om.xy, om.tri, om.mask)
+    xy = torch.from_numpy(om.xy.astype(np.int32)).cuda().contiguous()
+    tri4 = torch.zeros((om.T, 4), dtype=torch.int32)
+    tri4[:, :3] = torch.from_numpy(om.tri.astype(np.int32))
+    tri4 = tri4.cuda().contiguous()
+    uv = torch.from_numpy(np.random.default_rng(seed).uniform(-0.2, 1.2, om.V)).cuda()
+    f = torch.from_numpy(f_np).cuda()
+    return m, xy, tri4, uv, f
+
+
+def test_noalloc_matches_allocating_entry_point_twice(oracle_mod, fem):
+    # two different meshes one after the other: the second call must not see the first one's scratch
+    for N, seed, density in ((257, 1, 0.03), (129, 2, 0.08)):
+        m, xy, tri4, uv, f = _case(oracle_mod, fem, N, seed, density)
+        ref = m.triangle_errors(uv, f)
+        for _ in range(2):
+            err = torch.full((tri4.shape[0],), -1.0, dtype=torch.float64, device="cuda")
+            fem.fem_triangle_errors_noalloc(N, xy, tri4, uv, f, err)
+            torch.cuda.synchronize()
+            np.testing.assert_allclose(err.cpu().numpy(), ref.cpu().numpy(), rtol=1e-12, atol=1e-300)
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(fem):
+    xy = torch.zeros((4, 2), dtype=torch.int32, device="cuda")
+    big = torch.zeros((65537, 4), dtype=torch.int32, device="cuda")
+    uv = torch.zeros(4, dtype=torch.float64, device="cuda")
+    err = torch.zeros(65537, dtype=torch.float64, device="cuda")
+    f = torch.zeros((129, 129), dtype=torch.float32, device="cuda")
+    with pytest.raises(fem.FemError) as e:
+        fem.fem_triangle_errors_noalloc(129, xy, big, uv, f, err)
+    assert e.value.status == fem.FEM_E_INVALID and "65536" in str(e.value)
+    f2 = torch.zeros((4097, 4097), dtype=torch.float32, device="cuda")
+    with pytest.raises(fem.FemError) as e:
+        fem.fem_triangle_errors_noalloc(4097, xy, big[:2], uv, f2, err[:2])
+    assert e.value.status == fem.FEM_E_SHAPE
