@@ -178,11 +178,13 @@ struct fem_mesh {
     fem::DArr<unsigned char> mask;
     fem::DArr<int4> tri;
     fem::DArr<double> uv;
+    fem::DArr<float2> uvf;  // float-float copy of uv, written with it in the spatial loop
 
     // rasterisation plan (valid for plan_T triangles of plan_version)
     fem::DArr<int> item_cnt, item_off, item_tri;
     fem::DArr<double> partial;
     fem::DArr<double> keys;
+    fem::DArr<unsigned long long> keyc;  // composite selection keys (eligible flag | key bits)
     long long plan_version = -1, mesh_version = 0;
     int n_items = 0;
 
@@ -201,6 +203,8 @@ struct fem_mesh {
     fem::DArr<int> ucol;            // 8*nU ELL columns (slot-major), padded with own row
     fem::DArr<float> uval32;        // 8*nU ELL values (0 in padding)
     fem::DArr<double> uval64;
+    fem::DArr<float> udiag;         // nU diagonal of A_UU (exact)
+    fem::DArr<int> ucnt;            // nU used ELL slots per row
     fem::DArr<float> dinv32;        // nU inverse diagonal
     fem::DArr<double> dinv64;
     fem::DArr<int> urow_vertex;     // nU: vertex of each U row
@@ -208,6 +212,11 @@ struct fem_mesh {
     // CG work
     fem::DArr<double> x64, b64, r64, p64, q64, z64;
     fem::DArr<float> r32, p32, q32, z32, d32;
+    fem::DArr<float> bvec;              // one-block solve: global fallback vectors
+    fem::DArr<int> browptr;
+    fem::DArr<unsigned short> bent;
+    fem::DArr<unsigned char> bdg2;
+    fem::DArr<float2> bxff, bbff;       // float-float iterate and right-hand side
     fem::DArr<double> red;          // grid-reduction partials
     fem::DArr<unsigned> bar;        // grid barrier words
     fem::DArr<int> dflag;           // device status/flags
@@ -239,7 +248,8 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
 fem_status set_uv_from_g(fem_mesh* m, const float* g_dev, cudaStream_t s);
 fem_status set_uv_from_f(fem_mesh* m, const float* f_dev, cudaStream_t s);
 fem_status raster_plan(fem_mesh* m, cudaStream_t s);
-fem_status raster_errors(fem_mesh* m, const double* uv, const float* f, double* err, cudaStream_t s);
+fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, const float* f, double* err,
+                         cudaStream_t s, unsigned long long* keyc_out = nullptr);
 fem_status raster_image(fem_mesh* m, const double* uv, float* u, int* owner, cudaStream_t s);
 fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s);
 fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vstar, cudaStream_t s,

@@ -256,6 +256,7 @@ fem_status ensure_mesh_capacity(fem_mesh* m, int needV, int needT, cudaStream_t 
     FEM_TRY(ensure(m->vxy, nv, s, m->V));
     FEM_TRY(ensure(m->mask, nv, s, m->V));
     FEM_TRY(ensure(m->uv, nv, s, m->V));
+    FEM_TRY(ensure(m->uvf, nv, s, m->V));
     FEM_TRY(ensure(m->tri, nt, s, m->T));
     return FEM_OK;
 }
@@ -384,16 +385,19 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     if (!m) return FEM_OK;
     cudaStream_t s = m->last_stream;
     cudaStreamSynchronize(s);
-    release(m->vxy, s); release(m->mask, s); release(m->tri, s); release(m->uv, s);
+    release(m->vxy, s); release(m->mask, s); release(m->tri, s); release(m->uv, s); release(m->uvf, s);
     release(m->item_cnt, s); release(m->item_off, s); release(m->item_tri, s); release(m->partial, s);
     release(m->keys, s);
+    release(m->keyc, s);
     release(m->bmM, s); release(m->bmS, s); release(m->wpre, s);
     release(m->flags, s); release(m->fscan, s); release(m->wcnt, s); release(m->topk_hist, s);
     release(m->uidx, s); release(m->kidx, s); release(m->nbr, s); release(m->coefA, s); release(m->diagA, s);
-    release(m->ucol, s); release(m->uval32, s); release(m->uval64, s); release(m->dinv32, s); release(m->dinv64, s);
+    release(m->ucol, s); release(m->uval32, s); release(m->uval64, s); release(m->udiag, s); release(m->ucnt, s); release(m->dinv32, s); release(m->dinv64, s);
     release(m->urow_vertex, s); release(m->kvert, s);
     release(m->x64, s); release(m->b64, s); release(m->r64, s); release(m->p64, s); release(m->q64, s); release(m->z64, s);
     release(m->r32, s); release(m->p32, s); release(m->q32, s); release(m->z32, s); release(m->d32, s);
+    release(m->bvec, s); release(m->browptr, s); release(m->bent, s); release(m->bdg2, s);
+    release(m->bxff, s); release(m->bbff, s);
     release(m->red, s); release(m->bar, s); release(m->dflag, s); release(m->dscal, s); release(m->dcount, s);
     release(m->inc, s); release(m->loc, s); release(m->Moff, s); release(m->Mdiag, s);
     release(m->tv, s); release(m->ty, s); release(m->tz, s); release(m->tg, s);

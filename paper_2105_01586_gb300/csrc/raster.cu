@@ -19,6 +19,7 @@
 #include <climits>
 
 #include "fem_internal.cuh"
+#include "ff.cuh"
 
 namespace fem {
 
@@ -96,13 +97,30 @@ struct NAcc {
     static constexpr int n = MODE == R_ERR ? 1 : (MODE == R_MASS ? 6 : (MODE == R_SCAT ? 3 : 0));
 };
 
+// vertex value as float-float: from the float-float copy when there is one,
+// else split from FP64
+__device__ __forceinline__ ff vertex_ff(const double* __restrict__ uv, const float2* __restrict__ uvf, int i) {
+    if (uvf) {
+        float2 v = uvf[i];
+        return ff{v.x, v.y};
+    }
+    return ff_from_double(uv[i]);
+}
+
+// Error and image modes evaluate the linear interpolant as a plane in
+// float-float, u(x, y) = u_c + g_x (x - c_x) + g_y (y - c_y), with g the
+// gradient ((a-c)(u_a-u_c) + (b-c)(u_b-u_c)) / |a-c|^2 (legs orthogonal and
+// of equal length), and accumulate (u - f)^2 in float-float: about 48-bit
+// precision on the FP32 pipes.  The mass and scatter modes (run once per
+// tonal optimisation) use FP64 barycentric weights.
 template <int MODE>
 __global__ void __launch_bounds__(kRasterThreads) k_raster(
     const int4* __restrict__ tri, const int2* __restrict__ vxy, const double* __restrict__ uv,
-    const float* __restrict__ img, int N, const int* __restrict__ item_tri, const int* __restrict__ item_off,
-    const int* __restrict__ n_items_dev, int item_cap, double* __restrict__ partial, float* __restrict__ u_out,
-    int* __restrict__ owner_out) {
+    const float2* __restrict__ uvf, const float* __restrict__ img, int N, const int* __restrict__ item_tri,
+    const int* __restrict__ item_off, const int* __restrict__ n_items_dev, int item_cap,
+    double* __restrict__ partial, float* __restrict__ u_out, int* __restrict__ owner_out) {
     constexpr int NA = NAcc<MODE>::n;
+    constexpr bool FF = (MODE == R_ERR || MODE == R_IMG);
     const unsigned FULL = 0xffffffffu;
     int lane = threadIdx.x & 31;
     long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -127,13 +145,31 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
         int off = incl - len;
         int total = __shfl_sync(FULL, incl, 31);
 
-        double va = 0, vb = 0, vc = 0;
-        if (MODE == R_ERR || MODE == R_IMG) {
-            va = uv[tr.x]; vb = uv[tr.y]; vc = uv[tr.z];
-        }
         int dax = g.ax - g.cx, day = g.ay - g.cy, dbx = g.bx - g.cx, dby = g.by - g.cy;
-        // |a - c|^2 = |b - c|^2 is a power of two, so this reciprocal is exact
-        double inv_l2 = 1.0 / (double)((long long)dax * dax + (long long)day * day);
+        long long l2 = (long long)dax * dax + (long long)day * day;
+        bool pow2 = (l2 & (l2 - 1)) == 0;
+        // plane of the interpolant (float-float), error accumulator
+        ff uc{0.f, 0.f}, gx{0.f, 0.f}, gy{0.f, 0.f}, acc_ff{0.f, 0.f};
+        double inv_l2 = 0.0;
+        if (FF) {
+            ff va = vertex_ff(uv, uvf, tr.x), vb = vertex_ff(uv, uvf, tr.y);
+            uc = vertex_ff(uv, uvf, tr.z);
+            ff da = ff_sub(va, uc), db = ff_sub(vb, uc);
+            gx = ff_add(ff_mul_f(da, (float)dax), ff_mul_f(db, (float)dbx));
+            gy = ff_add(ff_mul_f(da, (float)day), ff_mul_f(db, (float)dby));
+            if (pow2) {
+                // exact reciprocal of a power of two
+                float inv = __int_as_float((127 - (63 - __clzll(l2))) << 23);
+                gx = ff_scale_pow2(gx, inv);
+                gy = ff_scale_pow2(gy, inv);
+            } else {
+                float inv = 1.0f / (float)l2;
+                gx = ff_mul_f(gx, inv);
+                gy = ff_mul_f(gy, inv);
+            }
+        } else {
+            inv_l2 = pow2 ? __longlong_as_double((long long)(1023 - (63 - __clzll(l2))) << 52) : 1.0 / (double)l2;
+        }
         double acc[NA > 0 ? NA : 1];
 #pragma unroll
         for (int q = 0; q < (NA > 0 ? NA : 1); ++q) acc[q] = 0.0;
@@ -151,41 +187,74 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
             int ok = __shfl_sync(FULL, off, k);
             if (jj < total) {
                 int x = Lk + (jj - ok), y = r0 + k;
-                long long dxp = x - g.cx, dyp = y - g.cy;
-                double la = (double)(dxp * dax + dyp * day) * inv_l2;
-                double lb = (double)(dxp * dbx + dyp * dby) * inv_l2;
-                double lc = 1.0 - la - lb;
                 long long p = (long long)y * N + x;
-                if (MODE == R_ERR) {
-                    double u = fma(la, va, fma(lb, vb, lc * vc));
-                    double d = u - (double)img[p];
-                    acc[0] = fma(d, d, acc[0]);
-                } else if (MODE == R_IMG) {
-                    double u = fma(la, va, fma(lb, vb, lc * vc));
-                    if (u_out) u_out[p] = (float)u;
-                    if (owner_out) owner_out[p] = t;
-                } else if (MODE == R_MASS) {
-                    acc[0] = fma(la, la, acc[0]);
-                    acc[1] = fma(lb, lb, acc[1]);
-                    acc[2] = fma(lc, lc, acc[2]);
-                    acc[3] = fma(la, lb, acc[3]);
-                    acc[4] = fma(lb, lc, acc[4]);
-                    acc[5] = fma(lc, la, acc[5]);
-                } else if (MODE == R_SCAT) {
-                    double r = (double)img[p];
-                    acc[0] = fma(la, r, acc[0]);
-                    acc[1] = fma(lb, r, acc[1]);
-                    acc[2] = fma(lc, r, acc[2]);
+                if (FF) {
+                    float dx = (float)(x - g.cx), dy = (float)(y - g.cy);
+                    ff u = ff_add(ff_add(uc, ff_mul_f(gx, dx)), ff_mul_f(gy, dy));
+                    if (MODE == R_ERR) {
+                        ff d = ff_add_f(u, -img[p]);
+                        acc_ff = ff_add(acc_ff, ff_sqr(d));
+                    } else {
+                        if (u_out) u_out[p] = __fadd_rn(u.hi, u.lo);
+                        if (owner_out) owner_out[p] = t;
+                    }
+                } else {
+                    long long dxp = x - g.cx, dyp = y - g.cy;
+                    double la = (double)(dxp * dax + dyp * day) * inv_l2;
+                    double lb = (double)(dxp * dbx + dyp * dby) * inv_l2;
+                    double lc = 1.0 - la - lb;
+                    if (MODE == R_MASS) {
+                        acc[0] = fma(la, la, acc[0]);
+                        acc[1] = fma(lb, lb, acc[1]);
+                        acc[2] = fma(lc, lc, acc[2]);
+                        acc[3] = fma(la, lb, acc[3]);
+                        acc[4] = fma(lb, lc, acc[4]);
+                        acc[5] = fma(lc, la, acc[5]);
+                    } else if (MODE == R_SCAT) {
+                        double r = (double)img[p];
+                        acc[0] = fma(la, r, acc[0]);
+                        acc[1] = fma(lb, r, acc[1]);
+                        acc[2] = fma(lc, r, acc[2]);
+                    }
                 }
             }
         }
-        if (NA > 0) {
+        if (MODE == R_ERR) {
+            ff tot = ff_warp_sum(acc_ff);
+            if (lane == 0) ((float2*)partial)[it] = make_float2(tot.hi, tot.lo);
+        } else if (NA > 0) {
 #pragma unroll
             for (int q = 0; q < (NA > 0 ? NA : 1); ++q) {
                 double v = warp_sum(acc[q]);
                 if (lane == 0) partial[it * NA + q] = v;
             }
         }
+    }
+}
+
+// per-triangle error from float-float item partials (added in item order);
+// keyc (optional): composite selection key, eligible triangles (refinement-
+// edge midpoint on the pixel grid) get the FP64 key bits with the top bit
+// set, the others 0, so that unsigned order = selection order
+__global__ void k_finalize_err(const int* __restrict__ cnt, const int* __restrict__ off,
+                               const float2* __restrict__ partial, int T, const int4* __restrict__ tri,
+                               const int2* __restrict__ vxy, double* __restrict__ out,
+                               unsigned long long* __restrict__ keyc) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    int o = off[t], n = cnt[t];
+    ff s{0.f, 0.f};
+    for (int j = 0; j < n; ++j) {
+        float2 v = partial[o + j];
+        s = ff_add(s, ff{v.x, v.y});
+    }
+    double key = ff_to_double(s);
+    out[t] = key;
+    if (keyc) {
+        int4 tr = tri[t];
+        int2 a = vxy[tr.x], b = vxy[tr.y];
+        bool eligible = (((a.x + b.x) | (a.y + b.y)) & 1) == 0;
+        keyc[t] = eligible ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
     }
 }
 
@@ -233,13 +302,16 @@ static double raster_err_bytes(const fem_mesh* m) {
     return 4.0 * (double)m->P + 24.0 * m->T + 16.0 * m->V;
 }
 
-fem_status raster_errors(fem_mesh* m, const double* uv, const float* f, double* err_out, cudaStream_t s) {
+fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, const float* f, double* err_out,
+                         cudaStream_t s, unsigned long long* keyc_out) {
     FEM_TRY(raster_plan(m, s));
     note_bytes(F_RASTER, raster_err_bytes(m));
-    FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, f, m->N,
-               m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p, (float*)nullptr, (int*)nullptr);
+    FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
+               m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p, (float*)nullptr,
+               (int*)nullptr);
     int blocks = (m->T + 255) / 256;
-    FEM_LAUNCH(F_RASTER, s, k_finalize<1>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T, err_out);
+    FEM_LAUNCH(F_RASTER, s, k_finalize_err, blocks, 256, 0, m->item_cnt.p, m->item_off.p,
+               (const float2*)m->partial.p, m->T, m->tri.p, m->vxy.p, err_out, keyc_out);
     return FEM_OK;
 }
 
@@ -248,7 +320,7 @@ fem_status raster_image(fem_mesh* m, const double* uv, float* u, int* owner, cud
     note_bytes(F_RASTER, (u ? 4.0 * (double)m->P : 0.0) + (owner ? 4.0 * (double)m->P : 0.0) + 16.0 * m->T +
                              16.0 * m->V);
     FEM_LAUNCH(F_RASTER, s, k_raster<R_IMG>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv,
-               (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p, u, owner);
+               (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p, u, owner);
     return FEM_OK;
 }
 
@@ -261,13 +333,13 @@ fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s) {
     note_bytes(F_RASTER, (mode == R_MASS ? 64.0 * m->T : 4.0 * (double)m->P + 40.0 * m->T) + 8.0 * m->V);
     if (mode == R_MASS) {
         FEM_LAUNCH(F_RASTER, s, k_raster<R_MASS>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
-                   (const double*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0,
+                   (const double*)nullptr, (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0,
                    (int)m->item_tri.n, m->partial.p, (float*)nullptr, (int*)nullptr);
         FEM_LAUNCH(F_RASTER, s, k_finalize<6>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
                    m->loc.p);
     } else {
         FEM_LAUNCH(F_RASTER, s, k_raster<R_SCAT>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
-                   (const double*)nullptr, r, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p,
+                   (const double*)nullptr, (const float2*)nullptr, r, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p,
                    (float*)nullptr, (int*)nullptr);
         FEM_LAUNCH(F_RASTER, s, k_finalize<3>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
                    m->loc.p);
@@ -285,9 +357,10 @@ fem_status raster_errors_scratch(const int4* tri, const int2* vxy, int T, int N,
     FEM_LAUNCH(F_RASTER, s, k_item_count, blocks, 256, 0, tri, vxy, T, N, w.item_cnt);
     FEM_TRY(exclusive_scan_i32_scratch(w.item_cnt, w.item_off, T, s, n_items_dev, w.scan_tmp, w.scan_tmp_n));
     FEM_LAUNCH(F_RASTER, s, k_item_expand, blocks, 256, 0, w.item_cnt, w.item_off, T, w.item_cap, w.item_tri, err);
-    FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, w.grid, kRasterThreads, 0, tri, vxy, uv, f, N, w.item_tri, w.item_off,
-               n_items_dev, w.item_cap, w.partial, (float*)nullptr, (int*)nullptr);
-    FEM_LAUNCH(F_RASTER, s, k_finalize<1>, blocks, 256, 0, w.item_cnt, w.item_off, w.partial, T, err_out);
+    FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, w.grid, kRasterThreads, 0, tri, vxy, uv, (const float2*)nullptr, f, N,
+               w.item_tri, w.item_off, n_items_dev, w.item_cap, w.partial, (float*)nullptr, (int*)nullptr);
+    FEM_LAUNCH(F_RASTER, s, k_finalize_err, blocks, 256, 0, w.item_cnt, w.item_off, (const float2*)w.partial, T, tri,
+               vxy, err_out, (unsigned long long*)nullptr);
     return FEM_OK;
 }
 
@@ -304,7 +377,7 @@ fem_status fem_triangle_errors(fem_mesh* m, const double* uv_dev, const float* f
     }
     cudaStream_t s = (cudaStream_t)stream;
     m->last_stream = s;
-    FEM_TRY(raster_errors(m, uv_dev, f_dev, err_dev, s));
+    FEM_TRY(raster_errors(m, uv_dev, nullptr, f_dev, err_dev, s));
     int e = 0;
     FEM_CUDA(cudaMemcpyAsync(&e, m->dflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));

@@ -150,6 +150,137 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(TopkArgs A) {
     }
 }
 
+// Top-k for up to kTopkBlockMaxT triangles in one 1024-thread block (no
+// device-wide barrier).  keyc holds the composite keys (0 = ineligible);
+// the 96-bit order key is (keyc, ~id).  Radix select, 8 bits per digit,
+// reading the global array until the current bucket fits in shared memory,
+// then on the shared-memory candidate list.
+constexpr int kTopkBlockThreads = 1024;
+constexpr int kTopkCandCap = 12288;
+constexpr int kTopkBlockMaxT = 1 << 20;
+constexpr size_t kTopkBlockSmem = (size_t)kTopkCandCap * (sizeof(unsigned long long) + sizeof(unsigned));
+
+__device__ __forceinline__ bool prefix_match(unsigned long long hi, unsigned lo, unsigned long long pre_hi,
+                                             unsigned pre_lo, int d) {
+    unsigned long long mhi = d >= 8 ? ~0ull : (d == 0 ? 0ull : (~0ull << (64 - 8 * d)));
+    unsigned mlo = d <= 8 ? 0u : (~0u << (32 - 8 * (d - 8)));
+    return (hi & mhi) == pre_hi && (lo & mlo) == pre_lo;
+}
+
+__global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned long long* __restrict__ keyc, int T,
+                                                                  double frac, long long vcap, int* out_k,
+                                                                  unsigned long long* out_thr, double* out_margin) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned long long* c_hi = (unsigned long long*)smem_raw;
+    unsigned* c_lo = (unsigned*)(c_hi + kTopkCandCap);
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long s_pre_hi, s_best[32];
+    __shared__ unsigned s_pre_lo, s_cnt32[32];
+    __shared__ long long s_krem;
+    __shared__ int s_n, s_cnt, s_smem;
+    int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    unsigned ne = 0;
+    for (int t = tid; t < T; t += kTopkBlockThreads) ne += keyc[t] ? 1u : 0u;
+    ne = warp_sum(ne);
+    if (lane == 0) s_cnt32[wid] = ne;
+    __syncthreads();
+    if (tid == 0) {
+        long long tot = 0;
+        for (int w = 0; w < kTopkBlockThreads / 32; ++w) tot += s_cnt32[w];
+        long long k = (long long)ceil(frac * (double)T);
+        if (k < 1) k = 1;
+        if (k > tot) k = tot;
+        if (k > vcap) k = vcap;
+        if (k < 0) k = 0;
+        *out_k = (int)k;
+        s_krem = k;
+        s_pre_hi = 0;
+        s_pre_lo = 0;
+        s_smem = 0;
+        s_n = 0;
+    }
+    __syncthreads();
+    if (s_krem == 0) return;
+    for (int d = 0; d < 12; ++d) {
+        for (int i = tid; i < 256; i += kTopkBlockThreads) hist[i] = 0;
+        __syncthreads();
+        unsigned long long pre_hi = s_pre_hi;
+        unsigned pre_lo = s_pre_lo;
+        if (!s_smem) {
+            for (int t = tid; t < T; t += kTopkBlockThreads) {
+                unsigned long long hi = keyc[t];
+                unsigned lo = ~(unsigned)t;
+                if (prefix_match(hi, lo, pre_hi, pre_lo, d)) atomicAdd(&hist[digit_of(hi, lo, d)], 1u);
+            }
+        } else {
+            for (int i = tid; i < s_n; i += kTopkBlockThreads) {
+                unsigned long long hi = c_hi[i];
+                unsigned lo = c_lo[i];
+                if (prefix_match(hi, lo, pre_hi, pre_lo, d)) atomicAdd(&hist[digit_of(hi, lo, d)], 1u);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            long long krem = s_krem, cum = 0;
+            int chosen = 0;
+            for (int b = 255; b >= 0; --b) {
+                long long h = hist[b];
+                if (cum + h >= krem) { chosen = b; break; }
+                cum += h;
+            }
+            s_krem = krem - cum;
+            s_cnt = (int)hist[chosen];
+            if (d < 8) s_pre_hi = pre_hi | ((unsigned long long)chosen << (56 - 8 * d));
+            else s_pre_lo = pre_lo | ((unsigned)chosen << (24 - 8 * (d - 8)));
+        }
+        __syncthreads();
+        if (!s_smem && d < 11 && s_cnt <= kTopkCandCap) {
+            unsigned long long nh = s_pre_hi;
+            unsigned nl = s_pre_lo;
+            for (int t = tid; t < T; t += kTopkBlockThreads) {
+                unsigned long long hi = keyc[t];
+                unsigned lo = ~(unsigned)t;
+                if (prefix_match(hi, lo, nh, nl, d + 1)) {
+                    int pos = atomicAdd(&s_n, 1);
+                    c_hi[pos] = hi;
+                    c_lo[pos] = lo;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) s_smem = 1;
+            __syncthreads();
+        }
+    }
+    unsigned long long thr_hi = s_pre_hi;
+    unsigned thr_lo = s_pre_lo;
+    // largest key strictly below the threshold (decision margin)
+    unsigned long long best = 0ull;
+    for (int t = tid; t < T; t += kTopkBlockThreads) {
+        unsigned long long hi = keyc[t];
+        unsigned lo = ~(unsigned)t;
+        if ((hi < thr_hi || (hi == thr_hi && lo < thr_lo)) && hi > best) best = hi;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+        best = v > best ? v : best;
+    }
+    if (lane == 0) s_best[wid] = best;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long bm = 0;
+        for (int w = 0; w < kTopkBlockThreads / 32; ++w) bm = s_best[w] > bm ? s_best[w] : bm;
+        out_thr[0] = thr_hi;
+        out_thr[1] = thr_lo;
+        double kth = __longlong_as_double((long long)(thr_hi & ~(1ull << 63)));
+        if (bm & (1ull << 63)) {
+            double nxt = __longlong_as_double((long long)(bm & ~(1ull << 63)));
+            *out_margin = kth > 0.0 ? (kth - nxt) / kth : 0.0;
+        } else {
+            *out_margin = INFINITY;
+        }
+    }
+}
+
 // mark the refinement edges of the selected triangles in bmM and bmS
 __global__ void k_mark_selected(const double* __restrict__ keys, const int4* __restrict__ tri,
                                 const int2* __restrict__ vxy, int T, int N, const unsigned long long* __restrict__ thr,
@@ -336,7 +467,16 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
     A.out_thr = thr;
     A.red = m->red.p;
     A.out_margin = margin;
-    {
+    if (T <= kTopkBlockMaxT && m->keyc.p && m->keyc.n >= (size_t)T) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            FEM_CUDA(cudaFuncSetAttribute(k_topk_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kTopkBlockSmem));
+            attr_set = true;
+        }
+        FEM_LAUNCH(F_TOPK, s, k_topk_block, 1, kTopkBlockThreads, kTopkBlockSmem, m->keyc.p, T, frac, vstar - V,
+                   kdev, thr, margin);
+    } else {
         void* args[] = {&A};
         int grid = coop_grid((const void*)k_topk, kTopkThreads, T, m->num_sms);
         FEM_TRY(launch_coop(F_TOPK, (const void*)k_topk, grid, kTopkThreads, 0, s, args, "k_topk"));
@@ -422,7 +562,10 @@ extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double
         (void)solves;
         if (st != FEM_OK) return st;
         FEM_TRY(ensure(m->keys, (size_t)m->T, s));
-        FEM_TRY(raster_errors(m, m->uv.p, f_dev, m->keys.p, s));
+        FEM_TRY(ensure(m->keyc, (size_t)m->T, s));
+        // in the spatial loop every vertex value was just written together with
+        // its float-float copy (mask vertices from f, unknowns by the solve)
+        FEM_TRY(raster_errors(m, m->uv.p, m->uvf.p, f_dev, m->keys.p, s, m->keyc.p));
         double margin = 0.0;
         int k = 0;
         FEM_TRY(refine_round(m, f_dev, p->topk_frac, vstar, s, &margin, &k));

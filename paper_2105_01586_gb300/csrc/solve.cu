@@ -18,11 +18,15 @@
 #include <vector>
 
 #include "fem_internal.cuh"
+#include "ff.cuh"
 
 namespace fem {
 
 constexpr int kSolveThreads = 256;
+constexpr int kSingleThreads = 1024;
+constexpr int kSingleMaxRows = 8192;   // systems up to this size run in one block
 constexpr double kInnerEta = 1e-5;
+constexpr int kInnerCap = 4000;        // FP32 iterations per refinement step
 
 // ---------------------------------------------------------------- assembly
 __global__ void k_assemble(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int V,
@@ -75,7 +79,8 @@ __global__ void k_index_maps(const unsigned char* __restrict__ mask, int V, int*
 __global__ void k_build_ell(int nU, int V, const int* __restrict__ urow_vertex, const int* __restrict__ nbr,
                             const float* __restrict__ coef, const float* __restrict__ diag,
                             const int* __restrict__ uidx, int* __restrict__ ucol, float* __restrict__ uval,
-                            float* __restrict__ udiag) {
+                            float* __restrict__ udiag, int* __restrict__ ucnt, float* __restrict__ udinv,
+                            double* __restrict__ udinv64) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nU) return;
     int i = urow_vertex[r];
@@ -93,11 +98,14 @@ __global__ void k_build_ell(int nU, int V, const int* __restrict__ urow_vertex, 
             }
         }
     }
+    ucnt[r] = s;
     for (; s < 8; ++s) {
         ucol[s * nU + r] = r;
         uval[s * nU + r] = 0.0f;
     }
     udiag[r] = diag[i];
+    udinv[r] = 1.0f / diag[i];
+    udinv64[r] = 1.0 / (double)diag[i];
 }
 
 // b_r = -sum over mask neighbours j of A_ij uv_j;  x_r = uv of the row's vertex
@@ -119,9 +127,14 @@ __global__ void k_rhs_and_start(int nU, int V, const int* __restrict__ urow_vert
 }
 
 __global__ void k_scatter_solution(int nU, const int* __restrict__ urow_vertex, const double* __restrict__ x,
-                                   double* __restrict__ uv) {
+                                   double* __restrict__ uv, float2* __restrict__ uvf) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < nU) uv[urow_vertex[r]] = x[r];
+    if (r >= nU) return;
+    int i = urow_vertex[r];
+    double v = x[r];
+    uv[i] = v;
+    ff q = ff_from_double(v);
+    uvf[i] = make_float2(q.hi, q.lo);
 }
 
 fem_status build_system(fem_mesh* m, cudaStream_t s) {
@@ -146,19 +159,21 @@ fem_status build_system(fem_mesh* m, cudaStream_t s) {
     FEM_TRY(exclusive_scan_i32(m->flags.p, m->uidx.p, V, s, nU_dev));
     FEM_LAUNCH(F_ASSEMBLY, s, k_index_maps, vb, 256, 0, m->mask.p, V, m->uidx.p, m->kidx.p, m->urow_vertex.p,
                m->kvert.p);
-    int nU = 0;
-    FEM_CUDA(cudaMemcpyAsync(m->host_stage, nU_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FEM_CUDA(cudaStreamSynchronize(s));
-    nU = *(int*)m->host_stage;
+    // the mask count is kept on the host by create / import / refinement, so
+    // the unknown count needs no read-back
+    int nU = V - m->nK;
     m->nU = nU;
-    m->nK = V - nU;
     size_t n = nU > 0 ? nU : 1;
     FEM_TRY(ensure(m->ucol, 8 * n, s));
     FEM_TRY(ensure(m->uval32, 8 * n, s));
-    FEM_TRY(ensure(m->dinv32, n, s));  // holds the diagonal of A_UU
+    FEM_TRY(ensure(m->udiag, n, s));
+    FEM_TRY(ensure(m->ucnt, n, s));
+    FEM_TRY(ensure(m->dinv32, n, s));
+    FEM_TRY(ensure(m->dinv64, n, s));
     if (nU > 0)
         FEM_LAUNCH(F_ASSEMBLY, s, k_build_ell, (nU + 255) / 256, 256, 0, nU, V, m->urow_vertex.p, m->nbr.p,
-                   m->coefA.p, m->diagA.p, m->uidx.p, m->ucol.p, m->uval32.p, m->dinv32.p);
+                   m->coefA.p, m->diagA.p, m->uidx.p, m->ucol.p, m->uval32.p, m->udiag.p, m->ucnt.p, m->dinv32.p,
+                   m->dinv64.p);
     m->sys_version = m->mesh_version;
     return FEM_OK;
 }
@@ -166,9 +181,12 @@ fem_status build_system(fem_mesh* m, cudaStream_t s) {
 // ------------------------------------------------------------ device solve
 struct SolveArgs {
     int n;
-    const int* col;
-    const float* val;
-    const float* diag;
+    const int* col;       // 8*n ELL columns, slot-major
+    const float* val;     // 8*n ELL values (exact)
+    const int* cnt;       // n entries used per row
+    const float* diag;    // n diagonal (exact)
+    const float* dinv;    // n 1/diag (FP32)
+    const double* dinv64; // n 1/diag (FP64)
     const double* b;
     double* x;
     double* r64;
@@ -185,140 +203,270 @@ struct SolveArgs {
     double* red;       // 2 * 2 * gridDim partials
     unsigned* bar;
     int* err;
-    double* out;       // [0] iterations, [1] relres, [2] status
+    double* out;       // [0] iterations, [1] relres, [2] status, [3] FP64 residual passes
 };
 
-// block-wide sum of two doubles; result valid in all threads
-__device__ __forceinline__ void block_sum2(double& a, double& b) {
-    __shared__ double s_a[kSolveThreads / 32], s_b[kSolveThreads / 32];
+// Reductions are written for GB300's FP64 rate (about 2 FP64 FMAs per clock
+// per SM, 1/64 of FP32): FP32 partials are summed per warp in FP32 and only
+// the warp sums are combined in FP64; FP64 partials are combined through
+// shared memory by a single warp instead of a shuffle tree in every warp.
+template <int BT>
+__device__ __forceinline__ void block_sum2_f(float a, float b, double& ra, double& rb) {
+    __shared__ double wa[BT / 32], wb[BT / 32];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     a = warp_sum(a);
     b = warp_sum(b);
+    if (lane == 0) { wa[w] = (double)a; wb[w] = (double)b; }
     __syncthreads();
-    if (lane == 0) { s_a[w] = a; s_b[w] = b; }
-    __syncthreads();
-    double ta = 0.0, tb = 0.0;
-#pragma unroll
-    for (int i = 0; i < kSolveThreads / 32; ++i) { ta += s_a[i]; tb += s_b[i]; }
-    a = ta;
-    b = tb;
-}
-
-// grid-wide deterministic sum of two doubles (same result in every block).
-// `parity` alternates between calls so that slow readers are never overwritten.
-__device__ __forceinline__ bool grid_sum2(double& a, double& b, double* red, unsigned* bar, int* err, int& parity) {
-    block_sum2(a, b);
-    int nb = gridDim.x;
-    double* buf = red + (size_t)parity * 2 * nb;
-    if (threadIdx.x == 0) { buf[2 * blockIdx.x] = a; buf[2 * blockIdx.x + 1] = b; }
-    parity ^= 1;
-    if (!grid_barrier(bar, err)) return false;
-    double ta = 0.0, tb = 0.0;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        ta += __ldcg(&buf[2 * k]);
-        tb += __ldcg(&buf[2 * k + 1]);
+    if (w == 0) {
+        double ta = lane < BT / 32 ? wa[lane] : 0.0, tb = lane < BT / 32 ? wb[lane] : 0.0;
+        ta = warp_sum(ta);
+        tb = warp_sum(tb);
+        if (lane == 0) { wa[0] = ta; wb[0] = tb; }
     }
-    block_sum2(ta, tb);
-    a = ta;
-    b = tb;
-    return true;
+    __syncthreads();
+    ra = wa[0];
+    rb = wb[0];
+    __syncthreads();
 }
 
-// y = A_UU v for rows of this thread (grid-stride); returns sum of v_r * y_r
-template <class T>
-__device__ __forceinline__ double spmv_rows(const SolveArgs& A, const T* __restrict__ v, T* __restrict__ y) {
-    double dot = 0.0;
+template <int BT>
+__device__ __forceinline__ void block_sum2_d(double& a, double& b) {
+    __shared__ double sa[BT], sb[BT];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    if (w == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int i = lane; i < BT; i += 32) { ta += sa[i]; tb += sb[i]; }
+        ta = warp_sum(ta);
+        tb = warp_sum(tb);
+        if (lane == 0) { sa[0] = ta; sb[0] = tb; }
+    }
+    __syncthreads();
+    a = sa[0];
+    b = sb[0];
+    __syncthreads();
+}
+
+// Synchronisation policies.  GridSync: a cooperative grid of 256-thread
+// blocks with bounded device-wide barriers; data written by other blocks is
+// read through L2 (__ldcg) because L1 is not coherent across SMs.
+// BlockSync: one 1024-thread block; barriers are __syncthreads and plain
+// loads see the block's own writes.
+struct GridSync {
+    static constexpr int BT = kSolveThreads;
+    __device__ static bool barrier(const SolveArgs& A) { return grid_barrier(A.bar, A.err); }
+    // block sums -> per-block partials -> every block adds them in the same
+    // order; `parity` alternates buffers so that slow readers are never overwritten
+    __device__ static bool combine(double& a, double& b, const SolveArgs& A, int& parity) {
+        int nb = gridDim.x;
+        double* buf = A.red + (size_t)parity * 2 * nb;
+        if (threadIdx.x == 0) { buf[2 * blockIdx.x] = a; buf[2 * blockIdx.x + 1] = b; }
+        parity ^= 1;
+        if (!grid_barrier(A.bar, A.err)) return false;
+        double ta = 0.0, tb = 0.0;
+        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+            ta += __ldcg(&buf[2 * k]);
+            tb += __ldcg(&buf[2 * k + 1]);
+        }
+        block_sum2_d<BT>(ta, tb);
+        a = ta;
+        b = tb;
+        return true;
+    }
+    __device__ static bool sum2f(float a, float b, double& ra, double& rb, const SolveArgs& A, int& parity) {
+        block_sum2_f<BT>(a, b, ra, rb);
+        return combine(ra, rb, A, parity);
+    }
+    __device__ static bool sum2d(double& a, double& b, const SolveArgs& A, int& parity) {
+        block_sum2_d<BT>(a, b);
+        return combine(a, b, A, parity);
+    }
+    template <class T>
+    __device__ static T ld(const T* p) { return __ldcg(p); }
+};
+
+struct BlockSync {
+    static constexpr int BT = kSingleThreads;
+    __device__ static bool barrier(const SolveArgs&) {
+        __syncthreads();
+        return true;
+    }
+    __device__ static bool sum2f(float a, float b, double& ra, double& rb, const SolveArgs&, int&) {
+        block_sum2_f<BT>(a, b, ra, rb);
+        return true;
+    }
+    __device__ static bool sum2d(double& a, double& b, const SolveArgs&, int&) {
+        block_sum2_d<BT>(a, b);
+        return true;
+    }
+    template <class T>
+    __device__ static T ld(const T* p) { return *p; }
+};
+
+// y = A_UU v over this thread's rows; returns the thread's part of v.y
+template <class T, class S>
+__device__ __forceinline__ T spmv_rows(const SolveArgs& A, const T* __restrict__ v, T* __restrict__ y) {
+    T dot = 0;
     int n = A.n;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        T vr = __ldcg(&v[r]);
+        T vr = S::ld(&v[r]);
         T s = (T)A.diag[r] * vr;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            int c = A.col[k * n + r];
-            T w = (T)A.val[k * n + r];
-            s += w * __ldcg(&v[c]);
-        }
+        int c = A.cnt[r];
+        for (int k = 0; k < c; ++k) s += (T)A.val[k * n + r] * S::ld(&v[A.col[k * n + r]]);
         y[r] = s;
-        dot += (double)vr * (double)s;
+        dot += vr * s;
     }
     return dot;
 }
 
-// PCG on A d = rhs from d = d0 (in: d), precision T.  Stops when
-// ||r|| <= eta ||rhs||.  Returns false on a barrier failure.
-template <class T>
-__device__ bool pcg(const SolveArgs& A, const T* rhs, T* d, T* r, T* z, T* p, T* q, double eta, int maxit,
-                    int& iters, double& rr_out, double& bb_out, int& parity) {
+// FP32 Jacobi-PCG on A d = rhs from the start in d; stops when
+// ||r|| <= eta ||rhs|| or after maxit iterations.  FP32 arithmetic
+// throughout; only the scalars of the recurrences are kept in FP64.  Every
+// branch depends on grid-uniform values, so all blocks take the same path.
+template <class S>
+__device__ bool pcg32(const SolveArgs& A, const float* rhs, float* d, float* r, float* z, float* p, float* q,
+                      double eta, int maxit, int& iters, int& parity) {
     int n = A.n;
     int stride = gridDim.x * blockDim.x;
     int tid0 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (!grid_barrier(A.bar, A.err)) return false;  // d and rhs complete
-    spmv_rows<T>(A, d, q);
-    double rz = 0.0, bb = 0.0;
+    if (!S::barrier(A)) return false;  // d and rhs complete
+    spmv_rows<float, S>(A, d, q);
+    float rz_t = 0.f, rr_t = 0.f, bb_t = 0.f;
     for (int i = tid0; i < n; i += stride) {
-        T ri = rhs[i] - q[i];
+        float ri = rhs[i] - q[i];
         r[i] = ri;
-        T zi = ri / (T)A.diag[i];
+        float zi = ri * A.dinv[i];
         z[i] = zi;
         p[i] = zi;
-        rz += (double)ri * (double)zi;
-        double bi = (double)rhs[i];
-        bb += bi * bi;
+        rz_t += ri * zi;
+        rr_t += ri * ri;
+        bb_t += rhs[i] * rhs[i];
     }
-    if (!grid_sum2(rz, bb, A.red, A.bar, A.err, parity)) return false;
-    double rr = 0.0, dummy = 0.0;
-    for (int i = tid0; i < n; i += stride) rr += (double)r[i] * (double)r[i];
-    if (!grid_sum2(rr, dummy, A.red, A.bar, A.err, parity)) return false;
-    bb_out = bb;
-    double lim = eta * eta * bb;
+    double rz, rr, bb, dm;
+    if (!S::sum2f(rz_t, rr_t, rz, rr, A, parity)) return false;
+    if (!S::sum2f(bb_t, 0.f, bb, dm, A, parity)) return false;
+    // CG scalars in FP32: every thread computes them, and an FP64 division
+    // replicated over a block costs microseconds on GB300's FP64 pipe
+    float lim = (float)eta * (float)eta * (float)bb;
+    float rzf = (float)rz, rrf = (float)rr;
     iters = 0;
-    while (rr > lim && iters < maxit) {
-        double pq = spmv_rows<T>(A, p, q), dm = 0.0;
-        if (!grid_sum2(pq, dm, A.red, A.bar, A.err, parity)) return false;
-        if (!(pq > 0.0)) break;  // breakdown guard (exact solution or loss of SPD in rounding)
-        T alpha = (T)(rz / pq);
-        double rz1 = 0.0, rr1 = 0.0;
+    while (rrf > lim && iters < maxit) {
+        float pq_t = spmv_rows<float, S>(A, p, q);
+        double pq;
+        if (!S::sum2f(pq_t, 0.f, pq, dm, A, parity)) return false;
+        float pqf = (float)pq;
+        if (!(pqf > 0.f)) break;  // breakdown guard
+        float alpha = rzf / pqf;
+        float rz1_t = 0.f, rr1_t = 0.f;
         for (int i = tid0; i < n; i += stride) {
             d[i] += alpha * p[i];
-            T ri = r[i] - alpha * q[i];
+            float ri = r[i] - alpha * q[i];
             r[i] = ri;
-            T zi = ri / (T)A.diag[i];
+            float zi = ri * A.dinv[i];
             z[i] = zi;
-            rz1 += (double)ri * (double)zi;
-            rr1 += (double)ri * (double)ri;
+            rz1_t += ri * zi;
+            rr1_t += ri * ri;
         }
-        if (!grid_sum2(rz1, rr1, A.red, A.bar, A.err, parity)) return false;
+        double rz1;
+        if (!S::sum2f(rz1_t, rr1_t, rz1, rr, A, parity)) return false;
         iters++;
-        rr = rr1;
-        T beta = (T)(rz1 / rz);
-        rz = rz1;
+        float rz1f = (float)rz1;
+        rrf = (float)rr;
+        float beta = rz1f / rzf;
+        rzf = rz1f;
         for (int i = tid0; i < n; i += stride) p[i] = z[i] + beta * p[i];
-        if (!grid_barrier(A.bar, A.err)) return false;  // p complete before the next SpMV
+        if (!S::barrier(A)) return false;  // p complete before the next SpMV
     }
-    rr_out = rr;
     return true;
 }
 
-// FP64 residual r = b - A x; returns (||r||^2, ||b||^2) grid-wide
+// a scalar computed by thread 0 and broadcast (keeps FP64 divisions off the
+// other 1023 threads' FP64 pipe time)
+__device__ __forceinline__ double bcast_div(double num, double den) {
+    __shared__ double s_v;
+    if (threadIdx.x == 0) s_v = num / den;
+    __syncthreads();
+    double v = s_v;
+    __syncthreads();
+    return v;
+}
+
+// Plain FP64 Jacobi-PCG on A x = b from the start in x (the FP64 comparator).
+template <class S>
+__device__ bool pcg64(const SolveArgs& A, double eta, int maxit, int& iters, int& parity) {
+    int n = A.n;
+    int stride = gridDim.x * blockDim.x;
+    int tid0 = blockIdx.x * blockDim.x + threadIdx.x;
+    double *x = A.x, *r = A.r64, *z = A.z64, *p = A.p64, *q = A.q64;
+    if (!S::barrier(A)) return false;
+    spmv_rows<double, S>(A, x, q);
+    double rz = 0.0, rr = 0.0, bb = 0.0, dm = 0.0;
+    for (int i = tid0; i < n; i += stride) {
+        double ri = A.b[i] - q[i];
+        r[i] = ri;
+        double zi = ri * A.dinv64[i];
+        z[i] = zi;
+        p[i] = zi;
+        rz += ri * zi;
+        rr += ri * ri;
+        bb += A.b[i] * A.b[i];
+    }
+    if (!S::sum2d(rz, rr, A, parity)) return false;
+    if (!S::sum2d(bb, dm, A, parity)) return false;
+    double lim = eta * eta * bb;
+    iters = 0;
+    while (rr > lim && iters < maxit) {
+        double pq = spmv_rows<double, S>(A, p, q);
+        dm = 0.0;
+        if (!S::sum2d(pq, dm, A, parity)) return false;
+        if (!(pq > 0.0)) break;
+        double alpha = bcast_div(rz, pq);
+        double rz1 = 0.0, rr1 = 0.0;
+        for (int i = tid0; i < n; i += stride) {
+            x[i] += alpha * p[i];
+            double ri = r[i] - alpha * q[i];
+            r[i] = ri;
+            double zi = ri * A.dinv64[i];
+            z[i] = zi;
+            rz1 += ri * zi;
+            rr1 += ri * ri;
+        }
+        if (!S::sum2d(rz1, rr1, A, parity)) return false;
+        iters++;
+        rr = rr1;
+        double beta = bcast_div(rz1, rz);
+        rz = rz1;
+        for (int i = tid0; i < n; i += stride) p[i] = z[i] + beta * p[i];
+        if (!S::barrier(A)) return false;
+    }
+    return true;
+}
+
+// FP64 residual r = b - A x over the used entries of each row; returns
+// (||r||^2, ||b||^2) grid-wide
+template <class S>
 __device__ bool residual64(const SolveArgs& A, double& rr, double& bb, int& parity) {
-    if (!grid_barrier(A.bar, A.err)) return false;  // x complete
+    if (!S::barrier(A)) return false;  // x complete
     int n = A.n;
     rr = 0.0;
     bb = 0.0;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        double s = (double)A.diag[r] * __ldcg(&A.x[r]);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) s += (double)A.val[k * n + r] * __ldcg(&A.x[A.col[k * n + r]]);
+        double s = (double)A.diag[r] * S::ld(&A.x[r]);
+        int c = A.cnt[r];
+        for (int k = 0; k < c; ++k) s += (double)A.val[k * n + r] * S::ld(&A.x[A.col[k * n + r]]);
         double ri = A.b[r] - s;
         A.r64[r] = ri;
         rr += ri * ri;
         bb += A.b[r] * A.b[r];
     }
-    return grid_sum2(rr, bb, A.red, A.bar, A.err, parity);
+    return S::sum2d(rr, bb, A, parity);
 }
 
-template <bool FP64_ONLY>
-__global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs A) {
+template <bool FP64_ONLY, class S>
+__device__ __forceinline__ void solve_body(const SolveArgs& A) {
     int parity = 0;
     int n = A.n;
     int stride = gridDim.x * blockDim.x;
@@ -326,7 +474,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs A) {
     int total_it = 0, n_res = 1;
     double rr = 0.0, bb = 0.0;
     int status = FEM_E_NOT_CONVERGED;
-    if (!residual64(A, rr, bb, parity)) goto fail;
+    if (!residual64<S>(A, rr, bb, parity)) goto fail;
     if (bb == 0.0) {
         for (int i = tid0; i < n; i += stride) A.x[i] = 0.0;
         rr = 0.0;
@@ -337,36 +485,34 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs A) {
         for (int attempt = 0; attempt < 4; ++attempt) {
             if (rr <= A.tol * A.tol * bb) { status = FEM_OK; break; }
             if (total_it >= A.maxit) break;
-            // solve A x = b from the current x: d = x, rhs = b
             int it = 0;
-            double rr_in = 0.0, bb_in = 0.0;
-            if (!pcg<double>(A, A.b, A.x, A.r64, A.z64, A.p64, A.q64, A.tol, A.maxit - total_it, it, rr_in, bb_in,
-                             parity))
-                goto fail;
+            if (!pcg64<S>(A, A.tol, A.maxit - total_it, it, parity)) goto fail;
             total_it += it;
             n_res++;
-            if (!residual64(A, rr, bb, parity)) goto fail;
+            if (!residual64<S>(A, rr, bb, parity)) goto fail;
         }
         if (rr <= A.tol * A.tol * bb) status = FEM_OK;
     } else {
         for (int step = 0; step < 64; ++step) {
             if (rr <= A.tol * A.tol * bb) { status = FEM_OK; break; }
             if (total_it >= A.maxit) break;
-            double scale = 1.0 / sqrt(rr);
+            // normalise the residual; any scale works as long as the step is
+            // scaled back by its inverse (FP32 scalars, see pcg32)
+            float sc = rsqrtf((float)rr), back = 1.0f / sc;
             for (int i = tid0; i < n; i += stride) {
-                A.r32[i] = (float)(A.r64[i] * scale);
+                A.r32[i] = (float)A.r64[i] * sc;
                 A.d32[i] = 0.0f;
             }
             int it = 0;
-            double rr_in = 0.0, bb_in = 0.0;
-            if (!pcg<float>(A, A.r32, A.d32, A.z32 /*r*/, A.q32 /*z*/, A.p32, A.q32 + n /*q*/, kInnerEta,
-                            A.maxit - total_it, it, rr_in, bb_in, parity))
+            int cap = A.maxit - total_it;
+            if (cap > kInnerCap) cap = kInnerCap;
+            if (!pcg32<S>(A, A.r32, A.d32, A.z32 /*r*/, A.q32 /*z*/, A.p32, A.q32 + n /*q*/, kInnerEta, cap, it,
+                          parity))
                 goto fail;
             total_it += it;
-            double back = sqrt(rr);
-            for (int i = tid0; i < n; i += stride) A.x[i] += back * (double)A.d32[i];
+            for (int i = tid0; i < n; i += stride) A.x[i] += (double)(back * A.d32[i]);
             n_res++;
-            if (!residual64(A, rr, bb, parity)) goto fail;
+            if (!residual64<S>(A, rr, bb, parity)) goto fail;
         }
         if (rr <= A.tol * A.tol * bb) status = FEM_OK;
     }
@@ -383,6 +529,234 @@ fail:
         A.out[0] = total_it;
         A.out[1] = -1.0;
         A.out[2] = FEM_E_TIMEOUT;
+        A.out[3] = n_res;
+    }
+}
+
+template <bool FP64_ONLY>
+__global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs A) {
+    solve_body<FP64_ONLY, GridSync>(A);
+}
+
+template <bool FP64_ONLY>
+__global__ void __launch_bounds__(kSingleThreads) k_solve_single(SolveArgs A) {
+    solve_body<FP64_ONLY, BlockSync>(A);
+}
+
+// ---------------------------------------------------------------------------
+// One-block FP32-IR solve for up to kBlockMaxRows unknowns, with no FP64
+// arithmetic in its loops:
+//  * A_UU's off-diagonal entries are -1/2 or -1 and its diagonal a multiple
+//    of 1/2 up to 8: the kernel builds a CSR copy in shared memory with
+//    16-bit entries ((column << 1) | (entry == -1)) and the diagonal as a
+//    byte (twice its value; 1/diag from a 17-entry table);
+//  * x and b are float-float (about 48 bits), scaled by an exact power of
+//    two so that max |b| is about 1 and FP32 squares of 1e-12 residuals stay
+//    normal; the refinement residual b - A x is computed in float-float;
+//  * the inner CG is FP32 with two block barriers per iteration: each
+//    reduction is one barrier over double-buffered warp slots, and the search
+//    direction p_new = D^{-1} r + beta p_old is formed inside the next SpMV
+//    (at neighbours on the fly, p double-buffered).
+// The five CG vectors and the CSR copy live in shared memory when they fit
+// (about 8k unknowns at 1.7 entries per row); otherwise the same code runs on
+// global buffers (generic pointers), decided on the device.
+constexpr int kBlockMaxRows = 16384;
+constexpr int kBlockSmemBytes = 200 * 1024;
+
+struct BlockRed {
+    float4 slot[2][kSingleThreads / 32];
+};
+
+// sums of up to three floats over the block with one barrier: warps reduce
+// by shuffles, lane 0 writes the warp sums to the current slot buffer, and
+// after the barrier every warp reduces the 32 warp sums again by shuffles and
+// takes lane 0's value, so all threads see the same bits
+__device__ __forceinline__ float3 block_sum3(BlockRed& R, int& par, float a, float b, float c) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    if (lane == 0) R.slot[par][w] = make_float4(a, b, c, 0.f);
+    __syncthreads();
+    float4 v = R.slot[par][lane];
+    float sa = warp_sum(v.x), sb = warp_sum(v.y), sc = warp_sum(v.z);
+    sa = __shfl_sync(0xffffffffu, sa, 0);
+    sb = __shfl_sync(0xffffffffu, sb, 0);
+    sc = __shfl_sync(0xffffffffu, sc, 0);
+    par ^= 1;
+    return make_float3(sa, sb, sc);
+}
+
+__device__ __forceinline__ float ent_val(unsigned short e) { return (e & 1u) ? -1.0f : -0.5f; }
+
+struct BlockScratch {
+    float* vec;             // 5 n floats (global fallback)
+    int* rowptr;            // n + 1 (global fallback)
+    unsigned short* ent;    // 8 n (global fallback)
+    unsigned char* dg2;     // n (global fallback)
+    float2* xff;            // n float-float iterate
+    float2* bff;            // n float-float right-hand side
+};
+
+__global__ void __launch_bounds__(kSingleThreads) k_solve_block(SolveArgs A, BlockScratch G, int smem_bytes) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ BlockRed R;
+    __shared__ float s_lut[17];
+    __shared__ int s_wsum[kSingleThreads / 32];
+    __shared__ float s_bmax[kSingleThreads / 32];
+    const int n = A.n, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid < 17) s_lut[tid] = tid ? 1.0f / (0.5f * (float)tid) : 0.0f;
+    // number of off-diagonal entries, and max |b|
+    int cnt_t = 0;
+    float bm = 0.f;
+    for (int i = tid; i < n; i += kSingleThreads) {
+        cnt_t += A.cnt[i];
+        bm = fmaxf(bm, fabsf((float)A.b[i]));
+    }
+    cnt_t = warp_sum(cnt_t);
+    for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+    if (lane == 0) { s_wsum[wid] = cnt_t; s_bmax[wid] = bm; }
+    __syncthreads();
+    int nnz = 0;
+    bm = 0.f;
+    for (int i = 0; i < kSingleThreads / 32; ++i) { nnz += s_wsum[i]; bm = fmaxf(bm, s_bmax[i]); }
+    // layout: floats (5n) | int rowptr (n+1) | u16 entries (nnz) | u8 diag (n)
+    size_t need = (size_t)20 * n + (size_t)4 * (n + 1) + (size_t)2 * nnz + (size_t)n;
+    bool in_smem = need <= (size_t)smem_bytes;
+    float* fv = in_smem ? (float*)sm_raw : G.vec;
+    int* rowptr = in_smem ? (int*)(sm_raw + (size_t)20 * n) : G.rowptr;
+    unsigned short* ent = in_smem ? (unsigned short*)(sm_raw + (size_t)24 * n + 4) : G.ent;
+    unsigned char* dg2 = in_smem ? (sm_raw + (size_t)24 * n + 4 + (size_t)2 * nnz) : G.dg2;
+    float *d = fv, *r = fv + n, *p0 = fv + 2 * n, *p1 = fv + 3 * n, *q = fv + 4 * n;
+    // CSR row starts: contiguous chunks per thread, block exclusive scan
+    int chunk = (n + kSingleThreads - 1) / kSingleThreads;
+    int lo = tid * chunk, hi = min(n, lo + chunk), loc = 0;
+    for (int i = lo; i < hi; ++i) loc += A.cnt[i];
+    int incl = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) s_wsum[wid] = incl;
+    __syncthreads();
+    int wbase = 0;
+    for (int i = 0; i < wid; ++i) wbase += s_wsum[i];
+    int run = wbase + incl - loc;
+    for (int i = lo; i < hi; ++i) {
+        rowptr[i] = run;
+        int c = A.cnt[i];
+        for (int k = 0; k < c; ++k)
+            ent[run + k] = (unsigned short)((A.col[k * n + i] << 1) | (A.val[k * n + i] == -1.0f ? 1 : 0));
+        dg2[i] = (unsigned char)(2.0f * A.diag[i]);
+        run += c;
+    }
+    if (tid == kSingleThreads - 1) rowptr[n] = nnz;
+    int total_it = 0, n_res = 0, status = FEM_E_NOT_CONVERGED, par = 0;
+    float rr = 0.f, bb = 0.f;
+    if (bm == 0.f) {
+        for (int i = tid; i < n; i += kSingleThreads) A.x[i] = 0.0;
+        status = FEM_OK;
+    } else {
+        // exact power-of-two normalisation: max |b| in [1, 2)
+        int e = ilogbf(bm);
+        float sigma = ldexpf(1.0f, -e);
+        double inv_sigma = ldexp(1.0, e);
+        for (int i = tid; i < n; i += kSingleThreads) {
+            ff bi = ff_scale_pow2(ff_from_double(A.b[i]), sigma);
+            ff xi = ff_scale_pow2(ff_from_double(A.x[i]), sigma);
+            G.bff[i] = make_float2(bi.hi, bi.lo);
+            G.xff[i] = make_float2(xi.hi, xi.lo);
+        }
+        __syncthreads();
+        float tol2 = (float)(A.tol * A.tol);
+        for (int step = 0; step < 64; ++step) {
+            // refinement residual r = b - A x in float-float, rounded to FP32
+            float rr_t = 0.f, bb_t = 0.f, rz_t = 0.f;
+            for (int i = tid; i < n; i += kSingleThreads) {
+                float2 xv = G.xff[i];
+                int dd = dg2[i];
+                ff s = ff_mul_f(ff{xv.x, xv.y}, 0.5f * (float)dd);
+                for (int k = rowptr[i], k1 = rowptr[i + 1]; k < k1; ++k) {
+                    unsigned short en = ent[k];
+                    float2 xc = G.xff[en >> 1];
+                    s = ff_add(s, ff_scale_pow2(ff{xc.x, xc.y}, ent_val(en)));
+                }
+                float2 bv = G.bff[i];
+                ff res = ff_sub(ff{bv.x, bv.y}, s);
+                float ri = __fadd_rn(res.hi, res.lo);
+                r[i] = ri;
+                d[i] = 0.f;
+                p0[i] = 0.f;
+                rr_t += ri * ri;
+                rz_t += ri * ri * s_lut[dd];
+                bb_t += bv.x * bv.x;
+            }
+            float3 red = block_sum3(R, par, rr_t, bb_t, rz_t);
+            n_res++;
+            rr = red.x;
+            bb = red.y;
+            if (rr <= tol2 * bb) { status = FEM_OK; break; }
+            if (total_it >= A.maxit) break;
+            // FP32 PCG on A d = r from d = 0; p_old = p0 = 0, beta = 0
+            float rz = red.z, rr_in = rr, lim = (float)(kInnerEta * kInnerEta) * rr, beta = 0.f;
+            int cap = A.maxit - total_it;
+            if (cap > kInnerCap) cap = kInnerCap;
+            int it = 0;
+            float *pold = p0, *pnew = p1;
+            while (rr_in > lim && it < cap) {
+                // p_new = D^-1 r + beta p_old and q = A p_new (neighbours on the fly)
+                float pq_t = 0.f;
+                for (int i = tid; i < n; i += kSingleThreads) {
+                    int dd = dg2[i];
+                    float pi = fmaf(beta, pold[i], s_lut[dd] * r[i]);
+                    pnew[i] = pi;
+                    float sacc = 0.5f * (float)dd * pi;
+                    for (int k = rowptr[i], k1 = rowptr[i + 1]; k < k1; ++k) {
+                        unsigned short en = ent[k];
+                        int col = en >> 1;
+                        sacc = fmaf(ent_val(en), fmaf(beta, pold[col], s_lut[dg2[col]] * r[col]), sacc);
+                    }
+                    q[i] = sacc;
+                    pq_t += pi * sacc;
+                }
+                float pq = block_sum3(R, par, pq_t, 0.f, 0.f).x;
+                if (!(pq > 0.f)) break;  // breakdown guard (uniform over the block)
+                float alpha = rz / pq;
+                float rz_t2 = 0.f, rr_t2 = 0.f;
+                for (int i = tid; i < n; i += kSingleThreads) {
+                    d[i] = fmaf(alpha, pnew[i], d[i]);
+                    float ri = fmaf(-alpha, q[i], r[i]);
+                    r[i] = ri;
+                    rz_t2 += ri * ri * s_lut[dg2[i]];
+                    rr_t2 += ri * ri;
+                }
+                float3 s2 = block_sum3(R, par, rz_t2, rr_t2, 0.f);
+                it++;
+                beta = s2.x / rz;
+                rz = s2.x;
+                rr_in = s2.y;
+                float* t = pold;
+                pold = pnew;
+                pnew = t;
+            }
+            total_it += it;
+            for (int i = tid; i < n; i += kSingleThreads) {
+                float2 xv = G.xff[i];
+                ff xi = ff_add_f(ff{xv.x, xv.y}, d[i]);
+                G.xff[i] = make_float2(xi.hi, xi.lo);
+            }
+            __syncthreads();
+        }
+        for (int i = tid; i < n; i += kSingleThreads) {
+            float2 xv = G.xff[i];
+            A.x[i] = ff_to_double(ff{xv.x, xv.y}) * inv_sigma;
+        }
+    }
+    if (tid == 0) {
+        A.out[0] = total_it;
+        A.out[1] = bb > 0.f ? sqrt((double)rr / (double)bb) : 0.0;
+        A.out[2] = status;
         A.out[3] = n_res;
     }
 }
@@ -422,14 +796,18 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
         FEM_TRY(ensure(m->z32, n, s));
         FEM_TRY(ensure(m->d32, n, s));
     }
+    bool single = nU <= kSingleMaxRows;
     const void* func = use_fp64 ? (const void*)k_solve<true> : (const void*)k_solve<false>;
-    int grid = coop_blocks(func, nU, m->num_sms);
+    int grid = single ? 1 : coop_blocks(func, nU, m->num_sms);
     FEM_TRY(ensure(m->red, (size_t)4 * grid + 8, s));
     SolveArgs A;
     A.n = nU;
     A.col = m->ucol.p;
     A.val = m->uval32.p;
-    A.diag = m->dinv32.p;
+    A.cnt = m->ucnt.p;
+    A.diag = m->udiag.p;
+    A.dinv = m->dinv32.p;
+    A.dinv64 = m->dinv64.p;
     A.b = b;
     A.x = x;
     A.r64 = m->r64.p;
@@ -442,8 +820,31 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
     A.err = m->dflag.p + 1;
     A.out = m->dscal.p;
     FEM_CUDA(cudaMemsetAsync(m->dflag.p + 1, 0, sizeof(int), s));
-    void* args[] = {&A};
-    FEM_TRY(launch_coop(F_CG, func, grid, kSolveThreads, 0, s, args, use_fp64 ? "k_solve<fp64>" : "k_solve<fp32ir>"));
+    if (!use_fp64 && nU <= kBlockMaxRows) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            FEM_CUDA(cudaFuncSetAttribute(k_solve_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kBlockSmemBytes));
+            attr_set = true;
+        }
+        FEM_TRY(ensure(m->bvec, (size_t)5 * nU, s));
+        FEM_TRY(ensure(m->browptr, (size_t)nU + 1, s));
+        FEM_TRY(ensure(m->bent, (size_t)8 * nU, s));
+        FEM_TRY(ensure(m->bdg2, (size_t)nU, s));
+        FEM_TRY(ensure(m->bxff, (size_t)nU, s));
+        FEM_TRY(ensure(m->bbff, (size_t)nU, s));
+        BlockScratch G{m->bvec.p, m->browptr.p, m->bent.p, m->bdg2.p, m->bxff.p, m->bbff.p};
+        FEM_LAUNCH(F_CG, s, k_solve_block, 1, kSingleThreads, (size_t)kBlockSmemBytes, A, G, kBlockSmemBytes);
+    } else if (single) {
+        if (use_fp64)
+            FEM_LAUNCH(F_CG, s, k_solve_single<true>, 1, kSingleThreads, 0, A);
+        else
+            FEM_LAUNCH(F_CG, s, k_solve_single<false>, 1, kSingleThreads, 0, A);
+    } else {
+        void* args[] = {&A};
+        FEM_TRY(launch_coop(F_CG, func, grid, kSolveThreads, 0, s, args,
+                            use_fp64 ? "k_solve<fp64>" : "k_solve<fp32ir>"));
+    }
     double* hs = (double*)m->host_stage;
     FEM_CUDA(cudaMemcpyAsync(hs, m->dscal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));
@@ -491,7 +892,7 @@ fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cuda
                m->uv.p, m->b64.p, m->x64.p);
     fem_status st = run_solve(m, m->b64.p, m->x64.p, use_fp64, tol, maxit, s, iters_out, relres_out);
     if (st != FEM_OK && st != FEM_E_NOT_CONVERGED) return st;
-    FEM_LAUNCH(F_CG, s, k_scatter_solution, b, 256, 0, nU, m->urow_vertex.p, m->x64.p, m->uv.p);
+    FEM_LAUNCH(F_CG, s, k_scatter_solution, b, 256, 0, nU, m->urow_vertex.p, m->x64.p, m->uv.p, m->uvf.p);
     return st;
 }
 
@@ -503,11 +904,13 @@ __global__ void k_uv_from_g(const unsigned char* __restrict__ mask, const int* _
 }
 
 __global__ void k_uv_from_f(const unsigned char* __restrict__ mask, const int2* __restrict__ vxy, int V, int N,
-                            const float* __restrict__ f, double* __restrict__ uv) {
+                            const float* __restrict__ f, double* __restrict__ uv, float2* __restrict__ uvf) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < V && mask[i]) {
         int2 p = vxy[i];
-        uv[i] = (double)f[(long long)p.y * N + p.x];
+        float v = f[(long long)p.y * N + p.x];
+        uv[i] = (double)v;
+        uvf[i] = make_float2(v, 0.0f);
     }
 }
 
@@ -526,7 +929,8 @@ fem_status set_uv_from_g(fem_mesh* m, const float* g_dev, cudaStream_t s) {
 }
 
 fem_status set_uv_from_f(fem_mesh* m, const float* f_dev, cudaStream_t s) {
-    FEM_LAUNCH(F_OTHER, s, k_uv_from_f, (m->V + 255) / 256, 256, 0, m->mask.p, m->vxy.p, m->V, m->N, f_dev, m->uv.p);
+    FEM_LAUNCH(F_OTHER, s, k_uv_from_f, (m->V + 255) / 256, 256, 0, m->mask.p, m->vxy.p, m->V, m->N, f_dev, m->uv.p,
+               m->uvf.p);
     return FEM_OK;
 }
 
