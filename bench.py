@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check after timing")
     ap.add_argument("--ncu-step", action="store_true",
                     help="for ncu launch lists: one warm-up step, then exactly one step, no timing output")
+    ap.add_argument("--solve-micro", action="store_true",
+                    help="time the Laplace solve alone on the refined mesh (FP32-IR and FP64), 20 solves each")
     return ap.parse_args()
 
 
@@ -192,6 +194,10 @@ def run_ours(a, world, rank, local):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
+    if a.solve_micro:
+        print(json.dumps(solve_micro(fem, torch, f, n, a)), flush=True)
+        return
+
     if a.ncu_step:
         step(f)
         torch.cuda.synchronize(dev)
@@ -310,6 +316,35 @@ def run_ours(a, world, rank, local):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def solve_micro(fem, torch, f, n, a):
+    """Laplace solves on the mesh of the spatial optimisation, with g = f at
+    the mask perturbed each call so that every solve iterates from the
+    previous solution.  Wall time per fem_inpaint call (host timer, includes
+    the launch and the result read-back) and CG iterations."""
+    import numpy as np
+    mesh = fem.Mesh(n)
+    mesh.spatial_refine(f, a.density, fem.params(topk_frac=a.frac))
+    g = mesh.g_from_f(f)
+    out = {"nU": mesh.V - mesh.nmask, "V": mesh.V}
+    for name, prec in (("fp32ir", fem.FEM_PREC_FP32_IR), ("fp64", fem.FEM_PREC_FP64)):
+        p = fem.params(precision=prec)
+        for _ in range(3):
+            fem.fem_inpaint(mesh.h, g, None, None, p)
+        times, its = [], []
+        idx = torch.arange(g.numel(), device=g.device, dtype=torch.float32)
+        for k in range(20):
+            gg = (g + 1e-3 * torch.sin(idx * (k + 1))).contiguous()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fem.fem_inpaint(mesh.h, gg, None, None, p)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            its.append(mesh.stats()["cg_iters"])
+        out[name] = {"ms_per_solve": round(1e3 * float(np.median(times)), 4), "cg_iters": float(np.median(its))}
+    mesh.close()
+    return out
 
 
 # ------------------------------------------------------- the oracle on CPU

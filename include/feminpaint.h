@@ -77,7 +77,7 @@ typedef struct {
     int rounds;            /* spatial: refinement rounds run */
     long long cg_iters;    /* CG iterations, all solves of the call */
     int solves;            /* Laplace solves run */
-    double relres;         /* last Laplace solve's FP64 relative residual */
+    double relres;         /* largest FP64 relative residual among the call's Laplace solves */
     int tonal_iters;       /* tonal: outer iterations */
     double tonal_relres;   /* tonal: ||B^T r|| / ||B^T f|| at exit */
     double min_margin;     /* spatial: smallest relative gap between the k-th and (k+1)-th key */

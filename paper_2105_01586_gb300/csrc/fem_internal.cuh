@@ -217,6 +217,10 @@ struct fem_mesh {
     fem::DArr<unsigned short> bent;
     fem::DArr<unsigned char> bdg2;
     fem::DArr<float2> bxff, bbff;       // float-float iterate and right-hand side
+    fem::DArr<unsigned long long> scan_status;  // look-back scan tile status words
+    fem::DArr<unsigned long long> scan_ctr;     // look-back scan tile counter
+    unsigned long long scan_tiles_issued = 0;
+    unsigned scan_epoch = 0;
     fem::DArr<double> red;          // grid-reduction partials
     fem::DArr<unsigned> bar;        // grid barrier words
     fem::DArr<int> dflag;           // device status/flags
@@ -240,11 +244,14 @@ struct fem_mesh {
 namespace fem {
 // helpers implemented in the .cu files
 fem_status exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, int* total_dev);
+fem_status scan_i32(fem_mesh* m, const int* in, int* out, int n, cudaStream_t s, int* total_dev);
 fem_status build_system(fem_mesh* m, cudaStream_t s);
 fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cudaStream_t s,
-                         int* iters_out, double* relres_out);
+                         int* iters_out, double* relres_out, bool deferred = false);
 fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, double tol, int maxit, cudaStream_t s,
-                     int* iters_out, double* relres_out);
+                     int* iters_out, double* relres_out, bool deferred = false);
+fem_status solve_totals_reset(fem_mesh* m, cudaStream_t s);
+fem_status solve_totals_read(fem_mesh* m, cudaStream_t s);
 fem_status set_uv_from_g(fem_mesh* m, const float* g_dev, cudaStream_t s);
 fem_status set_uv_from_f(fem_mesh* m, const float* f_dev, cudaStream_t s);
 fem_status raster_plan(fem_mesh* m, cudaStream_t s);

@@ -177,6 +177,102 @@ __global__ void k_scan_total(const int* in, const int* out, int n, int* total) {
     *total = n > 0 ? out[n - 1] + in[n - 1] : 0;
 }
 
+// Single-launch exclusive scan (decoupled look-back).  Tiles take their
+// index from an atomic counter in the order they start, so every tile's
+// predecessors are running or finished and a tile only ever waits on them.
+// Each tile publishes its aggregate, then its inclusive prefix, in a 64-bit
+// status word (epoch | flag | value) written with release semantics; the
+// epoch changes every call, so status words never need clearing.  Waits are
+// bounded: after kLookbackLimitNs the tile records FEM_E_TIMEOUT and stops.
+constexpr unsigned long long kLookbackLimitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long pack_status(unsigned epoch, unsigned flag, int value) {
+    return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | (unsigned)value;
+}
+
+__global__ void k_scan_lookback(const int* __restrict__ in, int* __restrict__ out, int n, int* __restrict__ total,
+                                unsigned long long* __restrict__ status, unsigned long long* __restrict__ ctr,
+                                unsigned long long base, unsigned epoch, int* __restrict__ err) {
+    __shared__ int s_tile, s_prefix;
+    if (threadIdx.x == 0) s_tile = (int)(atomicAdd(ctr, 1ull) - base);
+    __syncthreads();
+    int tile = s_tile;
+    int v[SCAN_IPT];
+    long long first = (long long)tile * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
+#pragma unroll
+    for (int i = 0; i < SCAN_IPT; ++i) v[i] = (first + i < n) ? in[first + i] : 0;
+    int agg = block_exclusive_scan(v);
+    if (threadIdx.x == 0) {
+        int prefix = 0;
+        if (tile == 0) {
+            st_release_u64(&status[0], pack_status(epoch, 2, agg));
+        } else {
+            st_release_u64(&status[tile], pack_status(epoch, 1, agg));
+            int p = tile - 1;
+            unsigned long long t0 = globaltimer_ns();
+            while (p >= 0) {
+                unsigned long long w = ld_acquire_u64(&status[p]);
+                unsigned ep = (unsigned)(w >> 34), flag = (unsigned)(w >> 32) & 3u;
+                if (ep != epoch || flag == 0) {
+                    if (globaltimer_ns() - t0 > kLookbackLimitNs) {
+                        atomicCAS(err, 0, (int)FEM_E_TIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                prefix += (int)(unsigned)w;
+                if (flag == 2) break;
+                --p;
+            }
+            st_release_u64(&status[tile], pack_status(epoch, 2, prefix + agg));
+        }
+        s_prefix = prefix;
+        if ((long long)(tile + 1) * SCAN_TILE >= n && total) *total = prefix + agg;
+    }
+    __syncthreads();
+    int pre = s_prefix;
+#pragma unroll
+    for (int i = 0; i < SCAN_IPT; ++i)
+        if (first + i < n) out[first + i] = v[i] + pre;
+}
+
+static std::mutex g_scan_mu;
+
+// out[i] = sum of in[0..i-1]; *total_dev (if non-null) = sum of all (one launch)
+fem_status scan_i32(fem_mesh* m, const int* in, int* out, int n, cudaStream_t s, int* total_dev) {
+    if (n <= 0) {
+        if (total_dev) FEM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int), s));
+        return FEM_OK;
+    }
+    int tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    unsigned long long* before = m->scan_status.p;
+    FEM_TRY(ensure(m->scan_status, (size_t)tiles, s));
+    if (m->scan_status.p != before)  // fresh memory: no word may look like one of this call's epoch
+        FEM_CUDA(cudaMemsetAsync(m->scan_status.p, 0, sizeof(unsigned long long) * m->scan_status.n, s));
+    if (!m->scan_ctr.p) {
+        FEM_TRY(ensure(m->scan_ctr, 1, s));
+        FEM_CUDA(cudaMemsetAsync(m->scan_ctr.p, 0, sizeof(unsigned long long), s));
+        m->scan_tiles_issued = 0;
+    }
+    unsigned long long base = m->scan_tiles_issued;
+    m->scan_tiles_issued += (unsigned long long)tiles;
+    unsigned epoch = (unsigned)(++m->scan_epoch & ((1u << 30) - 1));
+    if (epoch == 0) epoch = (unsigned)(++m->scan_epoch & ((1u << 30) - 1));
+    FEM_LAUNCH(F_OTHER, s, k_scan_lookback, tiles, SCAN_BT, 0, in, out, n, total_dev, m->scan_status.p,
+               m->scan_ctr.p, base, epoch, m->dflag.p + 8);
+    return FEM_OK;
+}
+
 // out[i] = sum of in[0..i-1]; *total_dev (if non-null) = sum of all.  out may alias in? no.
 fem_status exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, int* total_dev) {
     if (n <= 0) {
@@ -398,6 +494,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->r32, s); release(m->p32, s); release(m->q32, s); release(m->z32, s); release(m->d32, s);
     release(m->bvec, s); release(m->browptr, s); release(m->bent, s); release(m->bdg2, s);
     release(m->bxff, s); release(m->bbff, s);
+    release(m->scan_status, s); release(m->scan_ctr, s);
     release(m->red, s); release(m->bar, s); release(m->dflag, s); release(m->dscal, s); release(m->dcount, s);
     release(m->inc, s); release(m->loc, s); release(m->Moff, s); release(m->Mdiag, s);
     release(m->tv, s); release(m->ty, s); release(m->tz, s); release(m->tg, s);

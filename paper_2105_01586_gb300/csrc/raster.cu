@@ -289,7 +289,7 @@ fem_status raster_plan(fem_mesh* m, cudaStream_t s) {
     FEM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     int blocks = (T + 255) / 256;
     FEM_LAUNCH(F_RASTER, s, k_item_count, blocks, 256, 0, m->tri.p, m->vxy.p, T, m->N, m->item_cnt.p);
-    FEM_TRY(exclusive_scan_i32(m->item_cnt.p, m->item_off.p, T, s, n_items_dev));
+    FEM_TRY(scan_i32(m, m->item_cnt.p, m->item_off.p, T, s, n_items_dev));
     FEM_LAUNCH(F_RASTER, s, k_item_expand, blocks, 256, 0, m->item_cnt.p, m->item_off.p, T, (int)m->item_tri.n,
                m->item_tri.p, err);
     m->plan_version = m->mesh_version;

@@ -495,20 +495,21 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
     }
     int Wi = (int)W;
     FEM_LAUNCH(F_REFINE, s, k_word_popc, (Wi + 255) / 256, 256, 0, m->bmM.p, Wi, m->wcnt.p);
-    FEM_TRY(exclusive_scan_i32(m->wcnt.p, (int*)m->wpre.p, Wi, s, nnew));
+    FEM_TRY(scan_i32(m, m->wcnt.p, (int*)m->wpre.p, Wi, s, nnew));
     FEM_LAUNCH(F_REFINE, s, k_new_vertices, (Wi + 255) / 256, 256, 0, m->bmM.p, m->bmS.p, (const int*)m->wpre.p, Wi,
                N, V, m->vxy.p, m->mask.p, nmask_new);
     FEM_LAUNCH(F_REFINE, s, k_bisect_flags, tb, 256, 0, m->tri.p, m->vxy.p, T, N, m->bmM.p, m->flags.p);
-    FEM_TRY(exclusive_scan_i32(m->flags.p, m->fscan.p, 3 * T, s, ntri));
+    FEM_TRY(scan_i32(m, m->flags.p, m->fscan.p, 3 * T, s, ntri));
     FEM_LAUNCH(F_REFINE, s, k_bisect, tb, 256, 0, m->tri.p, m->vxy.p, T, N, m->bmM.p, (const int*)m->wpre.p, V,
                m->flags.p, m->fscan.p, m->uv.p);
     // read back k, sweeps, new counts, margin, error
     int* hs = (int*)m->host_stage;
     FEM_CUDA(cudaMemcpyAsync(hs, m->dcount.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaMemcpyAsync(hs + 8, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaMemcpyAsync(hs + 9, m->dflag.p + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaMemcpyAsync((double*)(hs + 16), margin, sizeof(double), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));
-    int k = hs[2], nn = hs[4], nt = hs[5], nkm = hs[6], e = hs[8];
+    int k = hs[2], nn = hs[4], nt = hs[5], nkm = hs[6], e = hs[8] ? hs[8] : hs[9];
     double mg = *(double*)(hs + 16);
     if (e) {
         cudaMemsetAsync(m->bar.p, 0, 2 * sizeof(unsigned), s);
@@ -550,16 +551,13 @@ extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double
     m->stats.min_margin = INFINITY;
     long long vstar = (long long)ceil(density * (double)m->P);
     int round = 0;
+    // solve results are accumulated on the device and read once at the end
+    FEM_TRY(solve_totals_reset(m, s));
+    FEM_CUDA(cudaMemsetAsync(m->dflag.p + 8, 0, sizeof(int), s));  // scan wait flag
     while ((long long)m->V < vstar && (p->max_rounds <= 0 || round < p->max_rounds)) {
         FEM_TRY(build_system(m, s));
         FEM_TRY(set_uv_from_f(m, f_dev, s));
-        int it = 0;
-        double rel = 0.0;
-        long long before = m->stats.cg_iters;
-        int solves = m->stats.solves;
-        fem_status st = solve_laplace(m, p->precision == FEM_PREC_FP64, p->tol, p->maxit, s, &it, &rel);
-        (void)before;
-        (void)solves;
+        fem_status st = solve_laplace(m, p->precision == FEM_PREC_FP64, p->tol, p->maxit, s, nullptr, nullptr, true);
         if (st != FEM_OK) return st;
         FEM_TRY(ensure(m->keys, (size_t)m->T, s));
         FEM_TRY(ensure(m->keyc, (size_t)m->T, s));
@@ -573,6 +571,7 @@ extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double
         if (margin < m->stats.min_margin) m->stats.min_margin = margin;
         round++;
     }
+    fem_status st = solve_totals_read(m, s);
     m->stats.rounds = round;
-    return FEM_OK;
+    return st;
 }

@@ -156,7 +156,7 @@ fem_status build_system(fem_mesh* m, cudaStream_t s) {
     int vb = (V + 255) / 256;
     FEM_LAUNCH(F_ASSEMBLY, s, k_unknown_flags, vb, 256, 0, m->mask.p, V, m->flags.p);
     int* nU_dev = m->dcount.p + 1;
-    FEM_TRY(exclusive_scan_i32(m->flags.p, m->uidx.p, V, s, nU_dev));
+    FEM_TRY(scan_i32(m, m->flags.p, m->uidx.p, V, s, nU_dev));
     FEM_LAUNCH(F_ASSEMBLY, s, k_index_maps, vb, 256, 0, m->mask.p, V, m->uidx.p, m->kidx.p, m->urow_vertex.p,
                m->kvert.p);
     // the mask count is kept on the host by create / import / refinement, so
@@ -203,8 +203,24 @@ struct SolveArgs {
     double* red;       // 2 * 2 * gridDim partials
     unsigned* bar;
     int* err;
-    double* out;       // [0] iterations, [1] relres, [2] status, [3] FP64 residual passes
+    double* out;       // [0] iterations, [1] relres, [2] status, [3] refinement residual passes
+    double* acc;       // optional running totals (see solve_accumulate)
+    double bytes_it;   // algorithmic bytes per CG iteration (for acc)
+    double bytes_res;  // algorithmic bytes per residual pass (for acc)
 };
+
+// Running totals of solves whose results are not read back one by one:
+// acc[0] CG iterations, [1] largest relative residual, [2] first failing
+// status, [3] solves, [4] algorithmic bytes.  Kernels on one stream run one
+// after another, so the single writing thread needs no atomics.
+__device__ __forceinline__ void solve_accumulate(const SolveArgs& A, int iters, double relres, int status, int nres) {
+    if (!A.acc) return;
+    A.acc[0] += iters;
+    if (relres > A.acc[1]) A.acc[1] = relres;
+    if (status != FEM_OK && A.acc[2] == 0.0) A.acc[2] = status;
+    A.acc[3] += 1.0;
+    A.acc[4] += A.bytes_it * iters + A.bytes_res * nres;
+}
 
 // Reductions are written for GB300's FP64 rate (about 2 FP64 FMAs per clock
 // per SM, 1/64 of FP32): FP32 partials are summed per warp in FP32 and only
@@ -522,6 +538,7 @@ done:
         A.out[1] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
         A.out[2] = status;
         A.out[3] = n_res;
+        solve_accumulate(A, total_it, A.out[1], status, n_res);
     }
     return;
 fail:
@@ -530,6 +547,7 @@ fail:
         A.out[1] = -1.0;
         A.out[2] = FEM_E_TIMEOUT;
         A.out[3] = n_res;
+        solve_accumulate(A, total_it, 1.0, FEM_E_TIMEOUT, n_res);
     }
 }
 
@@ -598,35 +616,18 @@ struct BlockScratch {
     float2* bff;            // n float-float right-hand side
 };
 
-__global__ void __launch_bounds__(kSingleThreads) k_solve_block(SolveArgs A, BlockScratch G, int smem_bytes) {
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    __shared__ BlockRed R;
-    __shared__ float s_lut[17];
-    __shared__ int s_wsum[kSingleThreads / 32];
-    __shared__ float s_bmax[kSingleThreads / 32];
+// The solve proper.  SMEM selects where the CG vectors and the CSR copy
+// live; each instantiation derives its pointers from one address space only,
+// so the shared-memory one compiles to shared-memory instructions.
+template <bool SMEM>
+__device__ __forceinline__ void block_solve_core(const SolveArgs& A, const BlockScratch& G, unsigned char* sm_raw,
+                                                 int nnz, float bm, BlockRed& R, const float* s_lut, int* s_wsum) {
     const int n = A.n, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid < 17) s_lut[tid] = tid ? 1.0f / (0.5f * (float)tid) : 0.0f;
-    // number of off-diagonal entries, and max |b|
-    int cnt_t = 0;
-    float bm = 0.f;
-    for (int i = tid; i < n; i += kSingleThreads) {
-        cnt_t += A.cnt[i];
-        bm = fmaxf(bm, fabsf((float)A.b[i]));
-    }
-    cnt_t = warp_sum(cnt_t);
-    for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
-    if (lane == 0) { s_wsum[wid] = cnt_t; s_bmax[wid] = bm; }
-    __syncthreads();
-    int nnz = 0;
-    bm = 0.f;
-    for (int i = 0; i < kSingleThreads / 32; ++i) { nnz += s_wsum[i]; bm = fmaxf(bm, s_bmax[i]); }
     // layout: floats (5n) | int rowptr (n+1) | u16 entries (nnz) | u8 diag (n)
-    size_t need = (size_t)20 * n + (size_t)4 * (n + 1) + (size_t)2 * nnz + (size_t)n;
-    bool in_smem = need <= (size_t)smem_bytes;
-    float* fv = in_smem ? (float*)sm_raw : G.vec;
-    int* rowptr = in_smem ? (int*)(sm_raw + (size_t)20 * n) : G.rowptr;
-    unsigned short* ent = in_smem ? (unsigned short*)(sm_raw + (size_t)24 * n + 4) : G.ent;
-    unsigned char* dg2 = in_smem ? (sm_raw + (size_t)24 * n + 4 + (size_t)2 * nnz) : G.dg2;
+    float* fv = SMEM ? (float*)sm_raw : G.vec;
+    int* rowptr = SMEM ? (int*)(sm_raw + (size_t)20 * n) : G.rowptr;
+    unsigned short* ent = SMEM ? (unsigned short*)(sm_raw + (size_t)24 * n + 4) : G.ent;
+    unsigned char* dg2 = SMEM ? (sm_raw + (size_t)24 * n + 4 + (size_t)2 * nnz) : G.dg2;
     float *d = fv, *r = fv + n, *p0 = fv + 2 * n, *p1 = fv + 3 * n, *q = fv + 4 * n;
     // CSR row starts: contiguous chunks per thread, block exclusive scan
     int chunk = (n + kSingleThreads - 1) / kSingleThreads;
@@ -758,7 +759,39 @@ __global__ void __launch_bounds__(kSingleThreads) k_solve_block(SolveArgs A, Blo
         A.out[1] = bb > 0.f ? sqrt((double)rr / (double)bb) : 0.0;
         A.out[2] = status;
         A.out[3] = n_res;
+        solve_accumulate(A, total_it, A.out[1], status, n_res);
     }
+}
+
+__global__ void __launch_bounds__(kSingleThreads) k_solve_block(SolveArgs A, BlockScratch G, int smem_bytes) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ BlockRed R;
+    __shared__ float s_lut[17];
+    __shared__ int s_wsum[kSingleThreads / 32];
+    __shared__ float s_bmax[kSingleThreads / 32];
+    const int n = A.n, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid < 17) s_lut[tid] = tid ? 1.0f / (0.5f * (float)tid) : 0.0f;
+    // number of off-diagonal entries, and max |b|
+    int cnt_t = 0;
+    float bm = 0.f;
+    for (int i = tid; i < n; i += kSingleThreads) {
+        cnt_t += A.cnt[i];
+        bm = fmaxf(bm, fabsf((float)A.b[i]));
+    }
+    cnt_t = warp_sum(cnt_t);
+    for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+    if (lane == 0) { s_wsum[wid] = cnt_t; s_bmax[wid] = bm; }
+    __syncthreads();
+    int nnz = 0;
+    bm = 0.f;
+    for (int i = 0; i < kSingleThreads / 32; ++i) { nnz += s_wsum[i]; bm = fmaxf(bm, s_bmax[i]); }
+    size_t need = (size_t)20 * n + (size_t)4 * (n + 1) + (size_t)2 * nnz + (size_t)n;
+    (void)lane;
+    (void)wid;
+    if (need <= (size_t)smem_bytes)
+        block_solve_core<true>(A, G, sm_raw, nnz, bm, R, s_lut, s_wsum);
+    else
+        block_solve_core<false>(A, G, sm_raw, nnz, bm, R, s_lut, s_wsum);
 }
 
 static int coop_blocks(const void* func, int n, int num_sms) {
@@ -777,7 +810,7 @@ static int coop_blocks(const void* func, int n, int num_sms) {
 
 // Solve A_UU x = b (device vectors of length nU; x holds the start).
 fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, double tol, int maxit, cudaStream_t s,
-                     int* iters_out, double* relres_out) {
+                     int* iters_out, double* relres_out, bool deferred) {
     FEM_TRY(build_system(m, s));
     int nU = m->nU;
     if (iters_out) *iters_out = 0;
@@ -819,6 +852,13 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
     A.bar = m->bar.p;
     A.err = m->dflag.p + 1;
     A.out = m->dscal.p;
+    // Algorithmic bytes per row: ELL matrix (8 columns + 8 values + diagonal,
+    // 68 B) per SpMV; FP32 CG iteration = SpMV 76 B + updates 44 B; FP64 CG
+    // iteration = SpMV 84 B + updates 84 B; FP64 residual pass 92 B; each FP32
+    // refinement step adds 36 B of conversions and the FP64 update.
+    A.bytes_it = (double)nU * (use_fp64 ? 168.0 : 120.0);
+    A.bytes_res = (double)nU * (92.0 + (use_fp64 ? 0.0 : 36.0));
+    A.acc = deferred ? m->dscal.p + 64 : nullptr;
     FEM_CUDA(cudaMemsetAsync(m->dflag.p + 1, 0, sizeof(int), s));
     if (!use_fp64 && nU <= kBlockMaxRows) {
         static bool attr_set = false;
@@ -845,6 +885,10 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
         FEM_TRY(launch_coop(F_CG, func, grid, kSolveThreads, 0, s, args,
                             use_fp64 ? "k_solve<fp64>" : "k_solve<fp32ir>"));
     }
+    if (deferred) {
+        if (profiling(F_CG)) note_bytes(F_CG, 0.0);  // bytes are added from the device totals at the end
+        return FEM_OK;
+    }
     double* hs = (double*)m->host_stage;
     FEM_CUDA(cudaMemcpyAsync(hs, m->dscal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));
@@ -852,13 +896,7 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
     double rel = hs[1];
     int st = (int)hs[2];
     int nres = (int)hs[3];
-    // Algorithmic bytes per row: ELL matrix (8 columns + 8 values + diagonal,
-    // 68 B) per SpMV; FP32 CG iteration = SpMV 76 B + updates 44 B; FP64 CG
-    // iteration = SpMV 84 B + updates 84 B; FP64 residual pass 92 B; each FP32
-    // refinement step adds 36 B of conversions and the FP64 update.
-    double per_it = use_fp64 ? 168.0 : 120.0;
-    double per_res = 92.0 + (use_fp64 ? 0.0 : 36.0);
-    note_bytes(F_CG, (double)nU * (per_it * its + per_res * nres));
+    note_bytes(F_CG, A.bytes_it * its + A.bytes_res * nres);
     m->stats.cg_iters += its;
     m->stats.solves += 1;
     m->stats.relres = rel;
@@ -876,10 +914,37 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
     return FEM_OK;
 }
 
+// Start / finish a sequence of deferred solves (running totals on the device).
+fem_status solve_totals_reset(fem_mesh* m, cudaStream_t s) {
+    FEM_CUDA(cudaMemsetAsync(m->dscal.p + 64, 0, 8 * sizeof(double), s));
+    return FEM_OK;
+}
+
+fem_status solve_totals_read(fem_mesh* m, cudaStream_t s) {
+    double* hs = (double*)m->host_stage;
+    FEM_CUDA(cudaMemcpyAsync(hs, m->dscal.p + 64, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    m->stats.cg_iters += (long long)hs[0];
+    m->stats.solves += (int)hs[3];
+    m->stats.relres = hs[1];
+    note_bytes(F_CG, hs[4]);
+    int st = (int)hs[2];
+    if (st == FEM_E_TIMEOUT) {
+        cudaMemsetAsync(m->bar.p, 0, 2 * sizeof(unsigned), s);
+        set_error("Laplace solve: a grid barrier wait ran out");
+        return FEM_E_TIMEOUT;
+    }
+    if (st != FEM_OK) {
+        set_error("Laplace solve: iteration cap reached, largest relative residual " + std::to_string(hs[1]));
+        return FEM_E_NOT_CONVERGED;
+    }
+    return FEM_OK;
+}
+
 // Laplace solve for the current vertex values: the entries of m->uv at K are
 // the Dirichlet data, those at U the start; the solution is written back.
 fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cudaStream_t s, int* iters_out,
-                         double* relres_out) {
+                         double* relres_out, bool deferred) {
     FEM_TRY(build_system(m, s));
     int nU = m->nU;
     if (iters_out) *iters_out = 0;
@@ -890,7 +955,7 @@ fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cuda
     int b = (nU + 255) / 256;
     FEM_LAUNCH(F_CG, s, k_rhs_and_start, b, 256, 0, nU, m->V, m->urow_vertex.p, m->nbr.p, m->coefA.p, m->mask.p,
                m->uv.p, m->b64.p, m->x64.p);
-    fem_status st = run_solve(m, m->b64.p, m->x64.p, use_fp64, tol, maxit, s, iters_out, relres_out);
+    fem_status st = run_solve(m, m->b64.p, m->x64.p, use_fp64, tol, maxit, s, iters_out, relres_out, deferred);
     if (st != FEM_OK && st != FEM_E_NOT_CONVERGED) return st;
     FEM_LAUNCH(F_CG, s, k_scatter_solution, b, 256, 0, nU, m->urow_vertex.p, m->x64.p, m->uv.p, m->uvf.p);
     return st;
