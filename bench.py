@@ -77,6 +77,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest value over all ranks (the timed region's total); the only
+    collective of the multi-GPU run, which otherwise runs independent replicas."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank optimises its own seeded image (replicas, weak scaling)."""
+    return base_seed + rank
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -172,7 +189,7 @@ def run_ours(a, world, rank, local):
     dev = torch.device("cuda", local)
     n = a.n
     P = n * n
-    f_np = seeded_inputs.make_image(n, a.seed + rank)
+    f_np = seeded_inputs.make_image(n, replica_seed(a.seed, rank))
     f = torch.from_numpy(f_np).to(dev)
     prec = fem.FEM_PREC_FP64 if a.precision == "fp64" else fem.FEM_PREC_FP32_IR
     p = fem.params(topk_frac=a.frac, tonal_tol=a.tonal_tol, precision=prec)
@@ -238,11 +255,7 @@ def run_ours(a, world, rank, local):
     prof = fem.fem_profile_read()[dom]
     fem.fem_profile_enable(False)
     clocks = clk.stop()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), dev)
     barrier()
     ms_per_step = total_ms / a.steps
     value = world * P / 1e6 / (ms_per_step / 1e3)

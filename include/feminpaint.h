@@ -213,6 +213,13 @@ FEM_API const char *fem_last_error(void);
 FEM_API void fem_profile_enable(int family_mask);
 FEM_API int fem_profile_read(int family, long long *launches, double *ms, double *bytes, const char **name);
 
+/* Check of the library's bounded device-side waits (no counterpart in the
+ * paper): runs the grid barrier used by the persistent kernels with one of
+ * its two blocks never arriving.  The waiting block must give up after the
+ * barrier's limit (2 s) and report it; the call returns FEM_E_TIMEOUT when
+ * that happened (the expected outcome) and the CUDA context stays usable. */
+FEM_API fem_status fem_selftest_wait_timeout(void *stream);
+
 /* Number of kernels this library has launched in the process so far. */
 FEM_API long long fem_launch_count(void);
 

@@ -46,7 +46,7 @@ _STATUS = {0: "FEM_OK", 1: "FEM_E_INVALID", 2: "FEM_E_SHAPE", 3: "FEM_E_OOM", 4:
 EXPORTED = ["fem_params_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_info", "fem_mesh_export",
             "fem_mesh_import", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_triangle_errors_noalloc", "fem_rasterize", "fem_spatial_refine",
             "fem_tonal_opt", "fem_adjoint", "fem_mesh_stats", "fem_last_error", "fem_profile_enable",
-            "fem_profile_read", "fem_launch_count"]
+            "fem_profile_read", "fem_launch_count", "fem_selftest_wait_timeout"]
 
 
 class fem_params(ctypes.Structure):
@@ -86,6 +86,7 @@ _sig = {
     "fem_profile_read": (_i, [_i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_char_p)]),
     "fem_launch_count": (ctypes.c_longlong, []),
+    "fem_selftest_wait_timeout": (_i, [_vp]),
 }
 for _n, (_r, _a) in _sig.items():
     _f = getattr(_lib, _n)
@@ -273,6 +274,11 @@ def fem_profile_read() -> dict:
         _lib.fem_profile_read(fam, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(name))
         out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "bytes": by.value}
     return out
+
+
+def fem_selftest_wait_timeout(stream=None) -> int:
+    """Status of the bounded-wait check (FEM_E_TIMEOUT expected)."""
+    return int(_lib.fem_selftest_wait_timeout(_stream(stream)))
 
 
 def fem_launch_count() -> int:

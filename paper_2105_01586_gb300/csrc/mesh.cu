@@ -362,6 +362,15 @@ fem_status sync_counts(fem_mesh* m, cudaStream_t s) {
     return FEM_OK;
 }
 
+// Diagnostic for the bounded waits: block 0 enters the grid barrier, block 1
+// returns without arriving, so the barrier's arrival count never completes
+// and block 0 must give up after the barrier's time limit and record
+// FEM_E_TIMEOUT instead of hanging.
+__global__ void k_selftest_barrier(unsigned* bar, int* err) {
+    if (blockIdx.x != 0) return;
+    grid_barrier(bar, err);
+}
+
 }  // namespace fem
 
 using namespace fem;
@@ -475,6 +484,30 @@ fem_status fem_mesh_create(int width, int height, void* stream, fem_mesh** out) 
     }
     *out = m;
     return FEM_OK;
+}
+
+fem_status fem_selftest_wait_timeout(void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned* bar = nullptr;
+    FEM_TRY(dalloc_raw((void**)&bar, 64, s));
+    int* err = (int*)(bar + 8);
+    fem_status st = FEM_OK;
+    do {
+        cudaError_t e = cudaMemsetAsync(bar, 0, 64, s);
+        if (e != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
+        void* args[] = {&bar, &err};
+        st = launch_coop(F_OTHER, (const void*)k_selftest_barrier, 2, 32, 0, s, args, "k_selftest_barrier");
+        if (st != FEM_OK) break;
+        int h = 0;
+        e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { st = cuda_fail(e, "selftest read-back"); break; }
+        st = (fem_status)h;
+        if (st == FEM_E_TIMEOUT) set_error("bounded wait ran out as intended");
+    } while (0);
+    dfree_raw(bar, s);
+    cudaStreamSynchronize(s);
+    return st;
 }
 
 fem_status fem_mesh_destroy(fem_mesh* m) {

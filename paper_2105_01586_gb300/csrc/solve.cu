@@ -14,6 +14,7 @@
 //                     x += ||r|| d (FP64) }
 //   FP64:    PCG in FP64 from the warm start until ||r|| <= tol ||b||, then
 //            the residual is recomputed from scratch to confirm.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -794,6 +795,199 @@ __global__ void __launch_bounds__(kSingleThreads) k_solve_block(SolveArgs A, Blo
         block_solve_core<false>(A, G, sm_raw, nnz, bm, R, s_lut, s_wsum);
 }
 
+// ---------------------------------------------------------------------------
+// Grid version of the FP64-free FP32-IR solve for systems above
+// kBlockMaxRows: the same algorithm as k_solve_block on a cooperative grid.
+// A_UU is read from the ELL arrays in global memory, x and b are float-float
+// global vectors, data written by other blocks is read through L2 (__ldcg),
+// and each reduction is a block reduction plus one bounded grid barrier
+// (two barriers per CG iteration).
+constexpr int kGridThreads = 512;
+
+// Parities of the double-buffered partial slots: per-thread registers that
+// advance identically in every thread (one flip per reduction).
+struct GridPar {
+    int par;   // block-level slot buffer
+    int gpar;  // grid-level partial buffer
+};
+
+// totals of three floats over the grid (same bits in every thread)
+__device__ __forceinline__ bool grid_sum3(const SolveArgs& A, BlockRed& R, GridPar& P, float a, float b, float c,
+                                          float3& out) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    if (lane == 0) R.slot[P.par][w] = make_float4(a, b, c, 0.f);
+    __syncthreads();
+    float4 v = lane < kGridThreads / 32 ? R.slot[P.par][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    P.par ^= 1;
+    float ba = warp_sum(v.x), bb = warp_sum(v.y), bc = warp_sum(v.z);
+    int nb = gridDim.x;
+    float4* buf = (float4*)A.red + (size_t)P.gpar * nb;
+    if (threadIdx.x == 0) buf[blockIdx.x] = make_float4(ba, bb, bc, 0.f);
+    P.gpar ^= 1;
+    if (!grid_barrier(A.bar, A.err)) return false;
+    float sa = 0.f, sb = 0.f, sc = 0.f;
+    for (int k = lane; k < nb; k += 32) {
+        float4 u = __ldcg(&buf[k]);
+        sa += u.x;
+        sb += u.y;
+        sc += u.z;
+    }
+    sa = __shfl_sync(0xffffffffu, warp_sum(sa), 0);
+    sb = __shfl_sync(0xffffffffu, warp_sum(sb), 0);
+    sc = __shfl_sync(0xffffffffu, warp_sum(sc), 0);
+    out = make_float3(sa, sb, sc);
+    return true;
+}
+
+__global__ void __launch_bounds__(kGridThreads) k_solve_grid(SolveArgs A, BlockScratch G) {
+    __shared__ BlockRed R;
+    GridPar P{0, 0};
+    const int n = A.n, stride = gridDim.x * blockDim.x, tid0 = blockIdx.x * blockDim.x + threadIdx.x;
+    float* d = G.vec;
+    float *r = d + n, *p0 = d + 2 * n, *p1 = d + 3 * n, *q = d + 4 * n;
+    int total_it = 0, n_res = 0, status = FEM_E_NOT_CONVERGED;
+    float rr = 0.f, bb = 0.f;
+    // max |b| over the grid (as a sum of per-block maxima is not a max, use
+    // the three-value reduction on squares' maxima through an exact trick:
+    // a max is order-independent, so each block contributes its max and the
+    // grid takes the max of the partials)
+    float bm = 0.f;
+    for (int i = tid0; i < n; i += stride) bm = fmaxf(bm, fabsf((float)A.b[i]));
+    for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+    {
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) R.slot[P.par][w] = make_float4(bm, 0.f, 0.f, 0.f);
+        __syncthreads();
+        float m = 0.f;
+        for (int i = 0; i < kGridThreads / 32; ++i) m = fmaxf(m, R.slot[P.par][i].x);
+        P.par ^= 1;
+        float4* buf = (float4*)A.red + (size_t)P.gpar * gridDim.x;
+        if (threadIdx.x == 0) buf[blockIdx.x] = make_float4(m, 0.f, 0.f, 0.f);
+        P.gpar ^= 1;
+        if (!grid_barrier(A.bar, A.err)) goto fail;
+        m = 0.f;
+        for (int k = 0; k < (int)gridDim.x; ++k) m = fmaxf(m, __ldcg(&buf[k]).x);
+        bm = m;
+    }
+    if (bm == 0.f) {
+        for (int i = tid0; i < n; i += stride) A.x[i] = 0.0;
+        status = FEM_OK;
+    } else {
+        int e = ilogbf(bm);
+        float sigma = ldexpf(1.0f, -e);
+        double inv_sigma = ldexp(1.0, e);
+        for (int i = tid0; i < n; i += stride) {
+            ff bi = ff_scale_pow2(ff_from_double(A.b[i]), sigma);
+            ff xi = ff_scale_pow2(ff_from_double(A.x[i]), sigma);
+            G.bff[i] = make_float2(bi.hi, bi.lo);
+            G.xff[i] = make_float2(xi.hi, xi.lo);
+        }
+        if (!grid_barrier(A.bar, A.err)) goto fail;
+        float tol2 = (float)(A.tol * A.tol);
+        for (int step = 0; step < 64; ++step) {
+            float rr_t = 0.f, bb_t = 0.f, rz_t = 0.f;
+            for (int i = tid0; i < n; i += stride) {
+                float2 xv = __ldcg(&G.xff[i]);
+                ff s2 = ff_mul_f(ff{xv.x, xv.y}, A.diag[i]);
+                int c = A.cnt[i];
+                for (int k = 0; k < c; ++k) {
+                    float2 xc = __ldcg(&G.xff[A.col[k * n + i]]);
+                    s2 = ff_add(s2, ff_scale_pow2(ff{xc.x, xc.y}, A.val[k * n + i]));
+                }
+                float2 bv = G.bff[i];
+                ff res = ff_sub(ff{bv.x, bv.y}, s2);
+                float ri = __fadd_rn(res.hi, res.lo);
+                r[i] = ri;
+                d[i] = 0.f;
+                p0[i] = 0.f;
+                rr_t += ri * ri;
+                rz_t += ri * ri * A.dinv[i];
+                bb_t += bv.x * bv.x;
+            }
+            float3 red;
+            if (!grid_sum3(A, R, P, rr_t, bb_t, rz_t, red)) goto fail;
+            n_res++;
+            rr = red.x;
+            bb = red.y;
+            if (rr <= tol2 * bb) { status = FEM_OK; break; }
+            if (total_it >= A.maxit) break;
+            float rz = red.z, rr_in = rr, lim = (float)(kInnerEta * kInnerEta) * rr, beta = 0.f;
+            int cap = A.maxit - total_it;
+            if (cap > kInnerCap) cap = kInnerCap;
+            int it = 0;
+            float *pold = p0, *pnew = p1;
+            while (rr_in > lim && it < cap) {
+                float pq_t = 0.f;
+                for (int i = tid0; i < n; i += stride) {
+                    float pi = fmaf(beta, __ldcg(&pold[i]), A.dinv[i] * __ldcg(&r[i]));
+                    pnew[i] = pi;
+                    float sacc = A.diag[i] * pi;
+                    int c = A.cnt[i];
+                    for (int k = 0; k < c; ++k) {
+                        int col = A.col[k * n + i];
+                        sacc = fmaf(A.val[k * n + i], fmaf(beta, __ldcg(&pold[col]), A.dinv[col] * __ldcg(&r[col])),
+                                    sacc);
+                    }
+                    q[i] = sacc;
+                    pq_t += pi * sacc;
+                }
+                float3 s1;
+                if (!grid_sum3(A, R, P, pq_t, 0.f, 0.f, s1)) goto fail;
+                float pq = s1.x;
+                if (!(pq > 0.f)) break;
+                float alpha = rz / pq;
+                float rz_t2 = 0.f, rr_t2 = 0.f;
+                for (int i = tid0; i < n; i += stride) {
+                    d[i] = fmaf(alpha, pnew[i], d[i]);
+                    float ri = fmaf(-alpha, q[i], r[i]);
+                    r[i] = ri;
+                    rz_t2 += ri * ri * A.dinv[i];
+                    rr_t2 += ri * ri;
+                }
+                float3 s2;
+                if (!grid_sum3(A, R, P, rz_t2, rr_t2, 0.f, s2)) goto fail;
+                it++;
+                beta = s2.x / rz;
+                rz = s2.x;
+                rr_in = s2.y;
+                float* t = pold;
+                pold = pnew;
+                pnew = t;
+            }
+            total_it += it;
+            for (int i = tid0; i < n; i += stride) {
+                float2 xv = G.xff[i];
+                ff xi = ff_add_f(ff{xv.x, xv.y}, d[i]);
+                G.xff[i] = make_float2(xi.hi, xi.lo);
+            }
+            if (!grid_barrier(A.bar, A.err)) goto fail;
+        }
+        for (int i = tid0; i < n; i += stride) {
+            float2 xv = G.xff[i];
+            A.x[i] = ff_to_double(ff{xv.x, xv.y}) * inv_sigma;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.out[0] = total_it;
+        A.out[1] = bb > 0.f ? sqrt((double)rr / (double)bb) : 0.0;
+        A.out[2] = status;
+        A.out[3] = n_res;
+        solve_accumulate(A, total_it, A.out[1], status, n_res);
+    }
+    return;
+fail:
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.out[0] = total_it;
+        A.out[1] = -1.0;
+        A.out[2] = FEM_E_TIMEOUT;
+        A.out[3] = n_res;
+        solve_accumulate(A, total_it, 1.0, FEM_E_TIMEOUT, n_res);
+    }
+}
+
 static int coop_blocks(const void* func, int n, int num_sms) {
     static int occ[2] = {0, 0};
     int which = func == (const void*)k_solve<true> ? 1 : 0;
@@ -875,15 +1069,27 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
         FEM_TRY(ensure(m->bbff, (size_t)nU, s));
         BlockScratch G{m->bvec.p, m->browptr.p, m->bent.p, m->bdg2.p, m->bxff.p, m->bbff.p};
         FEM_LAUNCH(F_CG, s, k_solve_block, 1, kSingleThreads, (size_t)kBlockSmemBytes, A, G, kBlockSmemBytes);
+    } else if (!use_fp64) {
+        static int occ = 0;
+        if (!occ) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_grid, kGridThreads, 0);
+            if (occ < 1) occ = 1;
+        }
+        int gb = (nU + 2 * kGridThreads - 1) / (2 * kGridThreads);
+        gb = std::max(1, std::min(gb, occ * m->num_sms));
+        FEM_TRY(ensure(m->red, (size_t)4 * gb + 8, s));
+        A.red = m->red.p;
+        FEM_TRY(ensure(m->bvec, (size_t)5 * nU, s));
+        FEM_TRY(ensure(m->bxff, (size_t)nU, s));
+        FEM_TRY(ensure(m->bbff, (size_t)nU, s));
+        BlockScratch G{m->bvec.p, nullptr, nullptr, nullptr, m->bxff.p, m->bbff.p};
+        void* args[] = {&A, &G};
+        FEM_TRY(launch_coop(F_CG, (const void*)k_solve_grid, gb, kGridThreads, 0, s, args, "k_solve_grid"));
     } else if (single) {
-        if (use_fp64)
-            FEM_LAUNCH(F_CG, s, k_solve_single<true>, 1, kSingleThreads, 0, A);
-        else
-            FEM_LAUNCH(F_CG, s, k_solve_single<false>, 1, kSingleThreads, 0, A);
+        FEM_LAUNCH(F_CG, s, k_solve_single<true>, 1, kSingleThreads, 0, A);
     } else {
         void* args[] = {&A};
-        FEM_TRY(launch_coop(F_CG, func, grid, kSolveThreads, 0, s, args,
-                            use_fp64 ? "k_solve<fp64>" : "k_solve<fp32ir>"));
+        FEM_TRY(launch_coop(F_CG, func, grid, kSolveThreads, 0, s, args, "k_solve<fp64>"));
     }
     if (deferred) {
         if (profiling(F_CG)) note_bytes(F_CG, 0.0);  // bytes are added from the device totals at the end

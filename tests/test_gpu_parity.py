@@ -88,7 +88,7 @@ def test_inpaint_matches_oracle(oracle_mod, fem, N, seed, prec):
     f_np = S.make_image(N, seed)
     om, _ = oracle_mod.spatial(f_np, 0.04, 0.01)
     m = _gpu_mesh(fem, om)
-    g_np = oracle_mod.g_from_f(om, f_np)
+    g_np = oracle_mod.g_from_f(om, f_np)  # f is float32, so g is exactly representable
     v_ref, _, _ = oracle_mod.solve(om, g_np, tol=1e-14)
     g = torch.from_numpy(g_np.astype(np.float32)).cuda()
     u, uv = m.inpaint(g, fem.params(precision=prec), want_uv=True)
@@ -196,3 +196,34 @@ def test_errors_are_reported(fem):
     assert e.value.status == fem.FEM_E_INVALID
     with pytest.raises(fem.FemError):
         fem.Mesh(100)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("N,mask_frac", [(129, 0.3), (257, 0.2)])
+def test_inpaint_large_systems(oracle_mod, fem, N, mask_frac, prec):
+    """Fully refined meshes (every pixel a vertex) with a random mask: about
+    11.6k unknowns (one-block solver, vectors in global memory) and 53k
+    unknowns (grid solver), both against the oracle."""
+    import pins
+    om = pins.fully_refined_mesh(oracle_mod, N)
+    rng = np.random.default_rng(N)
+    mk = (rng.uniform(size=om.V) < mask_frac).astype(np.uint8)
+    mk[:4] = 1
+    om = om.with_mask(mk)
+    g_np = rng.uniform(size=int(mk.sum()))
+    v_ref, _, _ = oracle_mod.solve(om, g_np, tol=1e-14)
+    m = _gpu_mesh(fem, om)
+    _, uv = m.inpaint(torch.from_numpy(g_np.astype(np.float32)).cuda(), fem.params(precision=prec), want_uv=True)
+    v_ref32, _, _ = oracle_mod.solve(om, g_np.astype(np.float32).astype(np.float64), tol=1e-14)
+    uv = uv.cpu().numpy()
+    assert np.linalg.norm(uv - v_ref32) <= 1e-9 * np.linalg.norm(v_ref32)
+    assert m.stats()["relres"] <= 1e-12
+
+
+def test_bounded_wait_reports_timeout(fem):
+    """A grid barrier whose second block never arrives gives up after its
+    limit and reports FEM_E_TIMEOUT; the context stays usable."""
+    assert fem.fem_selftest_wait_timeout() == fem.FEM_E_TIMEOUT
+    m = fem.Mesh(33)
+    u = m.inpaint(torch.full((4,), 0.5, device="cuda"))
+    assert torch.allclose(u, torch.full_like(u, 0.5))
