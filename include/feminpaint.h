@@ -104,6 +104,14 @@ FEM_API fem_status fem_mesh_info(const fem_mesh *m, int *V, int *T, int *nmask);
  * Synchronises the mesh's last stream. */
 FEM_API fem_status fem_mesh_export(fem_mesh *m, int *xy, int *tri, unsigned char *is_mask);
 
+/* The order in which the kernels visit the triangles (host buffer, T ints):
+ * for meshes grown by fem_spatial_refine from fem_mesh_create this is the
+ * space-filling curve of the bisection tree (consecutive triangles share the
+ * vertex where the curve leaves one and enters the next; *is_curve = 1);
+ * after fem_mesh_import it is the id order (*is_curve = 0).  Either pointer
+ * may be NULL. */
+FEM_API fem_status fem_mesh_curve_order(fem_mesh *m, int *order, int *is_curve);
+
 /* Replace the mesh by host arrays of the same layout (checkpoint/resume).
  * The arrays are checked: vertices on the grid, triangles positively
  * oriented and right-isosceles with c at the right angle, areas summing to

@@ -44,7 +44,7 @@ _STATUS = {0: "FEM_OK", 1: "FEM_E_INVALID", 2: "FEM_E_SHAPE", 3: "FEM_E_OOM", 4:
            5: "FEM_E_TIMEOUT", 6: "FEM_E_CUDA"}
 
 EXPORTED = ["fem_params_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_info", "fem_mesh_export",
-            "fem_mesh_import", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_triangle_errors_noalloc", "fem_rasterize", "fem_spatial_refine",
+            "fem_mesh_import", "fem_mesh_curve_order", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_triangle_errors_noalloc", "fem_rasterize", "fem_spatial_refine",
             "fem_tonal_opt", "fem_adjoint", "fem_mesh_stats", "fem_last_error", "fem_profile_enable",
             "fem_profile_read", "fem_launch_count", "fem_selftest_wait_timeout"]
 
@@ -73,6 +73,7 @@ _sig = {
     "fem_mesh_export": (_i, [_vp, _vp, _vp, _vp]),
     "fem_mesh_import": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
     "fem_gather_mask": (_i, [_vp, _vp, _vp, _vp]),
+    "fem_mesh_curve_order": (_i, [_vp, _vp, _ip]),
     "fem_inpaint": (_i, [_vp, _vp, _vp, _vp, _pp, _vp]),
     "fem_triangle_errors": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "fem_triangle_errors_noalloc": (_i, [_i, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
@@ -179,6 +180,15 @@ def fem_mesh_import(h: int, xy, tri, is_mask) -> None:
     mk = np.ascontiguousarray(is_mask, np.uint8).reshape(-1)
     _check(_lib.fem_mesh_import(h, len(xy), xy.ctypes.data, len(tri), tri.ctypes.data, mk.ctypes.data),
            "fem_mesh_import")
+
+
+def fem_mesh_curve_order(h: int):
+    """(order, is_curve): the triangle visiting order (see the header)."""
+    V, T, _ = fem_mesh_info(h)
+    order = np.zeros(T, np.int32)
+    ic = _i()
+    _check(_lib.fem_mesh_curve_order(h, order.ctypes.data, ctypes.byref(ic)), "fem_mesh_curve_order")
+    return order, bool(ic.value)
 
 
 def fem_gather_mask(h: int, f, g, stream=None):

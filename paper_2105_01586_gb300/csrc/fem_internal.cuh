@@ -178,6 +178,9 @@ struct fem_mesh {
     fem::DArr<unsigned char> mask;
     fem::DArr<int4> tri;
     fem::DArr<double> uv;
+    fem::DArr<int> order;      // triangle ids along the space-filling curve
+    fem::DArr<int> order_tmp, ocnt, ooff;
+    bool order_is_curve = true;  // false after an import (then id order)
     fem::DArr<float2> uvf;  // float-float copy of uv, written with it in the spatial loop
 
     // rasterisation plan (valid for plan_T triangles of plan_version)

@@ -354,6 +354,7 @@ fem_status ensure_mesh_capacity(fem_mesh* m, int needV, int needT, cudaStream_t 
     FEM_TRY(ensure(m->uv, nv, s, m->V));
     FEM_TRY(ensure(m->uvf, nv, s, m->V));
     FEM_TRY(ensure(m->tri, nt, s, m->T));
+    FEM_TRY(ensure(m->order, nt, s, m->T));
     return FEM_OK;
 }
 
@@ -467,10 +468,12 @@ fem_status fem_mesh_create(int width, int height, void* stream, fem_mesh** out) 
         unsigned char mk[4] = {1, 1, 1, 1};
         int4 tr[2] = {{0, 3, 2, 0}, {3, 0, 1, 0}};
         double uv0[4] = {0, 0, 0, 0};
+        int ord0[2] = {0, 1};  // the curve enters (v0,v3,v2) at v0 and leaves (v3,v0,v1) at v0
         e = cudaMemcpyAsync(m->vxy.p, xy, sizeof(xy), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(m->mask.p, mk, sizeof(mk), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(m->tri.p, tr, sizeof(tr), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(m->uv.p, uv0, sizeof(uv0), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(m->order.p, ord0, sizeof(ord0), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { st = cuda_fail(e, "fem_mesh_create upload"); break; }
         m->V = 4;
@@ -515,6 +518,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     cudaStream_t s = m->last_stream;
     cudaStreamSynchronize(s);
     release(m->vxy, s); release(m->mask, s); release(m->tri, s); release(m->uv, s); release(m->uvf, s);
+    release(m->order, s); release(m->order_tmp, s); release(m->ocnt, s); release(m->ooff, s);
     release(m->item_cnt, s); release(m->item_off, s); release(m->item_tri, s); release(m->partial, s);
     release(m->keys, s);
     release(m->keyc, s);
@@ -571,6 +575,14 @@ fem_status fem_mesh_export(fem_mesh* m, int* xy, int* tri, unsigned char* is_mas
     return FEM_OK;
 }
 
+fem_status fem_mesh_curve_order(fem_mesh* m, int* order, int* is_curve) {
+    FEM_TRY(check_mesh(m));
+    FEM_CUDA(cudaStreamSynchronize(m->last_stream));
+    if (order) FEM_CUDA(cudaMemcpy(order, m->order.p, sizeof(int) * m->T, cudaMemcpyDeviceToHost));
+    if (is_curve) *is_curve = m->order_is_curve ? 1 : 0;
+    return FEM_OK;
+}
+
 fem_status fem_mesh_import(fem_mesh* m, int V, const int* xy, int T, const int* tri, const unsigned char* is_mask) {
     FEM_TRY(check_mesh(m));
     if (V < 3 || T < 1 || !xy || !tri || !is_mask || (long long)V > m->P || (long long)T > 2LL * (m->N - 1) * (m->N - 1)) {
@@ -614,6 +626,13 @@ fem_status fem_mesh_import(fem_mesh* m, int V, const int* xy, int T, const int* 
     FEM_CUDA(cudaMemcpyAsync(m->mask.p, is_mask, V, cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemcpyAsync(m->tri.p, t4.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemsetAsync(m->uv.p, 0, sizeof(double) * V, s));
+    {
+        std::vector<int> ord(T);
+        for (int t = 0; t < T; ++t) ord[t] = t;
+        FEM_CUDA(cudaMemcpyAsync(m->order.p, ord.data(), sizeof(int) * T, cudaMemcpyHostToDevice, s));
+        FEM_CUDA(cudaStreamSynchronize(s));
+    }
+    m->order_is_curve = false;
     FEM_CUDA(cudaStreamSynchronize(s));
     int nk = 0;
     for (int i = 0; i < V; ++i) nk += is_mask[i] ? 1 : 0;

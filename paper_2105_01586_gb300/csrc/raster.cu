@@ -16,6 +16,7 @@
 // search over the lanes.  Consecutive lanes read consecutive pixels of a row.
 // Per-item partial sums are added per triangle in item order, so results do
 // not depend on scheduling.
+#include <algorithm>
 #include <climits>
 
 #include "fem_internal.cuh"
@@ -70,6 +71,15 @@ __device__ __forceinline__ void row_span(const TriGeom& g, int y, int N, int& L,
     len = n > 0 ? n : 0;
 }
 
+// Small triangles (bounding box at most kSmallSide pixels each way, at most
+// 153 pixels) are rasterised one per thread along the space-filling curve
+// (k_raster_small); only the larger ones are cut into warp items.
+constexpr int kSmallSide = 17;
+
+__device__ __forceinline__ bool is_small(const TriGeom& g) {
+    return g.maxw <= kSmallSide && (g.yend - g.ytop + 1) <= kSmallSide;
+}
+
 __global__ void k_item_count(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int N,
                              int* __restrict__ cnt) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,7 +87,7 @@ __global__ void k_item_count(const int4* __restrict__ tri, const int2* __restric
     TriGeom g = tri_geom(tri[t], vxy, N);
     int rows = g.yend - g.ytop + 1;
     int rpi = rows_per_item(g.maxw);
-    cnt[t] = rows > 0 ? (rows + rpi - 1) / rpi : 0;
+    cnt[t] = (rows > 0 && !is_small(g)) ? (rows + rpi - 1) / rpi : 0;
 }
 
 __global__ void k_item_expand(const int* __restrict__ cnt, const int* __restrict__ off, int T, int cap,
@@ -243,6 +253,7 @@ __global__ void k_finalize_err(const int* __restrict__ cnt, const int* __restric
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     int o = off[t], n = cnt[t];
+    if (n == 0) return;  // small triangle: written by k_raster_small
     ff s{0.f, 0.f};
     for (int j = 0; j < n; ++j) {
         float2 v = partial[o + j];
@@ -264,6 +275,7 @@ __global__ void k_finalize(const int* __restrict__ cnt, const int* __restrict__ 
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     int o = off[t], n = cnt[t];
+    if (n == 0) return;  // small triangle: written by k_raster_small
     double s[NA];
 #pragma unroll
     for (int q = 0; q < NA; ++q) s[q] = 0.0;
@@ -273,6 +285,102 @@ __global__ void k_finalize(const int* __restrict__ cnt, const int* __restrict__ 
 #pragma unroll
     for (int q = 0; q < NA; ++q) out[(long long)t * NA + q] = s[q];
 }
+
+// One small triangle per thread, threads in curve order (order == nullptr:
+// id order), so that neighbouring threads read neighbouring pixels.  Rows are
+// walked left to right; in the error and image modes the float-float
+// interpolant advances by the exact gradient g_x per pixel.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_raster_small(const int* __restrict__ order, const int4* __restrict__ tri,
+                                                      const int2* __restrict__ vxy, const double* __restrict__ uv,
+                                                      const float2* __restrict__ uvf, const float* __restrict__ img,
+                                                      int N, int T, double* __restrict__ out,
+                                                      unsigned long long* __restrict__ keyc,
+                                                      float* __restrict__ u_out, int* __restrict__ owner_out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
+        int t = order ? order[i] : i;
+        int4 tr = tri[t];
+        TriGeom g = tri_geom(tr, vxy, N);
+        if (!is_small(g)) continue;
+        int dax = g.ax - g.cx, day = g.ay - g.cy, dbx = g.bx - g.cx, dby = g.by - g.cy;
+        long long l2 = (long long)dax * dax + (long long)day * day;
+        bool pow2 = (l2 & (l2 - 1)) == 0;
+        if (MODE == R_ERR || MODE == R_IMG) {
+            ff va = vertex_ff(uv, uvf, tr.x), vb = vertex_ff(uv, uvf, tr.y), uc = vertex_ff(uv, uvf, tr.z);
+            ff da = ff_sub(va, uc), db = ff_sub(vb, uc);
+            ff gx = ff_add(ff_mul_f(da, (float)dax), ff_mul_f(db, (float)dbx));
+            ff gy = ff_add(ff_mul_f(da, (float)day), ff_mul_f(db, (float)dby));
+            if (pow2) {
+                float inv = __int_as_float((127 - (63 - __clzll(l2))) << 23);
+                gx = ff_scale_pow2(gx, inv);
+                gy = ff_scale_pow2(gy, inv);
+            } else {
+                float inv = 1.0f / (float)l2;
+                gx = ff_mul_f(gx, inv);
+                gy = ff_mul_f(gy, inv);
+            }
+            ff acc{0.f, 0.f};
+            for (int y = g.ytop; y <= g.yend; ++y) {
+                int L, len;
+                row_span(g, y, N, L, len);
+                if (len <= 0) continue;
+                ff u = ff_add(ff_add(uc, ff_mul_f(gx, (float)(L - g.cx))), ff_mul_f(gy, (float)(y - g.cy)));
+                long long p0 = (long long)y * N + L;
+#pragma unroll 4
+                for (int k = 0; k < len; ++k) {
+                    if (MODE == R_ERR) {
+                        ff d = ff_add_f(u, -img[p0 + k]);
+                        acc = ff_add(acc, ff_sqr(d));
+                    } else {
+                        if (u_out) u_out[p0 + k] = __fadd_rn(u.hi, u.lo);
+                        if (owner_out) owner_out[p0 + k] = t;
+                    }
+                    u = ff_add(u, gx);
+                }
+            }
+            if (MODE == R_ERR) {
+                double key = ff_to_double(acc);
+                out[t] = key;
+                if (keyc) {
+                    bool eligible = (((g.ax + g.bx) | (g.ay + g.by)) & 1) == 0;
+                    keyc[t] = eligible ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
+                }
+            }
+        } else {
+            double inv_l2 = pow2 ? __longlong_as_double((long long)(1023 - (63 - __clzll(l2))) << 52) : 1.0 / (double)l2;
+            double acc[6] = {0, 0, 0, 0, 0, 0};
+            for (int y = g.ytop; y <= g.yend; ++y) {
+                int L, len;
+                row_span(g, y, N, L, len);
+                for (int k = 0; k < len; ++k) {
+                    int x = L + k;
+                    long long dxp = x - g.cx, dyp = y - g.cy;
+                    double la = (double)(dxp * dax + dyp * day) * inv_l2;
+                    double lb = (double)(dxp * dbx + dyp * dby) * inv_l2;
+                    double lc = 1.0 - la - lb;
+                    if (MODE == R_MASS) {
+                        acc[0] = fma(la, la, acc[0]);
+                        acc[1] = fma(lb, lb, acc[1]);
+                        acc[2] = fma(lc, lc, acc[2]);
+                        acc[3] = fma(la, lb, acc[3]);
+                        acc[4] = fma(lb, lc, acc[4]);
+                        acc[5] = fma(lc, la, acc[5]);
+                    } else {
+                        double r = (double)img[(long long)y * N + x];
+                        acc[0] = fma(la, r, acc[0]);
+                        acc[1] = fma(lb, r, acc[1]);
+                        acc[2] = fma(lc, r, acc[2]);
+                    }
+                }
+            }
+            constexpr int NA = MODE == R_MASS ? 6 : 3;
+#pragma unroll
+            for (int q = 0; q < NA; ++q) out[(long long)t * NA + q] = acc[q];
+        }
+    }
+}
+
+static int small_grid(fem_mesh* m) { return std::max(1, std::min((m->T + 255) / 256, m->num_sms * 8)); }
 
 static int raster_grid(fem_mesh* m) { return m->num_sms * (2048 / kRasterThreads); }
 
@@ -312,6 +420,8 @@ fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, const
     int blocks = (m->T + 255) / 256;
     FEM_LAUNCH(F_RASTER, s, k_finalize_err, blocks, 256, 0, m->item_cnt.p, m->item_off.p,
                (const float2*)m->partial.p, m->T, m->tri.p, m->vxy.p, err_out, keyc_out);
+    FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv, uvf, f,
+               m->N, m->T, err_out, keyc_out, (float*)nullptr, (int*)nullptr);
     return FEM_OK;
 }
 
@@ -321,6 +431,9 @@ fem_status raster_image(fem_mesh* m, const double* uv, float* u, int* owner, cud
                              16.0 * m->V);
     FEM_LAUNCH(F_RASTER, s, k_raster<R_IMG>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv,
                (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p, u, owner);
+    FEM_LAUNCH(F_RASTER, s, k_raster_small<R_IMG>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv,
+               (const float2*)nullptr, (const float*)nullptr, m->N, m->T, (double*)nullptr,
+               (unsigned long long*)nullptr, u, owner);
     return FEM_OK;
 }
 
@@ -337,12 +450,18 @@ fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s) {
                    (int)m->item_tri.n, m->partial.p, (float*)nullptr, (int*)nullptr);
         FEM_LAUNCH(F_RASTER, s, k_finalize<6>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
                    m->loc.p);
+        FEM_LAUNCH(F_RASTER, s, k_raster_small<R_MASS>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p,
+                   (const double*)nullptr, (const float2*)nullptr, (const float*)nullptr, m->N, m->T, m->loc.p,
+                   (unsigned long long*)nullptr, (float*)nullptr, (int*)nullptr);
     } else {
         FEM_LAUNCH(F_RASTER, s, k_raster<R_SCAT>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
                    (const double*)nullptr, (const float2*)nullptr, r, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p,
                    (float*)nullptr, (int*)nullptr);
         FEM_LAUNCH(F_RASTER, s, k_finalize<3>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
                    m->loc.p);
+        FEM_LAUNCH(F_RASTER, s, k_raster_small<R_SCAT>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p,
+                   (const double*)nullptr, (const float2*)nullptr, r, m->N, m->T, m->loc.p,
+                   (unsigned long long*)nullptr, (float*)nullptr, (int*)nullptr);
     }
     return FEM_OK;
 }
@@ -361,6 +480,9 @@ fem_status raster_errors_scratch(const int4* tri, const int2* vxy, int T, int N,
                w.item_tri, w.item_off, n_items_dev, w.item_cap, w.partial, (float*)nullptr, (int*)nullptr);
     FEM_LAUNCH(F_RASTER, s, k_finalize_err, blocks, 256, 0, w.item_cnt, w.item_off, (const float2*)w.partial, T, tri,
                vxy, err_out, (unsigned long long*)nullptr);
+    FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, std::max(1, std::min(blocks, w.grid / 2)), 256, 0, (const int*)nullptr,
+               tri, vxy, uv, (const float2*)nullptr, f, N, T, err_out, (unsigned long long*)nullptr, (float*)nullptr,
+               (int*)nullptr);
     return FEM_OK;
 }
 

@@ -15,6 +15,7 @@
 // the flags [gen-1 bisections | gen-2 of kept children | gen-2 of new
 // children] gives every new triangle its id in (generation, parent id) order.
 #include <cmath>
+#include <utility>
 
 #include "fem_internal.cuh"
 
@@ -408,6 +409,57 @@ __global__ void k_bisect(int4* __restrict__ tri, const int2* __restrict__ vxy, i
     tri[id1] = fresh;
 }
 
+// Space-filling (Sierpinski) order of the triangles.  A newest-vertex
+// bisection mesh is the leaf set of a binary tree whose natural traversal is
+// a continuous curve: each triangle is entered at one end of its refinement
+// edge and left at the other, and its two children are visited in the order
+// that keeps the curve continuous.  With the two initial triangles entered at
+// a, the entry end depends only on the triangle's type: right-angle legs
+// along the axes -> entered at a, legs along the diagonals -> entered at b.
+// When a triangle entered at a is bisected, (c,a,m) comes first and both
+// children are entered at their b; entered at b, (b,c,m) comes first and both
+// are entered at their a.  order[] lists triangle ids along the curve;
+// refinement replaces each triangle by its children in curve order.
+__device__ __forceinline__ int entered_at_b(int2 a, int2 c) { return (c.x != a.x && c.y != a.y) ? 1 : 0; }
+
+__global__ void k_order_count(const int* __restrict__ order, const int* __restrict__ flags, int T,
+                              int* __restrict__ cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    int t = order[i];
+    cnt[i] = 1 + flags[t] + flags[T + t] + flags[2 * T + t];
+}
+
+// runs before k_bisect: reads the parents' geometry
+__global__ void k_order_expand(const int* __restrict__ order, const int* __restrict__ off,
+                               const int* __restrict__ flags, const int* __restrict__ fscan,
+                               const int4* __restrict__ tri, const int2* __restrict__ vxy, int T,
+                               int* __restrict__ order_new) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    int t = order[i];
+    int o = off[i];
+    if (!flags[t]) {
+        order_new[o] = t;
+        return;
+    }
+    int4 tr = tri[t];
+    int d = entered_at_b(vxy[tr.x], vxy[tr.z]);
+    int kept = t, fresh = T + fscan[t];
+    int e2 = flags[T + t], e1 = flags[2 * T + t];
+    int kn = e2 ? T + fscan[T + t] : -1;      // second child of (c,a,m)
+    int nn = e1 ? T + fscan[2 * T + t] : -1;  // second child of (b,c,m)
+    if (d == 0) {
+        // (c,a,m) part then (b,c,m) part; children are entered at b
+        if (e2) { order_new[o++] = kn; order_new[o++] = kept; } else { order_new[o++] = kept; }
+        if (e1) { order_new[o++] = nn; order_new[o++] = fresh; } else { order_new[o++] = fresh; }
+    } else {
+        // (b,c,m) part then (c,a,m) part; children are entered at a
+        if (e1) { order_new[o++] = fresh; order_new[o++] = nn; } else { order_new[o++] = fresh; }
+        if (e2) { order_new[o++] = kept; order_new[o++] = kn; } else { order_new[o++] = kept; }
+    }
+}
+
 static int coop_grid(const void* func, int threads, int work, int num_sms) {
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, 0);
@@ -500,6 +552,14 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
                N, V, m->vxy.p, m->mask.p, nmask_new);
     FEM_LAUNCH(F_REFINE, s, k_bisect_flags, tb, 256, 0, m->tri.p, m->vxy.p, T, N, m->bmM.p, m->flags.p);
     FEM_TRY(scan_i32(m, m->flags.p, m->fscan.p, 3 * T, s, ntri));
+    // curve order of the refined mesh (before k_bisect overwrites the parents)
+    FEM_TRY(ensure(m->ocnt, (size_t)T + 1, s));
+    FEM_TRY(ensure(m->ooff, (size_t)T + 1, s));
+    FEM_TRY(ensure(m->order_tmp, (size_t)4 * T, s));
+    FEM_LAUNCH(F_REFINE, s, k_order_count, tb, 256, 0, m->order.p, m->flags.p, T, m->ocnt.p);
+    FEM_TRY(scan_i32(m, m->ocnt.p, m->ooff.p, T, s, nullptr));
+    FEM_LAUNCH(F_REFINE, s, k_order_expand, tb, 256, 0, m->order.p, m->ooff.p, m->flags.p, m->fscan.p, m->tri.p,
+               m->vxy.p, T, m->order_tmp.p);
     FEM_LAUNCH(F_REFINE, s, k_bisect, tb, 256, 0, m->tri.p, m->vxy.p, T, N, m->bmM.p, (const int*)m->wpre.p, V,
                m->flags.p, m->fscan.p, m->uv.p);
     // read back k, sweeps, new counts, margin, error
@@ -523,6 +583,7 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
     if (k_out) *k_out = k;
     if (margin_out) *margin_out = mg;
     if (k > 0) {
+        std::swap(m->order, m->order_tmp);
         m->V = V + nn;
         m->T = T + nt;
         m->nK += nkm;

@@ -227,3 +227,23 @@ def test_bounded_wait_reports_timeout(fem):
     m = fem.Mesh(33)
     u = m.inpaint(torch.full((4,), 0.5, device="cuda"))
     assert torch.allclose(u, torch.full_like(u, 0.5))
+
+
+@pytest.mark.parametrize("N,density,frac", [(129, 0.1, 0.01), (513, 0.03, 0.01)])
+def test_curve_order_is_continuous(fem, N, density, frac):
+    """The triangles' visiting order after refinement is the bisection tree's
+    space-filling curve: a permutation in which each triangle is left at the
+    vertex where the next one is entered (axis-aligned legs: entered at a,
+    left at b; diagonal legs: entered at b, left at a)."""
+    f = torch.from_numpy(S.make_image(N, 3)).cuda()
+    m = fem.Mesh(N)
+    m.spatial_refine(f, density, fem.params(topk_frac=frac))
+    order, is_curve = fem.fem_mesh_curve_order(m.h)
+    xy, tri, _ = m.export()
+    assert is_curve and np.array_equal(np.sort(order), np.arange(m.T))
+    a, b, c = tri[order, 0], tri[order, 1], tri[order, 2]
+    diag = (xy[c, 0] != xy[a, 0]) & (xy[c, 1] != xy[a, 1])
+    entry = np.where(diag, b, a)
+    exit_ = np.where(diag, a, b)
+    assert (exit_[:-1] == entry[1:]).all()
+    assert entry[0] == 0 and exit_[-1] == 0  # the curve starts and ends at the corner (0, 0)
