@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check after timing")
     ap.add_argument("--ncu-step", action="store_true",
                     help="for ncu launch lists: one warm-up step, then exactly one step, no timing output")
+    ap.add_argument("--serve", action="store_true",
+                    help="configuration 5: serving with continuous batching (closed loop, then Poisson arrivals)")
+    ap.add_argument("--requests", type=int, default=512)
+    ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--solve-micro", action="store_true",
                     help="time the Laplace solve alone on the refined mesh (FP32-IR and FP64), 20 solves each")
     a = ap.parse_args()
@@ -500,6 +504,89 @@ def run_reference(a, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ serving
+def _make_image_job(args):
+    import seeded_inputs
+    n, seed = args
+    return n, seed, seeded_inputs.make_image(n, seed)
+
+
+def run_serving(a, world, rank):
+    """Configuration 5: requests with side drawn from {257, 513, 1025, 2049}
+    and density from U[2 %, 10 %], each a spatial + tonal optimisation of a
+    seeded image, served by fem_server (continuous batching, admission by
+    device memory).  Closed loop first (all requests at once) for the
+    saturated throughput, then Poisson arrivals at 0.8x and 0.5x of it."""
+    import numpy as np
+    from concurrent.futures import ProcessPoolExecutor
+    import multiprocessing as mp
+    if rank != 0:
+        return
+    R = a.requests
+    rng = np.random.default_rng(4)
+    sides = rng.choice([257, 513, 1025, 2049], size=R)
+    dens = rng.uniform(0.02, 0.10, size=R)
+    pool_n = 8
+    jobs = [(int(n), int(n) * 1000 + j) for n in (257, 513, 1025, 2049) for j in range(pool_n)]
+    with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4), mp_context=mp.get_context("spawn")) as ex:
+        images = {(n, sd): img for n, sd, img in ex.map(_make_image_job, jobs)}
+
+    def image(i):
+        n = int(sides[i])
+        return images[(n, n * 1000 + i % pool_n)]
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2105_01586_gb300 as fem
+    from paper_2105_01586_gb300.serving import Server
+    torch.cuda.init()
+    p = fem.params(tonal_tol=1e-6)
+    mpx = float(np.sum(sides.astype(np.float64) ** 2)) / 1e6
+
+    def run(arrivals):
+        with Server(slots=a.slots) as sv:
+            t0 = time.perf_counter()
+            ids = []
+            for i in range(R):
+                if arrivals is not None:
+                    dt = arrivals[i] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                ids.append(sv.submit(image(i), float(dens[i]), p))
+            res = []
+            for rid in ids:
+                sv.wait(rid)
+                res.append(sv.result(rid))
+                sv.release(rid)
+        lat = np.array([r["t_end"] - r["t_submit"] for r in res]) * 1e3
+        span = max(r["t_end"] for r in res) - min(r["t_submit"] for r in res)
+        bad = sum(1 for r in res if r["status"] not in (0, 4))
+        return {"requests": R, "makespan_s": round(span, 3), "mpixel_per_s": round(mpx / span, 3),
+                "requests_per_s": round(R / span, 3), "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                "p99_ms": round(float(np.percentile(lat, 99)), 2), "failed": bad}
+
+    # warm-up: one request of each size
+    with Server(slots=4) as sv:
+        for n in (257, 513, 1025, 2049):
+            rid = sv.submit(images[(n, n * 1000)], 0.05, p)
+            sv.wait(rid)
+    closed = run(None)
+    lam = closed["requests_per_s"]
+    out = {"closed_loop": closed}
+    for load in (0.8, 0.5):
+        arr = np.cumsum(np.random.default_rng(7).exponential(1.0 / (load * lam), size=R))
+        out[f"poisson_{load}"] = run(arr)
+    main = out["poisson_0.8"]
+    line = {"metric": "serving Mpixel/s and p50/p99 latency (Poisson arrivals at 0.8x saturated throughput)",
+            "value": main["mpixel_per_s"], "unit": "Mpixel/s", "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
+            "n_gpus": 1, "higher_is_better": True, "dtype": "fp32+fp64", "data": "synthetic",
+            "config": {"workload": f"{R} requests, side from {{257,513,1025,2049}}, density U[2%,10%], spatial + "
+                                   f"tonal (tol 1e-6) each", "slots": a.slots, "config_index": 5},
+            "runs": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     world, rank, local = dist_setup()
@@ -507,6 +594,8 @@ def main():
         a.warmup = 3
     if a.impl == "reference":
         run_reference(a, world, rank)
+    elif a.serve:
+        run_serving(a, world, rank)
     else:
         run_ours(a, world, rank, local)
 

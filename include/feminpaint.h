@@ -37,11 +37,14 @@
 #define FEM_API
 #endif
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
 
 typedef struct fem_mesh fem_mesh;
+typedef struct fem_server fem_server;
 
 typedef enum {
     FEM_OK = 0,
@@ -201,6 +204,50 @@ FEM_API fem_status fem_tonal_opt(fem_mesh *m, const float *f_dev, float *g_dev, 
  *   r_dev    in : width*height float32 pixel co-vector
  *   gbar_dev out: nmask float32 */
 FEM_API fem_status fem_adjoint(fem_mesh *m, const float *r_dev, float *gbar_dev, const fem_params *p, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Serving: continuous batching of whole data-optimisation jobs (configuration
+ * 5 of the benchmarks; the paper has no serving layer).  A server owns
+ * `slots` worker threads, each with its own CUDA stream on the current
+ * device.  Requests wait in a FIFO queue; the head request is admitted when a
+ * slot is free and its estimated device memory fits next to the running
+ * requests within `mem_budget_bytes` (0 = half of the free device memory; a
+ * request larger than the budget runs alone).  An admitted request runs the
+ * whole path on its slot's stream: fem_mesh_create, fem_spatial_refine,
+ * fem_gather_mask, fem_tonal_opt and the result read-back.  Requests in
+ * different slots overlap on the device; each computes exactly what it
+ * computes alone (deterministic kernels, no shared state between meshes).
+ * --------------------------------------------------------------------- */
+
+/* Start the worker threads.  *out receives the handle. */
+FEM_API fem_status fem_server_create(int slots, size_t mem_budget_bytes, fem_server **out);
+
+/* Queue one job: the width x width float32 image at f_host (copied before
+ * the call returns), the vertex density for fem_spatial_refine and the
+ * parameters for both optimisations (NULL = defaults).  *id_out receives the
+ * request id. */
+FEM_API fem_status fem_server_submit(fem_server *sv, int width, const float *f_host, double density,
+                                     const fem_params *p, long long *id_out);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a request; *done = 1 when
+ * it has finished (successfully or not). */
+FEM_API fem_status fem_server_wait(fem_server *sv, long long id, double timeout_s, int *done);
+
+/* Results of a finished request (host buffers, any may be NULL):
+ * sizes[4] = V, T, nmask, width; xy (2V), tri (3T), is_mask (V) as in
+ * fem_mesh_export; g (nmask float32, the tonally optimised values);
+ * times[8] = submit, start and end time (seconds, steady clock), spatial
+ * rounds, spatial CG iterations, tonal iterations, tonal relative residual,
+ * estimated device bytes.  Query the sizes first with NULL arrays.  Returns
+ * the request's own status (FEM_E_NOT_CONVERGED if the tonal cap was hit). */
+FEM_API fem_status fem_server_result(fem_server *sv, long long id, int *sizes, int *xy, int *tri,
+                                     unsigned char *is_mask, float *g, double *times);
+
+/* Drop a finished request's results. */
+FEM_API fem_status fem_server_release(fem_server *sv, long long id);
+
+/* Finish the queued work, stop the workers and free the server. */
+FEM_API fem_status fem_server_destroy(fem_server *sv);
 
 /* Counters of the last inpaint / refine / tonal / adjoint call on m. */
 FEM_API fem_status fem_mesh_stats(const fem_mesh *m, fem_stats *out);

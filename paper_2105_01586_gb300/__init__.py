@@ -46,7 +46,8 @@ _STATUS = {0: "FEM_OK", 1: "FEM_E_INVALID", 2: "FEM_E_SHAPE", 3: "FEM_E_OOM", 4:
 EXPORTED = ["fem_params_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_info", "fem_mesh_export",
             "fem_mesh_import", "fem_mesh_curve_order", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_triangle_errors_noalloc", "fem_rasterize", "fem_spatial_refine",
             "fem_tonal_opt", "fem_adjoint", "fem_mesh_stats", "fem_last_error", "fem_profile_enable",
-            "fem_profile_read", "fem_launch_count", "fem_selftest_wait_timeout"]
+            "fem_profile_read", "fem_launch_count", "fem_selftest_wait_timeout", "fem_server_create",
+            "fem_server_submit", "fem_server_wait", "fem_server_result", "fem_server_release", "fem_server_destroy"]
 
 
 class fem_params(ctypes.Structure):
@@ -88,6 +89,12 @@ _sig = {
                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_char_p)]),
     "fem_launch_count": (ctypes.c_longlong, []),
     "fem_selftest_wait_timeout": (_i, [_vp]),
+    "fem_server_create": (_i, [_i, ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "fem_server_submit": (_i, [_vp, _i, _vp, ctypes.c_double, _pp, ctypes.POINTER(ctypes.c_longlong)]),
+    "fem_server_wait": (_i, [_vp, ctypes.c_longlong, ctypes.c_double, _ip]),
+    "fem_server_result": (_i, [_vp, ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "fem_server_release": (_i, [_vp, ctypes.c_longlong]),
+    "fem_server_destroy": (_i, [_vp]),
 }
 for _n, (_r, _a) in _sig.items():
     _f = getattr(_lib, _n)

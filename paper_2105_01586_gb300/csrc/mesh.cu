@@ -98,13 +98,12 @@ void dfree_raw(void* p, cudaStream_t s) {
 }
 
 int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
+    static const int n = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
     return n;
 }
 
@@ -245,8 +244,6 @@ __global__ void k_scan_lookback(const int* __restrict__ in, int* __restrict__ ou
     for (int i = 0; i < SCAN_IPT; ++i)
         if (first + i < n) out[first + i] = v[i] + pre;
 }
-
-static std::mutex g_scan_mu;
 
 // out[i] = sum of in[0..i-1]; *total_dev (if non-null) = sum of all (one launch)
 fem_status scan_i32(fem_mesh* m, const int* in, int* out, int n, cudaStream_t s, int* total_dev) {

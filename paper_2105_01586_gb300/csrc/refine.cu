@@ -520,12 +520,12 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
     A.red = m->red.p;
     A.out_margin = margin;
     if (T <= kTopkBlockMaxT && m->keyc.p && m->keyc.n >= (size_t)T) {
-        static bool attr_set = false;
-        if (!attr_set) {
-            FEM_CUDA(cudaFuncSetAttribute(k_topk_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)kTopkBlockSmem));
-            attr_set = true;
-        }
+        // set once per process (thread-safe static initialisation); a failure shows at the launch
+        static const bool attr_set = [] {
+            return cudaFuncSetAttribute(k_topk_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kTopkBlockSmem) == cudaSuccess;
+        }();
+        (void)attr_set;
         FEM_LAUNCH(F_TOPK, s, k_topk_block, 1, kTopkBlockThreads, kTopkBlockSmem, m->keyc.p, T, frac, vstar - V,
                    kdev, thr, margin);
     } else {

@@ -988,15 +988,16 @@ fail:
     }
 }
 
+static int occupancy(const void* func, int threads) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, 0);
+    return nb > 0 ? nb : 1;
+}
+
 static int coop_blocks(const void* func, int n, int num_sms) {
-    static int occ[2] = {0, 0};
-    int which = func == (const void*)k_solve<true> ? 1 : 0;
-    if (!occ[which]) {
-        int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, kSolveThreads, 0);
-        occ[which] = nb > 0 ? nb : 1;
-    }
-    int maxb = occ[which] * num_sms;
+    static const int occ64 = occupancy((const void*)k_solve<true>, kSolveThreads);
+    static const int occ32 = occupancy((const void*)k_solve<false>, kSolveThreads);
+    int maxb = (func == (const void*)k_solve<true> ? occ64 : occ32) * num_sms;
     int want = (n + 4 * kSolveThreads - 1) / (4 * kSolveThreads);
     if (want < 1) want = 1;
     return want < maxb ? want : maxb;
@@ -1055,12 +1056,11 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
     A.acc = deferred ? m->dscal.p + 64 : nullptr;
     FEM_CUDA(cudaMemsetAsync(m->dflag.p + 1, 0, sizeof(int), s));
     if (!use_fp64 && nU <= kBlockMaxRows) {
-        static bool attr_set = false;
-        if (!attr_set) {
-            FEM_CUDA(cudaFuncSetAttribute(k_solve_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          kBlockSmemBytes));
-            attr_set = true;
-        }
+        static const bool attr_set = [] {
+            return cudaFuncSetAttribute(k_solve_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kBlockSmemBytes) == cudaSuccess;
+        }();
+        (void)attr_set;
         FEM_TRY(ensure(m->bvec, (size_t)5 * nU, s));
         FEM_TRY(ensure(m->browptr, (size_t)nU + 1, s));
         FEM_TRY(ensure(m->bent, (size_t)8 * nU, s));
@@ -1070,11 +1070,7 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
         BlockScratch G{m->bvec.p, m->browptr.p, m->bent.p, m->bdg2.p, m->bxff.p, m->bbff.p};
         FEM_LAUNCH(F_CG, s, k_solve_block, 1, kSingleThreads, (size_t)kBlockSmemBytes, A, G, kBlockSmemBytes);
     } else if (!use_fp64) {
-        static int occ = 0;
-        if (!occ) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_grid, kGridThreads, 0);
-            if (occ < 1) occ = 1;
-        }
+        static const int occ = occupancy((const void*)k_solve_grid, kGridThreads);
         int gb = (nU + 2 * kGridThreads - 1) / (2 * kGridThreads);
         gb = std::max(1, std::min(gb, occ * m->num_sms));
         FEM_TRY(ensure(m->red, (size_t)4 * gb + 8, s));

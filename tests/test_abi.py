@@ -64,3 +64,20 @@ def test_product_path_does_not_import_oracle():
             if fn.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dp, fn)).read()
                 assert "import oracle" not in txt and "oracle." not in txt, fn
+
+
+def test_server_entry_points_reject_bad_handles_on_the_host(fem):
+    """The serving calls marshal their arguments and reject a null server
+    before any CUDA work (runs without a GPU)."""
+    import numpy as np
+    sizes = np.zeros(4, np.int32)
+    f = np.zeros((5, 5), np.float32)
+    rid = ctypes.c_longlong()
+    done = ctypes.c_int()
+    assert fem._lib.fem_server_submit(None, 5, f.ctypes.data, 0.5, None, ctypes.byref(rid)) == fem.FEM_E_INVALID
+    assert fem._lib.fem_server_wait(None, 1, 0.0, ctypes.byref(done)) == fem.FEM_E_INVALID
+    assert fem._lib.fem_server_result(None, 1, sizes.ctypes.data, None, None, None, None, None) == fem.FEM_E_INVALID
+    assert fem._lib.fem_server_release(None, 1) == fem.FEM_E_INVALID
+    assert fem._lib.fem_server_destroy(None) == fem.FEM_OK
+    out = ctypes.c_void_p()
+    assert fem._lib.fem_server_create(0, 0, ctypes.byref(out)) == fem.FEM_E_INVALID
