@@ -210,7 +210,15 @@ struct fem_mesh {
     fem::DArr<int> ucnt;            // nU used ELL slots per row
     fem::DArr<float> dinv32;        // nU inverse diagonal
     fem::DArr<double> dinv64;
-    fem::DArr<int> urow_vertex;     // nU: vertex of each U row
+    fem::DArr<int> urow_vertex;     // nU: vertex of each U row (rows numbered by component)
+    // components of the unknown-vertex graph (components.cu)
+    fem::DArr<int> cc_parent, cc_root, cc_size, cc_fill, cc_cstart;
+    fem::DArr<int> rowcomp;     // nU: rows of the component starting at this row, else 0
+    fem::DArr<int> blk_list;    // first rows of the components above one warp
+    fem::DArr<int> warp_list;   // first rows of the components of 2..32 rows
+    fem::DArr<int> ccount;      // CC_* counters
+    fem::DArr<int> c_iters, c_nres, c_status;  // per-component solve results, at the first row
+    fem::DArr<double> c_rr, c_bb;
     fem::DArr<int> kvert;           // nK: vertex of each K index
     // CG work
     fem::DArr<double> x64, b64, r64, p64, q64, z64;
@@ -245,9 +253,23 @@ struct fem_mesh {
 };
 
 namespace fem {
+// component sizes: up to kWarpComp rows a warp solves the component, up to
+// kBlockComp a block; a larger component sends the whole system to the
+// grid-wide solver
+constexpr int kWarpComp = 32;
+constexpr int kBlockComp = 1024;
+// counters of the component search (fem_mesh::ccount)
+enum CcCounter { CC_NWARP = 0, CC_NROWS = 1, CC_NBLK = 2, CC_NBIG = 3, CC_ERR = 4, CC_WORK = 5, CC_DONE = 6,
+                 CC_COUNTERS = 16 };
+fem_status build_components(fem_mesh* m, cudaStream_t s);
+fem_status solve_components(fem_mesh* m, const double* b, double* x, bool use_fp64, double tol, int maxit,
+                            bool deferred, cudaStream_t s);
+
 // helpers implemented in the .cu files
 fem_status exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, int* total_dev);
 fem_status scan_i32(fem_mesh* m, const int* in, int* out, int n, cudaStream_t s, int* total_dev);
+fem_status scan_component_rows(fem_mesh* m, const unsigned char* mask, const int* root, const int* size, int* out,
+                               int n, cudaStream_t s, int* total_dev);
 fem_status build_system(fem_mesh* m, cudaStream_t s);
 fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cudaStream_t s,
                          int* iters_out, double* relres_out, bool deferred = false);

@@ -199,7 +199,20 @@ __device__ __forceinline__ unsigned long long pack_status(unsigned epoch, unsign
     return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | (unsigned)value;
 }
 
-__global__ void k_scan_lookback(const int* __restrict__ in, int* __restrict__ out, int n, int* __restrict__ total,
+// Scan input: in[i], or (when root is set) the component size at a root
+// vertex and 0 elsewhere: !mask[i] && root[i] == i ? size[i] : 0.
+struct ScanIn {
+    const int* in;
+    const unsigned char* mask;
+    const int* root;
+    const int* size;
+    __device__ __forceinline__ int operator()(long long i) const {
+        if (!root) return in[i];
+        return (!mask[i] && root[i] == (int)i) ? size[i] : 0;
+    }
+};
+
+__global__ void k_scan_lookback(ScanIn in, int* __restrict__ out, int n, int* __restrict__ total,
                                 unsigned long long* __restrict__ status, unsigned long long* __restrict__ ctr,
                                 unsigned long long base, unsigned epoch, int* __restrict__ err) {
     __shared__ int s_tile, s_prefix;
@@ -209,34 +222,51 @@ __global__ void k_scan_lookback(const int* __restrict__ in, int* __restrict__ ou
     int v[SCAN_IPT];
     long long first = (long long)tile * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
 #pragma unroll
-    for (int i = 0; i < SCAN_IPT; ++i) v[i] = (first + i < n) ? in[first + i] : 0;
+    for (int i = 0; i < SCAN_IPT; ++i) v[i] = (first + i < n) ? in(first + i) : 0;
     int agg = block_exclusive_scan(v);
-    if (threadIdx.x == 0) {
+    // look-back by the first warp, 32 predecessors per step: lane i reads
+    // the status of tile (p - i); the window is summed up to the nearest
+    // tile that already holds its inclusive prefix
+    if (threadIdx.x < 32) {
+        const unsigned FULL = 0xffffffffu;
+        const int lane = threadIdx.x;
         int prefix = 0;
         if (tile == 0) {
-            st_release_u64(&status[0], pack_status(epoch, 2, agg));
+            if (lane == 0) st_release_u64(&status[0], pack_status(epoch, 2, agg));
         } else {
-            st_release_u64(&status[tile], pack_status(epoch, 1, agg));
+            if (lane == 0) st_release_u64(&status[tile], pack_status(epoch, 1, agg));
             int p = tile - 1;
             unsigned long long t0 = globaltimer_ns();
+            bool timed_out = false;
             while (p >= 0) {
-                unsigned long long w = ld_acquire_u64(&status[p]);
+                int q = p - lane;
+                unsigned long long w = q >= 0 ? ld_acquire_u64(&status[q]) : pack_status(epoch, 2, 0);
                 unsigned ep = (unsigned)(w >> 34), flag = (unsigned)(w >> 32) & 3u;
-                if (ep != epoch || flag == 0) {
-                    if (globaltimer_ns() - t0 > kLookbackLimitNs) {
-                        atomicCAS(err, 0, (int)FEM_E_TIMEOUT);
-                        break;
-                    }
+                bool ready = ep == epoch && flag != 0;
+                // wait until every tile of the window up to the first
+                // inclusive one has published
+                unsigned incl = __ballot_sync(FULL, ready && flag == 2);
+                unsigned notready = __ballot_sync(FULL, !ready);
+                int stop = incl ? __ffs(incl) - 1 : 32;  // lanes 0..stop are summed
+                unsigned need = stop == 32 ? FULL : (stop == 31 ? FULL : ((2u << stop) - 1u));
+                if (notready & need) {
+                    // the decision to give up is taken by the whole warp
+                    bool late = globaltimer_ns() - t0 > kLookbackLimitNs;
+                    if (__any_sync(FULL, late)) { timed_out = true; break; }
                     continue;
                 }
-                prefix += (int)(unsigned)w;
-                if (flag == 2) break;
-                --p;
+                int val = lane <= stop ? (int)(unsigned)w : 0;
+                prefix += warp_sum(val);
+                if (stop < 32) break;
+                p -= 32;
             }
-            st_release_u64(&status[tile], pack_status(epoch, 2, prefix + agg));
+            if (timed_out && lane == 0) atomicCAS(err, 0, (int)FEM_E_TIMEOUT);
+            if (lane == 0) st_release_u64(&status[tile], pack_status(epoch, 2, prefix + agg));
         }
-        s_prefix = prefix;
-        if ((long long)(tile + 1) * SCAN_TILE >= n && total) *total = prefix + agg;
+        if (lane == 0) {
+            s_prefix = prefix;
+            if ((long long)(tile + 1) * SCAN_TILE >= n && total) *total = prefix + agg;
+        }
     }
     __syncthreads();
     int pre = s_prefix;
@@ -245,8 +275,20 @@ __global__ void k_scan_lookback(const int* __restrict__ in, int* __restrict__ ou
         if (first + i < n) out[first + i] = v[i] + pre;
 }
 
+static fem_status scan_lookback(fem_mesh* m, ScanIn in, int* out, int n, cudaStream_t s, int* total_dev);
+
 // out[i] = sum of in[0..i-1]; *total_dev (if non-null) = sum of all (one launch)
 fem_status scan_i32(fem_mesh* m, const int* in, int* out, int n, cudaStream_t s, int* total_dev) {
+    return scan_lookback(m, ScanIn{in, nullptr, nullptr, nullptr}, out, n, s, total_dev);
+}
+
+// out[v] = rows of the components whose root (smallest vertex) is below v
+fem_status scan_component_rows(fem_mesh* m, const unsigned char* mask, const int* root, const int* size, int* out,
+                               int n, cudaStream_t s, int* total_dev) {
+    return scan_lookback(m, ScanIn{nullptr, mask, root, size}, out, n, s, total_dev);
+}
+
+static fem_status scan_lookback(fem_mesh* m, ScanIn in, int* out, int n, cudaStream_t s, int* total_dev) {
     if (n <= 0) {
         if (total_dev) FEM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int), s));
         return FEM_OK;
@@ -456,6 +498,8 @@ fem_status fem_mesh_create(int width, int height, void* stream, fem_mesh** out) 
         if (st) break;
         st = ensure(m->dcount, 64, s);
         if (st) break;
+        st = ensure(m->ccount, CC_COUNTERS, s);
+        if (st) break;
         cudaError_t e = cudaMallocHost(&m->host_stage, 1 << 16);
         if (e != cudaSuccess) { st = cuda_fail(e, "cudaMallocHost"); break; }
         e = cudaMemsetAsync(m->bar.p, 0, 64 * sizeof(unsigned), s);
@@ -524,6 +568,10 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->uidx, s); release(m->kidx, s); release(m->nbr, s); release(m->coefA, s); release(m->diagA, s);
     release(m->ucol, s); release(m->uval32, s); release(m->uval64, s); release(m->udiag, s); release(m->ucnt, s); release(m->dinv32, s); release(m->dinv64, s);
     release(m->urow_vertex, s); release(m->kvert, s);
+    release(m->cc_parent, s); release(m->cc_root, s); release(m->cc_size, s); release(m->cc_fill, s);
+    release(m->cc_cstart, s); release(m->rowcomp, s); release(m->blk_list, s); release(m->warp_list, s);
+    release(m->ccount, s);
+    release(m->c_iters, s); release(m->c_nres, s); release(m->c_status, s); release(m->c_rr, s); release(m->c_bb, s);
     release(m->x64, s); release(m->b64, s); release(m->r64, s); release(m->p64, s); release(m->q64, s); release(m->z64, s);
     release(m->r32, s); release(m->p32, s); release(m->q32, s); release(m->z32, s); release(m->d32, s);
     release(m->bvec, s); release(m->browptr, s); release(m->bent, s); release(m->bdg2, s);

@@ -56,13 +56,31 @@ __global__ void k_assemble(const int4* __restrict__ tri, const int2* __restrict_
     atomicAdd(&diag[b], 0.5f);
 }
 
-__global__ void k_unknown_flags(const unsigned char* __restrict__ mask, int V, int* __restrict__ flag) {
+// Unknown flags, and the start state of the component search
+// (components.cu): the parent of an unknown vertex is its smallest unknown
+// neighbour through a nonzero entry (or itself), which leaves most small
+// components with shallow trees before any hooking.
+__global__ void k_unknown_flags(const unsigned char* __restrict__ mask, const int* __restrict__ nbr,
+                                const float* __restrict__ coef, int V, int* __restrict__ flag,
+                                int* __restrict__ parent, int* __restrict__ size, int* __restrict__ fill) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < V) flag[i] = mask[i] ? 0 : 1;
+    if (i >= V) return;
+    int pa = i;
+    if (!mask[i]) {
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            int j = nbr[d * V + i];
+            if (j >= 0 && j < pa && coef[d * V + i] != 0.0f && !mask[j]) pa = j;
+        }
+    }
+    flag[i] = mask[i] ? 0 : 1;
+    parent[i] = pa;
+    size[i] = 0;
+    fill[i] = 0;
 }
 
 __global__ void k_index_maps(const unsigned char* __restrict__ mask, int V, int* __restrict__ uidx,
-                             int* __restrict__ kidx, int* __restrict__ urow_vertex, int* __restrict__ kvert) {
+                             int* __restrict__ kidx, int* __restrict__ kvert) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= V) return;
     int u = uidx[i];  // exclusive count of unknowns before i
@@ -72,8 +90,8 @@ __global__ void k_index_maps(const unsigned char* __restrict__ mask, int V, int*
         kvert[k] = i;
         uidx[i] = -1;
     } else {
+        // rows of unknowns are numbered by component (build_components)
         kidx[i] = -1;
-        urow_vertex[u] = i;
     }
 }
 
@@ -155,15 +173,19 @@ fem_status build_system(fem_mesh* m, cudaStream_t s) {
     FEM_LAUNCH(F_ASSEMBLY, s, k_assemble, (T + 255) / 256, 256, 0, m->tri.p, m->vxy.p, T, V, m->nbr.p, m->coefA.p,
                m->diagA.p);
     int vb = (V + 255) / 256;
-    FEM_LAUNCH(F_ASSEMBLY, s, k_unknown_flags, vb, 256, 0, m->mask.p, V, m->flags.p);
+    FEM_TRY(ensure(m->cc_parent, V, s));
+    FEM_TRY(ensure(m->cc_size, V, s));
+    FEM_TRY(ensure(m->cc_fill, V, s));
+    FEM_LAUNCH(F_ASSEMBLY, s, k_unknown_flags, vb, 256, 0, m->mask.p, m->nbr.p, m->coefA.p, V, m->flags.p,
+               m->cc_parent.p, m->cc_size.p, m->cc_fill.p);
     int* nU_dev = m->dcount.p + 1;
     FEM_TRY(scan_i32(m, m->flags.p, m->uidx.p, V, s, nU_dev));
-    FEM_LAUNCH(F_ASSEMBLY, s, k_index_maps, vb, 256, 0, m->mask.p, V, m->uidx.p, m->kidx.p, m->urow_vertex.p,
-               m->kvert.p);
+    FEM_LAUNCH(F_ASSEMBLY, s, k_index_maps, vb, 256, 0, m->mask.p, V, m->uidx.p, m->kidx.p, m->kvert.p);
     // the mask count is kept on the host by create / import / refinement, so
     // the unknown count needs no read-back
     int nU = V - m->nK;
     m->nU = nU;
+    FEM_TRY(build_components(m, s));
     size_t n = nU > 0 ? nU : 1;
     FEM_TRY(ensure(m->ucol, 8 * n, s));
     FEM_TRY(ensure(m->uval32, 8 * n, s));
@@ -208,7 +230,14 @@ struct SolveArgs {
     double* acc;       // optional running totals (see solve_accumulate)
     double bytes_it;   // algorithmic bytes per CG iteration (for acc)
     double bytes_res;  // algorithmic bytes per residual pass (for acc)
+    const int* gate;   // optional: the component counters (CC_*); see gate_closed
 };
+
+// whole-system kernels launched behind the component solve return at once
+// unless some component is too large for it (and the search succeeded)
+__device__ __forceinline__ bool gate_closed(const SolveArgs& A) {
+    return A.gate && (A.gate[CC_NBIG] == 0 || A.gate[CC_ERR] != 0);
+}
 
 // Running totals of solves whose results are not read back one by one:
 // acc[0] CG iterations, [1] largest relative residual, [2] first failing
@@ -539,6 +568,8 @@ done:
         A.out[1] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
         A.out[2] = status;
         A.out[3] = n_res;
+        A.out[4] = (double)total_it * A.n;
+        A.out[5] = (double)n_res * A.n;
         solve_accumulate(A, total_it, A.out[1], status, n_res);
     }
     return;
@@ -548,17 +579,21 @@ fail:
         A.out[1] = -1.0;
         A.out[2] = FEM_E_TIMEOUT;
         A.out[3] = n_res;
+        A.out[4] = (double)total_it * A.n;
+        A.out[5] = (double)n_res * A.n;
         solve_accumulate(A, total_it, 1.0, FEM_E_TIMEOUT, n_res);
     }
 }
 
 template <bool FP64_ONLY>
 __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs A) {
+    if (gate_closed(A)) return;
     solve_body<FP64_ONLY, GridSync>(A);
 }
 
 template <bool FP64_ONLY>
 __global__ void __launch_bounds__(kSingleThreads) k_solve_single(SolveArgs A) {
+    if (gate_closed(A)) return;
     solve_body<FP64_ONLY, BlockSync>(A);
 }
 
@@ -760,6 +795,8 @@ __device__ __forceinline__ void block_solve_core(const SolveArgs& A, const Block
         A.out[1] = bb > 0.f ? sqrt((double)rr / (double)bb) : 0.0;
         A.out[2] = status;
         A.out[3] = n_res;
+        A.out[4] = (double)total_it * A.n;
+        A.out[5] = (double)n_res * A.n;
         solve_accumulate(A, total_it, A.out[1], status, n_res);
     }
 }
@@ -770,6 +807,7 @@ __global__ void __launch_bounds__(kSingleThreads) k_solve_block(SolveArgs A, Blo
     __shared__ float s_lut[17];
     __shared__ int s_wsum[kSingleThreads / 32];
     __shared__ float s_bmax[kSingleThreads / 32];
+    if (gate_closed(A)) return;
     const int n = A.n, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid < 17) s_lut[tid] = tid ? 1.0f / (0.5f * (float)tid) : 0.0f;
     // number of off-diagonal entries, and max |b|
@@ -844,6 +882,7 @@ __device__ __forceinline__ bool grid_sum3(const SolveArgs& A, BlockRed& R, GridP
 
 __global__ void __launch_bounds__(kGridThreads) k_solve_grid(SolveArgs A, BlockScratch G) {
     __shared__ BlockRed R;
+    if (gate_closed(A)) return;
     GridPar P{0, 0};
     const int n = A.n, stride = gridDim.x * blockDim.x, tid0 = blockIdx.x * blockDim.x + threadIdx.x;
     float* d = G.vec;
@@ -975,6 +1014,8 @@ __global__ void __launch_bounds__(kGridThreads) k_solve_grid(SolveArgs A, BlockS
         A.out[1] = bb > 0.f ? sqrt((double)rr / (double)bb) : 0.0;
         A.out[2] = status;
         A.out[3] = n_res;
+        A.out[4] = (double)total_it * A.n;
+        A.out[5] = (double)n_res * A.n;
         solve_accumulate(A, total_it, A.out[1], status, n_res);
     }
     return;
@@ -984,6 +1025,8 @@ fail:
         A.out[1] = -1.0;
         A.out[2] = FEM_E_TIMEOUT;
         A.out[3] = n_res;
+        A.out[4] = (double)total_it * A.n;
+        A.out[5] = (double)n_res * A.n;
         solve_accumulate(A, total_it, 1.0, FEM_E_TIMEOUT, n_res);
     }
 }
@@ -1055,6 +1098,11 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
     A.bytes_res = (double)nU * (92.0 + (use_fp64 ? 0.0 : 36.0));
     A.acc = deferred ? m->dscal.p + 64 : nullptr;
     FEM_CUDA(cudaMemsetAsync(m->dflag.p + 1, 0, sizeof(int), s));
+    // Components of at most kBlockComp rows are solved independently, all at
+    // once; when a component is larger, that kernel returns at once and the
+    // whole-system solver below (gated on the same device counter) runs.
+    FEM_TRY(solve_components(m, b, x, use_fp64, tol, maxit, deferred, s));
+    A.gate = m->ccount.p;
     if (!use_fp64 && nU <= kBlockMaxRows) {
         static const bool attr_set = [] {
             return cudaFuncSetAttribute(k_solve_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1092,13 +1140,13 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
         return FEM_OK;
     }
     double* hs = (double*)m->host_stage;
-    FEM_CUDA(cudaMemcpyAsync(hs, m->dscal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaMemcpyAsync(hs, m->dscal.p, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));
     int its = (int)hs[0];
     double rel = hs[1];
     int st = (int)hs[2];
-    int nres = (int)hs[3];
-    note_bytes(F_CG, A.bytes_it * its + A.bytes_res * nres);
+    // bytes from row-iterations and row-residual passes (out[4], out[5])
+    note_bytes(F_CG, (use_fp64 ? 168.0 : 120.0) * hs[4] + (use_fp64 ? 92.0 : 128.0) * hs[5]);
     m->stats.cg_iters += its;
     m->stats.solves += 1;
     m->stats.relres = rel;
@@ -1108,6 +1156,10 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
         cudaMemsetAsync(m->bar.p, 0, 2 * sizeof(unsigned), s);
         set_error("Laplace solve: a grid barrier wait ran out");
         return FEM_E_TIMEOUT;
+    }
+    if (st == FEM_E_INVALID) {
+        set_error("Laplace solve: the component search of A_UU failed (unknown count does not match the mesh)");
+        return FEM_E_INVALID;
     }
     if (st != FEM_OK) {
         set_error("Laplace solve: iteration cap reached, relative residual " + std::to_string(rel));
@@ -1135,6 +1187,10 @@ fem_status solve_totals_read(fem_mesh* m, cudaStream_t s) {
         cudaMemsetAsync(m->bar.p, 0, 2 * sizeof(unsigned), s);
         set_error("Laplace solve: a grid barrier wait ran out");
         return FEM_E_TIMEOUT;
+    }
+    if (st == FEM_E_INVALID) {
+        set_error("Laplace solve: the component search of A_UU failed (unknown count does not match the mesh)");
+        return FEM_E_INVALID;
     }
     if (st != FEM_OK) {
         set_error("Laplace solve: iteration cap reached, largest relative residual " + std::to_string(hs[1]));
