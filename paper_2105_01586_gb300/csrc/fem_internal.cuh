@@ -185,6 +185,7 @@ struct fem_mesh {
 
     // rasterisation plan (valid for plan_T triangles of plan_version)
     fem::DArr<int> item_cnt, item_off, item_tri;
+    fem::DArr<int> item_done;  // T: items finished per triangle (fused finalisation), 0 between passes
     fem::DArr<double> partial;
     fem::DArr<double> keys;
     fem::DArr<unsigned long long> keyc;  // composite selection keys (eligible flag | key bits)

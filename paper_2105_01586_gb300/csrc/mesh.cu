@@ -561,6 +561,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->vxy, s); release(m->mask, s); release(m->tri, s); release(m->uv, s); release(m->uvf, s);
     release(m->order, s); release(m->order_tmp, s); release(m->ocnt, s); release(m->ooff, s);
     release(m->item_cnt, s); release(m->item_off, s); release(m->item_tri, s); release(m->partial, s);
+    release(m->item_done, s);
     release(m->keys, s);
     release(m->keyc, s);
     release(m->bmM, s); release(m->bmS, s); release(m->wpre, s);

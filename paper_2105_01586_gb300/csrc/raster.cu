@@ -117,6 +117,18 @@ __device__ __forceinline__ ff vertex_ff(const double* __restrict__ uv, const flo
     return ff_from_double(uv[i]);
 }
 
+// Sum of a triangle's item partials (float-float) by one warp in a fixed
+// order: lane j adds items j, j + 32, ...; then a butterfly.  All lanes
+// return the same value.
+__device__ __forceinline__ ff warp_sum_partials(const float2* partial, int o, int n) {
+    ff s{0.f, 0.f};
+    for (int j = (int)(threadIdx.x & 31); j < n; j += 32) {
+        float2 v = __ldcg(&partial[o + j]);
+        s = ff_add(s, ff{v.x, v.y});
+    }
+    return ff_warp_sum(s);
+}
+
 // Error and image modes evaluate the linear interpolant as a plane in
 // float-float, u(x, y) = u_c + g_x (x - c_x) + g_y (y - c_y), with g the
 // gradient ((a-c)(u_a-u_c) + (b-c)(u_b-u_c)) / |a-c|^2 (legs orthogonal and
@@ -128,7 +140,9 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
     const int4* __restrict__ tri, const int2* __restrict__ vxy, const double* __restrict__ uv,
     const float2* __restrict__ uvf, const float* __restrict__ img, int N, const int* __restrict__ item_tri,
     const int* __restrict__ item_off, const int* __restrict__ n_items_dev, int item_cap,
-    double* __restrict__ partial, float* __restrict__ u_out, int* __restrict__ owner_out) {
+    double* __restrict__ partial, float* __restrict__ u_out, int* __restrict__ owner_out,
+    const int* __restrict__ item_cnt = nullptr, int* __restrict__ item_done = nullptr,
+    double* __restrict__ key_out = nullptr, unsigned long long* __restrict__ keyc_out = nullptr) {
     constexpr int NA = NAcc<MODE>::n;
     constexpr bool FF = (MODE == R_ERR || MODE == R_IMG);
     const unsigned FULL = 0xffffffffu;
@@ -184,28 +198,43 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
 #pragma unroll
         for (int q = 0; q < (NA > 0 ? NA : 1); ++q) acc[q] = 0.0;
 
-        for (int base = 0; base < total; base += 32) {
-            int jj = base + lane;
-            int k = 0;
+        // pixels are taken kPre chunks of 32 at a time: positions and image
+        // values of all chunks first (kPre loads in flight per lane), then
+        // the arithmetic
+        constexpr int kPre = 4;
+        constexpr bool READS = (MODE == R_ERR || MODE == R_SCAT);
+        for (int base0 = 0; base0 < total; base0 += 32 * kPre) {
+            int px[kPre], py[kPre];
+            float fv[kPre];
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                int cand = k + step;
-                int oc = __shfl_sync(FULL, off, cand & 31);
-                if (cand < nr && oc <= jj) k = cand;
+            for (int u = 0; u < kPre; ++u) {
+                int jj = base0 + 32 * u + lane;
+                int k = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    int cand = k + step;
+                    int oc = __shfl_sync(FULL, off, cand & 31);
+                    if (cand < nr && oc <= jj) k = cand;
+                }
+                int Lk = __shfl_sync(FULL, L, k);
+                int okk = __shfl_sync(FULL, off, k);
+                px[u] = jj < total ? Lk + (jj - okk) : -1;
+                py[u] = r0 + k;
+                fv[u] = (READS && jj < total) ? img[(long long)py[u] * N + px[u]] : 0.f;
             }
-            int Lk = __shfl_sync(FULL, L, k);
-            int ok = __shfl_sync(FULL, off, k);
-            if (jj < total) {
-                int x = Lk + (jj - ok), y = r0 + k;
+#pragma unroll
+            for (int u = 0; u < kPre; ++u) {
+            if (px[u] >= 0) {
+                int x = px[u], y = py[u];
                 long long p = (long long)y * N + x;
                 if (FF) {
                     float dx = (float)(x - g.cx), dy = (float)(y - g.cy);
-                    ff u = ff_add(ff_add(uc, ff_mul_f(gx, dx)), ff_mul_f(gy, dy));
+                    ff u_ = ff_add(ff_add(uc, ff_mul_f(gx, dx)), ff_mul_f(gy, dy));
                     if (MODE == R_ERR) {
-                        ff d = ff_add_f(u, -img[p]);
+                        ff d = ff_add_f(u_, -fv[u]);
                         acc_ff = ff_add(acc_ff, ff_sqr(d));
                     } else {
-                        if (u_out) u_out[p] = __fadd_rn(u.hi, u.lo);
+                        if (u_out) u_out[p] = __fadd_rn(u_.hi, u_.lo);
                         if (owner_out) owner_out[p] = t;
                     }
                 } else {
@@ -221,17 +250,43 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
                         acc[4] = fma(lb, lc, acc[4]);
                         acc[5] = fma(lc, la, acc[5]);
                     } else if (MODE == R_SCAT) {
-                        double r = (double)img[p];
+                        double r = (double)fv[u];
                         acc[0] = fma(la, r, acc[0]);
                         acc[1] = fma(lb, r, acc[1]);
                         acc[2] = fma(lc, r, acc[2]);
                     }
                 }
             }
+            }
         }
         if (MODE == R_ERR) {
             ff tot = ff_warp_sum(acc_ff);
-            if (lane == 0) ((float2*)partial)[it] = make_float2(tot.hi, tot.lo);
+            if (!item_done) {
+                if (lane == 0) ((float2*)partial)[it] = make_float2(tot.hi, tot.lo);
+            } else {
+                // fused finalisation: the warp that completes a triangle's
+                // items sums its partials and writes the key
+                int last = 0;
+                if (lane == 0) {
+                    ((float2*)partial)[it] = make_float2(tot.hi, tot.lo);
+                    __threadfence();
+                    last = atomicAdd(item_done + t, 1) == item_cnt[t] - 1;
+                }
+                last = __shfl_sync(FULL, last, 0);
+                if (last) {
+                    __threadfence();
+                    ff sum = warp_sum_partials((const float2*)partial, item_off[t], item_cnt[t]);
+                    if (lane == 0) {
+                        double key = ff_to_double(sum);
+                        key_out[t] = key;
+                        if (keyc_out) {
+                            bool eligible = (((g.ax + g.bx) | (g.ay + g.by)) & 1) == 0;
+                            keyc_out[t] = eligible ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
+                        }
+                        item_done[t] = 0;  // ready for the next pass
+                    }
+                }
+            }
         } else if (NA > 0) {
 #pragma unroll
             for (int q = 0; q < (NA > 0 ? NA : 1); ++q) {
@@ -242,30 +297,32 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
     }
 }
 
-// per-triangle error from float-float item partials (added in item order);
-// keyc (optional): composite selection key, eligible triangles (refinement-
-// edge midpoint on the pixel grid) get the FP64 key bits with the top bit
-// set, the others 0, so that unsigned order = selection order
+// per-triangle error from float-float item partials, one warp per
+// triangle (the summation of the fused path in k_raster); keyc (optional):
+// composite selection key, eligible triangles (refinement-edge midpoint on
+// the pixel grid) get the FP64 key bits with the top bit set, the others 0,
+// so that unsigned order = selection order
 __global__ void k_finalize_err(const int* __restrict__ cnt, const int* __restrict__ off,
                                const float2* __restrict__ partial, int T, const int4* __restrict__ tri,
                                const int2* __restrict__ vxy, double* __restrict__ out,
                                unsigned long long* __restrict__ keyc) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    int o = off[t], n = cnt[t];
-    if (n == 0) return;  // small triangle: written by k_raster_small
-    ff s{0.f, 0.f};
-    for (int j = 0; j < n; ++j) {
-        float2 v = partial[o + j];
-        s = ff_add(s, ff{v.x, v.y});
-    }
-    double key = ff_to_double(s);
-    out[t] = key;
-    if (keyc) {
-        int4 tr = tri[t];
-        int2 a = vxy[tr.x], b = vxy[tr.y];
-        bool eligible = (((a.x + b.x) | (a.y + b.y)) & 1) == 0;
-        keyc[t] = eligible ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
+    long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long tt = gw; tt < T; tt += nw) {
+        int t = (int)tt;
+        int o = off[t], n = cnt[t];
+        if (n == 0) continue;  // small triangle: written by the small-triangle kernel
+        ff s = warp_sum_partials(partial, o, n);
+        if ((threadIdx.x & 31) == 0) {
+            double key = ff_to_double(s);
+            out[t] = key;
+            if (keyc) {
+                int4 tr = tri[t];
+                int2 a = vxy[tr.x], b = vxy[tr.y];
+                bool eligible = (((a.x + b.x) | (a.y + b.y)) & 1) == 0;
+                keyc[t] = eligible ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
+            }
+        }
     }
 }
 
@@ -380,6 +437,113 @@ __global__ void __launch_bounds__(256) k_raster_small(const int* __restrict__ or
     }
 }
 
+// Error pass over the small triangles with the image staged in shared
+// memory: a block takes 128 consecutive entries of the curve order (a
+// compact patch of the image), loads the bounding box of its small
+// triangles with coalesced row reads, and every thread then walks its
+// triangle in shared memory.  Without the staging each thread waits on one
+// global load after another; the largest small triangles (up to 153
+// pixels) set the kernel's duration.  A block whose box exceeds the tile
+// reads the image directly.  Same arithmetic and summation order as
+// k_raster_small<R_ERR>.
+constexpr int kTileThreads = 128;
+constexpr int kTileCap = 12288;  // floats (48 KB)
+
+__global__ void __launch_bounds__(kTileThreads) k_raster_small_err_tiled(
+    const int* __restrict__ order, const int4* __restrict__ tri, const int2* __restrict__ vxy,
+    const double* __restrict__ uv, const float2* __restrict__ uvf, const float* __restrict__ img, int N, int T,
+    double* __restrict__ out, unsigned long long* __restrict__ keyc) {
+    __shared__ float s_img[kTileCap];
+    __shared__ int s_red[4][kTileThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int i = blockIdx.x * kTileThreads + tid;
+    int t = -1;
+    TriGeom g{};
+    bool act = false;
+    if (i < T) {
+        t = order ? order[i] : i;
+        g = tri_geom(tri[t], vxy, N);
+        act = is_small(g);
+    }
+    int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
+    if (act) {
+        x0 = min(g.ax, min(g.bx, g.cx));
+        x1 = max(g.ax, max(g.bx, g.cx));
+        y0 = g.ytop;
+        y1 = g.yend;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 = min(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        y0 = min(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        x1 = max(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y1 = max(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    }
+    if (lane == 0) { s_red[0][w] = x0; s_red[1][w] = y0; s_red[2][w] = x1; s_red[3][w] = y1; }
+    __syncthreads();
+    x0 = INT_MAX; y0 = INT_MAX; x1 = INT_MIN; y1 = INT_MIN;
+#pragma unroll
+    for (int k = 0; k < kTileThreads / 32; ++k) {
+        x0 = min(x0, s_red[0][k]);
+        y0 = min(y0, s_red[1][k]);
+        x1 = max(x1, s_red[2][k]);
+        y1 = max(y1, s_red[3][k]);
+    }
+    if (x1 < x0) return;  // no small triangle in this block (uniform)
+    const int W = x1 - x0 + 1, H = y1 - y0 + 1;
+    const bool staged = (long long)W * H <= kTileCap;
+    if (staged) {
+        // asynchronous 4-byte copies (cp.async): every copy of the tile is in
+        // flight at once, no register round trip per element
+        for (int r = w; r < H; r += kTileThreads / 32) {
+            const float* src = img + (long long)(y0 + r) * N + x0;
+            unsigned dst = (unsigned)__cvta_generic_to_shared(s_img + r * W);
+            for (int c = lane; c < W; c += 32)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4u * c), "l"(src + c) : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+    }
+    if (!act) return;
+    int dax = g.ax - g.cx, day = g.ay - g.cy, dbx = g.bx - g.cx, dby = g.by - g.cy;
+    long long l2 = (long long)dax * dax + (long long)day * day;
+    bool pow2 = (l2 & (l2 - 1)) == 0;
+    int4 tr = tri[t];
+    ff va = vertex_ff(uv, uvf, tr.x), vb = vertex_ff(uv, uvf, tr.y), uc = vertex_ff(uv, uvf, tr.z);
+    ff da = ff_sub(va, uc), db = ff_sub(vb, uc);
+    ff gx = ff_add(ff_mul_f(da, (float)dax), ff_mul_f(db, (float)dbx));
+    ff gy = ff_add(ff_mul_f(da, (float)day), ff_mul_f(db, (float)dby));
+    if (pow2) {
+        float inv = __int_as_float((127 - (63 - __clzll(l2))) << 23);
+        gx = ff_scale_pow2(gx, inv);
+        gy = ff_scale_pow2(gy, inv);
+    } else {
+        float inv = 1.0f / (float)l2;
+        gx = ff_mul_f(gx, inv);
+        gy = ff_mul_f(gy, inv);
+    }
+    ff acc{0.f, 0.f};
+    for (int y = g.ytop; y <= g.yend; ++y) {
+        int L, len;
+        row_span(g, y, N, L, len);
+        if (len <= 0) continue;
+        ff u = ff_add(ff_add(uc, ff_mul_f(gx, (float)(L - g.cx))), ff_mul_f(gy, (float)(y - g.cy)));
+        const float* rowp = staged ? s_img + (y - y0) * W + (L - x0) : img + (long long)y * N + L;
+#pragma unroll 4
+        for (int k = 0; k < len; ++k) {
+            ff d = ff_add_f(u, -rowp[k]);
+            acc = ff_add(acc, ff_sqr(d));
+            u = ff_add(u, gx);
+        }
+    }
+    double key = ff_to_double(acc);
+    out[t] = key;
+    if (keyc) {
+        bool eligible = (((g.ax + g.bx) | (g.ay + g.by)) & 1) == 0;
+        keyc[t] = eligible ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
+    }
+}
+
 static int small_grid(fem_mesh* m) { return std::max(1, std::min((m->T + 255) / 256, m->num_sms * 8)); }
 
 static int raster_grid(fem_mesh* m) { return m->num_sms * (2048 / kRasterThreads); }
@@ -413,15 +577,18 @@ static double raster_err_bytes(const fem_mesh* m) {
 fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, const float* f, double* err_out,
                          cudaStream_t s, unsigned long long* keyc_out) {
     FEM_TRY(raster_plan(m, s));
+    // per-triangle completion counters, zero between passes (each triangle's
+    // last warp resets its counter)
+    if (m->item_done.n < (size_t)m->T || !m->item_done.p) {
+        FEM_TRY(ensure(m->item_done, (size_t)m->T, s));
+        FEM_CUDA(cudaMemsetAsync(m->item_done.p, 0, sizeof(int) * m->item_done.n, s));
+    }
     note_bytes(F_RASTER, raster_err_bytes(m));
     FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
                m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p, (float*)nullptr,
-               (int*)nullptr);
-    int blocks = (m->T + 255) / 256;
-    FEM_LAUNCH(F_RASTER, s, k_finalize_err, blocks, 256, 0, m->item_cnt.p, m->item_off.p,
-               (const float2*)m->partial.p, m->T, m->tri.p, m->vxy.p, err_out, keyc_out);
-    FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv, uvf, f,
-               m->N, m->T, err_out, keyc_out, (float*)nullptr, (int*)nullptr);
+               (int*)nullptr, m->item_cnt.p, m->item_done.p, err_out, keyc_out);
+    FEM_LAUNCH(F_RASTER, s, k_raster_small_err_tiled, (m->T + kTileThreads - 1) / kTileThreads, kTileThreads, 0,
+               m->order.p, m->tri.p, m->vxy.p, uv, uvf, f, m->N, m->T, err_out, keyc_out);
     return FEM_OK;
 }
 
@@ -478,8 +645,8 @@ fem_status raster_errors_scratch(const int4* tri, const int2* vxy, int T, int N,
     FEM_LAUNCH(F_RASTER, s, k_item_expand, blocks, 256, 0, w.item_cnt, w.item_off, T, w.item_cap, w.item_tri, err);
     FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, w.grid, kRasterThreads, 0, tri, vxy, uv, (const float2*)nullptr, f, N,
                w.item_tri, w.item_off, n_items_dev, w.item_cap, w.partial, (float*)nullptr, (int*)nullptr);
-    FEM_LAUNCH(F_RASTER, s, k_finalize_err, blocks, 256, 0, w.item_cnt, w.item_off, (const float2*)w.partial, T, tri,
-               vxy, err_out, (unsigned long long*)nullptr);
+    FEM_LAUNCH(F_RASTER, s, k_finalize_err, std::max(1, std::min(w.grid, (T + 7) / 8)), 256, 0, w.item_cnt,
+               w.item_off, (const float2*)w.partial, T, tri, vxy, err_out, (unsigned long long*)nullptr);
     FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, std::max(1, std::min(blocks, w.grid / 2)), 256, 0, (const int*)nullptr,
                tri, vxy, uv, (const float2*)nullptr, f, N, T, err_out, (unsigned long long*)nullptr, (float*)nullptr,
                (int*)nullptr);

@@ -58,6 +58,47 @@ __device__ __forceinline__ unsigned long long comp_hi(const TopkArgs& A, int t) 
     return (unsigned long long)__double_as_longlong(A.keys[t]) | (1ull << 63);
 }
 
+// Bucket of the k-th largest element from a 256-bin histogram, by one warp:
+// lane i holds bins 255-8i .. 248-8i (from the top), a warp scan gives the
+// counts above each lane's group, and the lane whose group crosses krem
+// walks its 8 bins.  Returns the bin; *above = elements in higher bins.
+template <class Count>
+__device__ __forceinline__ int warp_pick_bucket(const Count* hist, long long krem, long long* above) {
+    const unsigned FULL = 0xffffffffu;
+    int lane = threadIdx.x & 31;
+    long long c[8], grp = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        c[j] = (long long)hist[255 - 8 * lane - j];
+        grp += c[j];
+    }
+    long long incl = grp;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    long long excl = incl - grp;
+    unsigned hit = __ballot_sync(FULL, excl < krem && incl >= krem);
+    int chosen = 0;
+    long long cum = 0;
+    if (hit) {
+        int l = __ffs(hit) - 1;
+        if (lane == l) {
+            cum = excl;
+            int b = 255 - 8 * lane;
+            for (int j = 0; j < 8; ++j, --b) {
+                if (cum + c[j] >= krem) { chosen = b; break; }
+                cum += c[j];
+            }
+        }
+        chosen = __shfl_sync(FULL, chosen, l);
+        cum = __shfl_sync(FULL, cum, l);
+    }
+    *above = cum;
+    return chosen;
+}
+
 __device__ __forceinline__ unsigned digit_of(unsigned long long hi, unsigned lo, int d) {
     return d < 8 ? (unsigned)(hi >> (56 - 8 * d)) & 255u : (lo >> (24 - 8 * (d - 8))) & 255u;
 }
@@ -68,8 +109,6 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(TopkArgs A) {
     __shared__ unsigned s_pre_lo;
     __shared__ long long s_krem;
     int tid0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-    int parity = 0;
-    (void)parity;
     // eligible count -> k
     __shared__ unsigned s_ne;
     if (threadIdx.x == 0) s_ne = 0;
@@ -108,17 +147,16 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(TopkArgs A) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x)
             if (s_hist[i]) atomicAdd(&A.hist[d * 256 + i], s_hist[i]);
         if (!grid_barrier(A.bar, A.err)) return;
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
+            for (int i = threadIdx.x; i < 256; i += 32) s_hist[i] = __ldcg(&A.hist[d * 256 + i]);
+            __syncwarp();
             long long krem = s_krem, cum = 0;
-            int chosen = 0;
-            for (int b = 255; b >= 0; --b) {
-                long long h = (long long)__ldcg(&A.hist[d * 256 + b]);
-                if (cum + h >= krem) { chosen = b; break; }
-                cum += h;
+            int chosen = warp_pick_bucket(s_hist, krem, &cum);
+            if (threadIdx.x == 0) {
+                s_krem = krem - cum;
+                if (d < 8) s_pre_hi = pre_hi | ((unsigned long long)chosen << (56 - 8 * d));
+                else s_pre_lo = pre_lo | ((unsigned)chosen << (24 - 8 * (d - 8)));
             }
-            s_krem = krem - cum;
-            if (d < 8) s_pre_hi = pre_hi | ((unsigned long long)chosen << (56 - 8 * d));
-            else s_pre_lo = pre_lo | ((unsigned)chosen << (24 - 8 * (d - 8)));
         }
         __syncthreads();
     }
@@ -221,18 +259,15 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
             }
         }
         __syncthreads();
-        if (tid == 0) {
+        if (tid < 32) {
             long long krem = s_krem, cum = 0;
-            int chosen = 0;
-            for (int b = 255; b >= 0; --b) {
-                long long h = hist[b];
-                if (cum + h >= krem) { chosen = b; break; }
-                cum += h;
+            int chosen = warp_pick_bucket(hist, krem, &cum);
+            if (tid == 0) {
+                s_krem = krem - cum;
+                s_cnt = (int)hist[chosen];
+                if (d < 8) s_pre_hi = pre_hi | ((unsigned long long)chosen << (56 - 8 * d));
+                else s_pre_lo = pre_lo | ((unsigned)chosen << (24 - 8 * (d - 8)));
             }
-            s_krem = krem - cum;
-            s_cnt = (int)hist[chosen];
-            if (d < 8) s_pre_hi = pre_hi | ((unsigned long long)chosen << (56 - 8 * d));
-            else s_pre_lo = pre_lo | ((unsigned)chosen << (24 - 8 * (d - 8)));
         }
         __syncthreads();
         if (!s_smem && d < 11 && s_cnt <= kTopkCandCap) {
@@ -538,8 +573,6 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
                m->bmS.p);
     {
         int max_sweeps = 48;
-        const unsigned* cbm = nullptr;
-        (void)cbm;
         void* args[] = {(void*)&m->tri.p, (void*)&m->vxy.p, (void*)&T, (void*)&N, (void*)&m->bmM.p,
                         (void*)&changed, (void*)&max_sweeps, (void*)&m->bar.p, (void*)&err, (void*)&sweeps};
         int grid = coop_grid((const void*)k_closure, 256, T, m->num_sms);
