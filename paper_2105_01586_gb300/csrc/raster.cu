@@ -438,16 +438,17 @@ __global__ void __launch_bounds__(256) k_raster_small(const int* __restrict__ or
 }
 
 // Error pass over the small triangles with the image staged in shared
-// memory: a block takes 128 consecutive entries of the curve order (a
-// compact patch of the image), loads the bounding box of its small
-// triangles with coalesced row reads, and every thread then walks its
-// triangle in shared memory.  Without the staging each thread waits on one
-// global load after another; the largest small triangles (up to 153
-// pixels) set the kernel's duration.  A block whose box exceeds the tile
-// reads the image directly.  Same arithmetic and summation order as
-// k_raster_small<R_ERR>.
+// memory.  A block takes 16 consecutive entries of the curve order (a
+// compact patch of the image), copies the bounding box of its small
+// triangles into shared memory with asynchronous copies (cp.async, all in
+// flight at once), and eight lanes share each triangle: lane j of a group
+// walks rows ytop + j, ytop + j + 8, ..., so no lane serialises more than
+// three rows of at most 17 pixels.  The eight float-float row sums are
+// combined by a fixed butterfly.  A block whose box exceeds the tile reads
+// the image directly.
 constexpr int kTileThreads = 128;
-constexpr int kTileCap = 12288;  // floats (48 KB)
+constexpr int kTileTris = kTileThreads / 8;
+constexpr int kTileCap = 4096;  // floats (16 KB)
 
 __global__ void __launch_bounds__(kTileThreads) k_raster_small_err_tiled(
     const int* __restrict__ order, const int4* __restrict__ tri, const int2* __restrict__ vxy,
@@ -455,8 +456,8 @@ __global__ void __launch_bounds__(kTileThreads) k_raster_small_err_tiled(
     double* __restrict__ out, unsigned long long* __restrict__ keyc) {
     __shared__ float s_img[kTileCap];
     __shared__ int s_red[4][kTileThreads / 32];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int i = blockIdx.x * kTileThreads + tid;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, sub = lane & 7;
+    const int i = blockIdx.x * kTileTris + (tid >> 3);
     int t = -1;
     TriGeom g{};
     bool act = false;
@@ -493,8 +494,6 @@ __global__ void __launch_bounds__(kTileThreads) k_raster_small_err_tiled(
     const int W = x1 - x0 + 1, H = y1 - y0 + 1;
     const bool staged = (long long)W * H <= kTileCap;
     if (staged) {
-        // asynchronous 4-byte copies (cp.async): every copy of the tile is in
-        // flight at once, no register round trip per element
         for (int r = w; r < H; r += kTileThreads / 32) {
             const float* src = img + (long long)(y0 + r) * N + x0;
             unsigned dst = (unsigned)__cvta_generic_to_shared(s_img + r * W);
@@ -504,43 +503,49 @@ __global__ void __launch_bounds__(kTileThreads) k_raster_small_err_tiled(
         asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
         __syncthreads();
     }
-    if (!act) return;
-    int dax = g.ax - g.cx, day = g.ay - g.cy, dbx = g.bx - g.cx, dby = g.by - g.cy;
-    long long l2 = (long long)dax * dax + (long long)day * day;
-    bool pow2 = (l2 & (l2 - 1)) == 0;
-    int4 tr = tri[t];
-    ff va = vertex_ff(uv, uvf, tr.x), vb = vertex_ff(uv, uvf, tr.y), uc = vertex_ff(uv, uvf, tr.z);
-    ff da = ff_sub(va, uc), db = ff_sub(vb, uc);
-    ff gx = ff_add(ff_mul_f(da, (float)dax), ff_mul_f(db, (float)dbx));
-    ff gy = ff_add(ff_mul_f(da, (float)day), ff_mul_f(db, (float)dby));
-    if (pow2) {
-        float inv = __int_as_float((127 - (63 - __clzll(l2))) << 23);
-        gx = ff_scale_pow2(gx, inv);
-        gy = ff_scale_pow2(gy, inv);
-    } else {
-        float inv = 1.0f / (float)l2;
-        gx = ff_mul_f(gx, inv);
-        gy = ff_mul_f(gy, inv);
-    }
     ff acc{0.f, 0.f};
-    for (int y = g.ytop; y <= g.yend; ++y) {
-        int L, len;
-        row_span(g, y, N, L, len);
-        if (len <= 0) continue;
-        ff u = ff_add(ff_add(uc, ff_mul_f(gx, (float)(L - g.cx))), ff_mul_f(gy, (float)(y - g.cy)));
-        const float* rowp = staged ? s_img + (y - y0) * W + (L - x0) : img + (long long)y * N + L;
+    if (act) {
+        int dax = g.ax - g.cx, day = g.ay - g.cy, dbx = g.bx - g.cx, dby = g.by - g.cy;
+        long long l2 = (long long)dax * dax + (long long)day * day;
+        bool pow2 = (l2 & (l2 - 1)) == 0;
+        int4 tr = tri[t];
+        ff va = vertex_ff(uv, uvf, tr.x), vb = vertex_ff(uv, uvf, tr.y), uc = vertex_ff(uv, uvf, tr.z);
+        ff da = ff_sub(va, uc), db = ff_sub(vb, uc);
+        ff gx = ff_add(ff_mul_f(da, (float)dax), ff_mul_f(db, (float)dbx));
+        ff gy = ff_add(ff_mul_f(da, (float)day), ff_mul_f(db, (float)dby));
+        if (pow2) {
+            float inv = __int_as_float((127 - (63 - __clzll(l2))) << 23);
+            gx = ff_scale_pow2(gx, inv);
+            gy = ff_scale_pow2(gy, inv);
+        } else {
+            float inv = 1.0f / (float)l2;
+            gx = ff_mul_f(gx, inv);
+            gy = ff_mul_f(gy, inv);
+        }
+        for (int y = g.ytop + sub; y <= g.yend; y += 8) {
+            int L, len;
+            row_span(g, y, N, L, len);
+            if (len <= 0) continue;
+            ff u = ff_add(ff_add(uc, ff_mul_f(gx, (float)(L - g.cx))), ff_mul_f(gy, (float)(y - g.cy)));
+            const float* rowp = staged ? s_img + (y - y0) * W + (L - x0) : img + (long long)y * N + L;
 #pragma unroll 4
-        for (int k = 0; k < len; ++k) {
-            ff d = ff_add_f(u, -rowp[k]);
-            acc = ff_add(acc, ff_sqr(d));
-            u = ff_add(u, gx);
+            for (int k = 0; k < len; ++k) {
+                ff d = ff_add_f(u, -rowp[k]);
+                acc = ff_add(acc, ff_sqr(d));
+                u = ff_add(u, gx);
+            }
         }
     }
-    double key = ff_to_double(acc);
-    out[t] = key;
-    if (keyc) {
-        bool eligible = (((g.ax + g.bx) | (g.ay + g.by)) & 1) == 0;
-        keyc[t] = eligible ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
+    // the eight lanes of a triangle: fixed butterfly (all lanes take part)
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) acc = ff_add(acc, ff_shfl_xor(acc, o));
+    if (act && sub == 0) {
+        double key = ff_to_double(acc);
+        out[t] = key;
+        if (keyc) {
+            bool eligible = (((g.ax + g.bx) | (g.ay + g.by)) & 1) == 0;
+            keyc[t] = eligible ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
+        }
     }
 }
 
@@ -587,7 +592,7 @@ fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, const
     FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
                m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p, (float*)nullptr,
                (int*)nullptr, m->item_cnt.p, m->item_done.p, err_out, keyc_out);
-    FEM_LAUNCH(F_RASTER, s, k_raster_small_err_tiled, (m->T + kTileThreads - 1) / kTileThreads, kTileThreads, 0,
+    FEM_LAUNCH(F_RASTER, s, k_raster_small_err_tiled, (m->T + kTileTris - 1) / kTileTris, kTileThreads, 0,
                m->order.p, m->tri.p, m->vxy.p, uv, uvf, f, m->N, m->T, err_out, keyc_out);
     return FEM_OK;
 }

@@ -495,12 +495,23 @@ __global__ void k_order_expand(const int* __restrict__ order, const int* __restr
     }
 }
 
+// Cooperative grid: one thread per work item, at most the co-resident
+// blocks (occupancy queried once per kernel).
 static int coop_grid(const void* func, int threads, int work, int num_sms) {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, 0);
-    if (nb < 1) nb = 1;
+    static const int nb_topk = [] {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k_topk, kTopkThreads, 0);
+        return nb < 1 ? 1 : nb;
+    }();
+    static const int nb_closure = [] {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k_closure, 256, 0);
+        return nb < 1 ? 1 : nb;
+    }();
+    int nb = func == (const void*)k_topk ? nb_topk : nb_closure;
+    (void)threads;
     int maxb = nb * num_sms;
-    int want = (work + threads * 4 - 1) / (threads * 4);
+    int want = (work + threads - 1) / threads;
     if (want < 1) want = 1;
     return want < maxb ? want : maxb;
 }
