@@ -193,7 +193,9 @@ struct fem_mesh {
     int n_items = 0;
 
     // refinement
-    fem::DArr<unsigned> bmM, bmS, wpre;
+    fem::DArr<unsigned> bmM, bmS, wpre;  // edge bitmaps: two buffers each, alternating by round
+    int bm_parity = 0;
+    bool bm_clean = false;              // the buffer of the next round is known to be clear
     fem::DArr<int> flags, fscan, wcnt;
     fem::DArr<unsigned> topk_hist;
 

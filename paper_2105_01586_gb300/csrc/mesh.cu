@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "fem_internal.cuh"
+#include "scan.cuh"
 
 namespace fem {
 
@@ -108,51 +109,6 @@ int sm_count() {
 }
 
 // ------------------------------------------------------------------- scans
-constexpr int SCAN_BT = 256;
-constexpr int SCAN_IPT = 8;
-constexpr int SCAN_TILE = SCAN_BT * SCAN_IPT;
-
-// exclusive scan of v[] within the block; returns the block total
-__device__ int block_exclusive_scan(int (&v)[SCAN_IPT]) {
-    __shared__ int s_warp[SCAN_BT / 32];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int sum = 0;
-#pragma unroll
-    for (int i = 0; i < SCAN_IPT; ++i) {
-        int t = v[i];
-        v[i] = sum;
-        sum += t;
-    }
-    int incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        int w = lane < SCAN_BT / 32 ? s_warp[lane] : 0;
-        int wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += y;
-        }
-        if (lane < SCAN_BT / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
-    }
-    __syncthreads();
-    int base = s_warp[wid] + incl - sum;
-#pragma unroll
-    for (int i = 0; i < SCAN_IPT; ++i) v[i] += base;
-    __shared__ int s_total;
-    if (threadIdx.x == SCAN_BT - 1) s_total = base + sum;
-    __syncthreads();
-    int tot = s_total;
-    __syncthreads();
-    return tot;
-}
-
 __global__ void k_scan_tiles(const int* __restrict__ in, int* __restrict__ out, int n, int* __restrict__ tile_sums) {
     int v[SCAN_IPT];
     long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
@@ -176,29 +132,6 @@ __global__ void k_scan_total(const int* in, const int* out, int n, int* total) {
     *total = n > 0 ? out[n - 1] + in[n - 1] : 0;
 }
 
-// Single-launch exclusive scan (decoupled look-back).  Tiles take their
-// index from an atomic counter in the order they start, so every tile's
-// predecessors are running or finished and a tile only ever waits on them.
-// Each tile publishes its aggregate, then its inclusive prefix, in a 64-bit
-// status word (epoch | flag | value) written with release semantics; the
-// epoch changes every call, so status words never need clearing.  Waits are
-// bounded: after kLookbackLimitNs the tile records FEM_E_TIMEOUT and stops.
-constexpr unsigned long long kLookbackLimitNs = 1000000000ull;
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long pack_status(unsigned epoch, unsigned flag, int value) {
-    return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | (unsigned)value;
-}
-
 // Scan input: in[i], or (when root is set) the component size at a root
 // vertex and 0 elsewhere: !mask[i] && root[i] == i ? size[i] : 0.
 struct ScanIn {
@@ -212,88 +145,20 @@ struct ScanIn {
     }
 };
 
-__global__ void k_scan_lookback(ScanIn in, int* __restrict__ out, int n, int* __restrict__ total,
-                                unsigned long long* __restrict__ status, unsigned long long* __restrict__ ctr,
-                                unsigned long long base, unsigned epoch, int* __restrict__ err) {
-    __shared__ int s_tile, s_prefix;
-    if (threadIdx.x == 0) s_tile = (int)(atomicAdd(ctr, 1ull) - base);
-    __syncthreads();
-    int tile = s_tile;
-    int v[SCAN_IPT];
-    long long first = (long long)tile * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
-#pragma unroll
-    for (int i = 0; i < SCAN_IPT; ++i) v[i] = (first + i < n) ? in(first + i) : 0;
-    int agg = block_exclusive_scan(v);
-    // look-back by the first warp, 32 predecessors per step: lane i reads
-    // the status of tile (p - i); the window is summed up to the nearest
-    // tile that already holds its inclusive prefix
-    if (threadIdx.x < 32) {
-        const unsigned FULL = 0xffffffffu;
-        const int lane = threadIdx.x;
-        int prefix = 0;
-        if (tile == 0) {
-            if (lane == 0) st_release_u64(&status[0], pack_status(epoch, 2, agg));
-        } else {
-            if (lane == 0) st_release_u64(&status[tile], pack_status(epoch, 1, agg));
-            int p = tile - 1;
-            unsigned long long t0 = globaltimer_ns();
-            bool timed_out = false;
-            while (p >= 0) {
-                int q = p - lane;
-                unsigned long long w = q >= 0 ? ld_acquire_u64(&status[q]) : pack_status(epoch, 2, 0);
-                unsigned ep = (unsigned)(w >> 34), flag = (unsigned)(w >> 32) & 3u;
-                bool ready = ep == epoch && flag != 0;
-                // wait until every tile of the window up to the first
-                // inclusive one has published
-                unsigned incl = __ballot_sync(FULL, ready && flag == 2);
-                unsigned notready = __ballot_sync(FULL, !ready);
-                int stop = incl ? __ffs(incl) - 1 : 32;  // lanes 0..stop are summed
-                unsigned need = stop == 32 ? FULL : (stop == 31 ? FULL : ((2u << stop) - 1u));
-                if (notready & need) {
-                    // the decision to give up is taken by the whole warp
-                    bool late = globaltimer_ns() - t0 > kLookbackLimitNs;
-                    if (__any_sync(FULL, late)) { timed_out = true; break; }
-                    continue;
-                }
-                int val = lane <= stop ? (int)(unsigned)w : 0;
-                prefix += warp_sum(val);
-                if (stop < 32) break;
-                p -= 32;
-            }
-            if (timed_out && lane == 0) atomicCAS(err, 0, (int)FEM_E_TIMEOUT);
-            if (lane == 0) st_release_u64(&status[tile], pack_status(epoch, 2, prefix + agg));
-        }
-        if (lane == 0) {
-            s_prefix = prefix;
-            if ((long long)(tile + 1) * SCAN_TILE >= n && total) *total = prefix + agg;
-        }
-    }
-    __syncthreads();
-    int pre = s_prefix;
-#pragma unroll
-    for (int i = 0; i < SCAN_IPT; ++i)
-        if (first + i < n) out[first + i] = v[i] + pre;
-}
-
-static fem_status scan_lookback(fem_mesh* m, ScanIn in, int* out, int n, cudaStream_t s, int* total_dev);
 
 // out[i] = sum of in[0..i-1]; *total_dev (if non-null) = sum of all (one launch)
 fem_status scan_i32(fem_mesh* m, const int* in, int* out, int n, cudaStream_t s, int* total_dev) {
-    return scan_lookback(m, ScanIn{in, nullptr, nullptr, nullptr}, out, n, s, total_dev);
+    return scan_fused<SCAN_IPT>(m, ScanIn{in, nullptr, nullptr, nullptr}, ScanStore{out}, n, s, total_dev, F_OTHER);
 }
 
 // out[v] = rows of the components whose root (smallest vertex) is below v
 fem_status scan_component_rows(fem_mesh* m, const unsigned char* mask, const int* root, const int* size, int* out,
                                int n, cudaStream_t s, int* total_dev) {
-    return scan_lookback(m, ScanIn{nullptr, mask, root, size}, out, n, s, total_dev);
+    return scan_fused<2>(m, ScanIn{nullptr, mask, root, size}, ScanStore{out}, n, s, total_dev, F_OTHER);
 }
 
-static fem_status scan_lookback(fem_mesh* m, ScanIn in, int* out, int n, cudaStream_t s, int* total_dev) {
-    if (n <= 0) {
-        if (total_dev) FEM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int), s));
-        return FEM_OK;
-    }
-    int tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+fem_status scan_plan(fem_mesh* m, int n, int tile, cudaStream_t s, ScanPlan* plan) {
+    int tiles = (n + tile - 1) / tile;
     unsigned long long* before = m->scan_status.p;
     FEM_TRY(ensure(m->scan_status, (size_t)tiles, s));
     if (m->scan_status.p != before)  // fresh memory: no word may look like one of this call's epoch
@@ -303,12 +168,15 @@ static fem_status scan_lookback(fem_mesh* m, ScanIn in, int* out, int n, cudaStr
         FEM_CUDA(cudaMemsetAsync(m->scan_ctr.p, 0, sizeof(unsigned long long), s));
         m->scan_tiles_issued = 0;
     }
-    unsigned long long base = m->scan_tiles_issued;
+    plan->tiles = tiles;
+    plan->status = m->scan_status.p;
+    plan->ctr = m->scan_ctr.p;
+    plan->base = m->scan_tiles_issued;
     m->scan_tiles_issued += (unsigned long long)tiles;
     unsigned epoch = (unsigned)(++m->scan_epoch & ((1u << 30) - 1));
     if (epoch == 0) epoch = (unsigned)(++m->scan_epoch & ((1u << 30) - 1));
-    FEM_LAUNCH(F_OTHER, s, k_scan_lookback, tiles, SCAN_BT, 0, in, out, n, total_dev, m->scan_status.p,
-               m->scan_ctr.p, base, epoch, m->dflag.p + 8);
+    plan->epoch = epoch;
+    plan->err = m->dflag.p + 8;
     return FEM_OK;
 }
 

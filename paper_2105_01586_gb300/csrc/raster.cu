@@ -21,6 +21,7 @@
 
 #include "fem_internal.cuh"
 #include "ff.cuh"
+#include "scan.cuh"
 
 namespace fem {
 
@@ -80,6 +81,41 @@ __device__ __forceinline__ bool is_small(const TriGeom& g) {
     return g.maxw <= kSmallSide && (g.yend - g.ytop + 1) <= kSmallSide;
 }
 
+// raster plan as one fused scan: the item count of triangle t is the input,
+// the output records its first item and writes its item list
+struct ItemCountIn {
+    const int4* tri;
+    const int2* vxy;
+    int N;
+    int* cnt;
+    __device__ __forceinline__ int operator()(long long lt) const {
+        int t = (int)lt;
+        TriGeom g = tri_geom(tri[t], vxy, N);
+        int rows = g.yend - g.ytop + 1;
+        int rpi = rows_per_item(g.maxw);
+        int c = (rows > 0 && !is_small(g)) ? (rows + rpi - 1) / rpi : 0;
+        cnt[t] = c;
+        return c;
+    }
+};
+
+struct ItemExpandOut {
+    int* off;
+    int* item_tri;
+    int cap;
+    int* err;
+    __device__ __forceinline__ void operator()(long long lt, int o, int n) const {
+        int t = (int)lt;
+        off[t] = o;
+        if (o + n > cap) {
+            atomicCAS(err, 0, (int)FEM_E_INVALID);
+            return;
+        }
+        for (int j = 0; j < n; ++j) item_tri[o + j] = t;
+    }
+};
+
+// separate kernels of the plan (used by the allocation-free error pass)
 __global__ void k_item_count(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int N,
                              int* __restrict__ cnt) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -564,11 +600,9 @@ fem_status raster_plan(fem_mesh* m, cudaStream_t s) {
     int* n_items_dev = m->dcount.p + 0;
     int* err = m->dflag.p + 0;
     FEM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    int blocks = (T + 255) / 256;
-    FEM_LAUNCH(F_RASTER, s, k_item_count, blocks, 256, 0, m->tri.p, m->vxy.p, T, m->N, m->item_cnt.p);
-    FEM_TRY(scan_i32(m, m->item_cnt.p, m->item_off.p, T, s, n_items_dev));
-    FEM_LAUNCH(F_RASTER, s, k_item_expand, blocks, 256, 0, m->item_cnt.p, m->item_off.p, T, (int)m->item_tri.n,
-               m->item_tri.p, err);
+    FEM_TRY(scan_fused(m, ItemCountIn{m->tri.p, m->vxy.p, m->N, m->item_cnt.p},
+                       ItemExpandOut{m->item_off.p, m->item_tri.p, (int)m->item_tri.n, err}, T, s, n_items_dev,
+                       F_RASTER));
     m->plan_version = m->mesh_version;
     return FEM_OK;
 }

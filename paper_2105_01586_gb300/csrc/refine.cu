@@ -18,6 +18,7 @@
 #include <utility>
 
 #include "fem_internal.cuh"
+#include "scan.cuh"
 
 namespace fem {
 
@@ -371,11 +372,7 @@ __global__ void k_closure(const int4* __restrict__ tri, const int2* __restrict__
     }
 }
 
-__global__ void k_word_popc(const unsigned* __restrict__ bm, int W, int* __restrict__ cnt) {
-    int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w < W) cnt[w] = __popc(bm[w]);
-}
-
+// id of the new vertex at midpoint pixel p: V0 + marks before p
 __device__ __forceinline__ int midpoint_id(const unsigned* __restrict__ bm, const int* __restrict__ wpre, int V0,
                                            long long p) {
     unsigned w = bm[p >> 5];
@@ -383,60 +380,110 @@ __device__ __forceinline__ int midpoint_id(const unsigned* __restrict__ bm, cons
     return V0 + wpre[p >> 5] + __popc(below);
 }
 
-__global__ void k_new_vertices(const unsigned* __restrict__ bmM, const unsigned* __restrict__ bmS,
-                               const int* __restrict__ wpre, int W, int N, int V0, int2* __restrict__ vxy,
-                               unsigned char* __restrict__ mask, int* __restrict__ n_new_mask) {
-    int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= W) return;
-    unsigned bits = bmM[w], sbits = bmS[w];
-    if (sbits & bits) atomicAdd(n_new_mask, __popc(sbits & bits));
-    int id = V0 + wpre[w];
-    while (bits) {
-        int b = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        long long p = (long long)w * 32 + b;
-        vxy[id] = make_int2((int)(p % N), (int)(p / N));
-        mask[id] = (unsigned char)((sbits >> b) & 1u);
-        id++;
+// New vertices as one fused scan over the bitmap words: the input is the
+// number of marked midpoints in word w (and clears word w of the other
+// round's bitmaps: the edge bitmaps alternate between two buffers), the
+// output numbers them V0 + (marks before them) and writes their positions
+// and mask flags.
+struct WordIn {
+    const unsigned* bmM;
+    unsigned* clearM;
+    unsigned* clearS;
+    __device__ __forceinline__ int operator()(long long w) const {
+        clearM[w] = 0u;
+        clearS[w] = 0u;
+        return __popc(bmM[w]);
     }
-}
+};
 
-__global__ void k_bisect_flags(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int N,
-                               const unsigned* __restrict__ bmM, int* __restrict__ flags) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    int4 tr = tri[t];
-    int2 a = vxy[tr.x], b = vxy[tr.y], c = vxy[tr.z];
-    int e0 = lattice_mid(a, b) && test_bit(bmM, mid_pixel(a, b, N));
-    int e1 = e0 && lattice_mid(b, c) && test_bit(bmM, mid_pixel(b, c, N));
-    int e2 = e0 && lattice_mid(c, a) && test_bit(bmM, mid_pixel(c, a, N));
-    flags[t] = e0;
-    flags[T + t] = e2;
-    flags[2 * T + t] = e1;
+struct NewVertexOut {
+    const unsigned* bmM;
+    const unsigned* bmS;
+    int* wpre;
+    int N, V0;
+    int2* vxy;
+    unsigned char* mask;
+    int* n_new_mask;
+    __device__ __forceinline__ void operator()(long long w, int pre, int) const {
+        wpre[w] = pre;
+        unsigned bits = bmM[w], sbits = bmS[w];
+        if (sbits & bits) atomicAdd(n_new_mask, __popc(sbits & bits));
+        int id = V0 + pre;
+        while (bits) {
+            int b = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            long long p = w * 32 + b;
+            vxy[id] = make_int2((int)(p % N), (int)(p / N));
+            mask[id] = (unsigned char)((sbits >> b) & 1u);
+            id++;
+        }
+    }
+};
+
+// Bisection flags [gen 1 | gen 2 of the kept child | gen 2 of the new
+// child] as the input of one fused scan (the scan numbers the new
+// triangles): element i of segment j = i / T belongs to triangle i - j T.
+struct BisectFlagIn {
+    const int4* tri;
+    const int2* vxy;
+    const unsigned* bmM;
+    int T, N;
+    int* flags;
+    __device__ __forceinline__ int operator()(long long li) const {
+        int seg = (int)(li / T), t = (int)(li - (long long)seg * T);
+        int4 tr = tri[t];
+        int2 a = vxy[tr.x], b = vxy[tr.y], c = vxy[tr.z];
+        int e0 = lattice_mid(a, b) && test_bit(bmM, mid_pixel(a, b, N));
+        int v = e0;
+        if (seg == 1) v = e0 && lattice_mid(c, a) && test_bit(bmM, mid_pixel(c, a, N));
+        if (seg == 2) v = e0 && lattice_mid(b, c) && test_bit(bmM, mid_pixel(b, c, N));
+        flags[li] = v;
+        return v;
+    }
+};
+
+// Value of a new vertex: a new mask vertex takes the image value (g = f in
+// the spatial optimisation; with its float-float copy), a new unknown the
+// mean of the edge's end values as the start of the next solve.
+__device__ __forceinline__ void new_vertex_value(int id, long long pix, int e0, int e1,
+                                                 const unsigned char* __restrict__ mask, const float* __restrict__ f,
+                                                 double* __restrict__ uv, float2* __restrict__ uvf) {
+    if (mask[id]) {
+        float v = f[pix];
+        uv[id] = (double)v;
+        uvf[id] = make_float2(v, 0.0f);
+    } else {
+        uv[id] = 0.5 * (uv[e0] + uv[e1]);
+    }
 }
 
 __global__ void k_bisect(int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int N,
                          const unsigned* __restrict__ bmM, const int* __restrict__ wpre, int V0,
-                         const int* __restrict__ flags, const int* __restrict__ fscan, double* __restrict__ uv) {
+                         const int* __restrict__ flags, const int* __restrict__ fscan,
+                         const unsigned char* __restrict__ mask, const float* __restrict__ f, double* __restrict__ uv,
+                         float2* __restrict__ uvf) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T || !flags[t]) return;
     int4 tr = tri[t];
     int a = tr.x, b = tr.y, c = tr.z;
     int2 pa = vxy[a], pb = vxy[b], pc = vxy[c];
-    int m = midpoint_id(bmM, wpre, V0, mid_pixel(pa, pb, N));
-    uv[m] = 0.5 * (uv[a] + uv[b]);
+    long long pm = mid_pixel(pa, pb, N);
+    int m = midpoint_id(bmM, wpre, V0, pm);
+    new_vertex_value(m, pm, a, b, mask, f, uv, uvf);
     int id1 = T + fscan[t];
     int4 kept = make_int4(c, a, m, 0);   // (c, a, m) keeps id t
     int4 fresh = make_int4(b, c, m, 0);  // (b, c, m) new id
     if (flags[T + t]) {  // kept child's refinement edge (c, a) is marked
-        int m2 = midpoint_id(bmM, wpre, V0, mid_pixel(pc, pa, N));
-        uv[m2] = 0.5 * (uv[c] + uv[a]);
+        long long p2 = mid_pixel(pc, pa, N);
+        int m2 = midpoint_id(bmM, wpre, V0, p2);
+        new_vertex_value(m2, p2, c, a, mask, f, uv, uvf);
         tri[T + fscan[T + t]] = make_int4(a, m, m2, 0);
         kept = make_int4(m, c, m2, 0);
     }
     if (flags[2 * T + t]) {  // new child's refinement edge (b, c) is marked
-        int m1 = midpoint_id(bmM, wpre, V0, mid_pixel(pb, pc, N));
-        uv[m1] = 0.5 * (uv[b] + uv[c]);
+        long long p1 = mid_pixel(pb, pc, N);
+        int m1 = midpoint_id(bmM, wpre, V0, p1);
+        new_vertex_value(m1, p1, b, c, mask, f, uv, uvf);
         tri[T + fscan[2 * T + t]] = make_int4(c, m, m1, 0);
         fresh = make_int4(m, b, m1, 0);
     }
@@ -457,43 +504,51 @@ __global__ void k_bisect(int4* __restrict__ tri, const int2* __restrict__ vxy, i
 // refinement replaces each triangle by its children in curve order.
 __device__ __forceinline__ int entered_at_b(int2 a, int2 c) { return (c.x != a.x && c.y != a.y) ? 1 : 0; }
 
-__global__ void k_order_count(const int* __restrict__ order, const int* __restrict__ flags, int T,
-                              int* __restrict__ cnt) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= T) return;
-    int t = order[i];
-    cnt[i] = 1 + flags[t] + flags[T + t] + flags[2 * T + t];
-}
+// Curve order of the refined mesh as one fused scan: the input is the
+// number of children that entry i of the order becomes, the output writes
+// them in curve order.
+struct OrderCountIn {
+    const int* order;
+    const int* flags;
+    int T;
+    __device__ __forceinline__ int operator()(long long i) const {
+        int t = order[i];
+        return 1 + flags[t] + flags[T + t] + flags[2 * T + t];
+    }
+};
 
 // runs before k_bisect: reads the parents' geometry
-__global__ void k_order_expand(const int* __restrict__ order, const int* __restrict__ off,
-                               const int* __restrict__ flags, const int* __restrict__ fscan,
-                               const int4* __restrict__ tri, const int2* __restrict__ vxy, int T,
-                               int* __restrict__ order_new) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= T) return;
-    int t = order[i];
-    int o = off[i];
-    if (!flags[t]) {
-        order_new[o] = t;
-        return;
+struct OrderExpandOut {
+    const int* order;
+    const int* flags;
+    const int* fscan;
+    const int4* tri;
+    const int2* vxy;
+    int T;
+    int* order_new;
+    __device__ __forceinline__ void operator()(long long i, int o, int) const {
+        int t = order[i];
+        if (!flags[t]) {
+            order_new[o] = t;
+            return;
+        }
+        int4 tr = tri[t];
+        int d = entered_at_b(vxy[tr.x], vxy[tr.z]);
+        int kept = t, fresh = T + fscan[t];
+        int e2 = flags[T + t], e1 = flags[2 * T + t];
+        int kn = e2 ? T + fscan[T + t] : -1;      // second child of (c,a,m)
+        int nn = e1 ? T + fscan[2 * T + t] : -1;  // second child of (b,c,m)
+        if (d == 0) {
+            // (c,a,m) part then (b,c,m) part; children are entered at b
+            if (e2) { order_new[o++] = kn; order_new[o++] = kept; } else { order_new[o++] = kept; }
+            if (e1) { order_new[o++] = nn; order_new[o++] = fresh; } else { order_new[o++] = fresh; }
+        } else {
+            // (b,c,m) part then (c,a,m) part; children are entered at a
+            if (e1) { order_new[o++] = fresh; order_new[o++] = nn; } else { order_new[o++] = fresh; }
+            if (e2) { order_new[o++] = kept; order_new[o++] = kn; } else { order_new[o++] = kept; }
+        }
     }
-    int4 tr = tri[t];
-    int d = entered_at_b(vxy[tr.x], vxy[tr.z]);
-    int kept = t, fresh = T + fscan[t];
-    int e2 = flags[T + t], e1 = flags[2 * T + t];
-    int kn = e2 ? T + fscan[T + t] : -1;      // second child of (c,a,m)
-    int nn = e1 ? T + fscan[2 * T + t] : -1;  // second child of (b,c,m)
-    if (d == 0) {
-        // (c,a,m) part then (b,c,m) part; children are entered at b
-        if (e2) { order_new[o++] = kn; order_new[o++] = kept; } else { order_new[o++] = kept; }
-        if (e1) { order_new[o++] = nn; order_new[o++] = fresh; } else { order_new[o++] = fresh; }
-    } else {
-        // (b,c,m) part then (c,a,m) part; children are entered at a
-        if (e1) { order_new[o++] = fresh; order_new[o++] = nn; } else { order_new[o++] = fresh; }
-        if (e2) { order_new[o++] = kept; order_new[o++] = kn; } else { order_new[o++] = kept; }
-    }
-}
+};
 
 // Cooperative grid: one thread per work item, at most the co-resident
 // blocks (occupancy queried once per kernel).
@@ -519,16 +574,28 @@ static int coop_grid(const void* func, int threads, int work, int num_sms) {
 // One refinement round on the current keys (m->keys).  Returns k via k_out.
 fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vstar, cudaStream_t s, double* margin_out,
                         int* k_out) {
-    (void)f;
     int T = m->T, V = m->V, N = m->N;
     long long W = (m->P + 31) / 32;
-    FEM_TRY(ensure(m->bmM, (size_t)W, s));
-    FEM_TRY(ensure(m->bmS, (size_t)W, s));
+    // two buffers per edge bitmap, alternating by round; fresh memory is
+    // cleared once, afterwards the new-vertex scan clears the other round's
+    // buffer
+    if (!m->bm_clean || !m->bmM.p || !m->bmS.p || m->bmM.n < (size_t)(2 * W) || m->bmS.n < (size_t)(2 * W)) {
+        FEM_TRY(ensure(m->bmM, (size_t)(2 * W), s));
+        FEM_TRY(ensure(m->bmS, (size_t)(2 * W), s));
+        FEM_CUDA(cudaMemsetAsync(m->bmM.p, 0, sizeof(unsigned) * m->bmM.n, s));
+        FEM_CUDA(cudaMemsetAsync(m->bmS.p, 0, sizeof(unsigned) * m->bmS.n, s));
+        m->bm_clean = true;
+        m->bm_parity = 0;
+    }
+    m->bm_clean = false;  // until this round's clearing pass is known to have run
+    unsigned* bmM = m->bmM.p + (m->bm_parity ? W : 0);
+    unsigned* bmS = m->bmS.p + (m->bm_parity ? W : 0);
+    unsigned* bmM_other = m->bmM.p + (m->bm_parity ? 0 : W);
+    unsigned* bmS_other = m->bmS.p + (m->bm_parity ? 0 : W);
     FEM_TRY(ensure(m->wpre, (size_t)W + 1, s));
     FEM_TRY(ensure(m->topk_hist, (size_t)12 * 256 + 8, s));
     FEM_TRY(ensure(m->flags, (size_t)3 * T + 1, s));
     FEM_TRY(ensure(m->fscan, (size_t)3 * T + 1, s));
-    FEM_TRY(ensure(m->wcnt, (size_t)W + 1, s));
     // capacity: at most one new vertex per edge (E = V + T - 1), at most 4 children per triangle
     FEM_TRY(ensure_mesh_capacity(m, V + T + V + 4, 4 * T, s));
     unsigned* hist = m->topk_hist.p;
@@ -541,14 +608,9 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
     unsigned long long* thr = (unsigned long long*)(m->dscal.p + 8);
     unsigned long long* below = (unsigned long long*)(m->dscal.p + 10);
     double* margin = m->dscal.p + 11;
-    int* err = m->dflag.p + 2;
-    FEM_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned) * (12 * 256 + 1), s));
-    FEM_CUDA(cudaMemsetAsync(below, 0, sizeof(unsigned long long), s));
-    FEM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    FEM_CUDA(cudaMemsetAsync(m->bmM.p, 0, sizeof(unsigned) * W, s));
-    FEM_CUDA(cudaMemsetAsync(m->bmS.p, 0, sizeof(unsigned) * W, s));
-    FEM_CUDA(cudaMemsetAsync(changed, 0, sizeof(int) * 48, s));
-    FEM_CUDA(cudaMemsetAsync(nmask_new, 0, sizeof(int), s));
+    int* err = m->dcount.p + 7;
+    // counters 6..63: new mask vertices, error flag, closure sweep flags
+    FEM_CUDA(cudaMemsetAsync(m->dcount.p + 6, 0, sizeof(int) * 58, s));
 
     TopkArgs A;
     A.keys = m->keys.p;
@@ -575,45 +637,43 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
         FEM_LAUNCH(F_TOPK, s, k_topk_block, 1, kTopkBlockThreads, kTopkBlockSmem, m->keyc.p, T, frac, vstar - V,
                    kdev, thr, margin);
     } else {
+        FEM_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned) * (12 * 256 + 1), s));
+        FEM_CUDA(cudaMemsetAsync(below, 0, sizeof(unsigned long long), s));
         void* args[] = {&A};
         int grid = coop_grid((const void*)k_topk, kTopkThreads, T, m->num_sms);
         FEM_TRY(launch_coop(F_TOPK, (const void*)k_topk, grid, kTopkThreads, 0, s, args, "k_topk"));
     }
     int tb = (T + 255) / 256;
-    FEM_LAUNCH(F_REFINE, s, k_mark_selected, tb, 256, 0, m->keys.p, m->tri.p, m->vxy.p, T, N, thr, kdev, m->bmM.p,
-               m->bmS.p);
+    FEM_LAUNCH(F_REFINE, s, k_mark_selected, tb, 256, 0, m->keys.p, m->tri.p, m->vxy.p, T, N, thr, kdev, bmM, bmS);
     {
         int max_sweeps = 48;
-        void* args[] = {(void*)&m->tri.p, (void*)&m->vxy.p, (void*)&T, (void*)&N, (void*)&m->bmM.p,
+        void* args[] = {(void*)&m->tri.p, (void*)&m->vxy.p, (void*)&T, (void*)&N, (void*)&bmM,
                         (void*)&changed, (void*)&max_sweeps, (void*)&m->bar.p, (void*)&err, (void*)&sweeps};
         int grid = coop_grid((const void*)k_closure, 256, T, m->num_sms);
         FEM_TRY(launch_coop(F_REFINE, (const void*)k_closure, grid, 256, 0, s, args, "k_closure"));
     }
     int Wi = (int)W;
-    FEM_LAUNCH(F_REFINE, s, k_word_popc, (Wi + 255) / 256, 256, 0, m->bmM.p, Wi, m->wcnt.p);
-    FEM_TRY(scan_i32(m, m->wcnt.p, (int*)m->wpre.p, Wi, s, nnew));
-    FEM_LAUNCH(F_REFINE, s, k_new_vertices, (Wi + 255) / 256, 256, 0, m->bmM.p, m->bmS.p, (const int*)m->wpre.p, Wi,
-               N, V, m->vxy.p, m->mask.p, nmask_new);
-    FEM_LAUNCH(F_REFINE, s, k_bisect_flags, tb, 256, 0, m->tri.p, m->vxy.p, T, N, m->bmM.p, m->flags.p);
-    FEM_TRY(scan_i32(m, m->flags.p, m->fscan.p, 3 * T, s, ntri));
+    FEM_TRY(scan_fused(m, WordIn{bmM, bmM_other, bmS_other},
+                       NewVertexOut{bmM, bmS, (int*)m->wpre.p, N, V, m->vxy.p, m->mask.p, nmask_new}, Wi, s, nnew,
+                       F_REFINE));
+    m->bm_parity ^= 1;
+    FEM_TRY(scan_fused(m, BisectFlagIn{m->tri.p, m->vxy.p, bmM, T, N, m->flags.p}, ScanStore{m->fscan.p}, 3 * T, s,
+                       ntri, F_REFINE));
     // curve order of the refined mesh (before k_bisect overwrites the parents)
-    FEM_TRY(ensure(m->ocnt, (size_t)T + 1, s));
-    FEM_TRY(ensure(m->ooff, (size_t)T + 1, s));
     FEM_TRY(ensure(m->order_tmp, (size_t)4 * T, s));
-    FEM_LAUNCH(F_REFINE, s, k_order_count, tb, 256, 0, m->order.p, m->flags.p, T, m->ocnt.p);
-    FEM_TRY(scan_i32(m, m->ocnt.p, m->ooff.p, T, s, nullptr));
-    FEM_LAUNCH(F_REFINE, s, k_order_expand, tb, 256, 0, m->order.p, m->ooff.p, m->flags.p, m->fscan.p, m->tri.p,
-               m->vxy.p, T, m->order_tmp.p);
-    FEM_LAUNCH(F_REFINE, s, k_bisect, tb, 256, 0, m->tri.p, m->vxy.p, T, N, m->bmM.p, (const int*)m->wpre.p, V,
-               m->flags.p, m->fscan.p, m->uv.p);
+    FEM_TRY(scan_fused(m, OrderCountIn{m->order.p, m->flags.p, T},
+                       OrderExpandOut{m->order.p, m->flags.p, m->fscan.p, m->tri.p, m->vxy.p, T, m->order_tmp.p}, T,
+                       s, nullptr, F_REFINE));
+    FEM_LAUNCH(F_REFINE, s, k_bisect, tb, 256, 0, m->tri.p, m->vxy.p, T, N, bmM, (const int*)m->wpre.p, V,
+               m->flags.p, m->fscan.p, m->mask.p, f, m->uv.p, m->uvf.p);
     // read back k, sweeps, new counts, margin, error
     int* hs = (int*)m->host_stage;
     FEM_CUDA(cudaMemcpyAsync(hs, m->dcount.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    FEM_CUDA(cudaMemcpyAsync(hs + 8, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaMemcpyAsync(hs + 9, m->dflag.p + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaMemcpyAsync((double*)(hs + 16), margin, sizeof(double), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));
-    int k = hs[2], nn = hs[4], nt = hs[5], nkm = hs[6], e = hs[8] ? hs[8] : hs[9];
+    int k = hs[2], nn = hs[4], nt = hs[5], nkm = hs[6], e = hs[7] ? hs[7] : hs[9];
+    m->bm_clean = true;  // the round ran to the end: the next buffer is clear
     double mg = *(double*)(hs + 16);
     if (e) {
         cudaMemsetAsync(m->bar.p, 0, 2 * sizeof(unsigned), s);
@@ -659,9 +719,11 @@ extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double
     // solve results are accumulated on the device and read once at the end
     FEM_TRY(solve_totals_reset(m, s));
     FEM_CUDA(cudaMemsetAsync(m->dflag.p + 8, 0, sizeof(int), s));  // scan wait flag
+    // mask vertices take their image values once; vertices made by the
+    // refinement get theirs when they are created (k_bisect)
+    FEM_TRY(set_uv_from_f(m, f_dev, s));
     while ((long long)m->V < vstar && (p->max_rounds <= 0 || round < p->max_rounds)) {
         FEM_TRY(build_system(m, s));
-        FEM_TRY(set_uv_from_f(m, f_dev, s));
         fem_status st = solve_laplace(m, p->precision == FEM_PREC_FP64, p->tol, p->maxit, s, nullptr, nullptr, true);
         if (st != FEM_OK) return st;
         FEM_TRY(ensure(m->keys, (size_t)m->T, s));

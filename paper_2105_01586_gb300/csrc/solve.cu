@@ -20,6 +20,7 @@
 
 #include "fem_internal.cuh"
 #include "ff.cuh"
+#include "scan.cuh"
 
 namespace fem {
 
@@ -56,44 +57,56 @@ __global__ void k_assemble(const int4* __restrict__ tri, const int2* __restrict_
     atomicAdd(&diag[b], 0.5f);
 }
 
-// Unknown flags, and the start state of the component search
-// (components.cu): the parent of an unknown vertex is its smallest unknown
-// neighbour through a nonzero entry (or itself), which leaves most small
-// components with shallow trees before any hooking.
-__global__ void k_unknown_flags(const unsigned char* __restrict__ mask, const int* __restrict__ nbr,
-                                const float* __restrict__ coef, int V, int* __restrict__ flag,
-                                int* __restrict__ parent, int* __restrict__ size, int* __restrict__ fill) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= V) return;
-    int pa = i;
-    if (!mask[i]) {
+// Unknown flags (scan input; also the start state of the component search
+// in components.cu: the parent of an unknown vertex is its smallest unknown
+// neighbour through a nonzero entry, or itself, which leaves most small
+// components with shallow trees before any hooking).
+struct UnknownIn {
+    const unsigned char* mask;
+    const int* nbr;
+    const float* coef;
+    int V;
+    int* parent;
+    int* size;
+    int* fill;
+    __device__ __forceinline__ int operator()(long long li) const {
+        int i = (int)li;
+        int pa = i;
+        bool unk = !mask[i];
+        if (unk) {
 #pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            int j = nbr[d * V + i];
-            if (j >= 0 && j < pa && coef[d * V + i] != 0.0f && !mask[j]) pa = j;
+            for (int d = 0; d < 8; ++d) {
+                int j = nbr[d * V + i];
+                if (j >= 0 && j < pa && coef[d * V + i] != 0.0f && !mask[j]) pa = j;
+            }
+        }
+        parent[i] = pa;
+        size[i] = 0;
+        fill[i] = 0;
+        return unk ? 1 : 0;
+    }
+};
+
+// index maps from the exclusive count u of unknowns before vertex i: mask
+// vertices are numbered i - u; rows of unknowns are numbered by component
+// (build_components), uidx is -1 at mask vertices
+struct IndexMapsOut {
+    const unsigned char* mask;
+    int* uidx;
+    int* kidx;
+    int* kvert;
+    __device__ __forceinline__ void operator()(long long li, int u, int unk) const {
+        int i = (int)li;
+        if (!unk) {
+            int k = i - u;
+            kidx[i] = k;
+            kvert[k] = i;
+            uidx[i] = -1;
+        } else {
+            kidx[i] = -1;
         }
     }
-    flag[i] = mask[i] ? 0 : 1;
-    parent[i] = pa;
-    size[i] = 0;
-    fill[i] = 0;
-}
-
-__global__ void k_index_maps(const unsigned char* __restrict__ mask, int V, int* __restrict__ uidx,
-                             int* __restrict__ kidx, int* __restrict__ kvert) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= V) return;
-    int u = uidx[i];  // exclusive count of unknowns before i
-    if (mask[i]) {
-        int k = i - u;
-        kidx[i] = k;
-        kvert[k] = i;
-        uidx[i] = -1;
-    } else {
-        // rows of unknowns are numbered by component (build_components)
-        kidx[i] = -1;
-    }
-}
+};
 
 __global__ void k_build_ell(int nU, int V, const int* __restrict__ urow_vertex, const int* __restrict__ nbr,
                             const float* __restrict__ coef, const float* __restrict__ diag,
@@ -164,7 +177,6 @@ fem_status build_system(fem_mesh* m, cudaStream_t s) {
     FEM_TRY(ensure(m->diagA, V, s));
     FEM_TRY(ensure(m->uidx, V, s));
     FEM_TRY(ensure(m->kidx, V, s));
-    FEM_TRY(ensure(m->flags, (size_t)V + 1, s));
     FEM_TRY(ensure(m->urow_vertex, V, s));
     FEM_TRY(ensure(m->kvert, V, s));
     FEM_CUDA(cudaMemsetAsync(m->nbr.p, 0xff, sizeof(int) * 8 * V, s));
@@ -172,15 +184,12 @@ fem_status build_system(fem_mesh* m, cudaStream_t s) {
     FEM_CUDA(cudaMemsetAsync(m->diagA.p, 0, sizeof(float) * V, s));
     FEM_LAUNCH(F_ASSEMBLY, s, k_assemble, (T + 255) / 256, 256, 0, m->tri.p, m->vxy.p, T, V, m->nbr.p, m->coefA.p,
                m->diagA.p);
-    int vb = (V + 255) / 256;
     FEM_TRY(ensure(m->cc_parent, V, s));
     FEM_TRY(ensure(m->cc_size, V, s));
     FEM_TRY(ensure(m->cc_fill, V, s));
-    FEM_LAUNCH(F_ASSEMBLY, s, k_unknown_flags, vb, 256, 0, m->mask.p, m->nbr.p, m->coefA.p, V, m->flags.p,
-               m->cc_parent.p, m->cc_size.p, m->cc_fill.p);
     int* nU_dev = m->dcount.p + 1;
-    FEM_TRY(scan_i32(m, m->flags.p, m->uidx.p, V, s, nU_dev));
-    FEM_LAUNCH(F_ASSEMBLY, s, k_index_maps, vb, 256, 0, m->mask.p, V, m->uidx.p, m->kidx.p, m->kvert.p);
+    FEM_TRY(scan_fused(m, UnknownIn{m->mask.p, m->nbr.p, m->coefA.p, V, m->cc_parent.p, m->cc_size.p, m->cc_fill.p},
+                       IndexMapsOut{m->mask.p, m->uidx.p, m->kidx.p, m->kvert.p}, V, s, nU_dev, F_ASSEMBLY));
     // the mask count is kept on the host by create / import / refinement, so
     // the unknown count needs no read-back
     int nU = V - m->nK;
