@@ -233,6 +233,7 @@ struct fem_mesh {
     fem::DArr<float2> bxff, bbff;       // float-float iterate and right-hand side
     fem::DArr<unsigned long long> scan_status;  // look-back scan tile status words
     fem::DArr<unsigned long long> scan_ctr;     // look-back scan tile counter
+    fem::DArr<int> scan_vals, scan_pre;         // unfused scans of large inputs: values, prefixes
     unsigned long long scan_tiles_issued = 0;
     unsigned scan_epoch = 0;
     fem::DArr<double> red;          // grid-reduction partials

@@ -148,13 +148,30 @@ struct ScanIn {
 
 // out[i] = sum of in[0..i-1]; *total_dev (if non-null) = sum of all (one launch)
 fem_status scan_i32(fem_mesh* m, const int* in, int* out, int n, cudaStream_t s, int* total_dev) {
-    return scan_fused<SCAN_IPT>(m, ScanIn{in, nullptr, nullptr, nullptr}, ScanStore{out}, n, s, total_dev, F_OTHER);
+    if (n <= 0) {
+        if (total_dev) FEM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int), s));
+        return FEM_OK;
+    }
+    return scan_fused_ipt<SCAN_IPT>(m, ScanIn{in, nullptr, nullptr, nullptr}, ScanStore{out}, n, s, total_dev,
+                                    F_OTHER);
 }
 
 // out[v] = rows of the components whose root (smallest vertex) is below v
 fem_status scan_component_rows(fem_mesh* m, const unsigned char* mask, const int* root, const int* size, int* out,
                                int n, cudaStream_t s, int* total_dev) {
-    return scan_fused<2>(m, ScanIn{nullptr, mask, root, size}, ScanStore{out}, n, s, total_dev, F_OTHER);
+    if (n <= 0) {
+        if (total_dev) FEM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int), s));
+        return FEM_OK;
+    }
+    return scan_fused_ipt<2>(m, ScanIn{nullptr, mask, root, size}, ScanStore{out}, n, s, total_dev, F_OTHER);
+}
+
+fem_status scan_scratch(fem_mesh* m, int n, cudaStream_t s, int** vals, int** pre) {
+    FEM_TRY(ensure(m->scan_vals, (size_t)n, s));
+    FEM_TRY(ensure(m->scan_pre, (size_t)n, s));
+    *vals = m->scan_vals.p;
+    *pre = m->scan_pre.p;
+    return FEM_OK;
 }
 
 fem_status scan_plan(fem_mesh* m, int n, int tile, cudaStream_t s, ScanPlan* plan) {
@@ -445,7 +462,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->r32, s); release(m->p32, s); release(m->q32, s); release(m->z32, s); release(m->d32, s);
     release(m->bvec, s); release(m->browptr, s); release(m->bent, s); release(m->bdg2, s);
     release(m->bxff, s); release(m->bbff, s);
-    release(m->scan_status, s); release(m->scan_ctr, s);
+    release(m->scan_status, s); release(m->scan_ctr, s); release(m->scan_vals, s); release(m->scan_pre, s);
     release(m->red, s); release(m->bar, s); release(m->dflag, s); release(m->dscal, s); release(m->dcount, s);
     release(m->inc, s); release(m->loc, s); release(m->Moff, s); release(m->Mdiag, s);
     release(m->tv, s); release(m->ty, s); release(m->tz, s); release(m->tg, s);

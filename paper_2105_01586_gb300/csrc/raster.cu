@@ -626,8 +626,15 @@ fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, const
     FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
                m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p, (float*)nullptr,
                (int*)nullptr, m->item_cnt.p, m->item_done.p, err_out, keyc_out);
-    FEM_LAUNCH(F_RASTER, s, k_raster_small_err_tiled, (m->T + kTileTris - 1) / kTileTris, kTileThreads, 0,
-               m->order.p, m->tri.p, m->vxy.p, uv, uvf, f, m->N, m->T, err_out, keyc_out);
+    // Few small triangles: eight lanes each over staged tiles, which shortens
+    // the longest thread.  Many (above about 1k per SM): one thread each,
+    // which avoids the eight-fold plane setup once every SM is full anyway.
+    if (m->T <= m->num_sms * 1024)
+        FEM_LAUNCH(F_RASTER, s, k_raster_small_err_tiled, (m->T + kTileTris - 1) / kTileTris, kTileThreads, 0,
+                   m->order.p, m->tri.p, m->vxy.p, uv, uvf, f, m->N, m->T, err_out, keyc_out);
+    else
+        FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv,
+                   uvf, f, m->N, m->T, err_out, keyc_out, (float*)nullptr, (int*)nullptr);
     return FEM_OK;
 }
 

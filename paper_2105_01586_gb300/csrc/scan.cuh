@@ -163,14 +163,8 @@ struct ScanPlan {
 };
 fem_status scan_plan(fem_mesh* m, int n, int tile, cudaStream_t s, ScanPlan* plan);
 
-// Fused scan: one launch.  *total_dev (if non-null) receives the sum of all
-// inputs; n == 0 only writes the total.
-template <int IPT = 1, class In, class Out>
-fem_status scan_fused(fem_mesh* m, In in, Out out, int n, cudaStream_t s, int* total_dev, int family) {
-    if (n <= 0) {
-        if (total_dev) FEM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int), s));
-        return FEM_OK;
-    }
+template <int IPT, class In, class Out>
+fem_status scan_fused_ipt(fem_mesh* m, In in, Out out, int n, cudaStream_t s, int* total_dev, int family) {
     ScanPlan sp;
     FEM_TRY(scan_plan(m, n, SCAN_BT * IPT, s, &sp));
     note_launch_begin(family, s);
@@ -179,6 +173,63 @@ fem_status scan_fused(fem_mesh* m, In in, Out out, int n, cudaStream_t s, int* t
     cudaError_t e = cudaGetLastError();
     note_launch_end(family, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_scan_fused");
+    return FEM_OK;
+}
+
+// producer and consumer as separate element-parallel kernels (large inputs)
+template <class In>
+__global__ void k_scan_apply_in(In in, int* __restrict__ vals, int n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) vals[i] = in(i);
+}
+
+template <class Out>
+__global__ void k_scan_apply_out(Out out, const int* __restrict__ pre, const int* __restrict__ vals, int n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out(i, pre[i], vals[i]);
+}
+
+struct ScanLoad {
+    const int* src;
+    __device__ __forceinline__ int operator()(long long i) const { return src[i]; }
+};
+struct ScanStoreTo {
+    int* dst;
+    __device__ __forceinline__ void operator()(long long i, int prefix, int) const { dst[i] = prefix; }
+};
+
+// two int scratch arrays of n elements for the unfused form; mesh.cu
+fem_status scan_scratch(fem_mesh* m, int n, cudaStream_t s, int** vals, int** pre);
+
+// Scan with producer in() and consumer out(): up to kScanSmallN elements
+// one fused launch with one element per thread (per-element work spread
+// over many blocks, no intermediate arrays); beyond, the producer, a plain
+// scan and the consumer as three element-parallel launches, which keep
+// every element's loads independent on large inputs.  *total_dev (if
+// non-null) receives the sum of all inputs; n == 0 only writes the total.
+constexpr int kScanSmallN = 1 << 17;
+
+template <class In, class Out>
+fem_status scan_fused(fem_mesh* m, In in, Out out, int n, cudaStream_t s, int* total_dev, int family) {
+    if (n <= 0) {
+        if (total_dev) FEM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int), s));
+        return FEM_OK;
+    }
+    if (n <= kScanSmallN) return scan_fused_ipt<1>(m, in, out, n, s, total_dev, family);
+    int *vals = nullptr, *pre = nullptr;
+    FEM_TRY(scan_scratch(m, n, s, &vals, &pre));
+    int blocks = (n + 255) / 256;
+    note_launch_begin(family, s);
+    k_scan_apply_in<In><<<blocks, 256, 0, s>>>(in, vals, n);
+    cudaError_t e = cudaGetLastError();
+    note_launch_end(family, s);
+    if (e != cudaSuccess) return cuda_fail(e, "k_scan_apply_in");
+    FEM_TRY(scan_fused_ipt<SCAN_IPT>(m, ScanLoad{vals}, ScanStoreTo{pre}, n, s, total_dev, family));
+    note_launch_begin(family, s);
+    k_scan_apply_out<Out><<<blocks, 256, 0, s>>>(out, pre, vals, n);
+    e = cudaGetLastError();
+    note_launch_end(family, s);
+    if (e != cudaSuccess) return cuda_fail(e, "k_scan_apply_out");
     return FEM_OK;
 }
 
