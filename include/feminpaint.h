@@ -63,7 +63,7 @@ enum {
 
 /* Solver and optimisation parameters.  fem_params_default() fills:
  * tol 1e-12, maxit 20000, precision FP32_IR, topk_frac 0.01, max_rounds 0,
- * tonal_tol 1e-8, tonal_maxit 2000, inner_tol 1e-11. */
+ * tonal_tol 1e-8, tonal_maxit 2000, inner_tol 1e-11, fast_keys -1. */
 typedef struct {
     double tol;         /* Laplace solve: stop at ||b - A x|| <= tol ||b|| (FP64 residual) */
     int maxit;          /* Laplace solve: cap on CG iterations summed over refinement steps */
@@ -73,6 +73,11 @@ typedef struct {
     double tonal_tol;   /* tonal: stop at ||B^T (f - B g)|| <= tonal_tol ||B^T f|| */
     int tonal_maxit;    /* tonal: cap on outer CG iterations */
     double inner_tol;   /* tonal and adjoint: relative tolerance of the inner Laplace solves */
+    int fast_keys;      /* spatial: how the selection keys are computed (the selected set is
+                           the same either way): 0 = float-float for every triangle; 1 = FP32
+                           with a rigorous error bound for every triangle and float-float only
+                           for the triangles whose bound straddles the k-th key; -1 = 1 from
+                           2049 x 2049 pixels on, else 0 */
 } fem_params;
 
 /* Counters of the last call on a mesh (host copy). */
@@ -170,6 +175,17 @@ FEM_API fem_status fem_triangle_errors(fem_mesh *m, const double *uv_dev, const 
 FEM_API fem_status fem_triangle_errors_noalloc(int width, int V, const int *xy_dev, int T, const int *tri_dev,
                                                const double *uv_dev, const float *f_dev, double *err_dev,
                                                void *stream);
+
+/* FP32 error bounds of the per-triangle squared errors (the fast keys of the
+ * spatial optimisation, Sec. 3 error map): for every triangle t an interval
+ * [lo_dev[t], hi_dev[t]] that contains the float-float key of
+ * fem_triangle_errors (u linear on t from the vertex values uv_dev, f the
+ * image).  The FP32 sum carries a rigorous bound from the number of
+ * roundings of the plane evaluation, the difference and the summation,
+ * widened by 1 %.  uv_dev: V doubles; f_dev: N*N floats; lo_dev, hi_dev: T
+ * doubles (device, caller-owned).  FEM_E_INVALID on null pointers. */
+FEM_API fem_status fem_triangle_error_bounds(fem_mesh *m, const double *uv_dev, const float *f_dev, double *lo_dev,
+                                             double *hi_dev, void *stream);
 
 /* Linear interpolation of vertex values to every pixel (end of Sec. 2.2).
  *   uv_dev    in : V float64 vertex values

@@ -44,7 +44,7 @@ _STATUS = {0: "FEM_OK", 1: "FEM_E_INVALID", 2: "FEM_E_SHAPE", 3: "FEM_E_OOM", 4:
            5: "FEM_E_TIMEOUT", 6: "FEM_E_CUDA"}
 
 EXPORTED = ["fem_params_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_info", "fem_mesh_export",
-            "fem_mesh_import", "fem_mesh_curve_order", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_triangle_errors_noalloc", "fem_rasterize", "fem_spatial_refine",
+            "fem_mesh_import", "fem_mesh_curve_order", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_triangle_error_bounds", "fem_triangle_errors_noalloc", "fem_rasterize", "fem_spatial_refine",
             "fem_tonal_opt", "fem_adjoint", "fem_mesh_stats", "fem_last_error", "fem_profile_enable",
             "fem_profile_read", "fem_launch_count", "fem_selftest_wait_timeout", "fem_server_create",
             "fem_server_submit", "fem_server_wait", "fem_server_result", "fem_server_release", "fem_server_destroy"]
@@ -53,7 +53,7 @@ EXPORTED = ["fem_params_default", "fem_mesh_create", "fem_mesh_destroy", "fem_me
 class fem_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
                 ("topk_frac", ctypes.c_double), ("max_rounds", ctypes.c_int), ("tonal_tol", ctypes.c_double),
-                ("tonal_maxit", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+                ("tonal_maxit", ctypes.c_int), ("inner_tol", ctypes.c_double), ("fast_keys", ctypes.c_int)]
 
 
 class fem_stats(ctypes.Structure):
@@ -77,6 +77,7 @@ _sig = {
     "fem_mesh_curve_order": (_i, [_vp, _vp, _ip]),
     "fem_inpaint": (_i, [_vp, _vp, _vp, _vp, _pp, _vp]),
     "fem_triangle_errors": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "fem_triangle_error_bounds": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "fem_triangle_errors_noalloc": (_i, [_i, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "fem_rasterize": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "fem_spatial_refine": (_i, [_vp, _vp, ctypes.c_double, _pp, _vp]),
@@ -219,6 +220,15 @@ def fem_triangle_errors(h: int, uv, f, err, stream=None):
                                     _dev_ptr(err, torch.float64, T, "err"), _stream(stream)), "fem_triangle_errors")
 
 
+def fem_triangle_error_bounds(h: int, uv, f, lo, hi, stream=None):
+    V, T, K = fem_mesh_info(h)
+    torch = _torch()
+    _check(_lib.fem_triangle_error_bounds(h, _dev_ptr(uv, torch.float64, V, "uv"),
+                                          _dev_ptr(f, torch.float32, None, "f"), _dev_ptr(lo, torch.float64, T, "lo"),
+                                          _dev_ptr(hi, torch.float64, T, "hi"), _stream(stream)),
+           "fem_triangle_error_bounds")
+
+
 def fem_triangle_errors_noalloc(width: int, xy, tri4, uv, f, err, stream=None):
     """Per-triangle errors without any device allocation (fixed library
     scratch; see include/feminpaint.h).  xy: (V, 2) int32, tri4: (T, 4)
@@ -358,6 +368,14 @@ class Mesh:
         err = torch.empty(self.T, dtype=torch.float64, device=f.device)
         fem_triangle_errors(self.h, uv, f, err, stream)
         return err
+
+    def triangle_error_bounds(self, uv, f, stream=None):
+        """FP32 intervals [lo, hi] that contain the keys of triangle_errors."""
+        torch = _torch()
+        lo = torch.empty(self.T, dtype=torch.float64, device=f.device)
+        hi = torch.empty(self.T, dtype=torch.float64, device=f.device)
+        fem_triangle_error_bounds(self.h, uv, f, lo, hi, stream)
+        return lo, hi
 
     def rasterize(self, uv, want_owner=False, stream=None):
         torch = _torch()

@@ -186,6 +186,10 @@ struct fem_mesh {
     // rasterisation plan (valid for plan_T triangles of plan_version)
     fem::DArr<int> item_cnt, item_off, item_tri;
     fem::DArr<int> item_done;  // T: items finished per triangle (fused finalisation), 0 between passes
+    // fast keys (FP32 with error bounds, exact band): intervals, histograms, band lists
+    fem::DArr<double> keys_lo, keys_hi;
+    fem::DArr<unsigned> fast_hist;
+    fem::DArr<int> band, band_items, band_small;
     fem::DArr<double> partial;
     fem::DArr<double> keys;
     fem::DArr<unsigned long long> keyc;  // composite selection keys (eligible flag | key bits)
@@ -287,9 +291,15 @@ fem_status raster_plan(fem_mesh* m, cudaStream_t s);
 fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, const float* f, double* err,
                          cudaStream_t s, unsigned long long* keyc_out = nullptr);
 fem_status raster_image(fem_mesh* m, const double* uv, float* u, int* owner, cudaStream_t s);
+fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, const float* f, double frac,
+                            long long vcap, cudaStream_t s);
 fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s);
 fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vstar, cudaStream_t s,
-                        double* margin_out, int* k_out);
+                        double* margin_out, int* k_out, bool band = false);
+// fast keys: histogram bins (top 16 bits of a non-negative float) and the
+// counters after the two histograms in fem_mesh::fast_hist
+constexpr int kFastBins = 32768;
+enum FastCounter { FC_IN = 0, FC_BAND = 1, FC_BAND_ITEMS = 2, FC_BAND_SMALL = 3 };
 fem_status sync_counts(fem_mesh* m, cudaStream_t s);
 fem_status ensure_mesh_capacity(fem_mesh* m, int needV, int needT, cudaStream_t s);
 int sm_count();

@@ -320,6 +320,7 @@ void fem_params_default(fem_params* p) {
     p->tonal_tol = 1e-8;
     p->tonal_maxit = 2000;
     p->inner_tol = 1e-11;
+    p->fast_keys = -1;
 }
 
 const char* fem_last_error(void) { return g_last_error.c_str(); }
@@ -446,7 +447,8 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->vxy, s); release(m->mask, s); release(m->tri, s); release(m->uv, s); release(m->uvf, s);
     release(m->order, s); release(m->order_tmp, s); release(m->ocnt, s); release(m->ooff, s);
     release(m->item_cnt, s); release(m->item_off, s); release(m->item_tri, s); release(m->partial, s);
-    release(m->item_done, s);
+    release(m->item_done, s); release(m->keys_lo, s); release(m->keys_hi, s); release(m->fast_hist, s);
+    release(m->band, s); release(m->band_items, s); release(m->band_small, s);
     release(m->keys, s);
     release(m->keyc, s);
     release(m->bmM, s); release(m->bmS, s); release(m->wpre, s);

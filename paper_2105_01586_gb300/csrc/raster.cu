@@ -178,15 +178,18 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
     const int* __restrict__ item_off, const int* __restrict__ n_items_dev, int item_cap,
     double* __restrict__ partial, float* __restrict__ u_out, int* __restrict__ owner_out,
     const int* __restrict__ item_cnt = nullptr, int* __restrict__ item_done = nullptr,
-    double* __restrict__ key_out = nullptr, unsigned long long* __restrict__ keyc_out = nullptr) {
+    double* __restrict__ key_out = nullptr, unsigned long long* __restrict__ keyc_out = nullptr,
+    const int* __restrict__ item_list = nullptr) {
     constexpr int NA = NAcc<MODE>::n;
     constexpr bool FF = (MODE == R_ERR || MODE == R_IMG);
     const unsigned FULL = 0xffffffffu;
     int lane = threadIdx.x & 31;
     long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    int n_items = min(*n_items_dev, item_cap);  // never past the plan's capacity
-    for (long long it = warp; it < n_items; it += nwarps) {
+    int n_items = min(*n_items_dev, item_cap);  // never past the capacity
+    for (long long ii = warp; ii < n_items; ii += nwarps) {
+        // item_list: a subset of the plan's items (the band of the fast keys)
+        long long it = item_list ? item_list[ii] : ii;
         int t = item_tri[it];
         int j = (int)(it - item_off[t]);
         int4 tr = tri[t];
@@ -196,14 +199,6 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
         int nr = min(rpi, g.yend + 1 - r0);
         int L = 0, len = 0;
         if (lane < nr) row_span(g, r0 + lane, N, L, len);
-        int incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        int off = incl - len;
-        int total = __shfl_sync(FULL, incl, 31);
 
         int dax = g.ax - g.cx, day = g.ay - g.cy, dbx = g.bx - g.cx, dby = g.by - g.cy;
         long long l2 = (long long)dax * dax + (long long)day * day;
@@ -234,29 +229,36 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
 #pragma unroll
         for (int q = 0; q < (NA > 0 ? NA : 1); ++q) acc[q] = 0.0;
 
-        // pixels are taken kPre chunks of 32 at a time: positions and image
-        // values of all chunks first (kPre loads in flight per lane), then
-        // the arithmetic
+        // The item's rows are cut into chunks of 32 pixels (chunk c of row r
+        // covers its pixels 32c .. 32c+31); lane r holds the first chunk of row
+        // r.  A warp step takes one chunk: a ballot over the lanes' chunk
+        // offsets gives its row, and lane l takes pixel 32c + l.  kPre chunks
+        // are located and their image values loaded before any arithmetic.
+        int ccnt = (len + 31) >> 5, cinc = ccnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL, cinc, o);
+            if (lane >= o) cinc += y;
+        }
+        const int coff = cinc - ccnt;
+        const int nchunks = __shfl_sync(FULL, cinc, 31);
         constexpr int kPre = 4;
         constexpr bool READS = (MODE == R_ERR || MODE == R_SCAT);
-        for (int base0 = 0; base0 < total; base0 += 32 * kPre) {
+        for (int q0 = 0; q0 < nchunks; q0 += kPre) {
             int px[kPre], py[kPre];
             float fv[kPre];
 #pragma unroll
             for (int u = 0; u < kPre; ++u) {
-                int jj = base0 + 32 * u + lane;
-                int k = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    int cand = k + step;
-                    int oc = __shfl_sync(FULL, off, cand & 31);
-                    if (cand < nr && oc <= jj) k = cand;
-                }
-                int Lk = __shfl_sync(FULL, L, k);
-                int okk = __shfl_sync(FULL, off, k);
-                px[u] = jj < total ? Lk + (jj - okk) : -1;
-                py[u] = r0 + k;
-                fv[u] = (READS && jj < total) ? img[(long long)py[u] * N + px[u]] : 0.f;
+                const int q = q0 + u;
+                const unsigned bq = __ballot_sync(FULL, lane < nr && coff <= q);
+                const int r = bq ? 31 - __clz(bq) : 0;
+                const int Lr = __shfl_sync(FULL, L, r), lr = __shfl_sync(FULL, len, r),
+                          cr = __shfl_sync(FULL, coff, r);
+                const int c = ((q - cr) << 5) + lane;
+                const bool ok = q < nchunks && c < lr;
+                px[u] = ok ? Lr + c : -1;
+                py[u] = r0 + r;
+                fv[u] = (READS && ok) ? img[(long long)py[u] * N + px[u]] : 0.f;
             }
 #pragma unroll
             for (int u = 0; u < kPre; ++u) {
@@ -302,16 +304,20 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
             } else {
                 // fused finalisation: the warp that completes a triangle's
                 // items sums its partials and writes the key
+                const int nit = item_cnt[t];
                 int last = 0;
-                if (lane == 0) {
+                if (nit > 1 && lane == 0) {
                     ((float2*)partial)[it] = make_float2(tot.hi, tot.lo);
                     __threadfence();
-                    last = atomicAdd(item_done + t, 1) == item_cnt[t] - 1;
+                    last = atomicAdd(item_done + t, 1) == nit - 1;
                 }
-                last = __shfl_sync(FULL, last, 0);
+                last = nit == 1 ? 1 : __shfl_sync(FULL, last, 0);
                 if (last) {
-                    __threadfence();
-                    ff sum = warp_sum_partials((const float2*)partial, item_off[t], item_cnt[t]);
+                    ff sum = tot;  // one item: its own sum (what the warp sum of one partial gives)
+                    if (nit > 1) {
+                        __threadfence();
+                        sum = warp_sum_partials((const float2*)partial, item_off[t], nit);
+                    }
                     if (lane == 0) {
                         double key = ff_to_double(sum);
                         key_out[t] = key;
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
                             bool eligible = (((g.ax + g.bx) | (g.ay + g.by)) & 1) == 0;
                             keyc_out[t] = eligible ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
                         }
-                        item_done[t] = 0;  // ready for the next pass
+                        if (nit > 1) item_done[t] = 0;  // ready for the next pass
                     }
                 }
             }
@@ -389,8 +395,11 @@ __global__ void __launch_bounds__(256) k_raster_small(const int* __restrict__ or
                                                       const float2* __restrict__ uvf, const float* __restrict__ img,
                                                       int N, int T, double* __restrict__ out,
                                                       unsigned long long* __restrict__ keyc,
-                                                      float* __restrict__ u_out, int* __restrict__ owner_out) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
+                                                      float* __restrict__ u_out, int* __restrict__ owner_out,
+                                                      const int* __restrict__ n_dev = nullptr) {
+    // n_dev: the order list has *n_dev entries (a device-side count, at most T)
+    const int Tn = n_dev ? min(*n_dev, T) : T;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Tn; i += gridDim.x * blockDim.x) {
         int t = order ? order[i] : i;
         int4 tr = tri[t];
         TriGeom g = tri_geom(tr, vxy, N);
@@ -736,3 +745,484 @@ fem_status fem_rasterize(fem_mesh* m, const double* uv_dev, float* u_dev, int* o
 }
 
 }  // extern "C"
+
+namespace fem {
+
+// ===================================================================== fast keys
+// FP32 keys with a rigorous error bound, for the selection of the spatial
+// optimisation on large images.
+//
+// Per triangle the FP32 pass returns S (the sum of FP32 squares) and an
+// interval [lo, hi] that contains the float-float key K of the exact pass:
+//  * u is evaluated in FP32 from the FP32-rounded plane (u_c, g_x, g_y) with
+//    at most three roundings, so |u - u*| <= delta = 5 u M with u = 2^-24 and
+//    M = |u_c| + |g_x| W_x + |g_y| W_y (W = the largest |x - c_x|, |y - c_y|
+//    over the vertices, which bounds it over the triangle);
+//  * d = fl(u - f) adds at most u |d|;
+//  * each partial sum is a chain of at most H FP32 additions of non-negative
+//    terms: |S - sum d^2| <= gamma_H sum d^2, gamma_H = H u / (1 - H u);
+//  * |sum d^2 - sum (u* - f)^2| <= 2 delta sqrt(n D) + 2.0001 u D + 2 n delta^2,
+//    D = S / (1 - gamma_H) >= sum d^2 (Cauchy-Schwarz on sum |d|);
+//  * K itself is within 2^-40 of the real sum (float-float keys).
+// The bound is widened by 1 %.  A histogram of the float bit patterns of lo
+// (rounded down) and hi (rounded up) brackets the k-th largest key between
+// two bin edges; triangles whose interval overlaps the bracket (the band)
+// get their exact float-float key, the others keep lo (surely selected:
+// lo above the upper edge) or hi (surely not: hi below the lower edge).
+// Selecting the k largest of these keys with ties by id gives the same set
+// as selecting on the exact keys: a surely selected key exceeds the k-th
+// exact key, a surely rejected one is below it, and the band is exact.
+// In the fast path triangles with a bounding box up to kFastSide pixels each
+// way are summed one per thread, the larger ones by items (the split of the
+// exact pass).  A wider split (64) was measured slower at 2049^2 and no
+// faster at 8193^2: one thread walking a medium triangle issues a warp load
+// over 32 different rows per pixel.
+constexpr int kFastSide = kSmallSide;
+
+__device__ __forceinline__ bool fast_small(const TriGeom& g) {
+    return g.maxw <= kFastSide && (g.yend - g.ytop + 1) <= kFastSide;
+}
+
+struct FastOut {
+    double* lo;
+    double* hi;
+    unsigned* hlo;
+    unsigned* hhi;
+};
+
+// The bound in FP32 (GB300's FP64 rate would make a per-triangle FP64
+// evaluation, with its divisions and square root, cost more than the pixels
+// of a small triangle).  Every division is replaced by an upper bound
+// (H u / (1 - H u) <= H u (1 + 2 H u) and S / (1 - g) <= S (1 + 2 g) for
+// H u, g <= 1/4), and the about 12 FP32 roundings of the expression (each at
+// most 2^-24 relative, all terms non-negative) are covered by the 2 %
+// widening.
+__device__ __forceinline__ void fast_interval(double S, float n, float M, float H, double& lo, double& hi) {
+    const float u = 5.9604645e-08f;  // 2^-24
+    float hu = H * u;
+    float gam = hu * (1.0f + 2.0f * hu);
+    float D = (float)S * (1.0f + 2.0f * gam) * (1.0f + 2.0f * u);  // (float)S may round down
+    float delta = 5.0f * u * M;
+    float B = gam * D + 2.0f * delta * sqrtf(n * D) + 2.0001f * u * D + 2.0f * n * delta * delta;
+    B = 1.02f * B + 9.094947e-13f * (D + B) + 1e-30f;  // + 2^-40 (D + B)
+    lo = fmax(0.0, S - (double)B);
+    hi = S + (double)B;
+}
+
+__device__ __forceinline__ unsigned fast_bin_lo(double lo) { return __float_as_uint(__double2float_rd(lo)) >> 16; }
+__device__ __forceinline__ unsigned fast_bin_hi(double hi) { return __float_as_uint(__double2float_ru(hi)) >> 16; }
+
+// M of the error bound from the plane and the triangle's extent (FP32; its
+// own rounding is covered by the widening of the bound)
+__device__ __forceinline__ float fast_M(const TriGeom& g, float ucf, float gxf, float gyf) {
+    float wx = (float)max(abs(g.ax - g.cx), abs(g.bx - g.cx));
+    float wy = (float)max(abs(g.ay - g.cy), abs(g.by - g.cy));
+    return (fabsf(ucf) + fabsf(gxf) * wx + fabsf(gyf) * wy) * (1.0f + 1e-6f);
+}
+
+// float-float plane of the interpolant (as in the exact kernels)
+__device__ __forceinline__ void tri_plane(const TriGeom& g, int4 tr, const double* uv, const float2* uvf, ff& uc,
+                                          ff& gx, ff& gy) {
+    int dax = g.ax - g.cx, day = g.ay - g.cy, dbx = g.bx - g.cx, dby = g.by - g.cy;
+    long long l2 = (long long)dax * dax + (long long)day * day;
+    bool pow2 = (l2 & (l2 - 1)) == 0;
+    ff va = vertex_ff(uv, uvf, tr.x), vb = vertex_ff(uv, uvf, tr.y);
+    uc = vertex_ff(uv, uvf, tr.z);
+    ff da = ff_sub(va, uc), db = ff_sub(vb, uc);
+    gx = ff_add(ff_mul_f(da, (float)dax), ff_mul_f(db, (float)dbx));
+    gy = ff_add(ff_mul_f(da, (float)day), ff_mul_f(db, (float)dby));
+    if (pow2) {
+        float inv = __int_as_float((127 - (63 - __clzll(l2))) << 23);
+        gx = ff_scale_pow2(gx, inv);
+        gy = ff_scale_pow2(gy, inv);
+    } else {
+        float inv = 1.0f / (float)l2;
+        gx = ff_mul_f(gx, inv);
+        gy = ff_mul_f(gy, inv);
+    }
+}
+
+__device__ __forceinline__ bool tri_eligible(const TriGeom& g) { return (((g.ax + g.bx) | (g.ay + g.by)) & 1) == 0; }
+
+// Large triangles: the item decomposition of k_raster in FP32.  Item
+// partials are (sum, pixel count); the warp that completes a triangle
+// combines them (float-float sum, integer count) and writes its interval.
+__global__ void __launch_bounds__(kRasterThreads) k_raster_fast(
+    const int4* __restrict__ tri, const int2* __restrict__ vxy, const double* __restrict__ uv,
+    const float2* __restrict__ uvf, const float* __restrict__ img, int N, const int* __restrict__ item_tri,
+    const int* __restrict__ item_off, const int* __restrict__ item_cnt, const int* __restrict__ n_items_dev,
+    int item_cap, float2* __restrict__ partial, int* __restrict__ item_done, FastOut F) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int n_items = min(*n_items_dev, item_cap);
+    for (long long it = warp; it < n_items; it += nwarps) {
+        int t = item_tri[it];
+        int j = (int)(it - item_off[t]);
+        int4 tr = tri[t];
+        TriGeom g = tri_geom(tr, vxy, N);
+        if (fast_small(g)) continue;  // summed by k_raster_small_fast (uniform over the warp)
+        int rpi = rows_per_item(g.maxw);
+        int r0 = g.ytop + j * rpi;
+        int nr = min(rpi, g.yend + 1 - r0);
+        int L = 0, len = 0;
+        if (lane < nr) row_span(g, r0 + lane, N, L, len);
+        int total = warp_sum(len);
+        // chunks of 32 pixels per row, located by a ballot (as in k_raster)
+        int ccnt = (len + 31) >> 5, cinc = ccnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL, cinc, o);
+            if (lane >= o) cinc += y;
+        }
+        const int coff = cinc - ccnt;
+        const int nchunks = __shfl_sync(FULL, cinc, 31);
+        ff uc, gx, gy;
+        tri_plane(g, tr, uv, uvf, uc, gx, gy);
+        const float ucf = __fadd_rn(uc.hi, uc.lo), gxf = __fadd_rn(gx.hi, gx.lo), gyf = __fadd_rn(gy.hi, gy.lo);
+        float acc = 0.f;
+        constexpr int kPre = 4;
+        for (int q0 = 0; q0 < nchunks; q0 += kPre) {
+            int px[kPre], py[kPre];
+            float fv[kPre];
+#pragma unroll
+            for (int u = 0; u < kPre; ++u) {
+                const int q = q0 + u;
+                const unsigned bq = __ballot_sync(FULL, lane < nr && coff <= q);
+                const int r = bq ? 31 - __clz(bq) : 0;
+                const int Lr = __shfl_sync(FULL, L, r), lr = __shfl_sync(FULL, len, r),
+                          cr = __shfl_sync(FULL, coff, r);
+                const int c = ((q - cr) << 5) + lane;
+                const bool ok = q < nchunks && c < lr;
+                px[u] = ok ? Lr + c : -1;
+                py[u] = r0 + r;
+                fv[u] = ok ? img[(long long)py[u] * N + px[u]] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kPre; ++u) {
+                if (px[u] >= 0) {
+                    float uu = fmaf(gyf, (float)(py[u] - g.cy), fmaf(gxf, (float)(px[u] - g.cx), ucf));
+                    float d = uu - fv[u];
+                    acc = fmaf(d, d, acc);
+                }
+            }
+        }
+        float tot = warp_sum(acc);
+        const int nit = item_cnt[t];
+        int last = 0;
+        if (nit > 1 && lane == 0) {
+            partial[it] = make_float2(tot, __int_as_float(total));
+            __threadfence();
+            last = atomicAdd(item_done + t, 1) == nit - 1;
+        }
+        last = nit == 1 ? 1 : __shfl_sync(FULL, last, 0);
+        if (last) {
+            ff s{tot, 0.f};
+            long long cnt = total;
+            if (nit > 1) {
+                __threadfence();
+                const int o = item_off[t];
+                s = ff{0.f, 0.f};
+                cnt = 0;
+                for (int q = lane; q < nit; q += 32) {
+                    float2 v = __ldcg(&partial[o + q]);
+                    s = ff_add_f(s, v.x);
+                    cnt += __float_as_int(v.y);
+                }
+                s = ff_warp_sum(s);
+                cnt = warp_sum(cnt);
+            }
+            if (lane == 0) {
+                // per lane at most 64 chunk pixels per item (32 rows plus 1024
+                // pixels in chunks), a 5-level butterfly, then the float-float
+                // combination of the items
+                double lo, hi;
+                fast_interval(ff_to_double(s), (float)cnt, fast_M(g, ucf, gxf, gyf), 64.0f + 5.0f + 2.0f, lo, hi);
+                F.lo[t] = lo;
+                F.hi[t] = hi;
+                if (tri_eligible(g)) {
+                    atomicAdd(F.hlo + fast_bin_lo(lo), 1u);
+                    atomicAdd(F.hhi + fast_bin_hi(hi), 1u);
+                }
+                if (nit > 1) item_done[t] = 0;
+            }
+        }
+    }
+}
+
+// Small triangles: one thread each along the curve order, FP32 with the
+// plane evaluated afresh per pixel (u = g_x k + u_row, no running sum).
+// Histogram updates are combined per warp for equal bins.
+__global__ void __launch_bounds__(256) k_raster_small_fast(const int* __restrict__ order, const int4* __restrict__ tri,
+                                                           const int2* __restrict__ vxy, const double* __restrict__ uv,
+                                                           const float2* __restrict__ uvf,
+                                                           const float* __restrict__ img, int N, int T, FastOut F) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
+        int t = order ? order[i] : i;
+        int4 tr = tri[t];
+        TriGeom g = tri_geom(tr, vxy, N);
+        bool small = fast_small(g);
+        unsigned blo = 0xffffffffu, bhi = 0xffffffffu;
+        if (small) {
+            ff uc, gx, gy;
+            tri_plane(g, tr, uv, uvf, uc, gx, gy);
+            const float ucf = __fadd_rn(uc.hi, uc.lo), gxf = __fadd_rn(gx.hi, gx.lo),
+                        gyf = __fadd_rn(gy.hi, gy.lo);
+            // row sums (at most kFastSide + 1 terms each), then the sum of the
+            // rows (at most kFastSide + 1 terms): chains of at most
+            // 2 (kFastSide + 1) additions
+            float acc = 0.f;
+            int n = 0;
+            for (int y = g.ytop; y <= g.yend; ++y) {
+                int L, len;
+                row_span(g, y, N, L, len);
+                if (len <= 0) continue;
+                float urow = fmaf(gyf, (float)(y - g.cy), fmaf(gxf, (float)(L - g.cx), ucf));
+                const float* rowp = img + (long long)y * N + L;
+                float racc = 0.f;
+#pragma unroll 4
+                for (int k = 0; k < len; ++k) {
+                    float u = fmaf(gxf, (float)k, urow);
+                    float d = u - rowp[k];
+                    racc = fmaf(d, d, racc);
+                }
+                acc += racc;
+                n += len;
+            }
+            double lo, hi;
+            fast_interval((double)acc, (float)n, fast_M(g, ucf, gxf, gyf), 2.0f * (kFastSide + 1) + 2.0f, lo, hi);
+            F.lo[t] = lo;
+            F.hi[t] = hi;
+            if (tri_eligible(g)) {
+                blo = fast_bin_lo(lo);
+                bhi = fast_bin_hi(hi);
+            }
+        }
+        // histogram: one atomic per distinct bin among the converged lanes
+        unsigned act = __activemask();
+        unsigned peers = __match_any_sync(act, blo);
+        if (blo != 0xffffffffu && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+            atomicAdd(F.hlo + blo, (unsigned)__popc(peers));
+        peers = __match_any_sync(act, bhi);
+        if (bhi != 0xffffffffu && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+            atomicAdd(F.hhi + bhi, (unsigned)__popc(peers));
+    }
+}
+
+// The bracket: k = max(1, ceil(frac T)) capped by the eligible count (the
+// histogram total) and V* - V; the bin of the k-th largest lo gives the
+// lower edge, the bin of the k-th largest hi the upper edge.  One block:
+// lane l of warp w holds the 32 bins starting kFastBins - 1 - 32 (32 w + l)
+// downwards; a warp scan and a scan over the 32 warp totals give every
+// lane the count above its bins, and the lane whose bins reach k walks them.
+constexpr int kBracketThreads = 1024;
+constexpr int kBinsPerThread = kFastBins / kBracketThreads;
+
+__global__ void __launch_bounds__(kBracketThreads) k_fast_bracket(const unsigned* __restrict__ hlo,
+                                                                   const unsigned* __restrict__ hhi, int T,
+                                                                   double frac, long long vcap, int* __restrict__ kdev,
+                                                                   double* __restrict__ tau) {
+    __shared__ int s_wl[kBracketThreads / 32], s_wh[kBracketThreads / 32];
+    __shared__ int s_blo, s_bhi;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int top = kFastBins - 1 - tid * kBinsPerThread;
+    int ml = 0, mh = 0;
+    {
+        // the thread's 32 bins are contiguous: top - 31 .. top
+        const uint4* vl = (const uint4*)(hlo + top - (kBinsPerThread - 1));
+        const uint4* vh = (const uint4*)(hhi + top - (kBinsPerThread - 1));
+#pragma unroll
+        for (int q = 0; q < kBinsPerThread / 4; ++q) {
+            uint4 a = vl[q], b = vh[q];
+            ml += (int)(a.x + a.y + a.z + a.w);
+            mh += (int)(b.x + b.y + b.z + b.w);
+        }
+    }
+    int il = ml, ih = mh;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int a = __shfl_up_sync(0xffffffffu, il, o), c = __shfl_up_sync(0xffffffffu, ih, o);
+        if (lane >= o) { il += a; ih += c; }
+    }
+    if (lane == 31) { s_wl[w] = il; s_wh[w] = ih; }
+    if (tid == 0) { s_blo = 0; s_bhi = 0; }
+    __syncthreads();
+    int bl = 0, bh = 0, tot = 0;
+#pragma unroll
+    for (int q = 0; q < kBracketThreads / 32; ++q) {
+        int vl = s_wl[q], vh = s_wh[q];
+        bl += q < w ? vl : 0;
+        bh += q < w ? vh : 0;
+        tot += vl;
+    }
+    const int exl = bl + il - ml, exh = bh + ih - mh;
+    long long k = (long long)ceil(frac * (double)T);
+    if (k < 1) k = 1;
+    if (k > tot) k = tot;
+    if (k > vcap) k = vcap;
+    if (k < 0) k = 0;
+    if (k > 0 && exl < k && exl + ml >= k) {
+        long long cum = exl;
+        for (int q = 0; q < kBinsPerThread; ++q) {
+            cum += hlo[top - q];
+            if (cum >= k) { s_blo = top - q; break; }
+        }
+    }
+    if (k > 0 && exh < k && exh + mh >= k) {
+        long long cum = exh;
+        for (int q = 0; q < kBinsPerThread; ++q) {
+            cum += hhi[top - q];
+            if (cum >= k) { s_bhi = top - q; break; }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        *kdev = (int)k;
+        tau[0] = (double)__uint_as_float((unsigned)s_blo << 16);
+        tau[1] = (double)__uint_as_float((unsigned)(s_bhi + 1) << 16);
+    }
+}
+
+// Classify every triangle against the bracket: surely selected (key := lo),
+// surely not (key := hi; the largest such composite is kept for the margin),
+// or band (listed; large ones by their items, small ones by id).
+__global__ void k_fast_classify(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int N,
+                                const double* __restrict__ lo, const double* __restrict__ hi,
+                                const double* __restrict__ tau, const int* __restrict__ item_cnt,
+                                const int* __restrict__ item_off, double* __restrict__ keys,
+                                unsigned long long* __restrict__ keyc, int* __restrict__ band,
+                                int* __restrict__ band_items, int* __restrict__ band_small, int* __restrict__ cnt,
+                                unsigned long long* __restrict__ max_out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int cls = 0;  // 0 ineligible / outside, 1 in, 2 out, 3 band
+    unsigned long long comp_out = 0ull;
+    if (t < T) {
+        TriGeom g = tri_geom(tri[t], vxy, N);
+        double l = lo[t], h = hi[t];
+        if (!tri_eligible(g)) {
+            keys[t] = l;
+            keyc[t] = 0ull;
+        } else if (l > tau[1]) {
+            cls = 1;
+            keys[t] = l;
+            keyc[t] = (unsigned long long)__double_as_longlong(l) | (1ull << 63);
+        } else if (h < tau[0]) {
+            cls = 2;
+            comp_out = (unsigned long long)__double_as_longlong(h) | (1ull << 63);
+            keys[t] = h;
+            keyc[t] = comp_out;
+        } else {
+            cls = 3;
+        }
+    }
+    // warp-combined counters
+    unsigned in_mask = __ballot_sync(FULL, cls == 1);
+    if (lane == 0 && in_mask) atomicAdd(cnt + 0, __popc(in_mask));
+    unsigned long long mo = comp_out;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(FULL, mo, o);
+        mo = v > mo ? v : mo;
+    }
+    if (lane == 0 && mo) atomicMax(max_out, mo);
+    unsigned band_mask = __ballot_sync(FULL, cls == 3);
+    int base = 0;
+    if (lane == 0 && band_mask) base = atomicAdd(cnt + 1, __popc(band_mask));
+    base = __shfl_sync(FULL, base, 0);
+    if (cls == 3) {
+        band[base + __popc(band_mask & ((1u << lane) - 1u))] = t;
+        int nc = item_cnt[t];
+        if (nc > 0) {
+            int ip = atomicAdd(cnt + 2, nc);
+            for (int q = 0; q < nc; ++q) band_items[ip + q] = item_off[t] + q;
+        } else {
+            band_small[atomicAdd(cnt + 3, 1)] = t;
+        }
+    }
+}
+
+// Keys of the spatial optimisation by the fast path: on return keys[] and
+// keyc[] hold, for every triangle, the exact key (band) or the substituted
+// bound (outside the band), kdev the total k, and the band list with its
+// counts for the selection (refine_round).
+fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, const float* f, double frac,
+                            long long vcap, cudaStream_t s) {
+    FEM_TRY(raster_plan(m, s));
+    int T = m->T;
+    if (m->item_done.n < (size_t)T || !m->item_done.p) {
+        FEM_TRY(ensure(m->item_done, (size_t)T, s));
+        FEM_CUDA(cudaMemsetAsync(m->item_done.p, 0, sizeof(int) * m->item_done.n, s));
+    }
+    FEM_TRY(ensure(m->keys_lo, (size_t)T, s));
+    FEM_TRY(ensure(m->keys_hi, (size_t)T, s));
+    FEM_TRY(ensure(m->band, (size_t)T, s));
+    FEM_TRY(ensure(m->band_small, (size_t)T, s));
+    FEM_TRY(ensure(m->band_items, m->item_tri.n, s));
+    FEM_TRY(ensure(m->fast_hist, (size_t)2 * kFastBins + 8, s));
+    unsigned* hist = m->fast_hist.p;
+    int* cnt = (int*)(hist + 2 * kFastBins);  // [0] in, [1] band, [2] band items, [3] band small
+    unsigned long long* max_out = (unsigned long long*)(m->dscal.p + 18);
+    double* tau = m->dscal.p + 16;
+    int* kdev = m->dcount.p + 2;
+    FEM_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned) * (2 * kFastBins + 8), s));
+    FEM_CUDA(cudaMemsetAsync(max_out, 0, sizeof(unsigned long long), s));
+    FastOut F{m->keys_lo.p, m->keys_hi.p, hist, hist + kFastBins};
+    // all pixels in FP32
+    note_bytes(F_RASTER, raster_err_bytes(m));
+    FEM_LAUNCH(F_RASTER, s, k_raster_fast, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
+               m->item_tri.p, m->item_off.p, m->item_cnt.p, m->dcount.p + 0, (int)m->item_tri.n,
+               (float2*)m->partial.p, m->item_done.p, F);
+    FEM_LAUNCH(F_RASTER, s, k_raster_small_fast, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv, uvf, f,
+               m->N, T, F);
+    // bracket and classification
+    FEM_LAUNCH(F_TOPK, s, k_fast_bracket, 1, kBracketThreads, 0, hist, hist + kFastBins, T, frac, vcap, kdev, tau);
+    FEM_LAUNCH(F_TOPK, s, k_fast_classify, (T + 255) / 256, 256, 0, m->tri.p, m->vxy.p, T, m->N, m->keys_lo.p,
+               m->keys_hi.p, tau, m->item_cnt.p, m->item_off.p, m->keys.p, m->keyc.p, m->band.p, m->band_items.p,
+               m->band_small.p, cnt, max_out);
+    // exact float-float keys of the band
+    FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
+               m->item_tri.p, m->item_off.p, cnt + 2, (int)m->band_items.n, m->partial.p, (float*)nullptr,
+               (int*)nullptr, m->item_cnt.p, m->item_done.p, m->keys.p, m->keyc.p, m->band_items.p);
+    FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, small_grid(m), 256, 0, m->band_small.p, m->tri.p, m->vxy.p, uv,
+               uvf, f, m->N, T, m->keys.p, m->keyc.p, (float*)nullptr, (int*)nullptr, cnt + 3);
+    return FEM_OK;
+}
+
+}  // namespace fem
+
+using namespace fem;
+
+extern "C" fem_status fem_triangle_error_bounds(fem_mesh* m, const double* uv_dev, const float* f_dev, double* lo_dev,
+                                                double* hi_dev, void* stream) {
+    if (!m || !uv_dev || !f_dev || !lo_dev || !hi_dev) {
+        set_error("fem_triangle_error_bounds: null argument");
+        return FEM_E_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    m->last_stream = s;
+    FEM_TRY(raster_plan(m, s));
+    int T = m->T;
+    if (m->item_done.n < (size_t)T || !m->item_done.p) {
+        FEM_TRY(ensure(m->item_done, (size_t)T, s));
+        FEM_CUDA(cudaMemsetAsync(m->item_done.p, 0, sizeof(int) * m->item_done.n, s));
+    }
+    FEM_TRY(ensure(m->fast_hist, (size_t)2 * kFastBins + 8, s));
+    FEM_CUDA(cudaMemsetAsync(m->fast_hist.p, 0, sizeof(unsigned) * (2 * kFastBins + 8), s));
+    FastOut F{lo_dev, hi_dev, m->fast_hist.p, m->fast_hist.p + kFastBins};
+    FEM_LAUNCH(F_RASTER, s, k_raster_fast, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv_dev,
+               (const float2*)nullptr, f_dev, m->N, m->item_tri.p, m->item_off.p, m->item_cnt.p, m->dcount.p + 0,
+               (int)m->item_tri.n, (float2*)m->partial.p, m->item_done.p, F);
+    FEM_LAUNCH(F_RASTER, s, k_raster_small_fast, small_grid(m), 256, 0, (const int*)nullptr, m->tri.p, m->vxy.p,
+               uv_dev, (const float2*)nullptr, f_dev, m->N, T, F);
+    int e = 0;
+    FEM_CUDA(cudaMemcpyAsync(&e, m->dflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    if (e) {
+        set_error("fem_triangle_error_bounds: rasterisation plan overflow");
+        return (fem_status)e;
+    }
+    return FEM_OK;
+}

@@ -207,9 +207,21 @@ __device__ __forceinline__ bool prefix_match(unsigned long long hi, unsigned lo,
     return (hi & mhi) == pre_hi && (lo & mlo) == pre_lo;
 }
 
+// Band mode (ids != nullptr): select among the *n_dev triangles ids[0..n)
+// only, k = *k_total - *k_sub of them (the surely selected ones are already
+// counted), out_k untouched; *extra_below (the largest key outside the
+// band and below it) joins the margin.
+__device__ __forceinline__ int topk_id(const int* ids, int i) { return ids ? ids[i] : i; }
+
 __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned long long* __restrict__ keyc, int T,
                                                                   double frac, long long vcap, int* out_k,
-                                                                  unsigned long long* out_thr, double* out_margin) {
+                                                                  unsigned long long* out_thr, double* out_margin,
+                                                                  const int* __restrict__ ids = nullptr,
+                                                                  const int* __restrict__ n_dev = nullptr,
+                                                                  const int* __restrict__ k_total = nullptr,
+                                                                  const int* __restrict__ k_sub = nullptr,
+                                                                  const unsigned long long* __restrict__ extra_below =
+                                                                      nullptr) {
     extern __shared__ unsigned char smem_raw[];
     unsigned long long* c_hi = (unsigned long long*)smem_raw;
     unsigned* c_lo = (unsigned*)(c_hi + kTopkCandCap);
@@ -219,20 +231,28 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
     __shared__ long long s_krem;
     __shared__ int s_n, s_cnt, s_smem;
     int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (ids) T = min(*n_dev, T);
     unsigned ne = 0;
-    for (int t = tid; t < T; t += kTopkBlockThreads) ne += keyc[t] ? 1u : 0u;
+    for (int t = tid; t < T; t += kTopkBlockThreads) ne += keyc[topk_id(ids, t)] ? 1u : 0u;
     ne = warp_sum(ne);
     if (lane == 0) s_cnt32[wid] = ne;
     __syncthreads();
     if (tid == 0) {
         long long tot = 0;
         for (int w = 0; w < kTopkBlockThreads / 32; ++w) tot += s_cnt32[w];
-        long long k = (long long)ceil(frac * (double)T);
-        if (k < 1) k = 1;
-        if (k > tot) k = tot;
-        if (k > vcap) k = vcap;
-        if (k < 0) k = 0;
-        *out_k = (int)k;
+        long long k;
+        if (ids) {
+            k = (long long)*k_total - (long long)*k_sub;
+            if (k > tot) k = tot;
+            if (k < 0) k = 0;
+        } else {
+            k = (long long)ceil(frac * (double)T);
+            if (k < 1) k = 1;
+            if (k > tot) k = tot;
+            if (k > vcap) k = vcap;
+            if (k < 0) k = 0;
+            *out_k = (int)k;
+        }
         s_krem = k;
         s_pre_hi = 0;
         s_pre_lo = 0;
@@ -247,7 +267,8 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
         unsigned long long pre_hi = s_pre_hi;
         unsigned pre_lo = s_pre_lo;
         if (!s_smem) {
-            for (int t = tid; t < T; t += kTopkBlockThreads) {
+            for (int i = tid; i < T; i += kTopkBlockThreads) {
+                int t = topk_id(ids, i);
                 unsigned long long hi = keyc[t];
                 unsigned lo = ~(unsigned)t;
                 if (prefix_match(hi, lo, pre_hi, pre_lo, d)) atomicAdd(&hist[digit_of(hi, lo, d)], 1u);
@@ -274,7 +295,8 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
         if (!s_smem && d < 11 && s_cnt <= kTopkCandCap) {
             unsigned long long nh = s_pre_hi;
             unsigned nl = s_pre_lo;
-            for (int t = tid; t < T; t += kTopkBlockThreads) {
+            for (int i = tid; i < T; i += kTopkBlockThreads) {
+                int t = topk_id(ids, i);
                 unsigned long long hi = keyc[t];
                 unsigned lo = ~(unsigned)t;
                 if (prefix_match(hi, lo, nh, nl, d + 1)) {
@@ -291,8 +313,9 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
     unsigned long long thr_hi = s_pre_hi;
     unsigned thr_lo = s_pre_lo;
     // largest key strictly below the threshold (decision margin)
-    unsigned long long best = 0ull;
-    for (int t = tid; t < T; t += kTopkBlockThreads) {
+    unsigned long long best = extra_below ? *extra_below : 0ull;
+    for (int i = tid; i < T; i += kTopkBlockThreads) {
+        int t = topk_id(ids, i);
         unsigned long long hi = keyc[t];
         unsigned lo = ~(unsigned)t;
         if ((hi < thr_hi || (hi == thr_hi && lo < thr_lo)) && hi > best) best = hi;
@@ -573,7 +596,7 @@ static int coop_grid(const void* func, int threads, int work, int num_sms) {
 
 // One refinement round on the current keys (m->keys).  Returns k via k_out.
 fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vstar, cudaStream_t s, double* margin_out,
-                        int* k_out) {
+                        int* k_out, bool band) {
     int T = m->T, V = m->V, N = m->N;
     long long W = (m->P + 31) / 32;
     // two buffers per edge bitmap, alternating by round; fresh memory is
@@ -627,13 +650,20 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
     A.out_thr = thr;
     A.red = m->red.p;
     A.out_margin = margin;
-    if (T <= kTopkBlockMaxT && m->keyc.p && m->keyc.n >= (size_t)T) {
-        // set once per process (thread-safe static initialisation); a failure shows at the launch
-        static const bool attr_set = [] {
-            return cudaFuncSetAttribute(k_topk_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)kTopkBlockSmem) == cudaSuccess;
-        }();
-        (void)attr_set;
+    // set once per process (thread-safe static initialisation); a failure shows at the launch
+    static const bool attr_set = [] {
+        return cudaFuncSetAttribute(k_topk_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kTopkBlockSmem) == cudaSuccess;
+    }();
+    (void)attr_set;
+    if (band) {
+        // fast keys: k and the band were set by raster_keys_fast; the exact
+        // selection runs over the band only
+        int* fc = (int*)(m->fast_hist.p + 2 * kFastBins);
+        FEM_LAUNCH(F_TOPK, s, k_topk_block, 1, kTopkBlockThreads, kTopkBlockSmem, m->keyc.p, T, frac, vstar - V,
+                   (int*)nullptr, thr, margin, m->band.p, fc + FC_BAND, kdev, fc + FC_IN,
+                   (const unsigned long long*)(m->dscal.p + 18));
+    } else if (T <= kTopkBlockMaxT && m->keyc.p && m->keyc.n >= (size_t)T) {
         FEM_LAUNCH(F_TOPK, s, k_topk_block, 1, kTopkBlockThreads, kTopkBlockSmem, m->keyc.p, T, frac, vstar - V,
                    kdev, thr, margin);
     } else {
@@ -730,10 +760,14 @@ extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double
         FEM_TRY(ensure(m->keyc, (size_t)m->T, s));
         // in the spatial loop every vertex value was just written together with
         // its float-float copy (mask vertices from f, unknowns by the solve)
-        FEM_TRY(raster_errors(m, m->uv.p, m->uvf.p, f_dev, m->keys.p, s, m->keyc.p));
+        bool band = p->fast_keys > 0 || (p->fast_keys < 0 && m->P >= 2049LL * 2049);
+        if (band)
+            FEM_TRY(raster_keys_fast(m, m->uv.p, m->uvf.p, f_dev, p->topk_frac, vstar - m->V, s));
+        else
+            FEM_TRY(raster_errors(m, m->uv.p, m->uvf.p, f_dev, m->keys.p, s, m->keyc.p));
         double margin = 0.0;
         int k = 0;
-        FEM_TRY(refine_round(m, f_dev, p->topk_frac, vstar, s, &margin, &k));
+        FEM_TRY(refine_round(m, f_dev, p->topk_frac, vstar, s, &margin, &k, band));
         if (k == 0) break;
         if (margin < m->stats.min_margin) m->stats.min_margin = margin;
         round++;

@@ -142,6 +142,46 @@ def test_spatial_refine_config_1025(oracle_mod, fem, prec):
     assert _same_mesh(m, om)
 
 
+@pytest.mark.parametrize("N,seed,density,frac", [(65, 0, 0.1, 0.0), (129, 1, 0.05, 0.01), (257, 0, 0.05, 0.0),
+                                                  (513, 7, 0.03, 0.01), (1025, 1, 0.03, 0.01)])
+def test_spatial_fast_keys_bit_exact(oracle_mod, fem, N, seed, density, frac):
+    """Selection on FP32 keys with error bounds plus an exact band (forced on
+    at every size): the same meshes as the oracle."""
+    f_np = S.make_image(N, seed)
+    om, log = oracle_mod.spatial(f_np, density, frac)
+    m = fem.Mesh(N)
+    m.spatial_refine(torch.from_numpy(f_np).cuda(), density, fem.params(topk_frac=frac, fast_keys=1))
+    assert m.stats()["rounds"] == len(log)
+    assert _same_mesh(m, om), "fast-key mesh differs from the oracle mesh"
+
+
+@pytest.mark.parametrize("N,seed,texture", [(257, 5, False), (1025, 1, False), (2049, 3, True)])
+def test_error_bounds_contain_exact_keys(oracle_mod, fem, N, seed, texture):
+    """The FP32 intervals contain the float-float keys (and the oracle's FP64
+    keys) for every triangle, and are narrow where the selection happens:
+    below 1e-4 relative over the largest 5 % of the keys.  (Small keys get
+    relatively wider intervals: the FP32 error of u, about 1e-7 |u|, enters
+    the bound through sqrt(n key).)"""
+    f_np = S.make_image(N, seed, texture=texture)
+    f = torch.from_numpy(f_np).cuda()
+    m = fem.Mesh(N)
+    m.spatial_refine(f, 0.03, fem.params(topk_frac=0.01, fast_keys=0))
+    g = m.g_from_f(f)
+    _, uv = m.inpaint(g, want_uv=True)
+    keys = m.triangle_errors(uv, f).cpu().numpy()
+    lo, hi = m.triangle_error_bounds(uv, f)
+    lo, hi = lo.cpu().numpy(), hi.cpu().numpy()
+    assert (lo <= keys).all() and (keys <= hi).all()
+    big = keys >= np.quantile(keys, 0.95)
+    assert ((hi - lo)[big] <= 1e-4 * keys[big]).all()
+    if N <= 257:
+        xy, tri, mk = m.export()
+        om = oracle_mod.Mesh(N, xy[:, 0].copy(), xy[:, 1].copy(), mk.copy(), tri[:, 0].copy(), tri[:, 1].copy(),
+                             tri[:, 2].copy())
+        _, kref, _ = oracle_mod.raster(om, uv.cpu().numpy(), f_np, owner=True)
+        assert (lo <= kref).all() and (kref <= hi).all()
+
+
 @pytest.mark.parametrize("N,seed", [(65, 2), (257, 3)])
 def test_tonal_matches_oracle(oracle_mod, fem, N, seed):
     f_np = S.make_image(N, seed)
