@@ -224,8 +224,7 @@ struct fem_mesh {
     fem::DArr<int> blk_list;    // first rows of the components above one warp
     fem::DArr<int> warp_list;   // first rows of the components of 2..32 rows
     fem::DArr<int> ccount;      // CC_* counters
-    fem::DArr<int> c_iters, c_nres, c_status;  // per-component solve results, at the first row
-    fem::DArr<double> c_rr, c_bb;
+    fem::DArr<unsigned long long> comp_stats;  // component solve totals, zero between launches
     fem::DArr<int> kvert;           // nK: vertex of each K index
     // CG work
     fem::DArr<double> x64, b64, r64, p64, q64, z64;

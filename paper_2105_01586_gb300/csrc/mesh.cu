@@ -459,7 +459,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->cc_parent, s); release(m->cc_root, s); release(m->cc_size, s); release(m->cc_fill, s);
     release(m->cc_cstart, s); release(m->rowcomp, s); release(m->blk_list, s); release(m->warp_list, s);
     release(m->ccount, s);
-    release(m->c_iters, s); release(m->c_nres, s); release(m->c_status, s); release(m->c_rr, s); release(m->c_bb, s);
+    release(m->comp_stats, s);
     release(m->x64, s); release(m->b64, s); release(m->r64, s); release(m->p64, s); release(m->q64, s); release(m->z64, s);
     release(m->r32, s); release(m->p32, s); release(m->q32, s); release(m->z32, s); release(m->d32, s);
     release(m->bvec, s); release(m->browptr, s); release(m->bent, s); release(m->bdg2, s);

@@ -20,10 +20,12 @@
 // One-row components (the most common kind) are solved directly, x = b / a,
 // one per thread.
 //
-// Statistics: per component the iterations, residual passes and the
-// unscaled ||r_c||^2 and ||b_c||^2; the last block to finish combines them
-// in row order (iterations: the largest over the components, i.e. the
-// length of the critical path; relative residual over all components).
+// Statistics: per component the iterations, residual passes and
+// ||r_c||^2 / ||b_c||^2, combined per block in shared memory and then across
+// blocks by integer atomics (maxima and integer sums: independent of
+// scheduling).  Iterations: the largest over the components, i.e. the length
+// of the critical path; relative residual: the largest over the components,
+// which bounds the relative residual of the whole system.
 // The kernel does nothing when some component is above kBlockComp rows: the
 // grid-wide solver then runs on the whole system instead.
 #include <algorithm>
@@ -54,11 +56,7 @@ struct CompArgs {
     double* x;
     double tol;
     int maxit;
-    int* c_iters;
-    int* c_nres;
-    int* c_status;
-    double* c_rr;
-    double* c_bb;
+    unsigned long long* gstats;  // [0] it max [1] nres max [2] worst [3] relmax bits [4] rowit [5] rowres (zero between launches)
     // per-component results are stored at the component's first row
     double* out;  // [0] iterations (critical path), [1] relres, [2] status, [3] residual passes, [4] row-iterations, [5] row-residual passes
     double* acc;  // optional running totals (as solve_accumulate)
@@ -71,13 +69,27 @@ __device__ __forceinline__ int comp_scale_exp(float bm) {
     return e < -120 ? -120 : (e > 120 ? 120 : e);
 }
 
-__device__ __forceinline__ void comp_record(const CompArgs& A, int c, int it, int nres, int status, double rr,
+// Statistics of the components a block solved, combined in shared memory
+// (each component's record takes a few shared atomics), then once per block
+// into the global totals: the largest iteration count and residual-pass
+// count, the worst status, the largest ||r_c||^2 / ||b_c||^2, and the row
+// sums of iterations and residual passes (for the byte count).  All are
+// maxima or integer sums, so the totals do not depend on scheduling.
+struct CompStats {
+    int itmax, nresmax, worst, pad;
+    unsigned long long relmax;  // bits of a non-negative double: ordered like the values
+    unsigned long long rowit, rowres;
+};
+
+__device__ __forceinline__ void comp_record(CompStats* S, int rows, int it, int nres, int status, double rr,
                                             double bb) {
-    A.c_iters[c] = it;
-    A.c_nres[c] = nres;
-    A.c_status[c] = status;
-    A.c_rr[c] = rr;
-    A.c_bb[c] = bb;
+    atomicMax(&S->itmax, it);
+    atomicMax(&S->nresmax, nres);
+    if (status != FEM_OK) atomicMax(&S->worst, status);
+    double q = bb > 0.0 ? rr / bb : 0.0;
+    atomicMax(&S->relmax, (unsigned long long)__double_as_longlong(q));
+    atomicAdd(&S->rowit, (unsigned long long)rows * (unsigned long long)it);
+    atomicAdd(&S->rowres, (unsigned long long)rows * (unsigned long long)nres);
 }
 
 __device__ __forceinline__ float warp_max(float v) {
@@ -89,10 +101,9 @@ __device__ __forceinline__ float warp_max(float v) {
 // ----------------------------------------------------------- one warp
 // Component of m <= 32 rows: lane i holds row i; columns are lane indices.
 template <bool FP64>
-__device__ void warp_comp(const CompArgs& A, int s0, int m) {
+__device__ void warp_comp(const CompArgs& A, int s0, int m, CompStats* S) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int c = s0;
     const bool act = lane < m;
     const int row = s0 + (act ? lane : 0);
     int lc[8];
@@ -121,7 +132,7 @@ __device__ void warp_comp(const CompArgs& A, int s0, int m) {
     float bm = warp_max(fabsf((float)b));
     if (bm == 0.f) {
         if (act) A.x[row] = 0.0;
-        if (lane == 0) comp_record(A, c, 0, 0, FEM_OK, 0.0, 0.0);
+        if (lane == 0) comp_record(S, m, 0, 0, FEM_OK, 0.0, 0.0);
         return;
     }
     int total_it = 0, nres = 0, status = FEM_E_NOT_CONVERGED;
@@ -146,35 +157,44 @@ __device__ void warp_comp(const CompArgs& A, int s0, int m) {
             nres++;
             if (rr <= tol2 * bb) { status = FEM_OK; break; }
             if (total_it >= A.maxit) break;
-            // FP32 Jacobi-PCG on A d = r from d = 0
-            float z = dinv * r, p = z, d = 0.f;
-            float rz = warp_sum(r * z), rr_in = rr;
+            // FP32 Jacobi-PCG on A d = r from d = 0 in the single-reduction
+            // form of Chronopoulos and Gear: s = A p is kept by recurrence, so
+            // each iteration has one SpMV (w = A z) and one fused reduction of
+            // (r.z, w.z, r.r): three independent butterflies instead of two
+            // dependent rounds
+            float d = 0.f, z = dinv * r;
+            float w = dg * z;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) w = fmaf(v[k], __shfl_sync(FULL, z, lc[k]), w);
+            float gamma = warp_sum(r * z), delta = warp_sum(w * z), rr_in = rr;
             const float lim = (float)(kCompInnerEta * kCompInnerEta) * rr;
             const int cap = min(A.maxit - total_it, kCompInnerCap);
             int it = 0;
-            while (rr_in > lim && it < cap) {
-                float q = dg * p;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) q = fmaf(v[k], __shfl_sync(FULL, p, lc[k]), q);
-                float pq = warp_sum(p * q);
-                if (!(pq > 0.f)) break;
-                float alpha = rz / pq;
+            float alpha = delta > 0.f ? gamma / delta : 0.f, p = z, sv = w;
+            while (delta > 0.f && rr_in > lim && it < cap) {
                 d = fmaf(alpha, p, d);
-                r = fmaf(-alpha, q, r);
-                z = dinv * r;
-                float rz2 = warp_sum(r * z);
-                rr_in = warp_sum(r * r);
+                r = fmaf(-alpha, sv, r);
                 it++;
-                float beta = rz2 / rz;
-                rz = rz2;
+                z = dinv * r;
+                w = dg * z;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) w = fmaf(v[k], __shfl_sync(FULL, z, lc[k]), w);
+                float gn = warp_sum(r * z), dn = warp_sum(w * z);
+                rr_in = warp_sum(r * r);
+                float beta = gn / gamma;
+                float den = dn - beta * gn / alpha;
+                if (!(den > 0.f)) break;  // breakdown guard (uniform over the warp)
+                alpha = gn / den;
+                gamma = gn;
                 p = fmaf(beta, p, z);
+                sv = fmaf(beta, sv, w);
             }
             total_it += it;
             xf = ff_add_f(xf, d);
             if (it == 0) break;  // breakdown: no progress possible
         }
         if (act) A.x[row] = ff_to_double(xf) * inv;
-        if (lane == 0) comp_record(A, c, total_it, nres, status, (double)rr * inv * inv, (double)bb * inv * inv);
+        if (lane == 0) comp_record(S, m, total_it, nres, status, (double)rr * inv * inv, (double)bb * inv * inv);
     } else {
         const double tol2 = A.tol * A.tol;
         double bb = warp_sum(b * b), rr = 0.0;
@@ -215,7 +235,7 @@ __device__ void warp_comp(const CompArgs& A, int s0, int m) {
             if (it == 0) break;
         }
         if (act) A.x[row] = x;
-        if (lane == 0) comp_record(A, c, total_it, nres, status, rr, bb);
+        if (lane == 0) comp_record(S, m, total_it, nres, status, rr, bb);
     }
 }
 
@@ -269,6 +289,29 @@ __device__ __forceinline__ void cta_sum2(CtaRed& R, int& par, T& a, T& b) {
     par ^= 1;
 }
 
+// three FP32 sums with one barrier (the same bits in every thread)
+__device__ __forceinline__ void cta_sum3f(CtaRed& R, int& par, float& a, float& b, float& c) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    float4* sl = (float4*)R.slot[par];
+    if (lane == 0) sl[w] = make_float4(a, b, c, 0.f);
+    __syncthreads();
+    float sa = 0.f, sb = 0.f, sc = 0.f;
+#pragma unroll
+    for (int i = 0; i < kCompThreads / 32; ++i) {
+        float4 t = sl[i];
+        sa += t.x;
+        sb += t.y;
+        sc += t.z;
+    }
+    a = sa;
+    b = sb;
+    c = sc;
+    par ^= 1;
+}
+
 __device__ __forceinline__ float cta_max(CtaRed& R, int& par, float a) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     a = warp_max(a);
@@ -288,10 +331,9 @@ __device__ __forceinline__ float code_val(unsigned short e) {
 }
 
 template <bool FP64>
-__device__ void cta_comp(const CompArgs& A, int s0, int m, unsigned char* raw, CtaRed& R) {
+__device__ void cta_comp(const CompArgs& A, int s0, int m, unsigned char* raw, CtaRed& R, CompStats* S) {
     using Real = typename std::conditional<FP64, double, float>::type;
     const int tid = threadIdx.x;
-    const int c = s0;
     // shared layout: ent[8][kBlockComp] u16 | dg[kBlockComp] f32 | z | p[2] | x (float2, FP32_IR only)
     unsigned short* ent = (unsigned short*)raw;
     float* dg_s = (float*)(raw + 16 * kBlockComp);
@@ -323,7 +365,7 @@ __device__ void cta_comp(const CompArgs& A, int s0, int m, unsigned char* raw, C
     float bm = cta_max(R, par, bmt);  // its barrier also publishes ent and dg_s
     if (bm == 0.f) {
         for (int i = tid; i < m; i += kCompThreads) A.x[s0 + i] = 0.0;
-        if (tid == 0) comp_record(A, c, 0, 0, FEM_OK, 0.0, 0.0);
+        if (tid == 0) comp_record(S, m, 0, 0, FEM_OK, 0.0, 0.0);
         return;
     }
     int total_it = 0, nres = 0, status = FEM_E_NOT_CONVERGED;
@@ -374,73 +416,96 @@ __device__ void cta_comp(const CompArgs& A, int s0, int m, unsigned char* raw, C
             nres++;
             if (rr <= tol2 * bb) { status = FEM_OK; break; }
             if (total_it >= A.maxit) break;
-            // FP32 Jacobi-PCG on A d = r from d = 0 (beta = 0, p_old = 0)
-            float rz_t = 0.f, dummy = 0.f;
+            // FP32 Jacobi-PCG on A d = r from d = 0 in the single-reduction
+            // form of Chronopoulos and Gear (see warp_comp): per iteration one
+            // barrier publishes z for the SpMV w = A z, one fused reduction of
+            // (r.z, w.z, r.r) follows; s = A p by recurrence
+            float* zf = (float*)z_s;
+            float zk[kCompRows], wk[kCompRows], pk[kCompRows], sk[kCompRows];
 #pragma unroll
             for (int k = 0; k < kCompRows; ++k) {
                 int i = tid + k * kCompThreads;
                 d[k] = 0.f;
+                zk[k] = 0.f;
                 if (i < m) {
-                    float zi = r[k] * dinv[k];
-                    z_s[i] = zi;
-                    p_s0[i] = 0.f;
-                    rz_t += r[k] * zi;
+                    zk[k] = r[k] * dinv[k];
+                    zf[i] = zk[k];
                 }
             }
-            cta_sum2(R, par, rz_t, dummy);  // publishes z and p_old = 0
-            float rz = rz_t, rr_in = rr, beta = 0.f;
+            __syncthreads();
+            float g_t = 0.f, d_t = 0.f, r_t = 0.f;
+#pragma unroll
+            for (int k = 0; k < kCompRows; ++k) {
+                int i = tid + k * kCompThreads;
+                wk[k] = 0.f;
+                if (i < m) {
+                    float sacc = dg_s[i] * zk[k];
+#pragma unroll
+                    for (int e2 = 0; e2 < 8; ++e2) {
+                        unsigned short en = ent[e2 * kBlockComp + i];
+                        sacc = fmaf(code_val(en), zf[en >> 2], sacc);
+                    }
+                    wk[k] = sacc;
+                    g_t += r[k] * zk[k];
+                    d_t += sacc * zk[k];
+                }
+            }
+            cta_sum3f(R, par, g_t, d_t, r_t);
+            float gamma = g_t, delta = d_t, rr_in = rr;
             const float lim = (float)(kCompInnerEta * kCompInnerEta) * rr;
             const int cap = min(A.maxit - total_it, kCompInnerCap);
             int it = 0;
-            float *pold = (float*)p_s0, *pnew = (float*)p_s1;
-            float* zf = (float*)z_s;
-            while (rr_in > lim && it < cap) {
-                float pq_t = 0.f, pk[kCompRows], qk[kCompRows];
+            float alpha = delta > 0.f ? gamma / delta : 0.f;
+#pragma unroll
+            for (int k = 0; k < kCompRows; ++k) {
+                pk[k] = zk[k];
+                sk[k] = wk[k];
+            }
+            while (delta > 0.f && rr_in > lim && it < cap) {
 #pragma unroll
                 for (int k = 0; k < kCompRows; ++k) {
                     int i = tid + k * kCompThreads;
-                    pk[k] = 0.f;
-                    qk[k] = 0.f;
                     if (i < m) {
-                        float pi = fmaf(beta, pold[i], zf[i]);
-                        float sacc = dg_s[i] * pi;
+                        d[k] = fmaf(alpha, pk[k], d[k]);
+                        r[k] = fmaf(-alpha, sk[k], r[k]);
+                        zk[k] = r[k] * dinv[k];
+                        zf[i] = zk[k];  // the last reads of z_s were before the previous reduction's barrier
+                    }
+                }
+                it++;
+                __syncthreads();
+                g_t = 0.f;
+                d_t = 0.f;
+                r_t = 0.f;
+#pragma unroll
+                for (int k = 0; k < kCompRows; ++k) {
+                    int i = tid + k * kCompThreads;
+                    wk[k] = 0.f;
+                    if (i < m) {
+                        float sacc = dg_s[i] * zk[k];
 #pragma unroll
                         for (int e2 = 0; e2 < 8; ++e2) {
                             unsigned short en = ent[e2 * kBlockComp + i];
-                            int j = en >> 2;
-                            sacc = fmaf(code_val(en), fmaf(beta, pold[j], zf[j]), sacc);
+                            sacc = fmaf(code_val(en), zf[en >> 2], sacc);
                         }
-                        pk[k] = pi;
-                        qk[k] = sacc;
-                        pq_t += pi * sacc;
+                        wk[k] = sacc;
+                        g_t += r[k] * zk[k];
+                        d_t += sacc * zk[k];
+                        r_t += r[k] * r[k];
                     }
                 }
-                float dummy2 = 0.f;
-                cta_sum2(R, par, pq_t, dummy2);
-                if (!(pq_t > 0.f)) break;
-                float alpha = rz / pq_t;
-                float rz_t2 = 0.f, rr_t2 = 0.f;
+                cta_sum3f(R, par, g_t, d_t, r_t);
+                rr_in = r_t;
+                float beta = g_t / gamma;
+                float den = d_t - beta * g_t / alpha;
+                if (!(den > 0.f)) break;  // breakdown guard (uniform over the block)
+                alpha = g_t / den;
+                gamma = g_t;
 #pragma unroll
                 for (int k = 0; k < kCompRows; ++k) {
-                    int i = tid + k * kCompThreads;
-                    if (i < m) {
-                        pnew[i] = pk[k];
-                        d[k] = fmaf(alpha, pk[k], d[k]);
-                        r[k] = fmaf(-alpha, qk[k], r[k]);
-                        float zi = r[k] * dinv[k];
-                        zf[i] = zi;
-                        rz_t2 += r[k] * zi;
-                        rr_t2 += r[k] * r[k];
-                    }
+                    pk[k] = fmaf(beta, pk[k], zk[k]);
+                    sk[k] = fmaf(beta, sk[k], wk[k]);
                 }
-                cta_sum2(R, par, rz_t2, rr_t2);
-                it++;
-                beta = rz_t2 / rz;
-                rz = rz_t2;
-                rr_in = rr_t2;
-                float* t = pold;
-                pold = pnew;
-                pnew = t;
             }
             total_it += it;
 #pragma unroll
@@ -459,7 +524,7 @@ __device__ void cta_comp(const CompArgs& A, int s0, int m, unsigned char* raw, C
             float2 xv = x_s[i];
             A.x[s0 + i] = ff_to_double(ff{xv.x, xv.y}) * inv;
         }
-        if (tid == 0) comp_record(A, c, total_it, nres, status, (double)rr * inv * inv, (double)bb * inv * inv);
+        if (tid == 0) comp_record(S, m, total_it, nres, status, (double)rr * inv * inv, (double)bb * inv * inv);
     } else {
         // plain FP64 PCG; the iterate stays in A.x (global memory, read back
         // through the block after a barrier for the residual passes)
@@ -564,7 +629,7 @@ __device__ void cta_comp(const CompArgs& A, int s0, int m, unsigned char* raw, C
             __syncthreads();
             if (it == 0 && !conv) break;
         }
-        if (tid == 0) comp_record(A, c, total_it, nres, status, rr, bb);
+        if (tid == 0) comp_record(S, m, total_it, nres, status, rr, bb);
     }
     __syncthreads();
 }
@@ -583,6 +648,9 @@ __global__ void __launch_bounds__(kCompThreads) k_solve_comp(CompArgs A) {
         return;
     }
     if (A.cnt[CC_NBIG] > 0) return;  // the grid-wide solver takes the system
+    __shared__ CompStats S;
+    if (threadIdx.x == 0) S = CompStats{0, 0, FEM_OK, 0, 0ull, 0ull, 0ull};
+    __syncthreads();
     const int nblk = A.cnt[CC_NBLK], nwarp = A.cnt[CC_NWARP];
     // components above one warp: one block each, taken in turn
     for (;;) {
@@ -592,13 +660,13 @@ __global__ void __launch_bounds__(kCompThreads) k_solve_comp(CompArgs A) {
         __syncthreads();
         if (i >= nblk) break;
         int s0 = A.blk_list[i];
-        cta_comp<FP64>(A, s0, A.rowcomp[s0], raw, R);
+        cta_comp<FP64>(A, s0, A.rowcomp[s0], raw, R, &S);
     }
     // components of 2..32 rows: one warp each
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = gw; i < nwarp; i += nw) {
         int s0 = A.warp_list[i];
-        warp_comp<FP64>(A, s0, A.rowcomp[s0]);
+        warp_comp<FP64>(A, s0, A.rowcomp[s0], &S);
     }
     // one-row components: x = b / a directly, one thread each
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < A.nU; p += gridDim.x * blockDim.x) {
@@ -607,69 +675,43 @@ __global__ void __launch_bounds__(kCompThreads) k_solve_comp(CompArgs A) {
         double x = b / a;
         double r = b - a * x;
         A.x[p] = x;
-        comp_record(A, p, 0, 1, FEM_OK, r * r, b * b);
+        comp_record(&S, 1, 0, 1, FEM_OK, r * r, b * b);
     }
-    // the last block to finish combines the statistics in row order
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(A.work + CC_DONE, 1) == (int)gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    int itmax = 0, nresmax = 0, worst = FEM_OK;
-    double rr = 0.0, bb = 0.0, rowit = 0.0, rowres = 0.0;
-    for (int c = threadIdx.x; c < A.nU; c += blockDim.x) {
-        int szc = A.rowcomp[c];
-        if (szc == 0) continue;
-        int it = __ldcg(A.c_iters + c), nr = __ldcg(A.c_nres + c), st = __ldcg(A.c_status + c);
-        double sz = (double)szc;
-        itmax = max(itmax, it);
-        nresmax = max(nresmax, nr);
-        if (st != FEM_OK) worst = st;
-        rr += __ldcg(A.c_rr + c);
-        bb += __ldcg(A.c_bb + c);
-        rowit += sz * it;
-        rowres += sz * nr;
-    }
-    __shared__ double s_d[4][kCompThreads / 32];
-    __shared__ int s_i[3][kCompThreads / 32];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    rr = warp_sum(rr);
-    bb = warp_sum(bb);
-    rowit = warp_sum(rowit);
-    rowres = warp_sum(rowres);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        itmax = max(itmax, __shfl_xor_sync(0xffffffffu, itmax, o));
-        nresmax = max(nresmax, __shfl_xor_sync(0xffffffffu, nresmax, o));
-        worst = max(worst, __shfl_xor_sync(0xffffffffu, worst, o));
-    }
-    if (lane == 0) {
-        s_d[0][w] = rr; s_d[1][w] = bb; s_d[2][w] = rowit; s_d[3][w] = rowres;
-        s_i[0][w] = itmax; s_i[1][w] = nresmax; s_i[2][w] = worst;
-    }
+    // block totals into the global totals; the last block to finish writes
+    // the solve's statistics and clears the totals for the next launch
     __syncthreads();
     if (threadIdx.x == 0) {
-        double trr = 0, tbb = 0, tit = 0, tres = 0;
-        int mit = 0, mres = 0, wst = FEM_OK;
-        for (int i = 0; i < kCompThreads / 32; ++i) {
-            trr += s_d[0][i]; tbb += s_d[1][i]; tit += s_d[2][i]; tres += s_d[3][i];
-            mit = max(mit, s_i[0][i]); mres = max(mres, s_i[1][i]); wst = max(wst, s_i[2][i]);
-        }
-        double rel = tbb > 0.0 ? sqrt(trr / tbb) : 0.0;
-        A.out[0] = mit;
-        A.out[1] = rel;
-        A.out[2] = wst;
-        A.out[3] = mres;
-        A.out[4] = tit;
-        A.out[5] = tres;
-        if (A.acc) {
-            A.acc[0] += mit;
-            if (rel > A.acc[1]) A.acc[1] = rel;
-            if (wst != FEM_OK && A.acc[2] == 0.0) A.acc[2] = wst;
-            A.acc[3] += 1.0;
-            A.acc[4] += A.bytes_row_it * tit + A.bytes_row_res * tres;
-        }
+        unsigned long long* G = A.gstats;
+        atomicMax(G + 0, (unsigned long long)S.itmax);
+        atomicMax(G + 1, (unsigned long long)S.nresmax);
+        atomicMax(G + 2, (unsigned long long)S.worst);
+        atomicMax(G + 3, S.relmax);
+        atomicAdd(G + 4, S.rowit);
+        atomicAdd(G + 5, S.rowres);
+        __threadfence();
+        s_last = atomicAdd(A.work + CC_DONE, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    unsigned long long* G = A.gstats;
+    int mit = (int)__ldcg(G + 0), mres = (int)__ldcg(G + 1), wst = (int)__ldcg(G + 2);
+    double rel = sqrt(__longlong_as_double((long long)__ldcg(G + 3)));
+    double tit = (double)__ldcg(G + 4), tres = (double)__ldcg(G + 5);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) G[q] = 0ull;
+    A.out[0] = mit;
+    A.out[1] = rel;  // largest ||r_c|| / ||b_c|| over the components (bounds the global one)
+    A.out[2] = wst;
+    A.out[3] = mres;
+    A.out[4] = tit;
+    A.out[5] = tres;
+    if (A.acc) {
+        A.acc[0] += mit;
+        if (rel > A.acc[1]) A.acc[1] = rel;
+        if (wst != FEM_OK && A.acc[2] == 0.0) A.acc[2] = wst;
+        A.acc[3] += 1.0;
+        A.acc[4] += A.bytes_row_it * tit + A.bytes_row_res * tres;
     }
 }
 
@@ -677,12 +719,10 @@ __global__ void __launch_bounds__(kCompThreads) k_solve_comp(CompArgs A) {
 fem_status solve_components(fem_mesh* m, const double* b, double* x, bool use_fp64, double tol, int maxit,
                             bool deferred, cudaStream_t s) {
     int nU = m->nU;
-    size_t n = (size_t)nU + 1;
-    FEM_TRY(ensure(m->c_iters, n, s));
-    FEM_TRY(ensure(m->c_nres, n, s));
-    FEM_TRY(ensure(m->c_status, n, s));
-    FEM_TRY(ensure(m->c_rr, n, s));
-    FEM_TRY(ensure(m->c_bb, n, s));
+    if (!m->comp_stats.p) {  // zero once; each launch's last block clears it again
+        FEM_TRY(ensure(m->comp_stats, 8, s));
+        FEM_CUDA(cudaMemsetAsync(m->comp_stats.p, 0, sizeof(unsigned long long) * m->comp_stats.n, s));
+    }
     CompArgs A;
     A.nU = nU;
     A.rowcomp = m->rowcomp.p;
@@ -697,11 +737,7 @@ fem_status solve_components(fem_mesh* m, const double* b, double* x, bool use_fp
     A.x = x;
     A.tol = tol;
     A.maxit = maxit;
-    A.c_iters = m->c_iters.p;
-    A.c_nres = m->c_nres.p;
-    A.c_status = m->c_status.p;
-    A.c_rr = m->c_rr.p;
-    A.c_bb = m->c_bb.p;
+    A.gstats = m->comp_stats.p;
     A.out = m->dscal.p;
     A.acc = deferred ? m->dscal.p + 64 : nullptr;
     // algorithmic bytes per row: as the grid-wide solver (ELL matrix 68 B per

@@ -155,6 +155,36 @@ def test_spatial_fast_keys_bit_exact(oracle_mod, fem, N, seed, density, frac):
     assert _same_mesh(m, om), "fast-key mesh differs from the oracle mesh"
 
 
+@pytest.mark.parametrize("fast", [0, 1])
+@pytest.mark.parametrize("N,value", [(65, 0.5), (257, 0.3)])
+def test_spatial_constant_image_ties_by_id(oracle_mod, fem, N, value, fast):
+    """A constant image: the solves reproduce the constant exactly, every key
+    is 0, and the selection is decided by triangle ids alone (both key modes)."""
+    f_np = np.full((N, N), value, dtype=np.float32)
+    om, log = oracle_mod.spatial(f_np, 0.05, 0.01)
+    m = fem.Mesh(N)
+    f = torch.from_numpy(f_np).cuda()
+    m.spatial_refine(f, 0.05, fem.params(topk_frac=0.01, fast_keys=fast))
+    assert m.stats()["rounds"] == len(log)
+    assert _same_mesh(m, om)
+    g = m.g_from_f(f)
+    _, uv = m.inpaint(g, want_uv=True)
+    assert float(m.triangle_errors(uv, f).abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("fast", [0, 1])
+@pytest.mark.parametrize("N,density,frac", [(3, 1.0, 0.0), (5, 0.8, 0.01), (9, 0.5, 1.0), (33, 0.3, 1.0)])
+def test_spatial_smallest_images_and_all_eligible(oracle_mod, fem, N, density, frac, fast):
+    """The smallest images (down to 3 x 3, where a full mesh is every pixel)
+    and frac = 1 (every eligible triangle selected each round): bit-exact."""
+    f_np = S.make_image(N, 11)
+    om, log = oracle_mod.spatial(f_np, density, frac)
+    m = fem.Mesh(N)
+    m.spatial_refine(torch.from_numpy(f_np).cuda(), density, fem.params(topk_frac=frac, fast_keys=fast))
+    assert m.stats()["rounds"] == len(log)
+    assert _same_mesh(m, om)
+
+
 @pytest.mark.parametrize("N,seed,texture", [(257, 5, False), (1025, 1, False), (2049, 3, True)])
 def test_error_bounds_contain_exact_keys(oracle_mod, fem, N, seed, texture):
     """The FP32 intervals contain the float-float keys (and the oracle's FP64
