@@ -232,8 +232,15 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
     __shared__ int s_n, s_cnt, s_smem;
     int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (ids) T = min(*n_dev, T);
+    // pass 1 over the keys: eligible count and the histogram of digit 0
+    for (int i = tid; i < 256; i += kTopkBlockThreads) hist[i] = 0;
+    __syncthreads();
     unsigned ne = 0;
-    for (int t = tid; t < T; t += kTopkBlockThreads) ne += keyc[topk_id(ids, t)] ? 1u : 0u;
+    for (int i = tid; i < T; i += kTopkBlockThreads) {
+        unsigned long long hi = keyc[topk_id(ids, i)];
+        ne += hi ? 1u : 0u;
+        atomicAdd(&hist[(unsigned)(hi >> 56)], 1u);
+    }
     ne = warp_sum(ne);
     if (lane == 0) s_cnt32[wid] = ne;
     __syncthreads();
@@ -261,26 +268,31 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
     }
     __syncthreads();
     if (s_krem == 0) return;
+    // largest key below the bucket of the threshold, over the keys left
+    // outside the shared-memory candidates (for the decision margin)
+    unsigned long long best = extra_below ? *extra_below : 0ull;
     for (int d = 0; d < 12; ++d) {
-        for (int i = tid; i < 256; i += kTopkBlockThreads) hist[i] = 0;
-        __syncthreads();
         unsigned long long pre_hi = s_pre_hi;
         unsigned pre_lo = s_pre_lo;
-        if (!s_smem) {
-            for (int i = tid; i < T; i += kTopkBlockThreads) {
-                int t = topk_id(ids, i);
-                unsigned long long hi = keyc[t];
-                unsigned lo = ~(unsigned)t;
-                if (prefix_match(hi, lo, pre_hi, pre_lo, d)) atomicAdd(&hist[digit_of(hi, lo, d)], 1u);
+        if (d > 0) {  // digit 0's histogram came with the eligible count
+            for (int i = tid; i < 256; i += kTopkBlockThreads) hist[i] = 0;
+            __syncthreads();
+            if (!s_smem) {
+                for (int i = tid; i < T; i += kTopkBlockThreads) {
+                    int t = topk_id(ids, i);
+                    unsigned long long hi = keyc[t];
+                    unsigned lo = ~(unsigned)t;
+                    if (prefix_match(hi, lo, pre_hi, pre_lo, d)) atomicAdd(&hist[digit_of(hi, lo, d)], 1u);
+                }
+            } else {
+                for (int i = tid; i < s_n; i += kTopkBlockThreads) {
+                    unsigned long long hi = c_hi[i];
+                    unsigned lo = c_lo[i];
+                    if (prefix_match(hi, lo, pre_hi, pre_lo, d)) atomicAdd(&hist[digit_of(hi, lo, d)], 1u);
+                }
             }
-        } else {
-            for (int i = tid; i < s_n; i += kTopkBlockThreads) {
-                unsigned long long hi = c_hi[i];
-                unsigned lo = c_lo[i];
-                if (prefix_match(hi, lo, pre_hi, pre_lo, d)) atomicAdd(&hist[digit_of(hi, lo, d)], 1u);
-            }
+            __syncthreads();
         }
-        __syncthreads();
         if (tid < 32) {
             long long krem = s_krem, cum = 0;
             int chosen = warp_pick_bucket(hist, krem, &cum);
@@ -293,16 +305,24 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
         }
         __syncthreads();
         if (!s_smem && d < 11 && s_cnt <= kTopkCandCap) {
+            // collect the bucket; every key outside it lies wholly above or
+            // wholly below it, and the largest below joins the margin
             unsigned long long nh = s_pre_hi;
             unsigned nl = s_pre_lo;
+            unsigned long long mhi = d + 1 >= 8 ? ~0ull : (~0ull << (64 - 8 * (d + 1)));
+            unsigned mlo = d + 1 <= 8 ? 0u : (~0u << (32 - 8 * (d + 1 - 8)));
             for (int i = tid; i < T; i += kTopkBlockThreads) {
                 int t = topk_id(ids, i);
                 unsigned long long hi = keyc[t];
                 unsigned lo = ~(unsigned)t;
-                if (prefix_match(hi, lo, nh, nl, d + 1)) {
+                unsigned long long ph = hi & mhi;
+                unsigned pl = lo & mlo;
+                if (ph == nh && pl == nl) {
                     int pos = atomicAdd(&s_n, 1);
                     c_hi[pos] = hi;
                     c_lo[pos] = lo;
+                } else if ((ph < nh || (ph == nh && pl < nl)) && hi > best) {
+                    best = hi;
                 }
             }
             __syncthreads();
@@ -312,13 +332,21 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
     }
     unsigned long long thr_hi = s_pre_hi;
     unsigned thr_lo = s_pre_lo;
-    // largest key strictly below the threshold (decision margin)
-    unsigned long long best = extra_below ? *extra_below : 0ull;
-    for (int i = tid; i < T; i += kTopkBlockThreads) {
-        int t = topk_id(ids, i);
-        unsigned long long hi = keyc[t];
-        unsigned lo = ~(unsigned)t;
-        if ((hi < thr_hi || (hi == thr_hi && lo < thr_lo)) && hi > best) best = hi;
+    // largest key strictly below the threshold among the candidates (or,
+    // when they never fitted in shared memory, among all keys)
+    if (s_smem) {
+        for (int i = tid; i < s_n; i += kTopkBlockThreads) {
+            unsigned long long hi = c_hi[i];
+            unsigned lo = c_lo[i];
+            if ((hi < thr_hi || (hi == thr_hi && lo < thr_lo)) && hi > best) best = hi;
+        }
+    } else {
+        for (int i = tid; i < T; i += kTopkBlockThreads) {
+            int t = topk_id(ids, i);
+            unsigned long long hi = keyc[t];
+            unsigned lo = ~(unsigned)t;
+            if ((hi < thr_hi || (hi == thr_hi && lo < thr_lo)) && hi > best) best = hi;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
@@ -753,7 +781,8 @@ extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double
     // refinement get theirs when they are created (k_bisect)
     FEM_TRY(set_uv_from_f(m, f_dev, s));
     while ((long long)m->V < vstar && (p->max_rounds <= 0 || round < p->max_rounds)) {
-        FEM_TRY(build_system(m, s));
+        // solve_laplace builds the system of the refined mesh (with its
+        // right-hand side in the same kernel)
         fem_status st = solve_laplace(m, p->precision == FEM_PREC_FP64, p->tol, p->maxit, s, nullptr, nullptr, true);
         if (st != FEM_OK) return st;
         FEM_TRY(ensure(m->keys, (size_t)m->T, s));

@@ -108,15 +108,20 @@ struct IndexMapsOut {
     }
 };
 
+// ELL rows of A_UU; with b and x (optional) also the right-hand side
+// b_r = -sum over mask neighbours of A_ij uv_j and the start x_r = uv_i of a
+// solve on the fresh system (k_rhs_and_start fused)
 __global__ void k_build_ell(int nU, int V, const int* __restrict__ urow_vertex, const int* __restrict__ nbr,
                             const float* __restrict__ coef, const float* __restrict__ diag,
                             const int* __restrict__ uidx, int* __restrict__ ucol, float* __restrict__ uval,
                             float* __restrict__ udiag, int* __restrict__ ucnt, float* __restrict__ udinv,
-                            double* __restrict__ udinv64) {
+                            double* __restrict__ udinv64, const double* __restrict__ uv = nullptr,
+                            double* __restrict__ b = nullptr, double* __restrict__ x = nullptr) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nU) return;
     int i = urow_vertex[r];
     int s = 0;
+    double bs = 0.0;
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         int j = nbr[d * V + i];
@@ -127,8 +132,14 @@ __global__ void k_build_ell(int nU, int V, const int* __restrict__ urow_vertex, 
                 ucol[s * nU + r] = uj;
                 uval[s * nU + r] = c;
                 s++;
+            } else if (b) {
+                bs -= (double)c * uv[j];
             }
         }
+    }
+    if (b) {
+        b[r] = bs;
+        x[r] = uv[i];
     }
     ucnt[r] = s;
     for (; s < 8; ++s) {
@@ -169,7 +180,16 @@ __global__ void k_scatter_solution(int nU, const int* __restrict__ urow_vertex, 
     uvf[i] = make_float2(q.hi, q.lo);
 }
 
-fem_status build_system(fem_mesh* m, cudaStream_t s) {
+static fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs);
+
+fem_status build_system(fem_mesh* m, cudaStream_t s) { return build_system_rhs(m, s, nullptr); }
+
+// with_rhs (optional): on input asks for b64/x64 of a solve on the current
+// vertex values to be filled by the ELL kernel; on output true when that
+// happened (the system was rebuilt), false when the caller must fill them
+static fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
+    bool want = with_rhs && *with_rhs;
+    if (with_rhs) *with_rhs = false;
     if (m->sys_version == m->mesh_version) return FEM_OK;
     int V = m->V, T = m->T;
     FEM_TRY(ensure(m->nbr, (size_t)8 * V, s));
@@ -202,10 +222,15 @@ fem_status build_system(fem_mesh* m, cudaStream_t s) {
     FEM_TRY(ensure(m->ucnt, n, s));
     FEM_TRY(ensure(m->dinv32, n, s));
     FEM_TRY(ensure(m->dinv64, n, s));
+    if (want && nU > 0) {
+        FEM_TRY(ensure(m->b64, (size_t)nU, s));
+        FEM_TRY(ensure(m->x64, (size_t)nU, s));
+    }
     if (nU > 0)
         FEM_LAUNCH(F_ASSEMBLY, s, k_build_ell, (nU + 255) / 256, 256, 0, nU, V, m->urow_vertex.p, m->nbr.p,
                    m->coefA.p, m->diagA.p, m->uidx.p, m->ucol.p, m->uval32.p, m->udiag.p, m->ucnt.p, m->dinv32.p,
-                   m->dinv64.p);
+                   m->dinv64.p, (const double*)m->uv.p, want ? m->b64.p : nullptr, want ? m->x64.p : nullptr);
+    if (want) *with_rhs = true;
     m->sys_version = m->mesh_version;
     return FEM_OK;
 }
@@ -1212,7 +1237,8 @@ fem_status solve_totals_read(fem_mesh* m, cudaStream_t s) {
 // the Dirichlet data, those at U the start; the solution is written back.
 fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cudaStream_t s, int* iters_out,
                          double* relres_out, bool deferred) {
-    FEM_TRY(build_system(m, s));
+    bool rhs_done = true;  // filled by the ELL kernel when the system is rebuilt here
+    FEM_TRY(build_system_rhs(m, s, &rhs_done));
     int nU = m->nU;
     if (iters_out) *iters_out = 0;
     if (relres_out) *relres_out = 0.0;
@@ -1220,8 +1246,9 @@ fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cuda
     FEM_TRY(ensure(m->b64, (size_t)nU, s));
     FEM_TRY(ensure(m->x64, (size_t)nU, s));
     int b = (nU + 255) / 256;
-    FEM_LAUNCH(F_CG, s, k_rhs_and_start, b, 256, 0, nU, m->V, m->urow_vertex.p, m->nbr.p, m->coefA.p, m->mask.p,
-               m->uv.p, m->b64.p, m->x64.p);
+    if (!rhs_done)
+        FEM_LAUNCH(F_CG, s, k_rhs_and_start, b, 256, 0, nU, m->V, m->urow_vertex.p, m->nbr.p, m->coefA.p, m->mask.p,
+                   m->uv.p, m->b64.p, m->x64.p);
     fem_status st = run_solve(m, m->b64.p, m->x64.p, use_fp64, tol, maxit, s, iters_out, relres_out, deferred);
     if (st != FEM_OK && st != FEM_E_NOT_CONVERGED) return st;
     FEM_LAUNCH(F_CG, s, k_scatter_solution, b, 256, 0, nU, m->urow_vertex.p, m->x64.p, m->uv.p, m->uvf.p);
