@@ -26,7 +26,14 @@
 namespace fem {
 
 enum RasterMode { R_ERR = 0, R_IMG = 1, R_MASS = 2, R_SCAT = 3 };
-constexpr int kItemPixels = 1024;
+// Pixels per item (about 1024): fewer items mean less fixed cost per pixel.
+// 256-pixel items at 1025^2, meant to shorten the longest item, measured
+// slower (the fixed cost of four times as many items), so every size uses
+// 1024; the plan and the kernels take the size as a parameter.
+__host__ __device__ __forceinline__ int item_pixels_for(long long P) {
+    (void)P;
+    return 1024;
+}
 constexpr int kRasterThreads = 256;
 
 struct TriGeom {
@@ -46,8 +53,8 @@ __device__ __forceinline__ TriGeom tri_geom(int4 tr, const int2* __restrict__ vx
     return g;
 }
 
-__device__ __forceinline__ int rows_per_item(int maxw) {
-    int r = kItemPixels / maxw;
+__device__ __forceinline__ int rows_per_item(int maxw, int item_px) {
+    int r = item_px / maxw;
     return r < 1 ? 1 : (r > 32 ? 32 : r);
 }
 
@@ -87,12 +94,13 @@ struct ItemCountIn {
     const int4* tri;
     const int2* vxy;
     int N;
+    int item_px;
     int* cnt;
     __device__ __forceinline__ int operator()(long long lt) const {
         int t = (int)lt;
         TriGeom g = tri_geom(tri[t], vxy, N);
         int rows = g.yend - g.ytop + 1;
-        int rpi = rows_per_item(g.maxw);
+        int rpi = rows_per_item(g.maxw, item_px);
         int c = (rows > 0 && !is_small(g)) ? (rows + rpi - 1) / rpi : 0;
         cnt[t] = c;
         return c;
@@ -117,12 +125,12 @@ struct ItemExpandOut {
 
 // separate kernels of the plan (used by the allocation-free error pass)
 __global__ void k_item_count(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int N,
-                             int* __restrict__ cnt) {
+                             int* __restrict__ cnt, int item_px) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     TriGeom g = tri_geom(tri[t], vxy, N);
     int rows = g.yend - g.ytop + 1;
-    int rpi = rows_per_item(g.maxw);
+    int rpi = rows_per_item(g.maxw, item_px);
     cnt[t] = (rows > 0 && !is_small(g)) ? (rows + rpi - 1) / rpi : 0;
 }
 
@@ -175,7 +183,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kRasterThreads) k_raster(
     const int4* __restrict__ tri, const int2* __restrict__ vxy, const double* __restrict__ uv,
     const float2* __restrict__ uvf, const float* __restrict__ img, int N, const int* __restrict__ item_tri,
-    const int* __restrict__ item_off, const int* __restrict__ n_items_dev, int item_cap,
+    const int* __restrict__ item_off, const int* __restrict__ n_items_dev, int item_cap, int item_px,
     double* __restrict__ partial, float* __restrict__ u_out, int* __restrict__ owner_out,
     const int* __restrict__ item_cnt = nullptr, int* __restrict__ item_done = nullptr,
     double* __restrict__ key_out = nullptr, unsigned long long* __restrict__ keyc_out = nullptr,
@@ -194,7 +202,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
         int j = (int)(it - item_off[t]);
         int4 tr = tri[t];
         TriGeom g = tri_geom(tr, vxy, N);
-        int rpi = rows_per_item(g.maxw);
+        int rpi = rows_per_item(g.maxw, item_px);
         int r0 = g.ytop + j * rpi;
         int nr = min(rpi, g.yend + 1 - r0);
         int L = 0, len = 0;
@@ -609,7 +617,7 @@ fem_status raster_plan(fem_mesh* m, cudaStream_t s) {
     int* n_items_dev = m->dcount.p + 0;
     int* err = m->dflag.p + 0;
     FEM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    FEM_TRY(scan_fused(m, ItemCountIn{m->tri.p, m->vxy.p, m->N, m->item_cnt.p},
+    FEM_TRY(scan_fused(m, ItemCountIn{m->tri.p, m->vxy.p, m->N, item_pixels_for(m->P), m->item_cnt.p},
                        ItemExpandOut{m->item_off.p, m->item_tri.p, (int)m->item_tri.n, err}, T, s, n_items_dev,
                        F_RASTER));
     m->plan_version = m->mesh_version;
@@ -633,8 +641,8 @@ fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, const
     }
     note_bytes(F_RASTER, raster_err_bytes(m));
     FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
-               m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p, (float*)nullptr,
-               (int*)nullptr, m->item_cnt.p, m->item_done.p, err_out, keyc_out);
+               m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p,
+               (float*)nullptr, (int*)nullptr, m->item_cnt.p, m->item_done.p, err_out, keyc_out);
     // Few small triangles: eight lanes each over staged tiles, which shortens
     // the longest thread.  Many (above about 1k per SM): one thread each,
     // which avoids the eight-fold plane setup once every SM is full anyway.
@@ -652,7 +660,7 @@ fem_status raster_image(fem_mesh* m, const double* uv, float* u, int* owner, cud
     note_bytes(F_RASTER, (u ? 4.0 * (double)m->P : 0.0) + (owner ? 4.0 * (double)m->P : 0.0) + 16.0 * m->T +
                              16.0 * m->V);
     FEM_LAUNCH(F_RASTER, s, k_raster<R_IMG>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv,
-               (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p, u, owner);
+               (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, u, owner);
     FEM_LAUNCH(F_RASTER, s, k_raster_small<R_IMG>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv,
                (const float2*)nullptr, (const float*)nullptr, m->N, m->T, (double*)nullptr,
                (unsigned long long*)nullptr, u, owner);
@@ -669,7 +677,7 @@ fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s) {
     if (mode == R_MASS) {
         FEM_LAUNCH(F_RASTER, s, k_raster<R_MASS>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
                    (const double*)nullptr, (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0,
-                   (int)m->item_tri.n, m->partial.p, (float*)nullptr, (int*)nullptr);
+                   (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, (float*)nullptr, (int*)nullptr);
         FEM_LAUNCH(F_RASTER, s, k_finalize<6>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
                    m->loc.p);
         FEM_LAUNCH(F_RASTER, s, k_raster_small<R_MASS>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p,
@@ -677,8 +685,8 @@ fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s) {
                    (unsigned long long*)nullptr, (float*)nullptr, (int*)nullptr);
     } else {
         FEM_LAUNCH(F_RASTER, s, k_raster<R_SCAT>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
-                   (const double*)nullptr, (const float2*)nullptr, r, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, m->partial.p,
-                   (float*)nullptr, (int*)nullptr);
+                   (const double*)nullptr, (const float2*)nullptr, r, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P),
+                   m->partial.p, (float*)nullptr, (int*)nullptr);
         FEM_LAUNCH(F_RASTER, s, k_finalize<3>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
                    m->loc.p);
         FEM_LAUNCH(F_RASTER, s, k_raster_small<R_SCAT>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p,
@@ -695,11 +703,12 @@ fem_status raster_errors_scratch(const int4* tri, const int2* vxy, int T, int N,
     int* n_items_dev = w.counters + 0;
     int* err = w.counters + 1;
     int blocks = (T + 255) / 256;
-    FEM_LAUNCH(F_RASTER, s, k_item_count, blocks, 256, 0, tri, vxy, T, N, w.item_cnt);
+    FEM_LAUNCH(F_RASTER, s, k_item_count, blocks, 256, 0, tri, vxy, T, N, w.item_cnt, item_pixels_for((long long)N * N));
     FEM_TRY(exclusive_scan_i32_scratch(w.item_cnt, w.item_off, T, s, n_items_dev, w.scan_tmp, w.scan_tmp_n));
     FEM_LAUNCH(F_RASTER, s, k_item_expand, blocks, 256, 0, w.item_cnt, w.item_off, T, w.item_cap, w.item_tri, err);
     FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, w.grid, kRasterThreads, 0, tri, vxy, uv, (const float2*)nullptr, f, N,
-               w.item_tri, w.item_off, n_items_dev, w.item_cap, w.partial, (float*)nullptr, (int*)nullptr);
+               w.item_tri, w.item_off, n_items_dev, w.item_cap, item_pixels_for((long long)N * N), w.partial, (float*)nullptr,
+               (int*)nullptr);
     FEM_LAUNCH(F_RASTER, s, k_finalize_err, std::max(1, std::min(w.grid, (T + 7) / 8)), 256, 0, w.item_cnt,
                w.item_off, (const float2*)w.partial, T, tri, vxy, err_out, (unsigned long long*)nullptr);
     FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, std::max(1, std::min(blocks, w.grid / 2)), 256, 0, (const int*)nullptr,
@@ -851,7 +860,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fast(
     const int4* __restrict__ tri, const int2* __restrict__ vxy, const double* __restrict__ uv,
     const float2* __restrict__ uvf, const float* __restrict__ img, int N, const int* __restrict__ item_tri,
     const int* __restrict__ item_off, const int* __restrict__ item_cnt, const int* __restrict__ n_items_dev,
-    int item_cap, float2* __restrict__ partial, int* __restrict__ item_done, FastOut F) {
+    int item_cap, int item_px, float2* __restrict__ partial, int* __restrict__ item_done, FastOut F) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -863,7 +872,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fast(
         int4 tr = tri[t];
         TriGeom g = tri_geom(tr, vxy, N);
         if (fast_small(g)) continue;  // summed by k_raster_small_fast (uniform over the warp)
-        int rpi = rows_per_item(g.maxw);
+        int rpi = rows_per_item(g.maxw, item_px);
         int r0 = g.ytop + j * rpi;
         int nr = min(rpi, g.yend + 1 - r0);
         int L = 0, len = 0;
@@ -1173,7 +1182,7 @@ fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, co
     // all pixels in FP32
     note_bytes(F_RASTER, raster_err_bytes(m));
     FEM_LAUNCH(F_RASTER, s, k_raster_fast, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
-               m->item_tri.p, m->item_off.p, m->item_cnt.p, m->dcount.p + 0, (int)m->item_tri.n,
+               m->item_tri.p, m->item_off.p, m->item_cnt.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P),
                (float2*)m->partial.p, m->item_done.p, F);
     FEM_LAUNCH(F_RASTER, s, k_raster_small_fast, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv, uvf, f,
                m->N, T, F);
@@ -1184,8 +1193,8 @@ fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, co
                m->band_small.p, cnt, max_out);
     // exact float-float keys of the band
     FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
-               m->item_tri.p, m->item_off.p, cnt + 2, (int)m->band_items.n, m->partial.p, (float*)nullptr,
-               (int*)nullptr, m->item_cnt.p, m->item_done.p, m->keys.p, m->keyc.p, m->band_items.p);
+               m->item_tri.p, m->item_off.p, cnt + 2, (int)m->band_items.n, item_pixels_for(m->P), m->partial.p,
+               (float*)nullptr, (int*)nullptr, m->item_cnt.p, m->item_done.p, m->keys.p, m->keyc.p, m->band_items.p);
     FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, small_grid(m), 256, 0, m->band_small.p, m->tri.p, m->vxy.p, uv,
                uvf, f, m->N, T, m->keys.p, m->keyc.p, (float*)nullptr, (int*)nullptr, cnt + 3);
     return FEM_OK;
@@ -1214,7 +1223,7 @@ extern "C" fem_status fem_triangle_error_bounds(fem_mesh* m, const double* uv_de
     FastOut F{lo_dev, hi_dev, m->fast_hist.p, m->fast_hist.p + kFastBins};
     FEM_LAUNCH(F_RASTER, s, k_raster_fast, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv_dev,
                (const float2*)nullptr, f_dev, m->N, m->item_tri.p, m->item_off.p, m->item_cnt.p, m->dcount.p + 0,
-               (int)m->item_tri.n, (float2*)m->partial.p, m->item_done.p, F);
+               (int)m->item_tri.n, item_pixels_for(m->P), (float2*)m->partial.p, m->item_done.p, F);
     FEM_LAUNCH(F_RASTER, s, k_raster_small_fast, small_grid(m), 256, 0, (const int*)nullptr, m->tri.p, m->vxy.p,
                uv_dev, (const float2*)nullptr, f_dev, m->N, T, F);
     int e = 0;

@@ -16,6 +16,8 @@
 #include <cmath>
 #include <vector>
 
+#include <cstring>
+
 #include "fem_internal.cuh"
 
 namespace fem {
@@ -186,6 +188,13 @@ __global__ void k_adj_combine(int nK, int V, const int* __restrict__ kvert, cons
     w[k] = s;
 }
 
+// scalars of the outer CG on the device (dscal + 32): |c|^2, p.N p, gamma =
+// r.r, the previous gamma, the stop threshold tol |c| (compared with
+// sqrt(gamma)), the stop flag and the number of completed iterations
+struct CgScalars {
+    double cc, pNp, gamma, gamma_old, thr, stop, iters;
+};
+
 __global__ void k_final_sum(int n, const double* __restrict__ partial, double* __restrict__ out) {
     __shared__ double sh[kVecThreads / 32];
     double t = 0.0;
@@ -200,10 +209,49 @@ __global__ void k_final_sum(int n, const double* __restrict__ partial, double* _
     }
 }
 
+// end of a CG update (mode 1): gamma_old = gamma, gamma = sum of the
+// partials, one more iteration, stop when sqrt(gamma) <= thr; a breakdown
+// (pNp <= 0) stops without an update
+__global__ void k_cg_update_sum(int nb, const double* __restrict__ partial, CgScalars* __restrict__ cg) {
+    __shared__ double sh[kVecThreads / 32];
+    if (cg->stop != 0.0) return;
+    if (!(cg->pNp > 0.0)) {
+        if (threadIdx.x == 0) cg->stop = 1.0;
+        return;
+    }
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) t += partial[i];
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double g = 0.0;
+        for (int w = 0; w < kVecThreads / 32; ++w) g += sh[w];
+        cg->gamma_old = cg->gamma;
+        cg->gamma = g;
+        cg->iters += 1.0;
+        if (sqrt(g) <= cg->thr) cg->stop = 1.0;
+    }
+}
+
 // mode 0: partial of x.y; mode 1: g += a p, r -= a w, partial of r.r;
-// mode 2: p = r + b p; mode 3: r = c - w, p = r, partial r.r
+// mode 2: p = r + b p; mode 3: r = c - w, p = r, partial r.r.
+// cg (optional, the outer CG's device scalars, see CgScalars): modes 1 and
+// 2 take a = gamma / pNp and b = gamma / gamma_old from it and do nothing
+// once the iteration has stopped, so no scalar is read back per iteration.
+
 __global__ void k_vec(int mode, int n, double a, double* __restrict__ x, double* __restrict__ y,
-                      double* __restrict__ z, const double* __restrict__ w, double* __restrict__ partial) {
+                      double* __restrict__ z, const double* __restrict__ w, double* __restrict__ partial,
+                      const CgScalars* __restrict__ cg = nullptr) {
+    if (cg) {
+        if (cg->stop != 0.0) return;
+        if (mode == 1) {
+            if (!(cg->pNp > 0.0)) return;
+            a = cg->gamma / cg->pNp;
+        } else if (mode == 2) {
+            a = cg->gamma / cg->gamma_old;
+        }
+    }
     double dot = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (mode == 0) {
@@ -291,6 +339,7 @@ struct InnerCfg {
     bool fp64;
     double tol;
     int maxit;
+    bool deferred;  // statistics stay on the device (solve_totals_*); no read-back per solve
 };
 
 // w = E^T y for the vertex vector y (m->ty); uses m->b64 / m->tz
@@ -298,7 +347,7 @@ static fem_status apply_ET(fem_mesh* m, const double* y, double* w, const InnerC
     int nU = m->nU, nK = m->nK;
     if (nU > 0) {
         FEM_LAUNCH(F_TONAL, s, k_gather_U, (nU + 255) / 256, 256, 0, nU, m->urow_vertex.p, y, m->b64.p, m->tz.p);
-        fem_status st = run_solve(m, m->b64.p, m->tz.p, c.fp64, c.tol, c.maxit, s, nullptr, nullptr);
+        fem_status st = run_solve(m, m->b64.p, m->tz.p, c.fp64, c.tol, c.maxit, s, nullptr, nullptr, c.deferred);
         if (st != FEM_OK) return st;
     }
     FEM_LAUNCH(F_TONAL, s, k_adj_combine, (nK + 255) / 256, 256, 0, nK, m->V, m->kvert.p, m->nbr.p, m->coefA.p,
@@ -313,7 +362,7 @@ static fem_status apply_N(fem_mesh* m, const double* p, double* w, double* pNp_d
     if (nU > 0) {
         FEM_LAUNCH(F_TONAL, s, k_fwd_rhs, (nU + 255) / 256, 256, 0, nU, V, m->urow_vertex.p, m->nbr.p, m->coefA.p,
                    m->mask.p, m->kidx.p, p, m->b64.p, m->x64.p);
-        fem_status st = run_solve(m, m->b64.p, m->x64.p, c.fp64, c.tol, c.maxit, s, nullptr, nullptr);
+        fem_status st = run_solve(m, m->b64.p, m->x64.p, c.fp64, c.tol, c.maxit, s, nullptr, nullptr, c.deferred);
         if (st != FEM_OK) return st;
     }
     FEM_LAUNCH(F_TONAL, s, k_assemble_v, (V + 255) / 256, 256, 0, V, m->mask.p, m->kidx.p, m->uidx.p, p, m->x64.p,
@@ -358,8 +407,11 @@ extern "C" fem_status fem_tonal_opt(fem_mesh* m, const float* f_dev, float* g_de
     FEM_TRY(prepare_tonal(m, s));
     FEM_TRY(ensure_tonal_vectors(m, s));
     int nK = m->nK;
-    InnerCfg c{p->precision == FEM_PREC_FP64, p->inner_tol, p->maxit};
-    double* sc = m->dscal.p + 32;  // [0] |c|^2 [1] pNp [2] gamma
+    // inner solves keep their statistics on the device (read once at the end)
+    InnerCfg c{p->precision == FEM_PREC_FP64, p->inner_tol, p->maxit, true};
+    FEM_TRY(solve_totals_reset(m, s));
+    CgScalars* cg = (CgScalars*)(m->dscal.p + 32);
+    double* sc = m->dscal.p + 32;  // [0] |c|^2 [1] pNp [2] gamma (the CgScalars layout)
     // c = B^T f
     FEM_TRY(scatter_PT(m, f_dev, s));
     FEM_TRY(apply_ET(m, m->ty.p, m->tc.p, c, s));
@@ -374,30 +426,68 @@ extern "C" fem_status fem_tonal_opt(fem_mesh* m, const float* f_dev, float* g_de
     double cnorm = sqrt(cc);
     int it = 0;
     fem_status st = FEM_E_NOT_CONVERGED;
-    for (;;) {
-        if (cnorm == 0.0 || sqrt(gamma) <= p->tonal_tol * cnorm) { st = FEM_OK; break; }
-        if (it >= p->tonal_maxit) break;
-        FEM_TRY(apply_N(m, m->tp.p, m->tw.p, sc + 1, c, s));
-        double pNp = 0.0;
-        FEM_TRY(read_scalar(m, sc + 1, &pNp, s));
-        if (!(pNp > 0.0)) { st = FEM_OK; break; }
-        double alpha = gamma / pNp;
-        FEM_TRY(vec_op(m, 1, nK, alpha, m->tg.p, m->tp.p, m->tr.p, m->tw.p, sc + 2, s));
-        double gamma1 = 0.0;
-        FEM_TRY(read_scalar(m, sc + 2, &gamma1, s));
-        double beta = gamma1 / gamma;
-        gamma = gamma1;
-        FEM_TRY(vec_op(m, 2, nK, beta, m->tp.p, nullptr, m->tr.p, nullptr, nullptr, s));
-        it++;
+    if (cnorm == 0.0 || sqrt(gamma) <= p->tonal_tol * cnorm) {
+        st = FEM_OK;
+    } else if (p->tonal_maxit > 0) {
+        // Outer CG with its scalars on the device: alpha = gamma / pNp and
+        // beta = gamma / gamma_old are formed by the vector kernels, the stop
+        // test (sqrt(gamma) <= tonal_tol |c|, or a breakdown pNp <= 0) by the
+        // update's reduction, after which the vector kernels do nothing.  The
+        // host reads the stop flag two iterations behind, so the GPU never
+        // waits for it; the one or two iterations enqueued beyond the stop
+        // leave g unchanged.
+        double* hs = (double*)m->host_stage;
+        // thr holds tol |c| and is compared with sqrt(gamma) (as above)
+        double init[4] = {gamma, p->tonal_tol * cnorm, 0.0, 0.0};  // gamma_old, thr, stop, iters
+        std::memcpy(hs, init, sizeof(init));
+        FEM_CUDA(cudaMemcpyAsync(&cg->gamma_old, hs, sizeof(init), cudaMemcpyHostToDevice, s));
+        cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+        fem_status lst = FEM_OK;
+        for (int q = 0; q < 3 && lst == FEM_OK; ++q) {
+            cudaError_t e = cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming);
+            if (e != cudaSuccess) lst = cuda_fail(e, "cudaEventCreate");
+        }
+        double* slot = hs + 8;  // three pinned (stop, iters) pairs
+        int G = vec_grid(m);
+        for (int k = 0; lst == FEM_OK && k < p->tonal_maxit; ++k) {
+            lst = apply_N(m, m->tp.p, m->tw.p, &cg->pNp, c, s);
+            if (lst != FEM_OK) break;
+            note_launch_begin(F_TONAL, s);
+            k_vec<<<G, kVecThreads, 0, s>>>(1, nK, 0.0, m->tg.p, m->tp.p, m->tr.p, m->tw.p, m->red.p, cg);
+            note_launch_end(F_TONAL, s);
+            note_launch_begin(F_TONAL, s);
+            k_cg_update_sum<<<1, kVecThreads, 0, s>>>(G, m->red.p, cg);
+            note_launch_end(F_TONAL, s);
+            note_launch_begin(F_TONAL, s);
+            k_vec<<<G, kVecThreads, 0, s>>>(2, nK, 0.0, m->tp.p, nullptr, m->tr.p, nullptr, m->red.p, cg);
+            note_launch_end(F_TONAL, s);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(slot + 2 * (k % 3), &cg->stop, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[k % 3], s);
+            if (e != cudaSuccess) { lst = cuda_fail(e, "tonal iteration"); break; }
+            if (k >= 2) {
+                e = cudaEventSynchronize(ev[(k - 2) % 3]);
+                if (e != cudaSuccess) { lst = cuda_fail(e, "cudaEventSynchronize"); break; }
+                if (slot[2 * ((k - 2) % 3)] != 0.0) break;
+            }
+        }
+        for (int q = 0; q < 3; ++q)
+            if (ev[q]) cudaEventDestroy(ev[q]);
+        FEM_TRY(lst);
+        double fin[7];
+        FEM_CUDA(cudaMemcpyAsync(hs, cg, sizeof(fin), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaStreamSynchronize(s));
+        std::memcpy(fin, hs, sizeof(fin));
+        gamma = fin[2];
+        it = (int)fin[6];
+        if (fin[5] != 0.0) st = FEM_OK;
     }
     FEM_LAUNCH(F_TONAL, s, k_d2f, (nK + 255) / 256, 256, 0, nK, m->tg.p, g_dev);
-    FEM_CUDA(cudaStreamSynchronize(s));
-    long long cgi = m->stats.cg_iters;
-    int solves = m->stats.solves;
+    fem_status sst = solve_totals_read(m, s);  // synchronises; inner-solve failures
     m->stats.tonal_iters = it;
     m->stats.tonal_relres = cnorm > 0 ? sqrt(gamma) / cnorm : 0.0;
-    m->stats.cg_iters = cgi;
-    m->stats.solves = solves;
+    if (sst != FEM_OK) return sst;
     if (st != FEM_OK) set_error("fem_tonal_opt: outer iteration cap reached");
     return st;
 }
@@ -415,7 +505,7 @@ extern "C" fem_status fem_adjoint(fem_mesh* m, const float* r_dev, float* gbar_d
     m->stats = fem_stats{};
     FEM_TRY(prepare_tonal(m, s));
     FEM_TRY(ensure_tonal_vectors(m, s));
-    InnerCfg c{p->precision == FEM_PREC_FP64, p->inner_tol, p->maxit};
+    InnerCfg c{p->precision == FEM_PREC_FP64, p->inner_tol, p->maxit, false};
     FEM_TRY(scatter_PT(m, r_dev, s));
     FEM_TRY(apply_ET(m, m->ty.p, m->tw.p, c, s));
     FEM_LAUNCH(F_TONAL, s, k_d2f, (m->nK + 255) / 256, 256, 0, m->nK, m->tw.p, gbar_dev);
