@@ -1,5 +1,15 @@
-// components.cu -- connected components of the unknown-vertex graph and a
-// component-ordered numbering of the unknowns (rows of A_UU, Sec. 2.2).
+// components.cu -- the Laplace system of a mesh in one cooperative kernel:
+// P1 stiffness per vertex and lattice direction (Sec. 2.2), the K/U split,
+// the connected components of the unknown-vertex graph, a component-ordered
+// numbering of the unknowns, and the ELL rows of A_UU.
+//
+// Every triangle of a newest-vertex-bisection mesh of the pixel square is a
+// right isosceles triangle, so its P1 stiffness matrix is the same for all
+// sizes: with c at the right angle, K_cc = 1, K_aa = K_bb = 1/2,
+// K_ac = K_bc = -1/2, K_ab = 0.  All entries of A are multiples of 1/2 and
+// exact in FP32, and their sums do not depend on the order of the additions.
+// All edges point in one of 8 lattice directions, so A is stored per vertex
+// and direction (nbr / coef, slot-major).
 //
 // A_UU couples two unknown vertices only through a mesh edge with a nonzero
 // stiffness entry.  In meshes made by the spatial optimisation nearly every
@@ -8,30 +18,41 @@
 // in 9,561 blocks, the largest with 224 rows.  When the unknowns are
 // numbered component by component, each block is a contiguous range of rows
 // whose columns stay inside the range, and the solver treats the blocks as
-// independent systems (solve_comp.cu).
+// independent systems (solve_comp.cu).  The numbering does not depend on
+// thread scheduling: components are ordered by their smallest vertex id, the
+// rows of a component by vertex id.
 //
-// The numbering does not depend on thread scheduling: components are
-// ordered by their smallest vertex id, the rows of a component by vertex id.
-//   1. union-find over the edges (parents start at the smallest unknown
-//      neighbour; the larger root is hooked under the smaller one by
-//      atomicCAS; finds halve paths), so the final root of a component is
-//      its smallest vertex;
-//   2. sizes per root, then one scan over the roots gives the first row of
-//      each component;
-//   3. members are dropped into their component's range in any order, and
-//      each range is sorted by vertex id (a warp with shuffles, a block in
-//      shared memory, or a block in global memory for long ranges).
-// Components are then addressed by their first row (rowcomp holds their
-// size there), listed by size class for the solver.
+// The phases, separated by bounded grid barriers (one launch instead of a
+// chain of eight kernels and three memsets):
+//   0. clear the per-vertex stiffness arrays and the component counters;
+//   1. assemble: per triangle, neighbours and stiffness per direction;
+//   2. scan of the unknown flags: mask vertices are numbered by the count of
+//      mask vertices before them; each unknown vertex's union-find parent
+//      starts at its smallest unknown neighbour through a nonzero entry;
+//   3. union-find over the edges (one thread per vertex and direction; the
+//      larger root is hooked under the smaller by atomicCAS; finds halve
+//      paths), so the final root of a component is its smallest vertex;
+//   4. final roots (a read-only walk) and component sizes;
+//   5. scan over the roots: the first row of each component;
+//   6. members dropped into their component's range in any order; sizes at
+//      the first rows; components listed by size class;
+//   7. every range sorted by vertex id (a warp with shuffles, a block in
+//      shared memory, or a block in global memory for long ranges);
+//   8. ELL rows of A_UU, and (optionally) the right-hand side and start of a
+//      solve on the current vertex values.
+// Data written in one phase and read in a later one is read through L2
+// (__ldcg): an SM's L1 is not kept coherent with other SMs' writes.
 #include <algorithm>
 #include <climits>
 
 #include "fem_internal.cuh"
+#include "scan.cuh"
 
 namespace fem {
 
-constexpr int kSortSmem = 4096;   // ranges up to this size are sorted in shared memory
-constexpr int kSortThreads = 256;
+constexpr int kBuildThreads = 256;
+static_assert(kBuildThreads == SCAN_BT, "the block scan assumes SCAN_BT threads");
+constexpr int kSortSmem = 4096;  // ranges up to this size are sorted in shared memory
 constexpr int kUniteCap = 1 << 20;
 
 // Root of x.  Parents only point to smaller ids, so the walk ends; path
@@ -47,80 +68,19 @@ __device__ __forceinline__ int cc_find(int* parent, int x) {
     }
 }
 
-// One thread per (vertex, direction) slot: each edge is united once, from
-// its larger endpoint.  A thread follows one chain of dependent loads only.
-__global__ void k_cc_hook(const unsigned char* __restrict__ mask, const int* __restrict__ nbr,
-                          const float* __restrict__ coef, int V, int* parent, int* __restrict__ err) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 8LL * V) return;
-    int v = (int)(t % V);
-    int j = nbr[t];
-    if (j < 0 || j >= v || mask[v] || coef[t] == 0.0f || mask[j]) return;
-    int a = v, b = j;
-    bool done = false;
-    for (int it = 0; it < kUniteCap && !done; ++it) {
-        a = cc_find(parent, a);
-        b = cc_find(parent, b);
-        if (a == b) { done = true; break; }
-        if (a < b) { int x = a; a = b; b = x; }
-        done = atomicCAS(parent + a, a, b) == a;
-    }
-    if (!done) atomicCAS(err, 0, (int)FEM_E_INVALID);
-}
-
-// Final root of every unknown vertex (into a separate array: a path-halving
-// find here could overwrite a root just stored by another thread with an
-// older ancestor) and the component sizes.  The forest no longer changes, so
-// a read-only walk suffices.
-__global__ void k_cc_flatten(const unsigned char* __restrict__ mask, int V, const int* __restrict__ parent,
-                             int* __restrict__ root, int* __restrict__ size) {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V || mask[v]) return;
-    int r = v;
-    for (int p = parent[r]; p != r; p = parent[r]) r = p;
-    root[v] = r;
-    atomicAdd(size + r, 1);
-}
-
-// Members into their ranges (any order).  Every member writes its slot of
-// rowcomp (the size at the component's first row, 0 elsewhere); the root
-// lists its component by size class; a one-row component needs no sort, so
-// its vertex gets its row here.
-__global__ void k_cc_place(const unsigned char* __restrict__ mask, int V, const int* __restrict__ root,
-                           const int* __restrict__ size, const int* __restrict__ cstart, int* __restrict__ fill,
-                           int* __restrict__ members, int* __restrict__ rowcomp, int* __restrict__ uidx,
-                           int* __restrict__ blk_list, int* __restrict__ warp_list, int* __restrict__ cnt, int nU) {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V || mask[v]) return;
-    int r = root[v], sz = size[r], st = cstart[r];
-    int slot = st + atomicAdd(fill + r, 1);
-    if (slot >= nU || st + sz > nU) {  // more unknowns than rows: a malformed mesh count
-        atomicCAS(cnt + CC_ERR, 0, (int)FEM_E_INVALID);
-        return;
-    }
-    members[slot] = v;
-    rowcomp[slot] = slot == st ? sz : 0;
-    if (sz == 1) uidx[v] = slot;
-    if (r == v) {
-        if (sz > kWarpComp) {
-            blk_list[atomicAdd(cnt + CC_NBLK, 1)] = st;
-            if (sz > kBlockComp) atomicAdd(cnt + CC_NBIG, 1);
-        } else if (sz > 1) {
-            warp_list[atomicAdd(cnt + CC_NWARP, 1)] = st;
-        }
-    }
-}
-
 // All-ascending bitonic network: for each merge size k, compare i with its
 // mirror i ^ (k - 1), then with i ^ s for s = k/4 .. 1; the smaller key goes
 // to the smaller index.  Keys past the range act as +infinity, which never
-// moves, so a range is sorted in place without padding.
+// moves, so a range is sorted in place without padding.  GLOBAL: the range
+// lives in global memory and was written by other blocks (loads through L2).
+template <bool GLOBAL>
 __device__ __forceinline__ void cas_asc(int* a, int lo, int hi, int n) {
     if (hi >= n) return;
-    int x = a[lo], y = a[hi];
+    int x = GLOBAL ? __ldcg(a + lo) : a[lo], y = GLOBAL ? __ldcg(a + hi) : a[hi];
     if (y < x) { a[lo] = y; a[hi] = x; }
 }
 
+template <bool GLOBAL>
 __device__ void block_sort_range(int* a, int n) {
     int P = 1;
     while (P < n) P <<= 1;
@@ -128,13 +88,13 @@ __device__ void block_sort_range(int* a, int n) {
         int h = k >> 1;
         for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
             int blk = i / h, off = i % h;
-            cas_asc(a, blk * k + off, blk * k + k - 1 - off, n);
+            cas_asc<GLOBAL>(a, blk * k + off, blk * k + k - 1 - off, n);
         }
         __syncthreads();
         for (int s = k >> 2; s > 0; s >>= 1) {
             for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
                 int lo = (i / s) * 2 * s + i % s;
-                cas_asc(a, lo, lo + s, n);
+                cas_asc<GLOBAL>(a, lo, lo + s, n);
             }
             __syncthreads();
         }
@@ -159,71 +119,415 @@ __device__ __forceinline__ int warp_sort_asc(int key) {
     return key;
 }
 
-// Sort every component's range by vertex id and write uidx (vertex -> row):
-// blocks take the components above one warp, warps those of 2..32 rows.
-__global__ void __launch_bounds__(kSortThreads) k_cc_sort(const int* __restrict__ rowcomp,
-                                                           const int* __restrict__ blk_list,
-                                                           const int* __restrict__ warp_list,
-                                                           const int* __restrict__ cnt, int* __restrict__ members,
-                                                           int* __restrict__ uidx) {
-    __shared__ int s_keys[kSortSmem];
-    if (cnt[CC_ERR] != 0) return;
-    const int nblk = cnt[CC_NBLK], nwarp = cnt[CC_NWARP];
-    for (int i = blockIdx.x; i < nblk; i += gridDim.x) {
-        int s0 = blk_list[i], n = rowcomp[s0];
-        int* rng = members + s0;
-        if (n <= kSortSmem) {
-            for (int k = threadIdx.x; k < n; k += blockDim.x) s_keys[k] = rng[k];
-            __syncthreads();
-            block_sort_range(s_keys, n);
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                int v = s_keys[k];
-                rng[k] = v;
-                uidx[v] = s0 + k;
+// integer sum over the block, the same value in every thread
+__device__ __forceinline__ int block_sum_int(int v) {
+    __shared__ int s_w[kBuildThreads / 32];
+    __shared__ int s_tot;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) s_w[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int i = 0; i < kBuildThreads / 32; ++i) t += s_w[i];
+        s_tot = t;
+    }
+    __syncthreads();
+    int t = s_tot;
+    __syncthreads();
+    return t;
+}
+
+// Exclusive scan over [0, n) inside the cooperative kernel: block b takes a
+// contiguous chunk; phase A evaluates in(i) once (kept in vals[i]) and sums
+// the chunk; after a grid barrier every block adds the sums of the chunks
+// before it and scans its chunk in steps of one element per thread, calling
+// out(i, prefix, value).  A second barrier publishes the outputs.
+template <class In, class Out>
+__device__ bool coop_scan(In in, Out out, int n, int* vals, int* tsum, int* total, unsigned* bar, int* err) {
+    const int nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+    const int chunk = (n + nb - 1) / nb;
+    const int lo = min(n, b * chunk), hi = min(n, lo + chunk);
+    int part = 0;
+    for (int i = lo + tid; i < hi; i += kBuildThreads) {
+        int v = in(i);
+        vals[i] = v;
+        part += v;
+    }
+    part = block_sum_int(part);
+    if (tid == 0) tsum[b] = part;
+    if (!grid_barrier(bar, err)) return false;
+    int pre = 0;
+    for (int j = tid; j < b; j += kBuildThreads) pre += __ldcg(tsum + j);
+    pre = block_sum_int(pre);
+    if (total && b == nb - 1 && tid == 0) *total = pre + __ldcg(tsum + b);
+    for (int base = lo; base < hi; base += kBuildThreads) {
+        int i = base + tid;
+        int v[1] = {i < hi ? vals[i] : 0};  // written by this thread in phase A
+        int own = v[0];
+        int seg = block_exclusive_scan<1>(v);
+        if (i < hi) out(i, pre + v[0], own);
+        pre += seg;
+    }
+    return grid_barrier(bar, err);
+}
+
+struct BuildArgs {
+    const int4* tri;
+    const int2* vxy;
+    const unsigned char* mask;
+    int T, V, nU;
+    int* nbr;
+    float* coef;
+    float* diag;
+    int* parent;
+    int* root;
+    int* size;
+    int* fill;
+    int* cstart;
+    int* uidx;
+    int* kidx;
+    int* kvert;
+    int* members;  // urow_vertex: vertex of each row
+    int* rowcomp;
+    int* blk_list;
+    int* warp_list;
+    int* cnt;      // CC_* counters
+    int* nU_dev;
+    int* ucol;
+    float* uval;
+    float* udiag;
+    int* ucnt;
+    float* udinv;
+    double* udinv64;
+    const double* uv;  // right-hand side and start (optional: b == nullptr)
+    double* b;
+    double* x;
+    int* vals;  // V scratch of the scans
+    int* tsum;  // gridDim scratch of the scans
+    unsigned* bar;
+    int* err;
+};
+
+struct UnknownFlagIn {
+    const BuildArgs* A;
+    __device__ __forceinline__ int operator()(int i) const {
+        const BuildArgs& a = *A;
+        int pa = i;
+        bool unk = !a.mask[i];
+        if (unk) {
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                int j = __ldcg(a.nbr + (size_t)d * a.V + i);
+                if (j >= 0 && j < pa && __ldcg(a.coef + (size_t)d * a.V + i) != 0.0f && !a.mask[j]) pa = j;
             }
-            __syncthreads();
+        }
+        a.parent[i] = pa;
+        a.size[i] = 0;
+        a.fill[i] = 0;
+        return unk ? 1 : 0;
+    }
+};
+
+struct IndexMapOut {
+    const BuildArgs* A;
+    __device__ __forceinline__ void operator()(int i, int u, int unk) const {
+        const BuildArgs& a = *A;
+        if (!unk) {
+            int k = i - u;
+            a.kidx[i] = k;
+            a.kvert[k] = i;
+            a.uidx[i] = -1;
         } else {
-            block_sort_range(rng, n);
-            for (int k = threadIdx.x; k < n; k += blockDim.x) uidx[rng[k]] = s0 + k;
-            __syncthreads();
+            a.kidx[i] = -1;
         }
     }
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = gw; i < nwarp; i += nw) {
-        int s0 = warp_list[i], n = rowcomp[s0];
-        int key = lane < n ? members[s0 + lane] : INT_MAX;
-        key = warp_sort_asc(key);
-        if (lane < n) {
-            members[s0 + lane] = key;
-            uidx[key] = s0 + lane;
+};
+
+struct RootSizeIn {
+    const BuildArgs* A;
+    __device__ __forceinline__ int operator()(int v) const {
+        const BuildArgs& a = *A;
+        return (!a.mask[v] && __ldcg(a.root + v) == v) ? __ldcg(a.size + v) : 0;
+    }
+};
+
+struct StoreOut {
+    int* dst;
+    __device__ __forceinline__ void operator()(int i, int pre, int) const { dst[i] = pre; }
+};
+
+// the kernel stops at a failed barrier; the solve then reports the code
+__device__ __forceinline__ void build_fail(const BuildArgs& A) {
+    if (threadIdx.x == 0) atomicCAS(A.cnt + CC_ERR, 0, (int)FEM_E_TIMEOUT);
+}
+
+__global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
+    __shared__ int s_keys[kSortSmem];
+    const int tid0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    const int V = A.V, T = A.T;
+    const long long V8 = 8LL * V;
+    // 0. clear
+    for (long long i = tid0; i < V8; i += stride) {
+        A.nbr[i] = -1;
+        A.coef[i] = 0.0f;
+    }
+    for (int i = tid0; i < V; i += stride) A.diag[i] = 0.0f;
+    if (tid0 < CC_COUNTERS) A.cnt[tid0] = 0;
+    if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
+    // 1. assemble: legs (c,a) and (c,b) carry -1/2 each, the hypotenuse is
+    //    adjacency only; K_cc = 1, K_aa = K_bb = 1/2 on the diagonal
+    for (int t = tid0; t < T; t += stride) {
+        int4 tr = A.tri[t];
+        int a = tr.x, b = tr.y, c = tr.z;
+        int2 pa = A.vxy[a], pb = A.vxy[b], pc = A.vxy[c];
+        int d = dir_index(pa.x - pc.x, pa.y - pc.y);
+        A.nbr[(size_t)d * V + c] = a;
+        atomicAdd(A.coef + (size_t)d * V + c, -0.5f);
+        d = (d + 4) & 7;
+        A.nbr[(size_t)d * V + a] = c;
+        atomicAdd(A.coef + (size_t)d * V + a, -0.5f);
+        d = dir_index(pb.x - pc.x, pb.y - pc.y);
+        A.nbr[(size_t)d * V + c] = b;
+        atomicAdd(A.coef + (size_t)d * V + c, -0.5f);
+        d = (d + 4) & 7;
+        A.nbr[(size_t)d * V + b] = c;
+        atomicAdd(A.coef + (size_t)d * V + b, -0.5f);
+        d = dir_index(pb.x - pa.x, pb.y - pa.y);
+        A.nbr[(size_t)d * V + a] = b;
+        A.nbr[(size_t)((d + 4) & 7) * V + b] = a;
+        atomicAdd(A.diag + c, 1.0f);
+        atomicAdd(A.diag + a, 0.5f);
+        atomicAdd(A.diag + b, 0.5f);
+    }
+    if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
+    // 2. unknown flags -> mask numbering, union-find start
+    if (!coop_scan(UnknownFlagIn{&A}, IndexMapOut{&A}, V, A.vals, A.tsum, A.nU_dev, A.bar, A.err)) {
+        build_fail(A);
+        return;
+    }
+    if (A.nU == 0) return;  // uniform: no unknowns, no components
+    // 3. union-find: each edge once, from its larger endpoint
+    for (long long e = tid0; e < V8; e += stride) {
+        int v = (int)(e % V);
+        int j = __ldcg(A.nbr + e);
+        if (j < 0 || j >= v || A.mask[v] || __ldcg(A.coef + e) == 0.0f || A.mask[j]) continue;
+        int a = v, b = j;
+        bool done = false;
+        for (int it = 0; it < kUniteCap && !done; ++it) {
+            a = cc_find(A.parent, a);
+            b = cc_find(A.parent, b);
+            if (a == b) { done = true; break; }
+            if (a < b) { int x = a; a = b; b = x; }
+            done = atomicCAS(A.parent + a, a, b) == a;
+        }
+        if (!done) atomicCAS(A.cnt + CC_ERR, 0, (int)FEM_E_INVALID);
+    }
+    if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
+    // 4. final roots (into a separate array: the forest no longer changes)
+    //    and component sizes
+    for (int v = tid0; v < V; v += stride) {
+        if (A.mask[v]) continue;
+        int r = v;
+        for (int p = __ldcg(A.parent + r); p != r; p = __ldcg(A.parent + r)) r = p;
+        A.root[v] = r;
+        atomicAdd(A.size + r, 1);
+    }
+    if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
+    // 5. first row of each component
+    if (!coop_scan(RootSizeIn{&A}, StoreOut{A.cstart}, V, A.vals, A.tsum, A.cnt + CC_NROWS, A.bar, A.err)) {
+        build_fail(A);
+        return;
+    }
+    // 6. members into their ranges; a one-row component needs no sort
+    for (int v = tid0; v < V; v += stride) {
+        if (A.mask[v]) continue;
+        int r = __ldcg(A.root + v), sz = __ldcg(A.size + r), st = __ldcg(A.cstart + r);
+        int slot = st + atomicAdd(A.fill + r, 1);
+        if (slot >= A.nU || st + sz > A.nU) {  // more unknowns than rows: a malformed mesh count
+            atomicCAS(A.cnt + CC_ERR, 0, (int)FEM_E_INVALID);
+            continue;
+        }
+        A.members[slot] = v;
+        A.rowcomp[slot] = slot == st ? sz : 0;
+        if (sz == 1) A.uidx[v] = slot;
+        if (r == v) {
+            if (sz > kWarpComp) {
+                A.blk_list[atomicAdd(A.cnt + CC_NBLK, 1)] = st;
+                if (sz > kBlockComp) atomicAdd(A.cnt + CC_NBIG, 1);
+            } else if (sz > 1) {
+                A.warp_list[atomicAdd(A.cnt + CC_NWARP, 1)] = st;
+            }
+        }
+    }
+    if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
+    // 7. sort every range by vertex id and write uidx (vertex -> row)
+    if (__ldcg(A.cnt + CC_ERR) == 0) {
+        const int nblk = __ldcg(A.cnt + CC_NBLK), nwarp = __ldcg(A.cnt + CC_NWARP);
+        for (int i = blockIdx.x; i < nblk; i += gridDim.x) {
+            int s0 = __ldcg(A.blk_list + i), n = __ldcg(A.rowcomp + s0);
+            int* rng = A.members + s0;
+            if (n <= kSortSmem) {
+                for (int k = threadIdx.x; k < n; k += blockDim.x) s_keys[k] = __ldcg(rng + k);
+                __syncthreads();
+                block_sort_range<false>(s_keys, n);
+                for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                    int v = s_keys[k];
+                    rng[k] = v;
+                    A.uidx[v] = s0 + k;
+                }
+                __syncthreads();
+            } else {
+                block_sort_range<true>(rng, n);
+                for (int k = threadIdx.x; k < n; k += blockDim.x) A.uidx[__ldcg(rng + k)] = s0 + k;
+                __syncthreads();
+            }
+        }
+        const int lane = threadIdx.x & 31;
+        const int gw = tid0 >> 5, nw = stride >> 5;
+        for (int i = gw; i < nwarp; i += nw) {
+            int s0 = __ldcg(A.warp_list + i), n = __ldcg(A.rowcomp + s0);
+            int key = lane < n ? __ldcg(A.members + s0 + lane) : INT_MAX;
+            key = warp_sort_asc(key);
+            if (lane < n) {
+                A.members[s0 + lane] = key;
+                A.uidx[key] = s0 + lane;
+            }
+        }
+    }
+    if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
+    if (__ldcg(A.cnt + CC_ERR) != 0) return;  // rows incomplete: the solve reports the code
+    // 8. ELL rows of A_UU (padded with the own row and value 0); with b the
+    //    right-hand side b_r = -sum over mask neighbours of A_ij uv_j and the
+    //    start x_r = uv of the row's vertex
+    const int nU = A.nU;
+    for (int r = tid0; r < nU; r += stride) {
+        int i = __ldcg(A.members + r);
+        int s = 0;
+        double bs = 0.0;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            int j = __ldcg(A.nbr + (size_t)d * V + i);
+            float c = __ldcg(A.coef + (size_t)d * V + i);
+            if (j >= 0 && c != 0.0f) {
+                int uj = __ldcg(A.uidx + j);
+                if (uj >= 0) {
+                    A.ucol[(size_t)s * nU + r] = uj;
+                    A.uval[(size_t)s * nU + r] = c;
+                    s++;
+                } else if (A.b) {
+                    bs -= (double)c * A.uv[j];
+                }
+            }
+        }
+        A.ucnt[r] = s;
+        for (; s < 8; ++s) {
+            A.ucol[(size_t)s * nU + r] = r;
+            A.uval[(size_t)s * nU + r] = 0.0f;
+        }
+        float dg = __ldcg(A.diag + i);
+        A.udiag[r] = dg;
+        A.udinv[r] = 1.0f / dg;
+        A.udinv64[r] = 1.0 / (double)dg;
+        if (A.b) {
+            A.b[r] = bs;
+            A.x[r] = A.uv[i];
         }
     }
 }
 
-fem_status build_components(fem_mesh* m, cudaStream_t s) {
-    int V = m->V, nU = m->nU;
-    size_t nr = (size_t)(nU > 0 ? nU : 1) + 1;
-    FEM_TRY(ensure(m->cc_root, (size_t)V, s));
+// with_rhs (optional): on input asks for b64/x64 of a solve on the current
+// vertex values to be filled with the system; on output true when that
+// happened (the system was rebuilt), false when the caller must fill them
+fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
+    bool want = with_rhs && *with_rhs;
+    if (with_rhs) *with_rhs = false;
+    if (m->sys_version == m->mesh_version) return FEM_OK;
+    const int V = m->V, T = m->T;
+    // the mask count is kept on the host by create / import / refinement, so
+    // the unknown count needs no read-back
+    const int nU = V - m->nK;
+    m->nU = nU;
+    const size_t n = nU > 0 ? nU : 1, nr = n + 1;
+    FEM_TRY(ensure(m->nbr, (size_t)8 * V, s));
+    FEM_TRY(ensure(m->coefA, (size_t)8 * V, s));
+    FEM_TRY(ensure(m->diagA, V, s));
+    FEM_TRY(ensure(m->uidx, V, s));
+    FEM_TRY(ensure(m->kidx, V, s));
+    FEM_TRY(ensure(m->urow_vertex, V, s));
+    FEM_TRY(ensure(m->kvert, V, s));
+    FEM_TRY(ensure(m->cc_parent, V, s));
+    FEM_TRY(ensure(m->cc_root, V, s));
+    FEM_TRY(ensure(m->cc_size, V, s));
+    FEM_TRY(ensure(m->cc_fill, V, s));
     FEM_TRY(ensure(m->cc_cstart, (size_t)V + 1, s));
     FEM_TRY(ensure(m->rowcomp, nr, s));
     FEM_TRY(ensure(m->blk_list, nr, s));
     FEM_TRY(ensure(m->warp_list, nr, s));
-    FEM_CUDA(cudaMemsetAsync(m->ccount.p, 0, sizeof(int) * CC_COUNTERS, s));
-    if (nU == 0) return FEM_OK;
-    int vb = (V + 255) / 256;
-    int* cnt = m->ccount.p;
-    FEM_LAUNCH(F_ASSEMBLY, s, k_cc_hook, (int)((8LL * V + 255) / 256), 256, 0, m->mask.p, m->nbr.p, m->coefA.p, V,
-               m->cc_parent.p, cnt + CC_ERR);
-    FEM_LAUNCH(F_ASSEMBLY, s, k_cc_flatten, vb, 256, 0, m->mask.p, V, m->cc_parent.p, m->cc_root.p, m->cc_size.p);
-    FEM_TRY(scan_component_rows(m, m->mask.p, m->cc_root.p, m->cc_size.p, m->cc_cstart.p, V, s, cnt + CC_NROWS));
-    FEM_LAUNCH(F_ASSEMBLY, s, k_cc_place, vb, 256, 0, m->mask.p, V, m->cc_root.p, m->cc_size.p, m->cc_cstart.p,
-               m->cc_fill.p, m->urow_vertex.p, m->rowcomp.p, m->uidx.p, m->blk_list.p, m->warp_list.p, cnt, nU);
-    // about one component of 2..32 rows per warp (at most half the rows)
-    int grid = std::max(1, std::min(m->num_sms * 8, (nU / 2 + 7) / 8));
-    FEM_LAUNCH(F_ASSEMBLY, s, k_cc_sort, grid, kSortThreads, 0, m->rowcomp.p, m->blk_list.p, m->warp_list.p, cnt,
-               m->urow_vertex.p, m->uidx.p);
+    FEM_TRY(ensure(m->ucol, 8 * n, s));
+    FEM_TRY(ensure(m->uval32, 8 * n, s));
+    FEM_TRY(ensure(m->udiag, n, s));
+    FEM_TRY(ensure(m->ucnt, n, s));
+    FEM_TRY(ensure(m->dinv32, n, s));
+    FEM_TRY(ensure(m->dinv64, n, s));
+    if (want && nU > 0) {
+        FEM_TRY(ensure(m->b64, (size_t)nU, s));
+        FEM_TRY(ensure(m->x64, (size_t)nU, s));
+    }
+    static const int occ = [] {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k_build_system, kBuildThreads, 0);
+        return nb < 1 ? 1 : nb;
+    }();
+    // about one vertex per thread, at most the co-resident blocks
+    const int grid = std::max(1, std::min(occ * m->num_sms, (V + kBuildThreads - 1) / kBuildThreads));
+    FEM_TRY(ensure(m->scan_vals, (size_t)V + 1, s));
+    FEM_TRY(ensure(m->scan_pre, (size_t)grid + 1, s));
+    BuildArgs A;
+    A.tri = m->tri.p;
+    A.vxy = m->vxy.p;
+    A.mask = m->mask.p;
+    A.T = T;
+    A.V = V;
+    A.nU = nU;
+    A.nbr = m->nbr.p;
+    A.coef = m->coefA.p;
+    A.diag = m->diagA.p;
+    A.parent = m->cc_parent.p;
+    A.root = m->cc_root.p;
+    A.size = m->cc_size.p;
+    A.fill = m->cc_fill.p;
+    A.cstart = m->cc_cstart.p;
+    A.uidx = m->uidx.p;
+    A.kidx = m->kidx.p;
+    A.kvert = m->kvert.p;
+    A.members = m->urow_vertex.p;
+    A.rowcomp = m->rowcomp.p;
+    A.blk_list = m->blk_list.p;
+    A.warp_list = m->warp_list.p;
+    A.cnt = m->ccount.p;
+    A.nU_dev = m->dcount.p + 1;
+    A.ucol = m->ucol.p;
+    A.uval = m->uval32.p;
+    A.udiag = m->udiag.p;
+    A.ucnt = m->ucnt.p;
+    A.udinv = m->dinv32.p;
+    A.udinv64 = m->dinv64.p;
+    A.uv = m->uv.p;
+    A.b = (want && nU > 0) ? m->b64.p : nullptr;
+    A.x = (want && nU > 0) ? m->x64.p : nullptr;
+    A.vals = m->scan_vals.p;
+    A.tsum = m->scan_pre.p;
+    A.bar = m->bar.p;
+    A.err = m->dflag.p + 2;
+    FEM_CUDA(cudaMemsetAsync(m->dflag.p + 2, 0, sizeof(int), s));
+    void* args[] = {&A};
+    FEM_TRY(launch_coop(F_ASSEMBLY, (const void*)k_build_system, grid, kBuildThreads, 0, s, args, "k_build_system"));
+    if (want && nU > 0) *with_rhs = true;
+    m->sys_version = m->mesh_version;
     return FEM_OK;
 }
+
+fem_status build_system(fem_mesh* m, cudaStream_t s) { return build_system_rhs(m, s, nullptr); }
 
 }  // namespace fem

@@ -268,16 +268,15 @@ constexpr int kBlockComp = 1024;
 // counters of the component search (fem_mesh::ccount)
 enum CcCounter { CC_NWARP = 0, CC_NROWS = 1, CC_NBLK = 2, CC_NBIG = 3, CC_ERR = 4, CC_WORK = 5, CC_DONE = 6,
                  CC_COUNTERS = 16 };
-fem_status build_components(fem_mesh* m, cudaStream_t s);
 fem_status solve_components(fem_mesh* m, const double* b, double* x, bool use_fp64, double tol, int maxit,
                             bool deferred, cudaStream_t s);
 
 // helpers implemented in the .cu files
 fem_status exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, int* total_dev);
-fem_status scan_i32(fem_mesh* m, const int* in, int* out, int n, cudaStream_t s, int* total_dev);
-fem_status scan_component_rows(fem_mesh* m, const unsigned char* mask, const int* root, const int* size, int* out,
-                               int n, cudaStream_t s, int* total_dev);
 fem_status build_system(fem_mesh* m, cudaStream_t s);
+// with_rhs (optional): on input asks for b64/x64 of a solve on the current
+// vertex values; on output true when the build filled them
+fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs);
 fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cudaStream_t s,
                          int* iters_out, double* relres_out, bool deferred = false);
 fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, double tol, int maxit, cudaStream_t s,

@@ -132,40 +132,6 @@ __global__ void k_scan_total(const int* in, const int* out, int n, int* total) {
     *total = n > 0 ? out[n - 1] + in[n - 1] : 0;
 }
 
-// Scan input: in[i], or (when root is set) the component size at a root
-// vertex and 0 elsewhere: !mask[i] && root[i] == i ? size[i] : 0.
-struct ScanIn {
-    const int* in;
-    const unsigned char* mask;
-    const int* root;
-    const int* size;
-    __device__ __forceinline__ int operator()(long long i) const {
-        if (!root) return in[i];
-        return (!mask[i] && root[i] == (int)i) ? size[i] : 0;
-    }
-};
-
-
-// out[i] = sum of in[0..i-1]; *total_dev (if non-null) = sum of all (one launch)
-fem_status scan_i32(fem_mesh* m, const int* in, int* out, int n, cudaStream_t s, int* total_dev) {
-    if (n <= 0) {
-        if (total_dev) FEM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int), s));
-        return FEM_OK;
-    }
-    return scan_fused_ipt<SCAN_IPT>(m, ScanIn{in, nullptr, nullptr, nullptr}, ScanStore{out}, n, s, total_dev,
-                                    F_OTHER);
-}
-
-// out[v] = rows of the components whose root (smallest vertex) is below v
-fem_status scan_component_rows(fem_mesh* m, const unsigned char* mask, const int* root, const int* size, int* out,
-                               int n, cudaStream_t s, int* total_dev) {
-    if (n <= 0) {
-        if (total_dev) FEM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int), s));
-        return FEM_OK;
-    }
-    return scan_fused_ipt<2>(m, ScanIn{nullptr, mask, root, size}, ScanStore{out}, n, s, total_dev, F_OTHER);
-}
-
 fem_status scan_scratch(fem_mesh* m, int n, cudaStream_t s, int** vals, int** pre) {
     FEM_TRY(ensure(m->scan_vals, (size_t)n, s));
     FEM_TRY(ensure(m->scan_pre, (size_t)n, s));

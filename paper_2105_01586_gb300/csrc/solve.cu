@@ -1,12 +1,6 @@
-// solve.cu -- P1 stiffness assembly and the Laplace solve on the unknown
-// vertices (Sec. 2.2): A_UU x_U = -A_UK g_K by Jacobi-preconditioned CG.
-//
-// Every triangle of a newest-vertex-bisection mesh of the pixel square is a
-// right isosceles triangle, so its P1 stiffness matrix is the same for all
-// sizes: with c at the right angle, K_cc = 1, K_aa = K_bb = 1/2,
-// K_ac = K_bc = -1/2, K_ab = 0.  All entries of A are multiples of 1/2 and
-// exact in FP32.  All edges point in one of 8 lattice directions, so A is
-// stored per vertex and direction (ELL with 8 slots, slot-major).
+// solve.cu -- the Laplace solve on the unknown vertices (Sec. 2.2):
+// A_UU x_U = -A_UK g_K by Jacobi-preconditioned CG.  The system itself
+// (stiffness, K/U split, ELL rows of A_UU) is built in components.cu.
 //
 // The solve is one cooperative kernel with bounded grid barriers:
 //   FP32_IR: repeat { r = b - A x in FP64; stop if ||r|| <= tol ||b||;
@@ -29,127 +23,6 @@ constexpr int kSingleThreads = 1024;
 constexpr int kSingleMaxRows = 8192;   // systems up to this size run in one block
 constexpr double kInnerEta = 1e-5;
 constexpr int kInnerCap = 4000;        // FP32 iterations per refinement step
-
-// ---------------------------------------------------------------- assembly
-__global__ void k_assemble(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int V,
-                           int* __restrict__ nbr, float* __restrict__ coef, float* __restrict__ diag) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    int4 tr = tri[t];
-    int a = tr.x, b = tr.y, c = tr.z;
-    int2 pa = vxy[a], pb = vxy[b], pc = vxy[c];
-    // legs (c,a) and (c,b)
-    int d;
-    d = dir_index(pa.x - pc.x, pa.y - pc.y);
-    nbr[d * V + c] = a; atomicAdd(&coef[d * V + c], -0.5f);
-    d = (d + 4) & 7;
-    nbr[d * V + a] = c; atomicAdd(&coef[d * V + a], -0.5f);
-    d = dir_index(pb.x - pc.x, pb.y - pc.y);
-    nbr[d * V + c] = b; atomicAdd(&coef[d * V + c], -0.5f);
-    d = (d + 4) & 7;
-    nbr[d * V + b] = c; atomicAdd(&coef[d * V + b], -0.5f);
-    // hypotenuse (a,b): adjacency only, zero stiffness
-    d = dir_index(pb.x - pa.x, pb.y - pa.y);
-    nbr[d * V + a] = b;
-    nbr[((d + 4) & 7) * V + b] = a;
-    atomicAdd(&diag[c], 1.0f);
-    atomicAdd(&diag[a], 0.5f);
-    atomicAdd(&diag[b], 0.5f);
-}
-
-// Unknown flags (scan input; also the start state of the component search
-// in components.cu: the parent of an unknown vertex is its smallest unknown
-// neighbour through a nonzero entry, or itself, which leaves most small
-// components with shallow trees before any hooking).
-struct UnknownIn {
-    const unsigned char* mask;
-    const int* nbr;
-    const float* coef;
-    int V;
-    int* parent;
-    int* size;
-    int* fill;
-    __device__ __forceinline__ int operator()(long long li) const {
-        int i = (int)li;
-        int pa = i;
-        bool unk = !mask[i];
-        if (unk) {
-#pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                int j = nbr[d * V + i];
-                if (j >= 0 && j < pa && coef[d * V + i] != 0.0f && !mask[j]) pa = j;
-            }
-        }
-        parent[i] = pa;
-        size[i] = 0;
-        fill[i] = 0;
-        return unk ? 1 : 0;
-    }
-};
-
-// index maps from the exclusive count u of unknowns before vertex i: mask
-// vertices are numbered i - u; rows of unknowns are numbered by component
-// (build_components), uidx is -1 at mask vertices
-struct IndexMapsOut {
-    const unsigned char* mask;
-    int* uidx;
-    int* kidx;
-    int* kvert;
-    __device__ __forceinline__ void operator()(long long li, int u, int unk) const {
-        int i = (int)li;
-        if (!unk) {
-            int k = i - u;
-            kidx[i] = k;
-            kvert[k] = i;
-            uidx[i] = -1;
-        } else {
-            kidx[i] = -1;
-        }
-    }
-};
-
-// ELL rows of A_UU; with b and x (optional) also the right-hand side
-// b_r = -sum over mask neighbours of A_ij uv_j and the start x_r = uv_i of a
-// solve on the fresh system (k_rhs_and_start fused)
-__global__ void k_build_ell(int nU, int V, const int* __restrict__ urow_vertex, const int* __restrict__ nbr,
-                            const float* __restrict__ coef, const float* __restrict__ diag,
-                            const int* __restrict__ uidx, int* __restrict__ ucol, float* __restrict__ uval,
-                            float* __restrict__ udiag, int* __restrict__ ucnt, float* __restrict__ udinv,
-                            double* __restrict__ udinv64, const double* __restrict__ uv = nullptr,
-                            double* __restrict__ b = nullptr, double* __restrict__ x = nullptr) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nU) return;
-    int i = urow_vertex[r];
-    int s = 0;
-    double bs = 0.0;
-#pragma unroll
-    for (int d = 0; d < 8; ++d) {
-        int j = nbr[d * V + i];
-        float c = coef[d * V + i];
-        if (j >= 0 && c != 0.0f) {
-            int uj = uidx[j];
-            if (uj >= 0) {
-                ucol[s * nU + r] = uj;
-                uval[s * nU + r] = c;
-                s++;
-            } else if (b) {
-                bs -= (double)c * uv[j];
-            }
-        }
-    }
-    if (b) {
-        b[r] = bs;
-        x[r] = uv[i];
-    }
-    ucnt[r] = s;
-    for (; s < 8; ++s) {
-        ucol[s * nU + r] = r;
-        uval[s * nU + r] = 0.0f;
-    }
-    udiag[r] = diag[i];
-    udinv[r] = 1.0f / diag[i];
-    udinv64[r] = 1.0 / (double)diag[i];
-}
 
 // b_r = -sum over mask neighbours j of A_ij uv_j;  x_r = uv of the row's vertex
 __global__ void k_rhs_and_start(int nU, int V, const int* __restrict__ urow_vertex, const int* __restrict__ nbr,
@@ -178,61 +51,6 @@ __global__ void k_scatter_solution(int nU, const int* __restrict__ urow_vertex, 
     uv[i] = v;
     ff q = ff_from_double(v);
     uvf[i] = make_float2(q.hi, q.lo);
-}
-
-static fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs);
-
-fem_status build_system(fem_mesh* m, cudaStream_t s) { return build_system_rhs(m, s, nullptr); }
-
-// with_rhs (optional): on input asks for b64/x64 of a solve on the current
-// vertex values to be filled by the ELL kernel; on output true when that
-// happened (the system was rebuilt), false when the caller must fill them
-static fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
-    bool want = with_rhs && *with_rhs;
-    if (with_rhs) *with_rhs = false;
-    if (m->sys_version == m->mesh_version) return FEM_OK;
-    int V = m->V, T = m->T;
-    FEM_TRY(ensure(m->nbr, (size_t)8 * V, s));
-    FEM_TRY(ensure(m->coefA, (size_t)8 * V, s));
-    FEM_TRY(ensure(m->diagA, V, s));
-    FEM_TRY(ensure(m->uidx, V, s));
-    FEM_TRY(ensure(m->kidx, V, s));
-    FEM_TRY(ensure(m->urow_vertex, V, s));
-    FEM_TRY(ensure(m->kvert, V, s));
-    FEM_CUDA(cudaMemsetAsync(m->nbr.p, 0xff, sizeof(int) * 8 * V, s));
-    FEM_CUDA(cudaMemsetAsync(m->coefA.p, 0, sizeof(float) * 8 * V, s));
-    FEM_CUDA(cudaMemsetAsync(m->diagA.p, 0, sizeof(float) * V, s));
-    FEM_LAUNCH(F_ASSEMBLY, s, k_assemble, (T + 255) / 256, 256, 0, m->tri.p, m->vxy.p, T, V, m->nbr.p, m->coefA.p,
-               m->diagA.p);
-    FEM_TRY(ensure(m->cc_parent, V, s));
-    FEM_TRY(ensure(m->cc_size, V, s));
-    FEM_TRY(ensure(m->cc_fill, V, s));
-    int* nU_dev = m->dcount.p + 1;
-    FEM_TRY(scan_fused(m, UnknownIn{m->mask.p, m->nbr.p, m->coefA.p, V, m->cc_parent.p, m->cc_size.p, m->cc_fill.p},
-                       IndexMapsOut{m->mask.p, m->uidx.p, m->kidx.p, m->kvert.p}, V, s, nU_dev, F_ASSEMBLY));
-    // the mask count is kept on the host by create / import / refinement, so
-    // the unknown count needs no read-back
-    int nU = V - m->nK;
-    m->nU = nU;
-    FEM_TRY(build_components(m, s));
-    size_t n = nU > 0 ? nU : 1;
-    FEM_TRY(ensure(m->ucol, 8 * n, s));
-    FEM_TRY(ensure(m->uval32, 8 * n, s));
-    FEM_TRY(ensure(m->udiag, n, s));
-    FEM_TRY(ensure(m->ucnt, n, s));
-    FEM_TRY(ensure(m->dinv32, n, s));
-    FEM_TRY(ensure(m->dinv64, n, s));
-    if (want && nU > 0) {
-        FEM_TRY(ensure(m->b64, (size_t)nU, s));
-        FEM_TRY(ensure(m->x64, (size_t)nU, s));
-    }
-    if (nU > 0)
-        FEM_LAUNCH(F_ASSEMBLY, s, k_build_ell, (nU + 255) / 256, 256, 0, nU, V, m->urow_vertex.p, m->nbr.p,
-                   m->coefA.p, m->diagA.p, m->uidx.p, m->ucol.p, m->uval32.p, m->udiag.p, m->ucnt.p, m->dinv32.p,
-                   m->dinv64.p, (const double*)m->uv.p, want ? m->b64.p : nullptr, want ? m->x64.p : nullptr);
-    if (want) *with_rhs = true;
-    m->sys_version = m->mesh_version;
-    return FEM_OK;
 }
 
 // ------------------------------------------------------------ device solve

@@ -640,10 +640,11 @@ __global__ void __launch_bounds__(kCompThreads) k_solve_comp(CompArgs A) {
     __shared__ __align__(16) unsigned char raw[kCompSmemBytes];
     __shared__ CtaRed R;
     __shared__ int s_item, s_last;
-    if (A.cnt[CC_ERR] != 0) {  // the component search failed: report, solve nothing
+    if (A.cnt[CC_ERR] != 0) {  // the system build failed: report its code, solve nothing
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-            A.out[0] = 0; A.out[1] = 0; A.out[2] = FEM_E_INVALID; A.out[3] = 0; A.out[4] = 0; A.out[5] = 0;
-            if (A.acc && A.acc[2] == 0.0) A.acc[2] = FEM_E_INVALID;
+            const int code = A.cnt[CC_ERR];
+            A.out[0] = 0; A.out[1] = 0; A.out[2] = code; A.out[3] = 0; A.out[4] = 0; A.out[5] = 0;
+            if (A.acc && A.acc[2] == 0.0) A.acc[2] = code;
         }
         return;
     }
