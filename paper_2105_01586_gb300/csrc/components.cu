@@ -23,17 +23,19 @@
 // rows of a component by vertex id.
 //
 // The phases, separated by bounded grid barriers (one launch instead of a
-// chain of eight kernels and three memsets):
-//   0. clear the per-vertex stiffness arrays and the component counters;
-//   1. assemble: per triangle, neighbours and stiffness per direction;
-//   2. scan of the unknown flags: mask vertices are numbered by the count of
-//      mask vertices before them; each unknown vertex's union-find parent
-//      starts at its smallest unknown neighbour through a nonzero entry;
-//   3. union-find over the edges (one thread per vertex and direction; the
-//      larger root is hooked under the smaller by atomicCAS; finds halve
-//      paths), so the final root of a component is its smallest vertex;
-//   4. final roots (a read-only walk) and component sizes;
-//   5. scan over the roots: the first row of each component;
+// chain of kernels and memsets):
+//   0. clear the per-vertex stiffness arrays, the union-find forest (every
+//      vertex its own parent) and the counters; count mask vertices per
+//      chunk of vertices;
+//   1. assemble: per triangle, neighbours and stiffness per direction; mask
+//      vertices are numbered by the count of mask vertices before them;
+//   2. union-find over the edges of A_UU (a thread per vertex takes the
+//      edges to its smaller neighbours; the larger root is hooked under the
+//      smaller by atomicCAS; finds halve paths), so the final root of a
+//      component is its smallest vertex;
+//   3. final roots (a read-only walk) and component sizes;
+//   4. sums of the sizes at the roots per chunk of vertices;
+//   5. their scan: the first row of each component;
 //   6. members dropped into their component's range in any order; sizes at
 //      the first rows; components listed by size class;
 //   7. every range sorted by vertex id (a warp with shuffles, a block in
@@ -138,38 +140,45 @@ __device__ __forceinline__ int block_sum_int(int v) {
     return t;
 }
 
-// Exclusive scan over [0, n) inside the cooperative kernel: block b takes a
-// contiguous chunk; phase A evaluates in(i) once (kept in vals[i]) and sums
-// the chunk; after a grid barrier every block adds the sums of the chunks
-// before it and scans its chunk in steps of one element per thread, calling
-// out(i, prefix, value).  A second barrier publishes the outputs.
-template <class In, class Out>
-__device__ bool coop_scan(In in, Out out, int n, int* vals, int* tsum, int* total, unsigned* bar, int* err) {
-    const int nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
-    const int chunk = (n + nb - 1) / nb;
-    const int lo = min(n, b * chunk), hi = min(n, lo + chunk);
+// Exclusive scan over [0, n) inside the cooperative kernel, in two halves
+// that the caller places in consecutive phases (a grid barrier between
+// them): block b owns a contiguous chunk; scan_count sums in(i) over the
+// chunk into tsum[b]; scan_emit adds the sums of the chunks before b and
+// scans the chunk one element per thread per step, calling
+// out(i, prefix, in(i)).  in(i) must give the same value in both halves.
+__device__ __forceinline__ void scan_chunk(int n, int& lo, int& hi) {
+    const int chunk = (n + gridDim.x - 1) / gridDim.x;
+    lo = min(n, (int)blockIdx.x * chunk);
+    hi = min(n, lo + chunk);
+}
+
+template <class In>
+__device__ void scan_count(In in, int n, int* tsum) {
+    int lo, hi;
+    scan_chunk(n, lo, hi);
     int part = 0;
-    for (int i = lo + tid; i < hi; i += kBuildThreads) {
-        int v = in(i);
-        vals[i] = v;
-        part += v;
-    }
+    for (int i = lo + threadIdx.x; i < hi; i += kBuildThreads) part += in(i);
     part = block_sum_int(part);
-    if (tid == 0) tsum[b] = part;
-    if (!grid_barrier(bar, err)) return false;
+    if (threadIdx.x == 0) tsum[blockIdx.x] = part;
+}
+
+template <class In, class Out>
+__device__ void scan_emit(In in, Out out, int n, const int* tsum, int* total) {
+    int lo, hi;
+    scan_chunk(n, lo, hi);
+    const int b = blockIdx.x;
     int pre = 0;
-    for (int j = tid; j < b; j += kBuildThreads) pre += __ldcg(tsum + j);
+    for (int j = threadIdx.x; j < b; j += kBuildThreads) pre += __ldcg(tsum + j);
     pre = block_sum_int(pre);
-    if (total && b == nb - 1 && tid == 0) *total = pre + __ldcg(tsum + b);
+    if (total && b == (int)gridDim.x - 1 && threadIdx.x == 0) *total = pre + __ldcg(tsum + b);
     for (int base = lo; base < hi; base += kBuildThreads) {
-        int i = base + tid;
-        int v[1] = {i < hi ? vals[i] : 0};  // written by this thread in phase A
-        int own = v[0];
-        int seg = block_exclusive_scan<1>(v);
+        const int i = base + threadIdx.x;
+        int v[1] = {i < hi ? in(i) : 0};
+        const int own = v[0];
+        const int seg = block_exclusive_scan<1>(v);
         if (i < hi) out(i, pre + v[0], own);
         pre += seg;
     }
-    return grid_barrier(bar, err);
 }
 
 struct BuildArgs {
@@ -203,30 +212,14 @@ struct BuildArgs {
     const double* uv;  // right-hand side and start (optional: b == nullptr)
     double* b;
     double* x;
-    int* vals;  // V scratch of the scans
-    int* tsum;  // gridDim scratch of the scans
+    int* tsum;  // per-block sums of the scans
     unsigned* bar;
     int* err;
 };
 
 struct UnknownFlagIn {
-    const BuildArgs* A;
-    __device__ __forceinline__ int operator()(int i) const {
-        const BuildArgs& a = *A;
-        int pa = i;
-        bool unk = !a.mask[i];
-        if (unk) {
-#pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                int j = __ldcg(a.nbr + (size_t)d * a.V + i);
-                if (j >= 0 && j < pa && __ldcg(a.coef + (size_t)d * a.V + i) != 0.0f && !a.mask[j]) pa = j;
-            }
-        }
-        a.parent[i] = pa;
-        a.size[i] = 0;
-        a.fill[i] = 0;
-        return unk ? 1 : 0;
-    }
+    const unsigned char* mask;
+    __device__ __forceinline__ int operator()(int i) const { return mask[i] ? 0 : 1; }
 };
 
 struct IndexMapOut {
@@ -267,16 +260,23 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
     const int tid0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
     const int V = A.V, T = A.T;
     const long long V8 = 8LL * V;
-    // 0. clear
+    // 0. clear; union-find forest of singletons; mask counts per chunk
     for (long long i = tid0; i < V8; i += stride) {
         A.nbr[i] = -1;
         A.coef[i] = 0.0f;
     }
-    for (int i = tid0; i < V; i += stride) A.diag[i] = 0.0f;
+    for (int i = tid0; i < V; i += stride) {
+        A.diag[i] = 0.0f;
+        A.parent[i] = i;
+        A.size[i] = 0;
+        A.fill[i] = 0;
+    }
     if (tid0 < CC_COUNTERS) A.cnt[tid0] = 0;
+    scan_count(UnknownFlagIn{A.mask}, V, A.tsum);
     if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
     // 1. assemble: legs (c,a) and (c,b) carry -1/2 each, the hypotenuse is
-    //    adjacency only; K_cc = 1, K_aa = K_bb = 1/2 on the diagonal
+    //    adjacency only; K_cc = 1, K_aa = K_bb = 1/2 on the diagonal.
+    //    Mask vertices are numbered by the count of mask vertices before them.
     for (int t = tid0; t < T; t += stride) {
         int4 tr = A.tri[t];
         int a = tr.x, b = tr.y, c = tr.z;
@@ -300,31 +300,42 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
         atomicAdd(A.diag + a, 0.5f);
         atomicAdd(A.diag + b, 0.5f);
     }
+    scan_emit(UnknownFlagIn{A.mask}, IndexMapOut{&A}, V, A.tsum, A.nU_dev);
     if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
-    // 2. unknown flags -> mask numbering, union-find start
-    if (!coop_scan(UnknownFlagIn{&A}, IndexMapOut{&A}, V, A.vals, A.tsum, A.nU_dev, A.bar, A.err)) {
-        build_fail(A);
-        return;
-    }
     if (A.nU == 0) return;  // uniform: no unknowns, no components
-    // 3. union-find: each edge once, from its larger endpoint
-    for (long long e = tid0; e < V8; e += stride) {
-        int v = (int)(e % V);
-        int j = __ldcg(A.nbr + e);
-        if (j < 0 || j >= v || A.mask[v] || __ldcg(A.coef + e) == 0.0f || A.mask[j]) continue;
-        int a = v, b = j;
-        bool done = false;
-        for (int it = 0; it < kUniteCap && !done; ++it) {
-            a = cc_find(A.parent, a);
-            b = cc_find(A.parent, b);
-            if (a == b) { done = true; break; }
-            if (a < b) { int x = a; a = b; b = x; }
-            done = atomicCAS(A.parent + a, a, b) == a;
+    // 2. union-find over the edges of A_UU, each from its larger endpoint;
+    //    the 8 slots of a vertex are loaded together
+    for (int v = tid0; v < V; v += stride) {
+        if (A.mask[v]) continue;
+        int nb[8];
+        float cf[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            nb[d] = __ldcg(A.nbr + (size_t)d * V + v);
+            cf[d] = __ldcg(A.coef + (size_t)d * V + v);
         }
-        if (!done) atomicCAS(A.cnt + CC_ERR, 0, (int)FEM_E_INVALID);
+        bool on[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) on[d] = nb[d] >= 0 && nb[d] < v && cf[d] != 0.0f;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) on[d] = on[d] && !A.mask[nb[d]];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            if (!on[d]) continue;
+            int a = v, b = nb[d];
+            bool done = false;
+            for (int it = 0; it < kUniteCap && !done; ++it) {
+                a = cc_find(A.parent, a);
+                b = cc_find(A.parent, b);
+                if (a == b) { done = true; break; }
+                if (a < b) { int x = a; a = b; b = x; }
+                done = atomicCAS(A.parent + a, a, b) == a;
+            }
+            if (!done) atomicCAS(A.cnt + CC_ERR, 0, (int)FEM_E_INVALID);
+        }
     }
     if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
-    // 4. final roots (into a separate array: the forest no longer changes)
+    // 3. final roots (into a separate array: the forest no longer changes)
     //    and component sizes
     for (int v = tid0; v < V; v += stride) {
         if (A.mask[v]) continue;
@@ -334,11 +345,11 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
         atomicAdd(A.size + r, 1);
     }
     if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
-    // 5. first row of each component
-    if (!coop_scan(RootSizeIn{&A}, StoreOut{A.cstart}, V, A.vals, A.tsum, A.cnt + CC_NROWS, A.bar, A.err)) {
-        build_fail(A);
-        return;
-    }
+    // 4.-5. first row of each component: scan of the sizes at the roots
+    scan_count(RootSizeIn{&A}, V, A.tsum);
+    if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
+    scan_emit(RootSizeIn{&A}, StoreOut{A.cstart}, V, A.tsum, A.cnt + CC_NROWS);
+    if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
     // 6. members into their ranges; a one-row component needs no sort
     for (int v = tid0; v < V; v += stride) {
         if (A.mask[v]) continue;
@@ -481,7 +492,6 @@ fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
     }();
     // about one vertex per thread, at most the co-resident blocks
     const int grid = std::max(1, std::min(occ * m->num_sms, (V + kBuildThreads - 1) / kBuildThreads));
-    FEM_TRY(ensure(m->scan_vals, (size_t)V + 1, s));
     FEM_TRY(ensure(m->scan_pre, (size_t)grid + 1, s));
     BuildArgs A;
     A.tri = m->tri.p;
@@ -516,7 +526,6 @@ fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
     A.uv = m->uv.p;
     A.b = (want && nU > 0) ? m->b64.p : nullptr;
     A.x = (want && nU > 0) ? m->x64.p : nullptr;
-    A.vals = m->scan_vals.p;
     A.tsum = m->scan_pre.p;
     A.bar = m->bar.p;
     A.err = m->dflag.p + 2;

@@ -80,10 +80,15 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// Bounded grid-wide barrier for cooperatively launched kernels.  bar[0] is
-// the arrival counter, bar[1] the generation.  A block that waits longer
-// than `limit_ns` records FEM_E_TIMEOUT in *err and stops waiting; once *err
-// is set every later barrier returns at once, so the kernel winds down.
+// Bounded grid-wide barrier for cooperatively launched kernels, one atomic
+// per block: block 0 adds 2^31 - (nb - 1) to bar[0], every other block adds
+// 1, so the nb arrivals add exactly 2^31: the top bit of bar[0] flips with
+// the last arrival and no earlier (every partial sum stays below 2^31), and
+// the low 31 bits return to their value before the barrier.  A block waits
+// until the top bit differs from the one its own arrival saw.  A block that
+// waits longer than kBarrierLimitNs records FEM_E_TIMEOUT in *err and stops
+// waiting; once *err is set every later barrier returns at once, so the
+// kernel winds down (the word must then be cleared before the next launch).
 // Returns false when the kernel must stop.
 constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // 2 s
 
@@ -92,17 +97,16 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-        unsigned gen = ld_acquire_u32(bar + 1);
+        const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+        const bool first = blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
+        const unsigned add = first ? 0x80000000u - (nb - 1u) : 1u;
         __threadfence();
-        unsigned arrived = atomicAdd(bar, 1u) + 1u;
-        if (arrived == nb) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        const unsigned old = atomicAdd(bar, add);
+        if (((old + add) ^ old) & 0x80000000u) {
+            // this arrival completed the barrier
         } else {
             unsigned long long t0 = globaltimer_ns();
-            while (ld_acquire_u32(bar + 1) == gen) {
+            while (!((ld_acquire_u32(bar) ^ old) & 0x80000000u)) {
                 if (ld_volatile_i32(err) != 0) { ok = 0; break; }
                 if (globaltimer_ns() - t0 > kBarrierLimitNs) {
                     atomicCAS(err, 0, (int)FEM_E_TIMEOUT);
