@@ -256,6 +256,7 @@ __device__ __forceinline__ void build_fail(const BuildArgs& A) {
 }
 
 __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
+    pdl_wait();
     __shared__ int s_keys[kSortSmem];
     const int tid0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
     const int V = A.V, T = A.T;

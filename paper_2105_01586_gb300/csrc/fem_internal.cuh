@@ -8,6 +8,7 @@
 //                   between rounds as the warm start
 // Per-round scratch is sized by capacity and reused.
 #pragma once
+#include <utility>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -43,13 +44,35 @@ void note_bytes(int family, double bytes);
 void note_launch_end(int family, cudaStream_t s);
 
 // Launch a kernel with accounting; returns FEM_E_CUDA on a launch error.
-#define FEM_LAUNCH(family, stream, kernel, grid, block, smem, ...)                   \
-    do {                                                                             \
-        ::fem::note_launch_begin((family), (stream));                                \
-        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                  \
-        cudaError_t e_ = cudaGetLastError();                                         \
-        ::fem::note_launch_end((family), (stream));                                  \
-        if (e_ != cudaSuccess) return ::fem::cuda_fail(e_, #kernel);                 \
+// Launches use programmatic dependent launch: the kernel may be set up
+// while the previous kernel of the stream is still running, and every
+// kernel of this library starts with pdl_wait(), which returns once the
+// previous grid has completed and its memory is visible.  So the stream
+// order of results is kept; only the launch latency is hidden.
+bool pdl_enabled();
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+#define FEM_LAUNCH(family, stream, kernel, grid, block, smem, ...)                                    \
+    do {                                                                                              \
+        ::fem::note_launch_begin((family), (stream));                                                 \
+        cudaError_t e_ = ::fem::launch_pdl(kernel, dim3(grid), dim3(block), (smem), (stream), __VA_ARGS__); \
+        ::fem::note_launch_end((family), (stream));                                                   \
+        if (e_ != cudaSuccess) return ::fem::cuda_fail(e_, #kernel);                                  \
     } while (0)
 
 // Cooperative launch (all blocks co-resident; used by kernels with grid barriers).
@@ -57,6 +80,10 @@ fem_status launch_coop(int family, const void* func, int grid, int block, size_t
                        void** args, const char* name);
 
 // ------------------------------------------------------------ device utils
+// First statement of every kernel: waits for the grid launched before it in
+// the stream (a no-op for launches without the programmatic attribute).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -259,6 +286,7 @@ struct fem_mesh {
 
     // host staging (pinned)
     void* host_stage = nullptr;
+    void* host_stage_dev = nullptr;  // the same memory as seen by kernels (mapped), or null
 
     fem_stats stats{};
 };
@@ -301,6 +329,8 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
 // fast keys: histogram bins (top 16 bits of a non-negative float) and the
 // counters after the two histograms in fem_mesh::fast_hist
 constexpr int kFastBins = 32768;
+// ints into fem_mesh::host_stage where a refinement round leaves its counters
+constexpr int kRoundStageInts = 1024;
 enum FastCounter { FC_IN = 0, FC_BAND = 1, FC_BAND_ITEMS = 2, FC_BAND_SMALL = 3 };
 fem_status sync_counts(fem_mesh* m, cudaStream_t s);
 fem_status ensure_mesh_capacity(fem_mesh* m, int needV, int needT, cudaStream_t s);

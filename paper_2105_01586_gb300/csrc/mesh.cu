@@ -2,6 +2,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -52,6 +53,15 @@ void note_bytes(int family, double bytes) {
     if (!profiling(family)) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_bytes[family] += bytes;
+}
+
+bool pdl_enabled() {
+    // FEM_PDL=0 turns programmatic dependent launch off (plain stream order)
+    static const bool on = [] {
+        const char* v = getenv("FEM_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
 }
 
 void note_launch_begin(int family, cudaStream_t s) {
@@ -110,6 +120,7 @@ int sm_count() {
 
 // ------------------------------------------------------------------- scans
 __global__ void k_scan_tiles(const int* __restrict__ in, int* __restrict__ out, int n, int* __restrict__ tile_sums) {
+    pdl_wait();
     int v[SCAN_IPT];
     long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
 #pragma unroll
@@ -122,6 +133,7 @@ __global__ void k_scan_tiles(const int* __restrict__ in, int* __restrict__ out, 
 }
 
 __global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ tile_off) {
+    pdl_wait();
     long long base = (long long)blockIdx.x * SCAN_TILE;
     int add = tile_off[blockIdx.x];
     for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_BT)
@@ -129,6 +141,7 @@ __global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__
 }
 
 __global__ void k_scan_total(const int* in, const int* out, int n, int* total) {
+    pdl_wait();
     *total = n > 0 ? out[n - 1] + in[n - 1] : 0;
 }
 
@@ -258,6 +271,7 @@ fem_status sync_counts(fem_mesh* m, cudaStream_t s) {
 // and block 0 must give up after the barrier's time limit and record
 // FEM_E_TIMEOUT instead of hanging.
 __global__ void k_selftest_barrier(unsigned* bar, int* err) {
+    pdl_wait();
     if (blockIdx.x != 0) return;
     grid_barrier(bar, err);
 }
@@ -354,6 +368,11 @@ fem_status fem_mesh_create(int width, int height, void* stream, fem_mesh** out) 
         if (st) break;
         cudaError_t e = cudaMallocHost(&m->host_stage, 1 << 16);
         if (e != cudaSuccess) { st = cuda_fail(e, "cudaMallocHost"); break; }
+        // kernels may write small results straight into the staging area
+        if (cudaHostGetDevicePointer(&m->host_stage_dev, m->host_stage, 0) != cudaSuccess) {
+            m->host_stage_dev = nullptr;
+            cudaGetLastError();
+        }
         e = cudaMemsetAsync(m->bar.p, 0, 64 * sizeof(unsigned), s);
         if (e != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
         int n1 = width - 1;

@@ -126,6 +126,7 @@ struct ItemExpandOut {
 // separate kernels of the plan (used by the allocation-free error pass)
 __global__ void k_item_count(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int N,
                              int* __restrict__ cnt, int item_px) {
+    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     TriGeom g = tri_geom(tri[t], vxy, N);
@@ -136,6 +137,7 @@ __global__ void k_item_count(const int4* __restrict__ tri, const int2* __restric
 
 __global__ void k_item_expand(const int* __restrict__ cnt, const int* __restrict__ off, int T, int cap,
                               int* __restrict__ item_tri, int* __restrict__ err) {
+    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     int o = off[t], n = cnt[t];
@@ -188,6 +190,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
     const int* __restrict__ item_cnt = nullptr, int* __restrict__ item_done = nullptr,
     double* __restrict__ key_out = nullptr, unsigned long long* __restrict__ keyc_out = nullptr,
     const int* __restrict__ item_list = nullptr) {
+    pdl_wait();
     constexpr int NA = NAcc<MODE>::n;
     constexpr bool FF = (MODE == R_ERR || MODE == R_IMG);
     const unsigned FULL = 0xffffffffu;
@@ -356,6 +359,7 @@ __global__ void k_finalize_err(const int* __restrict__ cnt, const int* __restric
                                const float2* __restrict__ partial, int T, const int4* __restrict__ tri,
                                const int2* __restrict__ vxy, double* __restrict__ out,
                                unsigned long long* __restrict__ keyc) {
+    pdl_wait();
     long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long tt = gw; tt < T; tt += nw) {
@@ -379,6 +383,7 @@ __global__ void k_finalize_err(const int* __restrict__ cnt, const int* __restric
 template <int NA>
 __global__ void k_finalize(const int* __restrict__ cnt, const int* __restrict__ off, const double* __restrict__ partial,
                            int T, double* __restrict__ out) {
+    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     int o = off[t], n = cnt[t];
@@ -405,6 +410,7 @@ __global__ void __launch_bounds__(256) k_raster_small(const int* __restrict__ or
                                                       unsigned long long* __restrict__ keyc,
                                                       float* __restrict__ u_out, int* __restrict__ owner_out,
                                                       const int* __restrict__ n_dev = nullptr) {
+    pdl_wait();
     // n_dev: the order list has *n_dev entries (a device-side count, at most T)
     const int Tn = n_dev ? min(*n_dev, T) : T;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Tn; i += gridDim.x * blockDim.x) {
@@ -507,6 +513,7 @@ __global__ void __launch_bounds__(kTileThreads) k_raster_small_err_tiled(
     const int* __restrict__ order, const int4* __restrict__ tri, const int2* __restrict__ vxy,
     const double* __restrict__ uv, const float2* __restrict__ uvf, const float* __restrict__ img, int N, int T,
     double* __restrict__ out, unsigned long long* __restrict__ keyc) {
+    pdl_wait();
     __shared__ float s_img[kTileCap];
     __shared__ int s_red[4][kTileThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, sub = lane & 7;
@@ -642,7 +649,7 @@ fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, const
     note_bytes(F_RASTER, raster_err_bytes(m));
     FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
                m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p,
-               (float*)nullptr, (int*)nullptr, m->item_cnt.p, m->item_done.p, err_out, keyc_out);
+               (float*)nullptr, (int*)nullptr, m->item_cnt.p, m->item_done.p, err_out, keyc_out, nullptr);
     // Few small triangles: eight lanes each over staged tiles, which shortens
     // the longest thread.  Many (above about 1k per SM): one thread each,
     // which avoids the eight-fold plane setup once every SM is full anyway.
@@ -651,7 +658,7 @@ fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, const
                    m->order.p, m->tri.p, m->vxy.p, uv, uvf, f, m->N, m->T, err_out, keyc_out);
     else
         FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv,
-                   uvf, f, m->N, m->T, err_out, keyc_out, (float*)nullptr, (int*)nullptr);
+                   uvf, f, m->N, m->T, err_out, keyc_out, (float*)nullptr, (int*)nullptr, nullptr);
     return FEM_OK;
 }
 
@@ -660,10 +667,10 @@ fem_status raster_image(fem_mesh* m, const double* uv, float* u, int* owner, cud
     note_bytes(F_RASTER, (u ? 4.0 * (double)m->P : 0.0) + (owner ? 4.0 * (double)m->P : 0.0) + 16.0 * m->T +
                              16.0 * m->V);
     FEM_LAUNCH(F_RASTER, s, k_raster<R_IMG>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv,
-               (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, u, owner);
+               (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, u, owner, nullptr, nullptr, nullptr, nullptr, nullptr);
     FEM_LAUNCH(F_RASTER, s, k_raster_small<R_IMG>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv,
                (const float2*)nullptr, (const float*)nullptr, m->N, m->T, (double*)nullptr,
-               (unsigned long long*)nullptr, u, owner);
+               (unsigned long long*)nullptr, u, owner, nullptr);
     return FEM_OK;
 }
 
@@ -677,21 +684,21 @@ fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s) {
     if (mode == R_MASS) {
         FEM_LAUNCH(F_RASTER, s, k_raster<R_MASS>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
                    (const double*)nullptr, (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0,
-                   (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, (float*)nullptr, (int*)nullptr);
+                   (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, (float*)nullptr, (int*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
         FEM_LAUNCH(F_RASTER, s, k_finalize<6>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
                    m->loc.p);
         FEM_LAUNCH(F_RASTER, s, k_raster_small<R_MASS>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p,
                    (const double*)nullptr, (const float2*)nullptr, (const float*)nullptr, m->N, m->T, m->loc.p,
-                   (unsigned long long*)nullptr, (float*)nullptr, (int*)nullptr);
+                   (unsigned long long*)nullptr, (float*)nullptr, (int*)nullptr, nullptr);
     } else {
         FEM_LAUNCH(F_RASTER, s, k_raster<R_SCAT>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
                    (const double*)nullptr, (const float2*)nullptr, r, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P),
-                   m->partial.p, (float*)nullptr, (int*)nullptr);
+                   m->partial.p, (float*)nullptr, (int*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
         FEM_LAUNCH(F_RASTER, s, k_finalize<3>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
                    m->loc.p);
         FEM_LAUNCH(F_RASTER, s, k_raster_small<R_SCAT>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p,
                    (const double*)nullptr, (const float2*)nullptr, r, m->N, m->T, m->loc.p,
-                   (unsigned long long*)nullptr, (float*)nullptr, (int*)nullptr);
+                   (unsigned long long*)nullptr, (float*)nullptr, (int*)nullptr, nullptr);
     }
     return FEM_OK;
 }
@@ -708,12 +715,12 @@ fem_status raster_errors_scratch(const int4* tri, const int2* vxy, int T, int N,
     FEM_LAUNCH(F_RASTER, s, k_item_expand, blocks, 256, 0, w.item_cnt, w.item_off, T, w.item_cap, w.item_tri, err);
     FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, w.grid, kRasterThreads, 0, tri, vxy, uv, (const float2*)nullptr, f, N,
                w.item_tri, w.item_off, n_items_dev, w.item_cap, item_pixels_for((long long)N * N), w.partial, (float*)nullptr,
-               (int*)nullptr);
+               (int*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
     FEM_LAUNCH(F_RASTER, s, k_finalize_err, std::max(1, std::min(w.grid, (T + 7) / 8)), 256, 0, w.item_cnt,
                w.item_off, (const float2*)w.partial, T, tri, vxy, err_out, (unsigned long long*)nullptr);
     FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, std::max(1, std::min(blocks, w.grid / 2)), 256, 0, (const int*)nullptr,
                tri, vxy, uv, (const float2*)nullptr, f, N, T, err_out, (unsigned long long*)nullptr, (float*)nullptr,
-               (int*)nullptr);
+               (int*)nullptr, nullptr);
     return FEM_OK;
 }
 
@@ -861,6 +868,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fast(
     const float2* __restrict__ uvf, const float* __restrict__ img, int N, const int* __restrict__ item_tri,
     const int* __restrict__ item_off, const int* __restrict__ item_cnt, const int* __restrict__ n_items_dev,
     int item_cap, int item_px, float2* __restrict__ partial, int* __restrict__ item_done, FastOut F) {
+    pdl_wait();
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -967,6 +975,7 @@ __global__ void __launch_bounds__(256) k_raster_small_fast(const int* __restrict
                                                            const int2* __restrict__ vxy, const double* __restrict__ uv,
                                                            const float2* __restrict__ uvf,
                                                            const float* __restrict__ img, int N, int T, FastOut F) {
+    pdl_wait();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
         int t = order ? order[i] : i;
         int4 tr = tri[t];
@@ -1032,6 +1041,7 @@ __global__ void __launch_bounds__(kBracketThreads) k_fast_bracket(const unsigned
                                                                    const unsigned* __restrict__ hhi, int T,
                                                                    double frac, long long vcap, int* __restrict__ kdev,
                                                                    double* __restrict__ tau) {
+    pdl_wait();
     __shared__ int s_wl[kBracketThreads / 32], s_wh[kBracketThreads / 32];
     __shared__ int s_blo, s_bhi;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -1103,6 +1113,7 @@ __global__ void k_fast_classify(const int4* __restrict__ tri, const int2* __rest
                                 unsigned long long* __restrict__ keyc, int* __restrict__ band,
                                 int* __restrict__ band_items, int* __restrict__ band_small, int* __restrict__ cnt,
                                 unsigned long long* __restrict__ max_out) {
+    pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;

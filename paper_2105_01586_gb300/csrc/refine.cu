@@ -105,6 +105,7 @@ __device__ __forceinline__ unsigned digit_of(unsigned long long hi, unsigned lo,
 }
 
 __global__ void __launch_bounds__(kTopkThreads) k_topk(TopkArgs A) {
+    pdl_wait();
     __shared__ unsigned s_hist[256];
     __shared__ unsigned long long s_pre_hi;
     __shared__ unsigned s_pre_lo;
@@ -222,6 +223,7 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
                                                                   const int* __restrict__ k_sub = nullptr,
                                                                   const unsigned long long* __restrict__ extra_below =
                                                                       nullptr) {
+    pdl_wait();
     extern __shared__ unsigned char smem_raw[];
     unsigned long long* c_hi = (unsigned long long*)smem_raw;
     unsigned* c_lo = (unsigned*)(c_hi + kTopkCandCap);
@@ -373,6 +375,7 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
 __global__ void k_mark_selected(const double* __restrict__ keys, const int4* __restrict__ tri,
                                 const int2* __restrict__ vxy, int T, int N, const unsigned long long* __restrict__ thr,
                                 const int* __restrict__ kdev, unsigned* __restrict__ bmM, unsigned* __restrict__ bmS) {
+    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T || *kdev == 0) return;
     int4 tr = tri[t];
@@ -394,6 +397,7 @@ __global__ void k_mark_selected(const double* __restrict__ keys, const int4* __r
 __global__ void k_closure(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int N,
                           unsigned* __restrict__ bmM, int* __restrict__ changed, int max_sweeps, unsigned* bar,
                           int* err, int* out_sweeps) {
+    pdl_wait();
     int tid0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
     for (int sw = 0; sw < max_sweeps; ++sw) {
         int any = 0;
@@ -512,8 +516,18 @@ __global__ void k_bisect(int4* __restrict__ tri, const int2* __restrict__ vxy, i
                          const unsigned* __restrict__ bmM, const int* __restrict__ wpre, int V0,
                          const int* __restrict__ flags, const int* __restrict__ fscan,
                          const unsigned char* __restrict__ mask, const float* __restrict__ f, double* __restrict__ uv,
-                         float2* __restrict__ uvf) {
+                         float2* __restrict__ uvf, const int* __restrict__ cnt, const int* __restrict__ scan_err,
+                         const double* __restrict__ margin, int* __restrict__ stage) {
+    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (stage && t == 0) {
+        // the round's counters are final (written by the kernels before
+        // this one): hand them to the host through mapped pinned memory
+#pragma unroll
+        for (int i = 0; i < 8; ++i) stage[i] = cnt[i];
+        stage[9] = *scan_err;
+        *(double*)(stage + 16) = *margin;
+    }
     if (t >= T || !flags[t]) return;
     int4 tr = tri[t];
     int a = tr.x, b = tr.y, c = tr.z;
@@ -693,7 +707,7 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
                    (const unsigned long long*)(m->dscal.p + 18));
     } else if (T <= kTopkBlockMaxT && m->keyc.p && m->keyc.n >= (size_t)T) {
         FEM_LAUNCH(F_TOPK, s, k_topk_block, 1, kTopkBlockThreads, kTopkBlockSmem, m->keyc.p, T, frac, vstar - V,
-                   kdev, thr, margin);
+                   kdev, thr, margin, nullptr, nullptr, nullptr, nullptr, nullptr);
     } else {
         FEM_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned) * (12 * 256 + 1), s));
         FEM_CUDA(cudaMemsetAsync(below, 0, sizeof(unsigned long long), s));
@@ -711,6 +725,7 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
         FEM_TRY(launch_coop(F_REFINE, (const void*)k_closure, grid, 256, 0, s, args, "k_closure"));
     }
     int Wi = (int)W;
+    int* stage_dev = m->host_stage_dev ? (int*)m->host_stage_dev + kRoundStageInts : nullptr;
     FEM_TRY(scan_fused(m, WordIn{bmM, bmM_other, bmS_other},
                        NewVertexOut{bmM, bmS, (int*)m->wpre.p, N, V, m->vxy.p, m->mask.p, nmask_new}, Wi, s, nnew,
                        F_REFINE));
@@ -723,12 +738,16 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
                        OrderExpandOut{m->order.p, m->flags.p, m->fscan.p, m->tri.p, m->vxy.p, T, m->order_tmp.p}, T,
                        s, nullptr, F_REFINE));
     FEM_LAUNCH(F_REFINE, s, k_bisect, tb, 256, 0, m->tri.p, m->vxy.p, T, N, bmM, (const int*)m->wpre.p, V,
-               m->flags.p, m->fscan.p, m->mask.p, f, m->uv.p, m->uvf.p);
-    // read back k, sweeps, new counts, margin, error
-    int* hs = (int*)m->host_stage;
-    FEM_CUDA(cudaMemcpyAsync(hs, m->dcount.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    FEM_CUDA(cudaMemcpyAsync(hs + 9, m->dflag.p + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FEM_CUDA(cudaMemcpyAsync((double*)(hs + 16), margin, sizeof(double), cudaMemcpyDeviceToHost, s));
+               m->flags.p, m->fscan.p, m->mask.p, f, m->uv.p, m->uvf.p, (const int*)m->dcount.p,
+               (const int*)(m->dflag.p + 8), (const double*)margin, m->host_stage_dev ? stage_dev : nullptr);
+    // k, sweeps, new counts, margin, error: written by k_bisect into mapped
+    // pinned memory, else copied
+    int* hs = (int*)m->host_stage + kRoundStageInts;
+    if (!m->host_stage_dev) {
+        FEM_CUDA(cudaMemcpyAsync(hs, m->dcount.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaMemcpyAsync(hs + 9, m->dflag.p + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaMemcpyAsync((double*)(hs + 16), margin, sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
     FEM_CUDA(cudaStreamSynchronize(s));
     int k = hs[2], nn = hs[4], nt = hs[5], nkm = hs[6], e = hs[7] ? hs[7] : hs[9];
     m->bm_clean = true;  // the round ran to the end: the next buffer is clear

@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(SCAN_BT) k_scan_fused(In in, Out out, int n, i
                                                          unsigned long long* __restrict__ ctr,
                                                          unsigned long long base, unsigned epoch,
                                                          int* __restrict__ err) {
+    pdl_wait();
     constexpr int TILE = SCAN_BT * IPT;
     __shared__ int s_tile, s_prefix;
     if (threadIdx.x == 0) s_tile = (int)(atomicAdd(ctr, 1ull) - base);
@@ -168,9 +169,8 @@ fem_status scan_fused_ipt(fem_mesh* m, In in, Out out, int n, cudaStream_t s, in
     ScanPlan sp;
     FEM_TRY(scan_plan(m, n, SCAN_BT * IPT, s, &sp));
     note_launch_begin(family, s);
-    k_scan_fused<In, Out, IPT><<<sp.tiles, SCAN_BT, 0, s>>>(in, out, n, total_dev, sp.status, sp.ctr, sp.base,
-                                                            sp.epoch, sp.err);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_scan_fused<In, Out, IPT>, dim3(sp.tiles), dim3(SCAN_BT), 0, s, in, out, n,
+                               total_dev, sp.status, sp.ctr, sp.base, sp.epoch, sp.err);
     note_launch_end(family, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_scan_fused");
     return FEM_OK;
@@ -179,12 +179,14 @@ fem_status scan_fused_ipt(fem_mesh* m, In in, Out out, int n, cudaStream_t s, in
 // producer and consumer as separate element-parallel kernels (large inputs)
 template <class In>
 __global__ void k_scan_apply_in(In in, int* __restrict__ vals, int n) {
+    pdl_wait();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) vals[i] = in(i);
 }
 
 template <class Out>
 __global__ void k_scan_apply_out(Out out, const int* __restrict__ pre, const int* __restrict__ vals, int n) {
+    pdl_wait();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out(i, pre[i], vals[i]);
 }
@@ -220,14 +222,12 @@ fem_status scan_fused(fem_mesh* m, In in, Out out, int n, cudaStream_t s, int* t
     FEM_TRY(scan_scratch(m, n, s, &vals, &pre));
     int blocks = (n + 255) / 256;
     note_launch_begin(family, s);
-    k_scan_apply_in<In><<<blocks, 256, 0, s>>>(in, vals, n);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_scan_apply_in<In>, dim3(blocks), dim3(256), 0, s, in, vals, n);
     note_launch_end(family, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_scan_apply_in");
     FEM_TRY(scan_fused_ipt<SCAN_IPT>(m, ScanLoad{vals}, ScanStoreTo{pre}, n, s, total_dev, family));
     note_launch_begin(family, s);
-    k_scan_apply_out<Out><<<blocks, 256, 0, s>>>(out, pre, vals, n);
-    e = cudaGetLastError();
+    e = launch_pdl(k_scan_apply_out<Out>, dim3(blocks), dim3(256), 0, s, out, (const int*)pre, (const int*)vals, n);
     note_launch_end(family, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_scan_apply_out");
     return FEM_OK;

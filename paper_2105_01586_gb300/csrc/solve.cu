@@ -28,6 +28,7 @@ constexpr int kInnerCap = 4000;        // FP32 iterations per refinement step
 __global__ void k_rhs_and_start(int nU, int V, const int* __restrict__ urow_vertex, const int* __restrict__ nbr,
                                 const float* __restrict__ coef, const unsigned char* __restrict__ mask,
                                 const double* __restrict__ uv, double* __restrict__ b, double* __restrict__ x) {
+    pdl_wait();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nU) return;
     int i = urow_vertex[r];
@@ -44,6 +45,7 @@ __global__ void k_rhs_and_start(int nU, int V, const int* __restrict__ urow_vert
 
 __global__ void k_scatter_solution(int nU, const int* __restrict__ urow_vertex, const double* __restrict__ x,
                                    double* __restrict__ uv, float2* __restrict__ uvf) {
+    pdl_wait();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nU) return;
     int i = urow_vertex[r];
@@ -439,12 +441,14 @@ fail:
 
 template <bool FP64_ONLY>
 __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs A) {
+    pdl_wait();
     if (gate_closed(A)) return;
     solve_body<FP64_ONLY, GridSync>(A);
 }
 
 template <bool FP64_ONLY>
 __global__ void __launch_bounds__(kSingleThreads) k_solve_single(SolveArgs A) {
+    pdl_wait();
     if (gate_closed(A)) return;
     solve_body<FP64_ONLY, BlockSync>(A);
 }
@@ -654,6 +658,7 @@ __device__ __forceinline__ void block_solve_core(const SolveArgs& A, const Block
 }
 
 __global__ void __launch_bounds__(kSingleThreads) k_solve_block(SolveArgs A, BlockScratch G, int smem_bytes) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char sm_raw[];
     __shared__ BlockRed R;
     __shared__ float s_lut[17];
@@ -733,6 +738,7 @@ __device__ __forceinline__ bool grid_sum3(const SolveArgs& A, BlockRed& R, GridP
 }
 
 __global__ void __launch_bounds__(kGridThreads) k_solve_grid(SolveArgs A, BlockScratch G) {
+    pdl_wait();
     __shared__ BlockRed R;
     if (gate_closed(A)) return;
     GridPar P{0, 0};
@@ -1076,12 +1082,14 @@ fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cuda
 // ------------------------------------------------------- vertex data setup
 __global__ void k_uv_from_g(const unsigned char* __restrict__ mask, const int* __restrict__ kidx, int V,
                             const float* __restrict__ g, double* __restrict__ uv) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < V && mask[i]) uv[i] = (double)g[kidx[i]];
 }
 
 __global__ void k_uv_from_f(const unsigned char* __restrict__ mask, const int2* __restrict__ vxy, int V, int N,
                             const float* __restrict__ f, double* __restrict__ uv, float2* __restrict__ uvf) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < V && mask[i]) {
         int2 p = vxy[i];
@@ -1093,6 +1101,7 @@ __global__ void k_uv_from_f(const unsigned char* __restrict__ mask, const int2* 
 
 __global__ void k_gather_mask(const int* __restrict__ kvert, const int2* __restrict__ vxy, int nK, int N,
                               const float* __restrict__ f, float* __restrict__ g) {
+    pdl_wait();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nK) return;
     int2 p = vxy[kvert[k]];

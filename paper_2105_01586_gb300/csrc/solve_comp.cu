@@ -637,6 +637,7 @@ __device__ void cta_comp(const CompArgs& A, int s0, int m, unsigned char* raw, C
 // ------------------------------------------------------------- kernel
 template <bool FP64>
 __global__ void __launch_bounds__(kCompThreads) k_solve_comp(CompArgs A) {
+    pdl_wait();
     __shared__ __align__(16) unsigned char raw[kCompSmemBytes];
     __shared__ CtaRed R;
     __shared__ int s_item, s_last;

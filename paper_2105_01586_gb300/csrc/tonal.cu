@@ -42,6 +42,7 @@ __device__ __forceinline__ int octant(int dx, int dy) {
 
 __global__ void k_incidence(const int4* __restrict__ tri, const int2* __restrict__ vxy, int T, int V,
                             int* __restrict__ inc) {
+    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     int4 tr = tri[t];
@@ -66,6 +67,7 @@ __device__ __forceinline__ int mass_off_slot(int r, int s) {
 __global__ void k_gather_mass(int V, const int* __restrict__ inc, const int4* __restrict__ tri,
                               const int2* __restrict__ vxy, const double* __restrict__ loc6,
                               double* __restrict__ Mdiag, double* __restrict__ Moff) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= V) return;
     double dsum = 0.0, off[8];
@@ -95,6 +97,7 @@ __global__ void k_gather_mass(int V, const int* __restrict__ inc, const int4* __
 // s_i = sum over the triangles around i of their local scatter sums
 __global__ void k_gather_scatter(int V, const int* __restrict__ inc, const double* __restrict__ loc3,
                                  double* __restrict__ s) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= V) return;
     double acc = 0.0;
@@ -110,6 +113,7 @@ __global__ void k_fwd_rhs(int nU, int V, const int* __restrict__ urow_vertex, co
                           const float* __restrict__ coef, const unsigned char* __restrict__ mask,
                           const int* __restrict__ kidx, const double* __restrict__ p, double* __restrict__ b,
                           double* __restrict__ x) {
+    pdl_wait();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nU) return;
     int i = urow_vertex[r];
@@ -128,6 +132,7 @@ __global__ void k_fwd_rhs(int nU, int V, const int* __restrict__ urow_vertex, co
 __global__ void k_assemble_v(int V, const unsigned char* __restrict__ mask, const int* __restrict__ kidx,
                              const int* __restrict__ uidx, const double* __restrict__ p, const double* __restrict__ x,
                              double* __restrict__ v) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= V) return;
     v[i] = mask[i] ? p[kidx[i]] : x[uidx[i]];
@@ -137,6 +142,7 @@ __global__ void k_assemble_v(int V, const unsigned char* __restrict__ mask, cons
 __global__ void k_mass_spmv(int V, const double* __restrict__ Mdiag, const double* __restrict__ Moff,
                             const int* __restrict__ nbr, const double* __restrict__ v, double* __restrict__ y,
                             double* __restrict__ partial) {
+    pdl_wait();
     double dot = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
         double vi = v[i];
@@ -162,6 +168,7 @@ __global__ void k_mass_spmv(int V, const double* __restrict__ Mdiag, const doubl
 
 __global__ void k_gather_U(int nU, const int* __restrict__ urow_vertex, const double* __restrict__ y,
                            double* __restrict__ b, double* __restrict__ x) {
+    pdl_wait();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nU) return;
     b[r] = y[urow_vertex[r]];
@@ -172,6 +179,7 @@ __global__ void k_gather_U(int nU, const int* __restrict__ urow_vertex, const do
 __global__ void k_adj_combine(int nK, int V, const int* __restrict__ kvert, const int* __restrict__ nbr,
                               const float* __restrict__ coef, const int* __restrict__ uidx,
                               const double* __restrict__ y, const double* __restrict__ z, double* __restrict__ w) {
+    pdl_wait();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nK) return;
     int i = kvert[k];
@@ -196,6 +204,7 @@ struct CgScalars {
 };
 
 __global__ void k_final_sum(int n, const double* __restrict__ partial, double* __restrict__ out) {
+    pdl_wait();
     __shared__ double sh[kVecThreads / 32];
     double t = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) t += partial[i];
@@ -213,6 +222,7 @@ __global__ void k_final_sum(int n, const double* __restrict__ partial, double* _
 // partials, one more iteration, stop when sqrt(gamma) <= thr; a breakdown
 // (pNp <= 0) stops without an update
 __global__ void k_cg_update_sum(int nb, const double* __restrict__ partial, CgScalars* __restrict__ cg) {
+    pdl_wait();
     __shared__ double sh[kVecThreads / 32];
     if (cg->stop != 0.0) return;
     if (!(cg->pNp > 0.0)) {
@@ -243,6 +253,7 @@ __global__ void k_cg_update_sum(int nb, const double* __restrict__ partial, CgSc
 __global__ void k_vec(int mode, int n, double a, double* __restrict__ x, double* __restrict__ y,
                       double* __restrict__ z, const double* __restrict__ w, double* __restrict__ partial,
                       const CgScalars* __restrict__ cg = nullptr) {
+    pdl_wait();
     if (cg) {
         if (cg->stop != 0.0) return;
         if (mode == 1) {
@@ -283,11 +294,13 @@ __global__ void k_vec(int mode, int n, double a, double* __restrict__ x, double*
 }
 
 __global__ void k_f2d(int n, const float* __restrict__ a, double* __restrict__ b) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (double)a[i];
 }
 
 __global__ void k_d2f(int n, const double* __restrict__ a, float* __restrict__ b) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
 }
@@ -377,7 +390,7 @@ static fem_status apply_N(fem_mesh* m, const double* p, double* w, double* pNp_d
 static fem_status vec_op(fem_mesh* m, int mode, int n, double a, double* x, double* y, double* z, const double* w,
                          double* out_dev, cudaStream_t s) {
     int G = vec_grid(m);
-    FEM_LAUNCH(F_TONAL, s, k_vec, G, kVecThreads, 0, mode, n, a, x, y, z, w, m->red.p);
+    FEM_LAUNCH(F_TONAL, s, k_vec, G, kVecThreads, 0, mode, n, a, x, y, z, w, m->red.p, nullptr);
     if (mode != 2) FEM_LAUNCH(F_TONAL, s, k_final_sum, 1, kVecThreads, 0, G, m->red.p, out_dev);
     return FEM_OK;
 }
