@@ -301,7 +301,7 @@ constexpr int kBlockComp = 1024;
 enum CcCounter { CC_NWARP = 0, CC_NROWS = 1, CC_NBLK = 2, CC_NBIG = 3, CC_ERR = 4, CC_WORK = 5, CC_DONE = 6,
                  CC_COUNTERS = 16 };
 fem_status solve_components(fem_mesh* m, const double* b, double* x, bool use_fp64, double tol, int maxit,
-                            bool deferred, cudaStream_t s);
+                            bool deferred, bool scatter, int* clear_word, cudaStream_t s);
 
 // helpers implemented in the .cu files
 fem_status exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, int* total_dev);
@@ -311,8 +311,9 @@ fem_status build_system(fem_mesh* m, cudaStream_t s);
 fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs);
 fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cudaStream_t s,
                          int* iters_out, double* relres_out, bool deferred = false);
+// scatter: the solution also goes to m->uv / m->uvf at the rows' vertices
 fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, double tol, int maxit, cudaStream_t s,
-                     int* iters_out, double* relres_out, bool deferred = false);
+                     int* iters_out, double* relres_out, bool deferred = false, bool scatter = false);
 fem_status solve_totals_reset(fem_mesh* m, cudaStream_t s);
 fem_status solve_totals_read(fem_mesh* m, cudaStream_t s);
 fem_status set_uv_from_g(fem_mesh* m, const float* g_dev, cudaStream_t s);

@@ -82,10 +82,34 @@ void note_launch_end(int family, cudaStream_t s) {
     t_begin_ev = nullptr;
 }
 
+// Cooperative launches also take the programmatic-launch attribute (the
+// kernels start with pdl_wait); if the runtime refuses the combination, the
+// attribute is dropped for the rest of the process.
+static std::atomic<bool> g_coop_pdl_ok{true};
+
 fem_status launch_coop(int family, const void* func, int grid, int block, size_t smem, cudaStream_t s,
                        void** args, const char* name) {
     note_launch_begin(family, s);
-    cudaError_t e = cudaLaunchCooperativeKernel(func, dim3(grid), dim3(block), args, smem, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    const bool pdl = pdl_enabled() && g_coop_pdl_ok.load(std::memory_order_relaxed);
+    cfg.numAttrs = pdl ? 2 : 1;
+    cudaError_t e = cudaLaunchKernelExC(&cfg, func, args);
+    if (e != cudaSuccess && pdl && (e == cudaErrorInvalidValue || e == cudaErrorNotSupported)) {
+        cudaGetLastError();
+        g_coop_pdl_ok.store(false);
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelExC(&cfg, func, args);
+    }
     note_launch_end(family, s);
     if (e != cudaSuccess) return cuda_fail(e, name);
     return FEM_OK;

@@ -43,12 +43,15 @@ __global__ void k_rhs_and_start(int nU, int V, const int* __restrict__ urow_vert
     x[r] = uv[i];
 }
 
-__global__ void k_scatter_solution(int nU, const int* __restrict__ urow_vertex, const double* __restrict__ x,
-                                   double* __restrict__ uv, float2* __restrict__ uvf) {
+// x -> vertex values; nothing when the system build failed (gate: the
+// component counters), since the row order is then incomplete
+__global__ void k_scatter_solution(int nU, int V, const int* __restrict__ urow_vertex, const double* __restrict__ x,
+                                   double* __restrict__ uv, float2* __restrict__ uvf, const int* __restrict__ gate) {
     pdl_wait();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nU) return;
+    if (r >= nU || gate[CC_ERR] != 0) return;
     int i = urow_vertex[r];
+    if (i < 0 || i >= V) return;
     double v = x[r];
     uv[i] = v;
     ff q = ff_from_double(v);
@@ -85,6 +88,11 @@ struct SolveArgs {
     double bytes_it;   // algorithmic bytes per CG iteration (for acc)
     double bytes_res;  // algorithmic bytes per residual pass (for acc)
     const int* gate;   // optional: the component counters (CC_*); see gate_closed
+    // optional: the solution also goes to the vertex values (uv, float-float
+    // uvf) of the row's vertex scat_row[r]
+    const int* scat_row;
+    double* scat_uv;
+    float2* scat_uvf;
 };
 
 // whole-system kernels launched behind the component solve return at once
@@ -688,6 +696,16 @@ __global__ void __launch_bounds__(kSingleThreads) k_solve_block(SolveArgs A, Blo
         block_solve_core<true>(A, G, sm_raw, nnz, bm, R, s_lut, s_wsum);
     else
         block_solve_core<false>(A, G, sm_raw, nnz, bm, R, s_lut, s_wsum);
+    if (A.scat_uv) {
+        __syncthreads();
+        for (int i = tid; i < n; i += kSingleThreads) {
+            const double v = A.x[i];
+            const int vi = A.scat_row[i];
+            A.scat_uv[vi] = v;
+            const ff q = ff_from_double(v);
+            A.scat_uvf[vi] = make_float2(q.hi, q.lo);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -906,7 +924,7 @@ static int coop_blocks(const void* func, int n, int num_sms) {
 
 // Solve A_UU x = b (device vectors of length nU; x holds the start).
 fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, double tol, int maxit, cudaStream_t s,
-                     int* iters_out, double* relres_out, bool deferred) {
+                     int* iters_out, double* relres_out, bool deferred, bool scatter) {
     FEM_TRY(build_system(m, s));
     int nU = m->nU;
     if (iters_out) *iters_out = 0;
@@ -955,11 +973,14 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
     A.bytes_it = (double)nU * (use_fp64 ? 168.0 : 120.0);
     A.bytes_res = (double)nU * (92.0 + (use_fp64 ? 0.0 : 36.0));
     A.acc = deferred ? m->dscal.p + 64 : nullptr;
-    FEM_CUDA(cudaMemsetAsync(m->dflag.p + 1, 0, sizeof(int), s));
+    A.scat_row = scatter ? m->urow_vertex.p : nullptr;
+    A.scat_uv = scatter ? m->uv.p : nullptr;
+    A.scat_uvf = scatter ? m->uvf.p : nullptr;
     // Components of at most kBlockComp rows are solved independently, all at
     // once; when a component is larger, that kernel returns at once and the
     // whole-system solver below (gated on the same device counter) runs.
-    FEM_TRY(solve_components(m, b, x, use_fp64, tol, maxit, deferred, s));
+    // The component kernel also clears the error word of that solver.
+    FEM_TRY(solve_components(m, b, x, use_fp64, tol, maxit, deferred, scatter, m->dflag.p + 1, s));
     A.gate = m->ccount.p;
     if (!use_fp64 && nU <= kBlockMaxRows) {
         static const bool attr_set = [] {
@@ -992,6 +1013,12 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
     } else {
         void* args[] = {&A};
         FEM_TRY(launch_coop(F_CG, func, grid, kSolveThreads, 0, s, args, "k_solve<fp64>"));
+    }
+    if (scatter && !(!use_fp64 && nU <= kBlockMaxRows)) {
+        // these whole-system solvers leave the scatter to a kernel of its own
+        // (it repeats what the component solver wrote when that one solved)
+        FEM_LAUNCH(F_CG, s, k_scatter_solution, (nU + 255) / 256, 256, 0, nU, m->V, (const int*)m->urow_vertex.p,
+                   (const double*)x, m->uv.p, m->uvf.p, (const int*)m->ccount.p);
     }
     if (deferred) {
         if (profiling(F_CG)) note_bytes(F_CG, 0.0);  // bytes are added from the device totals at the end
@@ -1073,10 +1100,8 @@ fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cuda
     if (!rhs_done)
         FEM_LAUNCH(F_CG, s, k_rhs_and_start, b, 256, 0, nU, m->V, m->urow_vertex.p, m->nbr.p, m->coefA.p, m->mask.p,
                    m->uv.p, m->b64.p, m->x64.p);
-    fem_status st = run_solve(m, m->b64.p, m->x64.p, use_fp64, tol, maxit, s, iters_out, relres_out, deferred);
-    if (st != FEM_OK && st != FEM_E_NOT_CONVERGED) return st;
-    FEM_LAUNCH(F_CG, s, k_scatter_solution, b, 256, 0, nU, m->urow_vertex.p, m->x64.p, m->uv.p, m->uvf.p);
-    return st;
+    // the solvers write the solution back to the vertex values themselves
+    return run_solve(m, m->b64.p, m->x64.p, use_fp64, tol, maxit, s, iters_out, relres_out, deferred, true);
 }
 
 // ------------------------------------------------------- vertex data setup

@@ -61,7 +61,23 @@ struct CompArgs {
     double* out;  // [0] iterations (critical path), [1] relres, [2] status, [3] residual passes, [4] row-iterations, [5] row-residual passes
     double* acc;  // optional running totals (as solve_accumulate)
     double bytes_row_it, bytes_row_res;
+    // optional: the solution also goes to the vertex values (uv, float-float
+    // uvf) of the row's vertex scat_row[r]
+    const int* scat_row;
+    double* scat_uv;
+    float2* scat_uvf;
+    int* clear_word;  // optional: set to 0 at the start (the next solver's error word)
 };
+
+__device__ __forceinline__ void comp_store(const CompArgs& A, int row, double v) {
+    A.x[row] = v;
+    if (A.scat_uv) {
+        const int vi = A.scat_row[row];
+        A.scat_uv[vi] = v;
+        const ff q = ff_from_double(v);
+        A.scat_uvf[vi] = make_float2(q.hi, q.lo);
+    }
+}
 
 // exact power-of-two scale that brings max |b| to [1, 2), kept in the normal range
 __device__ __forceinline__ int comp_scale_exp(float bm) {
@@ -131,7 +147,7 @@ __device__ void warp_comp(const CompArgs& A, int s0, int m, CompStats* S) {
     }
     float bm = warp_max(fabsf((float)b));
     if (bm == 0.f) {
-        if (act) A.x[row] = 0.0;
+        if (act) comp_store(A, row, 0.0);
         if (lane == 0) comp_record(S, m, 0, 0, FEM_OK, 0.0, 0.0);
         return;
     }
@@ -193,7 +209,7 @@ __device__ void warp_comp(const CompArgs& A, int s0, int m, CompStats* S) {
             xf = ff_add_f(xf, d);
             if (it == 0) break;  // breakdown: no progress possible
         }
-        if (act) A.x[row] = ff_to_double(xf) * inv;
+        if (act) comp_store(A, row, ff_to_double(xf) * inv);
         if (lane == 0) comp_record(S, m, total_it, nres, status, (double)rr * inv * inv, (double)bb * inv * inv);
     } else {
         const double tol2 = A.tol * A.tol;
@@ -234,7 +250,7 @@ __device__ void warp_comp(const CompArgs& A, int s0, int m, CompStats* S) {
             total_it += it;
             if (it == 0) break;
         }
-        if (act) A.x[row] = x;
+        if (act) comp_store(A, row, x);
         if (lane == 0) comp_record(S, m, total_it, nres, status, rr, bb);
     }
 }
@@ -364,7 +380,7 @@ __device__ void cta_comp(const CompArgs& A, int s0, int m, unsigned char* raw, C
     }
     float bm = cta_max(R, par, bmt);  // its barrier also publishes ent and dg_s
     if (bm == 0.f) {
-        for (int i = tid; i < m; i += kCompThreads) A.x[s0 + i] = 0.0;
+        for (int i = tid; i < m; i += kCompThreads) comp_store(A, s0 + i, 0.0);
         if (tid == 0) comp_record(S, m, 0, 0, FEM_OK, 0.0, 0.0);
         return;
     }
@@ -522,7 +538,7 @@ __device__ void cta_comp(const CompArgs& A, int s0, int m, unsigned char* raw, C
         }
         for (int i = tid; i < m; i += kCompThreads) {
             float2 xv = x_s[i];
-            A.x[s0 + i] = ff_to_double(ff{xv.x, xv.y}) * inv;
+            comp_store(A, s0 + i, ff_to_double(ff{xv.x, xv.y}) * inv);
         }
         if (tid == 0) comp_record(S, m, total_it, nres, status, (double)rr * inv * inv, (double)bb * inv * inv);
     } else {
@@ -629,6 +645,8 @@ __device__ void cta_comp(const CompArgs& A, int s0, int m, unsigned char* raw, C
             __syncthreads();
             if (it == 0 && !conv) break;
         }
+        if (A.scat_uv)  // the last pass stored x (read back after its barrier)
+            for (int i = tid; i < m; i += kCompThreads) comp_store(A, s0 + i, A.x[s0 + i]);
         if (tid == 0) comp_record(S, m, total_it, nres, status, rr, bb);
     }
     __syncthreads();
@@ -641,6 +659,7 @@ __global__ void __launch_bounds__(kCompThreads) k_solve_comp(CompArgs A) {
     __shared__ __align__(16) unsigned char raw[kCompSmemBytes];
     __shared__ CtaRed R;
     __shared__ int s_item, s_last;
+    if (A.clear_word && blockIdx.x == 0 && threadIdx.x == 0) *A.clear_word = 0;
     if (A.cnt[CC_ERR] != 0) {  // the system build failed: report its code, solve nothing
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             const int code = A.cnt[CC_ERR];
@@ -676,7 +695,7 @@ __global__ void __launch_bounds__(kCompThreads) k_solve_comp(CompArgs A) {
         double a = (double)A.diag[p], b = A.b[p];
         double x = b / a;
         double r = b - a * x;
-        A.x[p] = x;
+        comp_store(A, p, x);
         comp_record(&S, 1, 0, 1, FEM_OK, r * r, b * b);
     }
     // block totals into the global totals; the last block to finish writes
@@ -702,6 +721,9 @@ __global__ void __launch_bounds__(kCompThreads) k_solve_comp(CompArgs A) {
     double tit = (double)__ldcg(G + 4), tres = (double)__ldcg(G + 5);
 #pragma unroll
     for (int q = 0; q < 6; ++q) G[q] = 0ull;
+    // work counters back to zero for the next launch (every block is done)
+    A.work[CC_WORK] = 0;
+    A.work[CC_DONE] = 0;
     A.out[0] = mit;
     A.out[1] = rel;  // largest ||r_c|| / ||b_c|| over the components (bounds the global one)
     A.out[2] = wst;
@@ -719,7 +741,7 @@ __global__ void __launch_bounds__(kCompThreads) k_solve_comp(CompArgs A) {
 
 // Launch the component solve (results in x, statistics in dscal / its totals).
 fem_status solve_components(fem_mesh* m, const double* b, double* x, bool use_fp64, double tol, int maxit,
-                            bool deferred, cudaStream_t s) {
+                            bool deferred, bool scatter, int* clear_word, cudaStream_t s) {
     int nU = m->nU;
     if (!m->comp_stats.p) {  // zero once; each launch's last block clears it again
         FEM_TRY(ensure(m->comp_stats, 8, s));
@@ -747,7 +769,12 @@ fem_status solve_components(fem_mesh* m, const double* b, double* x, bool use_fp
     // plus 36 B of conversions per FP32 refinement step)
     A.bytes_row_it = use_fp64 ? 168.0 : 120.0;
     A.bytes_row_res = use_fp64 ? 92.0 : 128.0;
-    FEM_CUDA(cudaMemsetAsync(m->ccount.p + CC_WORK, 0, 2 * sizeof(int), s));
+    A.scat_row = scatter ? m->urow_vertex.p : nullptr;
+    A.scat_uv = scatter ? m->uv.p : nullptr;
+    A.scat_uvf = scatter ? m->uvf.p : nullptr;
+    A.clear_word = clear_word;
+    // CC_WORK / CC_DONE are zero here: cleared by the system build, and
+    // again by the last block of every launch
     // about one component of 2..32 rows per warp (at most half the rows),
     // at most a few blocks per SM
     int grid = std::max(1, std::min(m->num_sms * 4, (nU / 2 + 7) / 8));
