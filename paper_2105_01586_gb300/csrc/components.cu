@@ -530,7 +530,8 @@ fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
     A.tsum = m->scan_pre.p;
     A.bar = m->bar.p;
     A.err = m->dflag.p + 2;
-    FEM_CUDA(cudaMemsetAsync(m->dflag.p + 2, 0, sizeof(int), s));
+    // *A.err is zero: cleared at creation, left at zero by every completed
+    // launch, and cleared again after a failed one (reset_coop_state)
     void* args[] = {&A};
     FEM_TRY(launch_coop(F_ASSEMBLY, (const void*)k_build_system, grid, kBuildThreads, 0, s, args, "k_build_system"));
     if (want && nU > 0) *with_rhs = true;

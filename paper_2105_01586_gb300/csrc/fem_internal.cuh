@@ -287,6 +287,7 @@ struct fem_mesh {
     // host staging (pinned)
     void* host_stage = nullptr;
     void* host_stage_dev = nullptr;  // the same memory as seen by kernels (mapped), or null
+    bool round_ctr_clear = true;     // dcount[6..63] known to be zero (refinement rounds)
 
     fem_stats stats{};
 };
@@ -335,6 +336,7 @@ constexpr int kRoundStageInts = 1024;
 enum FastCounter { FC_IN = 0, FC_BAND = 1, FC_BAND_ITEMS = 2, FC_BAND_SMALL = 3 };
 fem_status sync_counts(fem_mesh* m, cudaStream_t s);
 fem_status ensure_mesh_capacity(fem_mesh* m, int needV, int needT, cudaStream_t s);
+void reset_coop_state(fem_mesh* m, cudaStream_t s);
 int sm_count();
 
 // caller-provided scratch for the allocation-free error pass

@@ -115,6 +115,13 @@ fem_status launch_coop(int family, const void* func, int grid, int block, size_t
     return FEM_OK;
 }
 
+// After a failed cooperative kernel: barrier words and the system build's
+// error word back to zero (a completed kernel leaves both at zero).
+void reset_coop_state(fem_mesh* m, cudaStream_t s) {
+    cudaMemsetAsync(m->bar.p, 0, 2 * sizeof(unsigned), s);
+    cudaMemsetAsync(m->dflag.p + 2, 0, sizeof(int), s);
+}
+
 // ------------------------------------------------------------------ memory
 fem_status dalloc_raw(void** p, size_t bytes, cudaStream_t s) {
     if (bytes == 0) bytes = 16;
@@ -398,6 +405,8 @@ fem_status fem_mesh_create(int width, int height, void* stream, fem_mesh** out) 
             cudaGetLastError();
         }
         e = cudaMemsetAsync(m->bar.p, 0, 64 * sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->dflag.p, 0, 64 * sizeof(int), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->dcount.p, 0, 64 * sizeof(int), s);
         if (e != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
         int n1 = width - 1;
         int2 xy[4] = {{0, 0}, {n1, 0}, {0, n1}, {n1, n1}};

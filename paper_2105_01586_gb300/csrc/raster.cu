@@ -622,8 +622,8 @@ fem_status raster_plan(fem_mesh* m, cudaStream_t s) {
     FEM_TRY(ensure(m->item_tri, cap, s));
     FEM_TRY(ensure(m->partial, cap * 6, s));
     int* n_items_dev = m->dcount.p + 0;
+    // overflow flag: sticky until a host check reads it (and clears it)
     int* err = m->dflag.p + 0;
-    FEM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     FEM_TRY(scan_fused(m, ItemCountIn{m->tri.p, m->vxy.p, m->N, item_pixels_for(m->P), m->item_cnt.p},
                        ItemExpandOut{m->item_off.p, m->item_tri.p, (int)m->item_tri.n, err}, T, s, n_items_dev,
                        F_RASTER));
@@ -742,6 +742,8 @@ fem_status fem_triangle_errors(fem_mesh* m, const double* uv_dev, const float* f
     FEM_CUDA(cudaMemcpyAsync(&e, m->dflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));
     if (e) {
+        cudaMemsetAsync(m->dflag.p, 0, sizeof(int), s);
+        m->plan_version = -1;
         set_error("fem_triangle_errors: rasterisation plan overflow");
         return (fem_status)e;
     }
@@ -1241,6 +1243,8 @@ extern "C" fem_status fem_triangle_error_bounds(fem_mesh* m, const double* uv_de
     FEM_CUDA(cudaMemcpyAsync(&e, m->dflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));
     if (e) {
+        cudaMemsetAsync(m->dflag.p, 0, sizeof(int), s);
+        m->plan_version = -1;
         set_error("fem_triangle_error_bounds: rasterisation plan overflow");
         return (fem_status)e;
     }

@@ -192,20 +192,99 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(TopkArgs A) {
 }
 
 // Top-k for up to kTopkBlockMaxT triangles in one 1024-thread block (no
-// device-wide barrier).  keyc holds the composite keys (0 = ineligible);
-// the 96-bit order key is (keyc, ~id).  Radix select, 8 bits per digit,
-// reading the global array until the current bucket fits in shared memory,
-// then on the shared-memory candidate list.
+// device-wide barrier).  keyc holds the composite keys (0 = ineligible;
+// else bit 63 set and the error's FP64 bits below it); the 96-bit order key
+// is (keyc, ~id).  Radix select from the top, reading the global array until
+// the current bucket fits in shared memory, then on the shared-memory
+// candidate list; once the bucket holds at most kTopkRankCap keys, the
+// threshold is found by counting.  The first digit is 12 bits wide (the
+// flag and the 11 exponent bits), so one pass over the keys already splits
+// them by binary order of magnitude; the other digits are 8 bits, the last 4.
 constexpr int kTopkBlockThreads = 1024;
 constexpr int kTopkCandCap = 12288;
 constexpr int kTopkBlockMaxT = 1 << 20;
+constexpr int kTopkBins0 = 4096;
+constexpr int kTopkDigits = 12;
+constexpr int kTopkRankCap = 1024;  // buckets up to this size are finished by counting
 constexpr size_t kTopkBlockSmem = (size_t)kTopkCandCap * (sizeof(unsigned long long) + sizeof(unsigned));
 
-__device__ __forceinline__ bool prefix_match(unsigned long long hi, unsigned lo, unsigned long long pre_hi,
-                                             unsigned pre_lo, int d) {
-    unsigned long long mhi = d >= 8 ? ~0ull : (d == 0 ? 0ull : (~0ull << (64 - 8 * d)));
-    unsigned mlo = d <= 8 ? 0u : (~0u << (32 - 8 * (d - 8)));
-    return (hi & mhi) == pre_hi && (lo & mlo) == pre_lo;
+// digit d covers key bits [tk_low(d), tk_low(d) + tk_width(d)) (bit 0 = bit 0 of lo)
+__device__ __forceinline__ int tk_width(int d) { return d == 0 ? 12 : (d == kTopkDigits - 1 ? 4 : 8); }
+__device__ __forceinline__ int tk_low(int d) { return d == kTopkDigits - 1 ? 0 : 84 - 8 * d; }
+
+__device__ __forceinline__ unsigned tk_digit(unsigned long long hi, unsigned lo, int d) {
+    const int low = tk_low(d);
+    const unsigned long long v = low >= 32 ? hi >> (low - 32) : (hi << (32 - low)) | ((unsigned long long)lo >> low);
+    return (unsigned)v & ((1u << tk_width(d)) - 1u);
+}
+
+// masks of the key bits at and above bit `low` (the prefix fixed so far)
+__device__ __forceinline__ void tk_masks(int low, unsigned long long& mhi, unsigned& mlo) {
+    const int P = 96 - low;  // fixed bits from the top
+    mhi = P >= 64 ? ~0ull : (P <= 0 ? 0ull : ~0ull << (64 - P));
+    const int lb = P - 64;
+    mlo = lb <= 0 ? 0u : (lb >= 32 ? ~0u : ~0u << (32 - lb));
+}
+
+__device__ __forceinline__ void tk_set(unsigned long long& phi, unsigned& plo, int d, unsigned c) {
+    const int low = tk_low(d);
+    if (low >= 32) {
+        phi |= (unsigned long long)c << (low - 32);
+    } else {
+        plo |= c << low;
+        if (low + tk_width(d) > 32) phi |= (unsigned long long)(c >> (32 - low));
+    }
+}
+
+// one increment of bin b (b == ~0u: none).  Aggregating equal bins per warp
+// (__match_any_sync) measured slower here than plain shared atomics.
+__device__ __forceinline__ void tk_hist_add(unsigned* hist, unsigned b) {
+    if (b != ~0u) atomicAdd(&hist[b], 1u);
+}
+
+// Bucket of the krem-th largest key from the 4096-bin histogram, by the
+// whole block: thread t holds bins 4095-4t .. 4092-4t (from the top); a
+// block scan gives the count above each thread's group.
+__device__ __forceinline__ void tk_block_pick(const unsigned* hist, long long krem, unsigned* s_w, int* s_bin,
+                                              long long* s_above) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    unsigned c[4], grp = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        c[j] = hist[kTopkBins0 - 1 - 4 * tid - j];
+        grp += c[j];
+    }
+    unsigned incl = grp;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const unsigned w = s_w[lane];
+        unsigned wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        s_w[lane] = wi - w;
+    }
+    __syncthreads();
+    const long long excl = (long long)s_w[wid] + (long long)(incl - grp);
+    if (excl < krem && excl + (long long)grp >= krem) {
+        long long cum = excl;
+        int b = kTopkBins0 - 1 - 4 * tid;
+        for (int j = 0; j < 4; ++j, --b) {
+            if (cum + (long long)c[j] >= krem) break;
+            cum += c[j];
+        }
+        *s_bin = b;
+        *s_above = cum;
+    }
+    __syncthreads();
 }
 
 // Band mode (ids != nullptr): select among the *n_dev triangles ids[0..n)
@@ -227,21 +306,32 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
     extern __shared__ unsigned char smem_raw[];
     unsigned long long* c_hi = (unsigned long long*)smem_raw;
     unsigned* c_lo = (unsigned*)(c_hi + kTopkCandCap);
-    __shared__ unsigned hist[256];
+    __shared__ unsigned hist[kTopkBins0];
     __shared__ unsigned long long s_pre_hi, s_best[32];
     __shared__ unsigned s_pre_lo, s_cnt32[32];
-    __shared__ long long s_krem;
-    __shared__ int s_n, s_cnt, s_smem;
-    int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    __shared__ long long s_krem, s_above;
+    __shared__ int s_n, s_cnt, s_smem, s_bin, s_m;
+    __shared__ unsigned long long sv_hi[kTopkRankCap];
+    __shared__ unsigned sv_lo[kTopkRankCap];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int U = 4;  // keys per thread per step of a pass over the global keys
     if (ids) T = min(*n_dev, T);
     // pass 1 over the keys: eligible count and the histogram of digit 0
-    for (int i = tid; i < 256; i += kTopkBlockThreads) hist[i] = 0;
+    for (int i = tid; i < kTopkBins0; i += kTopkBlockThreads) hist[i] = 0;
     __syncthreads();
     unsigned ne = 0;
-    for (int i = tid; i < T; i += kTopkBlockThreads) {
-        unsigned long long hi = keyc[topk_id(ids, i)];
-        ne += hi ? 1u : 0u;
-        atomicAdd(&hist[(unsigned)(hi >> 56)], 1u);
+    for (int i0 = 0; i0 < T; i0 += U * kTopkBlockThreads) {
+        unsigned long long h[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * kTopkBlockThreads + tid;
+            h[u] = i < T ? keyc[topk_id(ids, i)] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ne += h[u] ? 1u : 0u;
+            tk_hist_add(hist, h[u] ? tk_digit(h[u], 0u, 0) : ~0u);
+        }
     }
     ne = warp_sum(ne);
     if (lane == 0) s_cnt32[wid] = ne;
@@ -273,85 +363,170 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
     // largest key below the bucket of the threshold, over the keys left
     // outside the shared-memory candidates (for the decision margin)
     unsigned long long best = extra_below ? *extra_below : 0ull;
-    for (int d = 0; d < 12; ++d) {
-        unsigned long long pre_hi = s_pre_hi;
-        unsigned pre_lo = s_pre_lo;
+    for (int d = 0; d < kTopkDigits; ++d) {
+        const unsigned long long pre_hi = s_pre_hi;
+        const unsigned pre_lo = s_pre_lo;
         if (d > 0) {  // digit 0's histogram came with the eligible count
+            unsigned long long mhi;
+            unsigned mlo;
+            tk_masks(tk_low(d - 1), mhi, mlo);
             for (int i = tid; i < 256; i += kTopkBlockThreads) hist[i] = 0;
             __syncthreads();
             if (!s_smem) {
-                for (int i = tid; i < T; i += kTopkBlockThreads) {
-                    int t = topk_id(ids, i);
-                    unsigned long long hi = keyc[t];
-                    unsigned lo = ~(unsigned)t;
-                    if (prefix_match(hi, lo, pre_hi, pre_lo, d)) atomicAdd(&hist[digit_of(hi, lo, d)], 1u);
+                for (int i0 = 0; i0 < T; i0 += U * kTopkBlockThreads) {
+                    unsigned long long h[U];
+                    unsigned l[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int i = i0 + u * kTopkBlockThreads + tid;
+                        const int t = i < T ? topk_id(ids, i) : 0;
+                        h[u] = i < T ? keyc[t] : 0ull;
+                        l[u] = ~(unsigned)t;
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const bool in = h[u] && (h[u] & mhi) == pre_hi && (l[u] & mlo) == pre_lo;
+                        tk_hist_add(hist, in ? tk_digit(h[u], l[u], d) : ~0u);
+                    }
                 }
             } else {
-                for (int i = tid; i < s_n; i += kTopkBlockThreads) {
-                    unsigned long long hi = c_hi[i];
-                    unsigned lo = c_lo[i];
-                    if (prefix_match(hi, lo, pre_hi, pre_lo, d)) atomicAdd(&hist[digit_of(hi, lo, d)], 1u);
+                const int n = s_n;
+                for (int i0 = 0; i0 < n; i0 += kTopkBlockThreads) {
+                    const int i = i0 + tid;
+                    bool in = false;
+                    unsigned b = ~0u;
+                    if (i < n) {
+                        const unsigned long long hi = c_hi[i];
+                        const unsigned lo = c_lo[i];
+                        in = (hi & mhi) == pre_hi && (lo & mlo) == pre_lo;
+                        if (in) b = tk_digit(hi, lo, d);
+                    }
+                    tk_hist_add(hist, b);
                 }
             }
             __syncthreads();
         }
-        if (tid < 32) {
-            long long krem = s_krem, cum = 0;
-            int chosen = warp_pick_bucket(hist, krem, &cum);
+        if (d == 0) {
+            tk_block_pick(hist, s_krem, s_cnt32, &s_bin, &s_above);
+        } else if (tid < 32) {
+            long long cum = 0;
+            const int chosen = warp_pick_bucket(hist, s_krem, &cum);
             if (tid == 0) {
-                s_krem = krem - cum;
-                s_cnt = (int)hist[chosen];
-                if (d < 8) s_pre_hi = pre_hi | ((unsigned long long)chosen << (56 - 8 * d));
-                else s_pre_lo = pre_lo | ((unsigned)chosen << (24 - 8 * (d - 8)));
+                s_bin = chosen;
+                s_above = cum;
             }
         }
         __syncthreads();
-        if (!s_smem && d < 11 && s_cnt <= kTopkCandCap) {
+        if (tid == 0) {
+            const unsigned c = (unsigned)s_bin;
+            s_krem -= s_above;
+            s_cnt = (int)hist[c];
+            unsigned long long ph = pre_hi;
+            unsigned pl = pre_lo;
+            tk_set(ph, pl, d, c);
+            s_pre_hi = ph;
+            s_pre_lo = pl;
+        }
+        __syncthreads();
+        if (!s_smem && d < kTopkDigits - 1 && s_cnt <= kTopkCandCap) {
             // collect the bucket; every key outside it lies wholly above or
             // wholly below it, and the largest below joins the margin
-            unsigned long long nh = s_pre_hi;
-            unsigned nl = s_pre_lo;
-            unsigned long long mhi = d + 1 >= 8 ? ~0ull : (~0ull << (64 - 8 * (d + 1)));
-            unsigned mlo = d + 1 <= 8 ? 0u : (~0u << (32 - 8 * (d + 1 - 8)));
-            for (int i = tid; i < T; i += kTopkBlockThreads) {
-                int t = topk_id(ids, i);
-                unsigned long long hi = keyc[t];
-                unsigned lo = ~(unsigned)t;
-                unsigned long long ph = hi & mhi;
-                unsigned pl = lo & mlo;
-                if (ph == nh && pl == nl) {
-                    int pos = atomicAdd(&s_n, 1);
-                    c_hi[pos] = hi;
-                    c_lo[pos] = lo;
-                } else if ((ph < nh || (ph == nh && pl < nl)) && hi > best) {
-                    best = hi;
+            const unsigned long long nh = s_pre_hi;
+            const unsigned nl = s_pre_lo;
+            unsigned long long mhi;
+            unsigned mlo;
+            tk_masks(tk_low(d), mhi, mlo);
+            for (int i0 = 0; i0 < T; i0 += U * kTopkBlockThreads) {
+                unsigned long long h[U];
+                unsigned l[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * kTopkBlockThreads + tid;
+                    const int t = i < T ? topk_id(ids, i) : 0;
+                    h[u] = i < T ? keyc[t] : 0ull;
+                    l[u] = ~(unsigned)t;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (!h[u]) continue;  // ineligible (or past the end)
+                    const unsigned long long ph = h[u] & mhi;
+                    const unsigned pl = l[u] & mlo;
+                    if (ph == nh && pl == nl) {
+                        const int pos = atomicAdd(&s_n, 1);
+                        c_hi[pos] = h[u];
+                        c_lo[pos] = l[u];
+                    } else if ((ph < nh || (ph == nh && pl < nl)) && h[u] > best) {
+                        best = h[u];
+                    }
                 }
             }
             __syncthreads();
             if (tid == 0) s_smem = 1;
             __syncthreads();
         }
+        if (s_smem && s_cnt <= kTopkRankCap) {
+            // few keys left in the bucket: copy them out of the candidates
+            // and take the krem-th largest by counting, for each, the keys
+            // above it (keys are distinct: the id is part of the key)
+            const unsigned long long nh = s_pre_hi;
+            const unsigned nl = s_pre_lo;
+            unsigned long long mhi;
+            unsigned mlo;
+            tk_masks(tk_low(d), mhi, mlo);
+            if (tid == 0) s_m = 0;
+            __syncthreads();
+            const int n = s_n;
+            for (int i = tid; i < n; i += kTopkBlockThreads) {
+                const unsigned long long hi = c_hi[i];
+                const unsigned lo = c_lo[i];
+                if ((hi & mhi) == nh && (lo & mlo) == nl) {
+                    const int pos = atomicAdd(&s_m, 1);
+                    if (pos < kTopkRankCap) {
+                        sv_hi[pos] = hi;
+                        sv_lo[pos] = lo;
+                    }
+                }
+            }
+            __syncthreads();
+            const int m = min(s_m, kTopkRankCap);
+            const long long krem = s_krem;
+            if (tid < m) {
+                const unsigned long long hi = sv_hi[tid];
+                const unsigned lo = sv_lo[tid];
+                int above = 0;
+                for (int j = 0; j < m; ++j) {
+                    const unsigned long long hj = sv_hi[j];
+                    above += (hj > hi || (hj == hi && sv_lo[j] > lo)) ? 1 : 0;
+                }
+                if ((long long)above == krem - 1) {
+                    s_pre_hi = hi;
+                    s_pre_lo = lo;
+                }
+            }
+            __syncthreads();
+            break;
+        }
     }
-    unsigned long long thr_hi = s_pre_hi;
-    unsigned thr_lo = s_pre_lo;
+    const unsigned long long thr_hi = s_pre_hi;
+    const unsigned thr_lo = s_pre_lo;
     // largest key strictly below the threshold among the candidates (or,
     // when they never fitted in shared memory, among all keys)
     if (s_smem) {
         for (int i = tid; i < s_n; i += kTopkBlockThreads) {
-            unsigned long long hi = c_hi[i];
-            unsigned lo = c_lo[i];
+            const unsigned long long hi = c_hi[i];
+            const unsigned lo = c_lo[i];
             if ((hi < thr_hi || (hi == thr_hi && lo < thr_lo)) && hi > best) best = hi;
         }
     } else {
         for (int i = tid; i < T; i += kTopkBlockThreads) {
-            int t = topk_id(ids, i);
-            unsigned long long hi = keyc[t];
-            unsigned lo = ~(unsigned)t;
+            const int t = topk_id(ids, i);
+            const unsigned long long hi = keyc[t];
+            const unsigned lo = ~(unsigned)t;
             if ((hi < thr_hi || (hi == thr_hi && lo < thr_lo)) && hi > best) best = hi;
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
         best = v > best ? v : best;
     }
     if (lane == 0) s_best[wid] = best;
@@ -361,9 +536,9 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
         for (int w = 0; w < kTopkBlockThreads / 32; ++w) bm = s_best[w] > bm ? s_best[w] : bm;
         out_thr[0] = thr_hi;
         out_thr[1] = thr_lo;
-        double kth = __longlong_as_double((long long)(thr_hi & ~(1ull << 63)));
+        const double kth = __longlong_as_double((long long)(thr_hi & ~(1ull << 63)));
         if (bm & (1ull << 63)) {
-            double nxt = __longlong_as_double((long long)(bm & ~(1ull << 63)));
+            const double nxt = __longlong_as_double((long long)(bm & ~(1ull << 63)));
             *out_margin = kth > 0.0 ? (kth - nxt) / kth : 0.0;
         } else {
             *out_margin = INFINITY;
@@ -517,16 +692,27 @@ __global__ void k_bisect(int4* __restrict__ tri, const int2* __restrict__ vxy, i
                          const int* __restrict__ flags, const int* __restrict__ fscan,
                          const unsigned char* __restrict__ mask, const float* __restrict__ f, double* __restrict__ uv,
                          float2* __restrict__ uvf, const int* __restrict__ cnt, const int* __restrict__ scan_err,
-                         const double* __restrict__ margin, int* __restrict__ stage) {
+                         const double* __restrict__ margin, int* __restrict__ stage, int* __restrict__ plan_err,
+                         int* __restrict__ clear) {
     pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (stage && t == 0) {
+    if (t == 0) {
         // the round's counters are final (written by the kernels before
-        // this one): hand them to the host through mapped pinned memory
+        // this one): hand them to the host (through mapped pinned memory,
+        // else the host copies them) and clear the per-round counters
+        // (new mask vertices, error flag, closure sweep flags) and the
+        // rasterisation plan's overflow flag for the next round
+        if (stage) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) stage[i] = cnt[i];
-        stage[9] = *scan_err;
-        *(double*)(stage + 16) = *margin;
+            for (int i = 0; i < 8; ++i) stage[i] = cnt[i];
+            stage[9] = *scan_err;
+            stage[10] = *plan_err;
+            *(double*)(stage + 16) = *margin;
+        }
+        if (clear) {
+            for (int i = 6; i < 64; ++i) clear[i] = 0;
+            *plan_err = 0;
+        }
     }
     if (t >= T || !flags[t]) return;
     int4 tr = tri[t];
@@ -674,8 +860,11 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
     unsigned long long* below = (unsigned long long*)(m->dscal.p + 10);
     double* margin = m->dscal.p + 11;
     int* err = m->dcount.p + 7;
-    // counters 6..63: new mask vertices, error flag, closure sweep flags
-    FEM_CUDA(cudaMemsetAsync(m->dcount.p + 6, 0, sizeof(int) * 58, s));
+    // counters 6..63 (new mask vertices, error flag, closure sweep flags)
+    // are zero: cleared at creation and by the previous round's k_bisect,
+    // or here when a round stopped before it
+    if (!m->round_ctr_clear) FEM_CUDA(cudaMemsetAsync(m->dcount.p + 6, 0, sizeof(int) * 58, s));
+    m->round_ctr_clear = false;
 
     TopkArgs A;
     A.keys = m->keys.p;
@@ -739,21 +928,31 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
                        s, nullptr, F_REFINE));
     FEM_LAUNCH(F_REFINE, s, k_bisect, tb, 256, 0, m->tri.p, m->vxy.p, T, N, bmM, (const int*)m->wpre.p, V,
                m->flags.p, m->fscan.p, m->mask.p, f, m->uv.p, m->uvf.p, (const int*)m->dcount.p,
-               (const int*)(m->dflag.p + 8), (const double*)margin, m->host_stage_dev ? stage_dev : nullptr);
-    // k, sweeps, new counts, margin, error: written by k_bisect into mapped
-    // pinned memory, else copied
+               (const int*)(m->dflag.p + 8), (const double*)margin, m->host_stage_dev ? stage_dev : nullptr,
+               m->dflag.p + 0, m->host_stage_dev ? m->dcount.p : nullptr);
+    // k, sweeps, new counts, margin, errors: written by k_bisect into mapped
+    // pinned memory, else copied (and the counters cleared here)
     int* hs = (int*)m->host_stage + kRoundStageInts;
     if (!m->host_stage_dev) {
         FEM_CUDA(cudaMemcpyAsync(hs, m->dcount.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
         FEM_CUDA(cudaMemcpyAsync(hs + 9, m->dflag.p + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaMemcpyAsync(hs + 10, m->dflag.p + 0, sizeof(int), cudaMemcpyDeviceToHost, s));
         FEM_CUDA(cudaMemcpyAsync((double*)(hs + 16), margin, sizeof(double), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaMemsetAsync(m->dflag.p + 0, 0, sizeof(int), s));
+    } else {
+        m->round_ctr_clear = true;
     }
     FEM_CUDA(cudaStreamSynchronize(s));
     int k = hs[2], nn = hs[4], nt = hs[5], nkm = hs[6], e = hs[7] ? hs[7] : hs[9];
+    if (hs[10]) {  // the rasterisation plan of this round overflowed: its keys are incomplete
+        m->plan_version = -1;
+        set_error("refinement: rasterisation plan overflow");
+        return FEM_E_INVALID;
+    }
     m->bm_clean = true;  // the round ran to the end: the next buffer is clear
     double mg = *(double*)(hs + 16);
     if (e) {
-        cudaMemsetAsync(m->bar.p, 0, 2 * sizeof(unsigned), s);
+        reset_coop_state(m, s);
         set_error(e == FEM_E_TIMEOUT ? "refinement: a grid barrier wait ran out" : "refinement: closure did not settle");
         return (fem_status)e;
     }

@@ -1038,7 +1038,7 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
     if (iters_out) *iters_out = its;
     if (relres_out) *relres_out = rel;
     if (st == FEM_E_TIMEOUT) {
-        cudaMemsetAsync(m->bar.p, 0, 2 * sizeof(unsigned), s);
+        reset_coop_state(m, s);
         set_error("Laplace solve: a grid barrier wait ran out");
         return FEM_E_TIMEOUT;
     }
@@ -1069,7 +1069,7 @@ fem_status solve_totals_read(fem_mesh* m, cudaStream_t s) {
     note_bytes(F_CG, hs[4]);
     int st = (int)hs[2];
     if (st == FEM_E_TIMEOUT) {
-        cudaMemsetAsync(m->bar.p, 0, 2 * sizeof(unsigned), s);
+        reset_coop_state(m, s);
         set_error("Laplace solve: a grid barrier wait ran out");
         return FEM_E_TIMEOUT;
     }
