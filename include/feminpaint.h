@@ -152,9 +152,10 @@ FEM_API fem_status fem_triangle_errors(fem_mesh *m, const double *uv_dev, const 
 
 /* The per-triangle errors of fem_triangle_errors for callers that cannot
  * allocate device memory (no counterpart in the paper).  Some callers cannot
- * call cudaMalloc: code running while a CUDA graph is captured on their
- * stream, programs whose allocator owns all device memory, or loops that
- * must not allocate after start-up.  This call allocates nothing: the
+ * call cudaMalloc: programs whose own caching allocator has reserved all
+ * device memory, and real-time or serving loops that must not allocate after
+ * start-up (cudaMalloc can synchronise the device and takes unbounded
+ * time).  This call allocates nothing: the
  * caller passes the mesh arrays, the vertex values, the image and the
  * output; the scratch it needs is a fixed 3.4 MB device array inside the
  * library, present on every GPU that loads the library until the process

@@ -1,10 +1,11 @@
 // noalloc.cu -- per-triangle squared errors for callers that cannot allocate
 // device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is
-// being captured on their stream, allocators that forbid foreign
-// allocations (a caching pool that owns all device memory), or real-time
-// loops that must not allocate after start-up.  For them this file offers
+// Some callers cannot call cudaMalloc: programs whose own caching allocator
+// has reserved all device memory (a foreign allocation would fail or
+// fragment it), and real-time or serving loops that must not allocate after
+// start-up (cudaMalloc can synchronise the device and its latency is
+// unbounded).  For them this file offers
 // one entry point that computes the same per-triangle errors as
 // fem_triangle_errors on mesh arrays the caller owns, using as scratch a
 // file-scope device array of fixed size instead of any allocation.

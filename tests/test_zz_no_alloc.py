@@ -1,8 +1,8 @@
 """The allocation-free error entry point (fem_triangle_errors_noalloc).
 
-It serves callers that cannot allocate device memory (graph capture in
-progress, allocators that own all device memory, loops that must not
-allocate).  It must give the same per-triangle errors as
+It serves callers that cannot allocate device memory (programs whose own
+caching allocator has reserved all device memory, loops that must not
+allocate after start-up).  It must give the same per-triangle errors as
 fem_triangle_errors, on two calls in a row (the shared scratch keeps the
 previous call's contents), alone in a fresh process or after other tests.
 This file is named so that pytest collects it last.
