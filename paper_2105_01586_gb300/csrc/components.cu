@@ -56,6 +56,10 @@ constexpr int kBuildThreads = 256;
 static_assert(kBuildThreads == SCAN_BT, "the block scan assumes SCAN_BT threads");
 constexpr int kSortSmem = 4096;  // ranges up to this size are sorted in shared memory
 constexpr int kUniteCap = 1 << 20;
+// Up to this many vertices one block builds the whole system: its phases are
+// then separated by block barriers, which cost far less than grid barriers,
+// while each thread takes a few more vertices per phase.
+constexpr int kBuildOneBlockV = 512;
 
 // Root of x.  Parents only point to smaller ids, so the walk ends; path
 // halving stores an ancestor, which stays an ancestor as trees merge.
@@ -491,8 +495,11 @@ fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k_build_system, kBuildThreads, 0);
         return nb < 1 ? 1 : nb;
     }();
-    // about one vertex per thread, at most the co-resident blocks
-    const int grid = std::max(1, std::min(occ * m->num_sms, (V + kBuildThreads - 1) / kBuildThreads));
+    // one block for small systems; else about one vertex per thread, at most
+    // the co-resident blocks
+    const int grid = V <= kBuildOneBlockV
+                         ? 1
+                         : std::max(1, std::min(occ * m->num_sms, (V + kBuildThreads - 1) / kBuildThreads));
     FEM_TRY(ensure(m->scan_pre, (size_t)grid + 1, s));
     BuildArgs A;
     A.tri = m->tri.p;
@@ -534,6 +541,14 @@ fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
     // launch, and cleared again after a failed one (reset_coop_state)
     void* args[] = {&A};
     FEM_TRY(launch_coop(F_ASSEMBLY, (const void*)k_build_system, grid, kBuildThreads, 0, s, args, "k_build_system"));
+    // algorithmic bytes of a build: the mesh read once (16 B per triangle,
+    // 9 B per vertex), the stencil and index maps written once (76 B per
+    // vertex, 4 B per mask vertex), the ELL rows with diagonal, inverse
+    // diagonals, row counts, vertex and component of each row (92 B per
+    // unknown); with the right-hand side, 8 B per vertex read and 16 B per
+    // unknown written.  The union-find forest is working state, not counted.
+    note_bytes(F_ASSEMBLY, 16.0 * T + 85.0 * V + 4.0 * (V - nU) + 92.0 * nU +
+                               (A.b ? 8.0 * V + 16.0 * nU : 0.0));
     if (want && nU > 0) *with_rhs = true;
     m->sys_version = m->mesh_version;
     return FEM_OK;

@@ -116,11 +116,14 @@ __device__ __forceinline__ T warp_sum(T v) {
 // waits longer than kBarrierLimitNs records FEM_E_TIMEOUT in *err and stops
 // waiting; once *err is set every later barrier returns at once, so the
 // kernel winds down (the word must then be cleared before the next launch).
+// A grid of one block needs only the block barrier, which orders the block's
+// global memory accesses; no other block can time out, so *err is not read.
 // Returns false when the kernel must stop.
 constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // 2 s
 
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
     __syncthreads();
+    if (gridDim.x * gridDim.y * gridDim.z == 1) return true;
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;

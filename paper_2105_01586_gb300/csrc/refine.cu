@@ -803,6 +803,10 @@ struct OrderExpandOut {
 
 // Cooperative grid: one thread per work item, at most the co-resident
 // blocks (occupancy queried once per kernel).
+// Up to this many triangles one block runs the closure sweeps (block
+// barriers between sweeps instead of grid barriers).
+constexpr int kClosureOneBlockT = 512;
+
 static int coop_grid(const void* func, int threads, int work, int num_sms) {
     static const int nb_topk = [] {
         int nb = 0;
@@ -910,7 +914,7 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
         int max_sweeps = 48;
         void* args[] = {(void*)&m->tri.p, (void*)&m->vxy.p, (void*)&T, (void*)&N, (void*)&bmM,
                         (void*)&changed, (void*)&max_sweeps, (void*)&m->bar.p, (void*)&err, (void*)&sweeps};
-        int grid = coop_grid((const void*)k_closure, 256, T, m->num_sms);
+        int grid = T <= kClosureOneBlockT ? 1 : coop_grid((const void*)k_closure, 256, T, m->num_sms);
         FEM_TRY(launch_coop(F_REFINE, (const void*)k_closure, grid, 256, 0, s, args, "k_closure"));
     }
     int Wi = (int)W;
