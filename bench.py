@@ -200,9 +200,12 @@ def traffic_record(family):
         rec = json.load(fh).get(family)
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_2105_01586_gb300", "csrc", rec["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.exists(src) else None
-    return rec["dram_bytes_per_launch"] if h == rec.get("source_sha256_16") else None
+    for name, want in rec.get("sources", {}).items():
+        src = os.path.join(ROOT, "paper_2105_01586_gb300", "csrc", name)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.exists(src) else None
+        if h != want:
+            return None
+    return rec["dram_bytes_per_launch"] if rec.get("sources") else None
 
 
 # --------------------------------------------------------------- our arm
@@ -389,8 +392,8 @@ def run_ours(a, world, rank, local):
 
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "fp32+fp64", "data": "synthetic",
-            "config": config(a, world), "roofline": roofline, "e2e": e2e, "clocks": clocks,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "fp32+fp64",
+            "data": "synthetic", "config": config(a, world), "roofline": roofline, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches)}
     line.update(extra)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
