@@ -982,7 +982,13 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
     // The component kernel also clears the error word of that solver.
     FEM_TRY(solve_components(m, b, x, use_fp64, tol, maxit, deferred, scatter, m->dflag.p + 1, s));
     A.gate = m->ccount.p;
-    if (!use_fp64 && nU <= kBlockMaxRows) {
+    // With at most kBlockComp unknowns no component can be larger, so the
+    // whole-system solvers (and their scatter) would return at once: they
+    // are not launched.
+    const bool whole_system = nU > kBlockComp;
+    if (!whole_system) {
+        // nothing more to launch
+    } else if (!use_fp64 && nU <= kBlockMaxRows) {
         static const bool attr_set = [] {
             return cudaFuncSetAttribute(k_solve_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kBlockSmemBytes) == cudaSuccess;
@@ -1014,7 +1020,7 @@ fem_status run_solve(fem_mesh* m, const double* b, double* x, bool use_fp64, dou
         void* args[] = {&A};
         FEM_TRY(launch_coop(F_CG, func, grid, kSolveThreads, 0, s, args, "k_solve<fp64>"));
     }
-    if (scatter && !(!use_fp64 && nU <= kBlockMaxRows)) {
+    if (scatter && whole_system && !(!use_fp64 && nU <= kBlockMaxRows)) {
         // these whole-system solvers leave the scatter to a kernel of its own
         // (it repeats what the component solver wrote when that one solved)
         FEM_LAUNCH(F_CG, s, k_scatter_solution, (nU + 255) / 256, 256, 0, nU, m->V, (const int*)m->urow_vertex.p,
