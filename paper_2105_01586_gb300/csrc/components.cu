@@ -219,6 +219,16 @@ struct BuildArgs {
     int* tsum;  // per-block sums of the scans
     unsigned* bar;
     int* err;
+    // ahead of the host (dV != nullptr): V and T are the counts before the
+    // refinement round and the refined mesh has V + *dV vertices and
+    // T + *dT triangles; nothing is built when the round failed (guard[7]:
+    // closure or top-k error, guard[9]: scan error) or when the refined mesh
+    // exceeds the capacities Vcap (every per-vertex and per-unknown array)
+    // and Tcap (triangles).  nU < 0: the unknown count is the kernel's own.
+    const int* dV;
+    const int* dT;
+    const int* guard;
+    int Vcap, Tcap;
 };
 
 struct UnknownFlagIn {
@@ -263,7 +273,14 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
     pdl_wait();
     __shared__ int s_keys[kSortSmem];
     const int tid0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-    const int V = A.V, T = A.T;
+    int V = A.V, T = A.T;
+    if (A.dV) {
+        // every block reads the same words, so all return or none does
+        if (ld_volatile_i32(A.guard + 7) != 0 || ld_volatile_i32(A.guard + 9) != 0) return;
+        V += __ldcg(A.dV);
+        T += __ldcg(A.dT);
+        if (V > A.Vcap || T > A.Tcap) return;
+    }
     const long long V8 = 8LL * V;
     // 0. clear; union-find forest of singletons; mask counts per chunk
     for (long long i = tid0; i < V8; i += stride) {
@@ -307,7 +324,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
     }
     scan_emit(UnknownFlagIn{A.mask}, IndexMapOut{&A}, V, A.tsum, A.nU_dev);
     if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
-    if (A.nU == 0) return;  // uniform: no unknowns, no components
+    const int nU = A.nU >= 0 ? A.nU : __ldcg(A.nU_dev);
+    if (nU == 0) return;  // uniform: no unknowns, no components
     // 2. union-find over the edges of A_UU, each from its larger endpoint;
     //    the 8 slots of a vertex are loaded together
     for (int v = tid0; v < V; v += stride) {
@@ -360,7 +378,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
         if (A.mask[v]) continue;
         int r = __ldcg(A.root + v), sz = __ldcg(A.size + r), st = __ldcg(A.cstart + r);
         int slot = st + atomicAdd(A.fill + r, 1);
-        if (slot >= A.nU || st + sz > A.nU) {  // more unknowns than rows: a malformed mesh count
+        if (slot >= nU || st + sz > nU) {  // more unknowns than rows: a malformed mesh count
             atomicCAS(A.cnt + CC_ERR, 0, (int)FEM_E_INVALID);
             continue;
         }
@@ -416,7 +434,6 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
     // 8. ELL rows of A_UU (padded with the own row and value 0); with b the
     //    right-hand side b_r = -sum over mask neighbours of A_ij uv_j and the
     //    start x_r = uv of the row's vertex
-    const int nU = A.nU;
     for (int r = tid0; r < nU; r += stride) {
         int i = __ldcg(A.members + r);
         int s = 0;
@@ -452,31 +469,36 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
     }
 }
 
-// with_rhs (optional): on input asks for b64/x64 of a solve on the current
-// vertex values to be filled with the system; on output true when that
-// happened (the system was rebuilt), false when the caller must fill them
-fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
-    bool want = with_rhs && *with_rhs;
-    if (with_rhs) *with_rhs = false;
-    if (m->sys_version == m->mesh_version) return FEM_OK;
-    const int V = m->V, T = m->T;
-    // the mask count is kept on the host by create / import / refinement, so
-    // the unknown count needs no read-back
-    const int nU = V - m->nK;
-    m->nU = nU;
-    const size_t n = nU > 0 ? nU : 1, nr = n + 1;
-    FEM_TRY(ensure(m->nbr, (size_t)8 * V, s));
-    FEM_TRY(ensure(m->coefA, (size_t)8 * V, s));
-    FEM_TRY(ensure(m->diagA, V, s));
-    FEM_TRY(ensure(m->uidx, V, s));
-    FEM_TRY(ensure(m->kidx, V, s));
-    FEM_TRY(ensure(m->urow_vertex, V, s));
-    FEM_TRY(ensure(m->kvert, V, s));
-    FEM_TRY(ensure(m->cc_parent, V, s));
-    FEM_TRY(ensure(m->cc_root, V, s));
-    FEM_TRY(ensure(m->cc_size, V, s));
-    FEM_TRY(ensure(m->cc_fill, V, s));
-    FEM_TRY(ensure(m->cc_cstart, (size_t)V + 1, s));
+// algorithmic bytes of a build: the mesh read once (16 B per triangle,
+// 9 B per vertex), the stencil and index maps written once (76 B per
+// vertex, 4 B per mask vertex), the ELL rows with diagonal, inverse
+// diagonals, row counts, vertex and component of each row (92 B per
+// unknown); with the right-hand side, 8 B per vertex read and 16 B per
+// unknown written.  The union-find forest is working state, not counted.
+double build_bytes(long long T, long long V, long long nU, bool rhs) {
+    return 16.0 * T + 85.0 * V + 4.0 * (V - nU) + 92.0 * nU + (rhs ? 8.0 * V + 16.0 * nU : 0.0);
+}
+
+namespace {
+
+// Ensure the system arrays for nv vertices and nu unknowns (nu <= nv) and
+// launch k_build_system on the mesh counts V, T (host) or, ahead of the
+// host, on the counts of the round in flight (dV, dT, guard; then nU < 0).
+fem_status launch_build(fem_mesh* m, cudaStream_t s, int V, int T, int nU, size_t nv, size_t nu, bool rhs,
+                        const int* dV, const int* dT, const int* guard, int Vcap, int Tcap) {
+    const size_t n = nu > 0 ? nu : 1, nr = n + 1;
+    FEM_TRY(ensure(m->nbr, (size_t)8 * nv, s));
+    FEM_TRY(ensure(m->coefA, (size_t)8 * nv, s));
+    FEM_TRY(ensure(m->diagA, nv, s));
+    FEM_TRY(ensure(m->uidx, nv, s));
+    FEM_TRY(ensure(m->kidx, nv, s));
+    FEM_TRY(ensure(m->urow_vertex, nv, s));
+    FEM_TRY(ensure(m->kvert, nv, s));
+    FEM_TRY(ensure(m->cc_parent, nv, s));
+    FEM_TRY(ensure(m->cc_root, nv, s));
+    FEM_TRY(ensure(m->cc_size, nv, s));
+    FEM_TRY(ensure(m->cc_fill, nv, s));
+    FEM_TRY(ensure(m->cc_cstart, nv + 1, s));
     FEM_TRY(ensure(m->rowcomp, nr, s));
     FEM_TRY(ensure(m->blk_list, nr, s));
     FEM_TRY(ensure(m->warp_list, nr, s));
@@ -486,9 +508,9 @@ fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
     FEM_TRY(ensure(m->ucnt, n, s));
     FEM_TRY(ensure(m->dinv32, n, s));
     FEM_TRY(ensure(m->dinv64, n, s));
-    if (want && nU > 0) {
-        FEM_TRY(ensure(m->b64, (size_t)nU, s));
-        FEM_TRY(ensure(m->x64, (size_t)nU, s));
+    if (rhs) {
+        FEM_TRY(ensure(m->b64, n, s));
+        FEM_TRY(ensure(m->x64, n, s));
     }
     static const int occ = [] {
         int nb = 0;
@@ -532,26 +554,65 @@ fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
     A.udinv = m->dinv32.p;
     A.udinv64 = m->dinv64.p;
     A.uv = m->uv.p;
-    A.b = (want && nU > 0) ? m->b64.p : nullptr;
-    A.x = (want && nU > 0) ? m->x64.p : nullptr;
+    A.b = rhs ? m->b64.p : nullptr;
+    A.x = rhs ? m->x64.p : nullptr;
     A.tsum = m->scan_pre.p;
     A.bar = m->bar.p;
     A.err = m->dflag.p + 2;
+    A.dV = dV;
+    A.dT = dT;
+    A.guard = guard;
+    A.Vcap = Vcap;
+    A.Tcap = Tcap;
     // *A.err is zero: cleared at creation, left at zero by every completed
     // launch, and cleared again after a failed one (reset_coop_state)
     void* args[] = {&A};
-    FEM_TRY(launch_coop(F_ASSEMBLY, (const void*)k_build_system, grid, kBuildThreads, 0, s, args, "k_build_system"));
-    // algorithmic bytes of a build: the mesh read once (16 B per triangle,
-    // 9 B per vertex), the stencil and index maps written once (76 B per
-    // vertex, 4 B per mask vertex), the ELL rows with diagonal, inverse
-    // diagonals, row counts, vertex and component of each row (92 B per
-    // unknown); with the right-hand side, 8 B per vertex read and 16 B per
-    // unknown written.  The union-find forest is working state, not counted.
-    note_bytes(F_ASSEMBLY, 16.0 * T + 85.0 * V + 4.0 * (V - nU) + 92.0 * nU +
-                               (A.b ? 8.0 * V + 16.0 * nU : 0.0));
-    if (want && nU > 0) *with_rhs = true;
+    return launch_coop(F_ASSEMBLY, (const void*)k_build_system, grid, kBuildThreads, 0, s, args, "k_build_system");
+}
+
+}  // namespace
+
+// with_rhs (optional): on input asks for b64/x64 of a solve on the current
+// vertex values to be filled with the system; on output true when that
+// happened (the system was rebuilt, or built ahead with them by the last
+// refinement round), false when the caller must fill them
+fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
+    bool want = with_rhs && *with_rhs;
+    if (with_rhs) *with_rhs = false;
+    if (m->sys_version == m->mesh_version) {
+        if (want && m->rhs_fresh) *with_rhs = true;
+        m->rhs_fresh = false;
+        return FEM_OK;
+    }
+    m->rhs_fresh = false;
+    const int V = m->V, T = m->T;
+    // the mask count is kept on the host by create / import / refinement, so
+    // the unknown count needs no read-back
+    const int nU = V - m->nK;
+    m->nU = nU;
+    const bool rhs = want && nU > 0;
+    FEM_TRY(launch_build(m, s, V, T, nU, (size_t)V, (size_t)(nU > 0 ? nU : 1), rhs, nullptr, nullptr, nullptr, 0, 0));
+    note_bytes(F_ASSEMBLY, build_bytes(T, V, nU, rhs));
+    if (rhs) *with_rhs = true;
     m->sys_version = m->mesh_version;
     return FEM_OK;
+}
+
+// The system of the mesh that the refinement round in flight produces,
+// launched behind that round's last kernel before the host has read the
+// round's counts (mesh of V vertices and T triangles before the round; the
+// refined counts are the round's device counters, guard the round's staged
+// status words).  The arrays are sized for V + V/4 + 64 vertices; the kernel
+// builds nothing when the refined mesh is larger, or when the round failed.
+// *Vcap / *Tcap receive the capacities: the caller knows the system is built
+// once it has read counts within them.
+fem_status build_system_ahead(fem_mesh* m, cudaStream_t s, int V, int T, const int* guard, int* Vcap, int* Tcap) {
+    const size_t nv = (size_t)V + V / 4 + 64;
+    long long vc = (long long)std::min({nv, m->vxy.n, m->mask.n, m->uv.n, m->uvf.n});
+    long long tc = (long long)m->tri.n;
+    *Vcap = (int)std::min<long long>(vc, INT_MAX);
+    *Tcap = (int)std::min<long long>(tc, INT_MAX);
+    return launch_build(m, s, V, T, -1, nv, nv, true, m->dcount.p + 4, m->dcount.p + 5, guard, *Vcap, *Tcap);
 }
 
 fem_status build_system(fem_mesh* m, cudaStream_t s) { return build_system_rhs(m, s, nullptr); }

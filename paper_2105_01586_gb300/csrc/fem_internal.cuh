@@ -239,6 +239,8 @@ struct fem_mesh {
 
     // Laplace system on U
     long long sys_version = -1;
+    bool rhs_fresh = false;         // b64/x64 hold the right-hand side and start of the built system
+    cudaEvent_t round_ev = nullptr; // end of a refinement round's last kernel
     fem::DArr<int> uidx;            // vertex -> U row or -1
     fem::DArr<int> kidx;            // vertex -> K index or -1
     fem::DArr<int> nbr;             // 8*V neighbour per direction (-1 none)
@@ -313,6 +315,11 @@ fem_status build_system(fem_mesh* m, cudaStream_t s);
 // with_rhs (optional): on input asks for b64/x64 of a solve on the current
 // vertex values; on output true when the build filled them
 fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs);
+// the system of the mesh the refinement round in flight produces, launched
+// before the host reads the round's counts (components.cu)
+fem_status build_system_ahead(fem_mesh* m, cudaStream_t s, int V, int T, const int* guard, int* Vcap, int* Tcap);
+// algorithmic bytes of one system build
+double build_bytes(long long T, long long V, long long nU, bool rhs);
 fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cudaStream_t s,
                          int* iters_out, double* relres_out, bool deferred = false);
 // scatter: the solution also goes to m->uv / m->uvf at the rows' vertices

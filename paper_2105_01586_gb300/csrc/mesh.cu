@@ -489,6 +489,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->tr, s); release(m->tp, s); release(m->tw, s); release(m->tc, s);
     cudaStreamSynchronize(s);
     if (m->host_stage) cudaFreeHost(m->host_stage);
+    if (m->round_ev) cudaEventDestroy(m->round_ev);
     cudaGetLastError();
     delete m;
     return FEM_OK;

@@ -937,17 +937,29 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
     // k, sweeps, new counts, margin, errors: written by k_bisect into mapped
     // pinned memory, else copied (and the counters cleared here)
     int* hs = (int*)m->host_stage + kRoundStageInts;
+    bool ahead = false;
+    int Vcap = 0, Tcap = 0;
     if (!m->host_stage_dev) {
         FEM_CUDA(cudaMemcpyAsync(hs, m->dcount.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
         FEM_CUDA(cudaMemcpyAsync(hs + 9, m->dflag.p + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
         FEM_CUDA(cudaMemcpyAsync(hs + 10, m->dflag.p + 0, sizeof(int), cudaMemcpyDeviceToHost, s));
         FEM_CUDA(cudaMemcpyAsync((double*)(hs + 16), margin, sizeof(double), cudaMemcpyDeviceToHost, s));
         FEM_CUDA(cudaMemsetAsync(m->dflag.p + 0, 0, sizeof(int), s));
+        FEM_CUDA(cudaStreamSynchronize(s));
     } else {
         m->round_ctr_clear = true;
+        // The next round starts with the system of the refined mesh: it is
+        // launched behind k_bisect (it takes the refined counts from the
+        // device), and the host waits for k_bisect alone, so the build runs
+        // while the host reads the counts and prepares the next launches.
+        if (!m->round_ev) FEM_CUDA(cudaEventCreateWithFlags(&m->round_ev, cudaEventDisableTiming));
+        FEM_CUDA(cudaEventRecord(m->round_ev, s));
+        FEM_TRY(build_system_ahead(m, s, V, T, stage_dev, &Vcap, &Tcap));
+        ahead = true;
+        FEM_CUDA(cudaEventSynchronize(m->round_ev));
     }
-    FEM_CUDA(cudaStreamSynchronize(s));
     int k = hs[2], nn = hs[4], nt = hs[5], nkm = hs[6], e = hs[7] ? hs[7] : hs[9];
+    if (ahead && (hs[10] || e || (k > 0 && nn <= 0))) m->sys_version = -1;  // the build saw another mesh
     if (hs[10]) {  // the rasterisation plan of this round overflowed: its keys are incomplete
         m->plan_version = -1;
         set_error("refinement: rasterisation plan overflow");
@@ -973,6 +985,14 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
         m->nK += nkm;
         m->nU = m->V - m->nK;
         m->mesh_version++;
+        // the build ahead ran to the end when the refined mesh fit its
+        // capacities: the system and the next solve's right-hand side and
+        // start (from the vertex values k_bisect completed) are in place
+        if (ahead && m->V <= Vcap && m->T <= Tcap) {
+            m->sys_version = m->mesh_version;
+            m->rhs_fresh = m->nU > 0;
+            note_bytes(F_ASSEMBLY, build_bytes(m->T, m->V, m->nU, m->nU > 0));
+        }
     }
     return FEM_OK;
 }
@@ -1023,6 +1043,7 @@ extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double
         if (margin < m->stats.min_margin) m->stats.min_margin = margin;
         round++;
     }
+    m->rhs_fresh = false;  // only the loop's next solve may take the right-hand side built ahead
     fem_status st = solve_totals_read(m, s);
     m->stats.rounds = round;
     return st;

@@ -76,12 +76,13 @@ namespace {
 // Upper estimate of the device memory a request holds at its peak: the
 // image, the per-pixel bitmaps, and per-vertex / per-triangle arrays (with
 // the capacity doubling of the growing mesh) for V* = ceil(density * P)
-// vertices and about 2 V* triangles.
+// vertices and about 2 V* triangles.  The systems built ahead of the host
+// size their per-unknown arrays for 1.25 times the vertices (140 B each).
 size_t estimate_bytes(int width, double density) {
     double P = (double)width * width;
     double V = std::ceil(density * P) * 1.2 + 64;
     double T = 2.0 * V;
-    return (size_t)(4.0 * P + 0.5 * P + 2.0 * (260.0 * V + 220.0 * T) + (64 << 20));
+    return (size_t)(4.0 * P + 0.5 * P + 2.0 * (260.0 * V + 220.0 * T + 140.0 * V) + (64 << 20));
 }
 
 fem_status run_request(Request& r, cudaStream_t s) {
