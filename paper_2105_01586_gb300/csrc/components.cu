@@ -15,7 +15,7 @@
 // stiffness entry.  In meshes made by the spatial optimisation nearly every
 // unknown vertex sits among mask vertices, so A_UU splits into many small
 // independent blocks: a 4 % mesh of a 2049 x 2049 image has 19,622 unknowns
-// in 9,561 blocks, the largest with 224 rows.  When the unknowns are
+// in 10,233 blocks, the largest with 216 rows.  When the unknowns are
 // numbered component by component, each block is a contiguous range of rows
 // whose columns stay inside the range, and the solver treats the blocks as
 // independent systems (solve_comp.cu).  The numbering does not depend on
