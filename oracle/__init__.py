@@ -42,7 +42,7 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into the checker library (gcc, plain C11)."""
+    """Compile oracle.c into the oracle library used by the tests (gcc, plain C11)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + ".tmp.%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])

@@ -3,7 +3,7 @@
  * spatial and tonal data optimisation (Chizhov & Weickert, "Efficient Data
  * Optimisation for Harmonic Inpainting with Finite Elements", arXiv 2105.01586).
  *
- * TEST INFRASTRUCTURE ONLY.  This file is compiled into a checker library that
+ * TEST INFRASTRUCTURE ONLY.  This file is compiled into a test library that
  * only the tests, the smoke check and the CPU-baseline leg of the benchmark
  * load.  The product path (the CUDA library and its Python binding) never
  * includes, links or calls it, and it shares no code with that path.
