@@ -801,12 +801,12 @@ struct OrderExpandOut {
     }
 };
 
-// Cooperative grid: one thread per work item, at most the co-resident
-// blocks (occupancy queried once per kernel).
 // Up to this many triangles one block runs the closure sweeps (block
 // barriers between sweeps instead of grid barriers).
 constexpr int kClosureOneBlockT = 512;
 
+// Cooperative grid: one thread per work item, at most the co-resident
+// blocks (occupancy queried once per kernel).
 static int coop_grid(const void* func, int threads, int work, int num_sms) {
     static const int nb_topk = [] {
         int nb = 0;
@@ -954,7 +954,13 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
         // while the host reads the counts and prepares the next launches.
         if (!m->round_ev) FEM_CUDA(cudaEventCreateWithFlags(&m->round_ev, cudaEventDisableTiming));
         FEM_CUDA(cudaEventRecord(m->round_ev, s));
-        FEM_TRY(build_system_ahead(m, s, V, T, stage_dev, &Vcap, &Tcap));
+        fem_status st = build_system_ahead(m, s, V, T, stage_dev, &Vcap, &Tcap);
+        if (st != FEM_OK) {
+            // its arrays may have been reallocated: no system is valid now
+            m->sys_version = -1;
+            cudaEventSynchronize(m->round_ev);
+            return st;
+        }
         ahead = true;
         FEM_CUDA(cudaEventSynchronize(m->round_ev));
     }
