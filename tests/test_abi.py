@@ -81,3 +81,20 @@ def test_server_entry_points_reject_bad_handles_on_the_host(fem):
     assert fem._lib.fem_server_destroy(None) == fem.FEM_OK
     out = ctypes.c_void_p()
     assert fem._lib.fem_server_create(0, 0, ctypes.byref(out)) == fem.FEM_E_INVALID
+
+
+def test_noalloc_entry_point_checks_sizes_on_the_host(fem):
+    """The allocation-free error pass rejects sizes beyond its fixed scratch,
+    null pointers and misaligned arrays before any CUDA call (no GPU needed)."""
+    L = fem._lib
+    ok_ptr = 1 << 12  # aligned, never dereferenced: the checks fail first
+    args = lambda w, V, T, xy=ok_ptr, tri=ok_ptr: (w, V, xy, T, tri, ok_ptr, ok_ptr, ok_ptr, None)
+    assert L.fem_triangle_errors_noalloc(*args(4097, 4, 2)) == fem.FEM_E_SHAPE
+    assert L.fem_triangle_errors_noalloc(*args(100, 4, 2)) == fem.FEM_E_SHAPE      # not 2^L + 1
+    assert L.fem_triangle_errors_noalloc(*args(129, 4, 65537)) == fem.FEM_E_INVALID
+    assert b"65536" in L.fem_last_error()
+    assert L.fem_triangle_errors_noalloc(*args(129, 4, 0)) == fem.FEM_E_INVALID
+    assert L.fem_triangle_errors_noalloc(*args(129, 4, 2, xy=None)) == fem.FEM_E_INVALID
+    assert b"null" in L.fem_last_error()
+    assert L.fem_triangle_errors_noalloc(*args(129, 4, 2, tri=ok_ptr + 4)) == fem.FEM_E_INVALID
+    assert b"aligned" in L.fem_last_error()
