@@ -189,8 +189,12 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
     double* __restrict__ partial, float* __restrict__ u_out, int* __restrict__ owner_out,
     const int* __restrict__ item_cnt = nullptr, int* __restrict__ item_done = nullptr,
     double* __restrict__ key_out = nullptr, unsigned long long* __restrict__ keyc_out = nullptr,
-    const int* __restrict__ item_list = nullptr) {
+    const int* __restrict__ item_list = nullptr, const int* __restrict__ plan_err = nullptr) {
     pdl_wait();
+    // An overflowing plan left item slots unwritten (they may hold another
+    // mesh's triangle ids): read none of them.  Every thread reads the same
+    // word, so the whole grid returns or none of it does.
+    if (plan_err && *plan_err) return;
     constexpr int NA = NAcc<MODE>::n;
     constexpr bool FF = (MODE == R_ERR || MODE == R_IMG);
     const unsigned FULL = 0xffffffffu;
@@ -358,14 +362,16 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
 __global__ void k_finalize_err(const int* __restrict__ cnt, const int* __restrict__ off,
                                const float2* __restrict__ partial, int T, const int4* __restrict__ tri,
                                const int2* __restrict__ vxy, double* __restrict__ out,
-                               unsigned long long* __restrict__ keyc) {
+                               unsigned long long* __restrict__ keyc, int item_cap, const int* __restrict__ plan_err) {
     pdl_wait();
+    if (plan_err && *plan_err) return;  // the plan overflowed: no partial is valid
     long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long tt = gw; tt < T; tt += nw) {
         int t = (int)tt;
         int o = off[t], n = cnt[t];
         if (n == 0) continue;  // small triangle: written by the small-triangle kernel
+        if ((long long)o + n > item_cap) continue;  // never past the partials' capacity
         ff s = warp_sum_partials(partial, o, n);
         if ((threadIdx.x & 31) == 0) {
             double key = ff_to_double(s);
@@ -649,7 +655,8 @@ fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, const
     note_bytes(F_RASTER, raster_err_bytes(m));
     FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
                m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p,
-               (float*)nullptr, (int*)nullptr, m->item_cnt.p, m->item_done.p, err_out, keyc_out, nullptr);
+               (float*)nullptr, (int*)nullptr, m->item_cnt.p, m->item_done.p, err_out, keyc_out, nullptr,
+               (const int*)(m->dflag.p + 0));
     // Few small triangles: eight lanes each over staged tiles, which shortens
     // the longest thread.  Many (above about 1k per SM): one thread each,
     // which avoids the eight-fold plane setup once every SM is full anyway.
@@ -667,7 +674,8 @@ fem_status raster_image(fem_mesh* m, const double* uv, float* u, int* owner, cud
     note_bytes(F_RASTER, (u ? 4.0 * (double)m->P : 0.0) + (owner ? 4.0 * (double)m->P : 0.0) + 16.0 * m->T +
                              16.0 * m->V);
     FEM_LAUNCH(F_RASTER, s, k_raster<R_IMG>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv,
-               (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, u, owner, nullptr, nullptr, nullptr, nullptr, nullptr);
+               (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, u, owner, nullptr, nullptr, nullptr, nullptr, nullptr,
+               (const int*)(m->dflag.p + 0));
     FEM_LAUNCH(F_RASTER, s, k_raster_small<R_IMG>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv,
                (const float2*)nullptr, (const float*)nullptr, m->N, m->T, (double*)nullptr,
                (unsigned long long*)nullptr, u, owner, nullptr);
@@ -684,7 +692,8 @@ fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s) {
     if (mode == R_MASS) {
         FEM_LAUNCH(F_RASTER, s, k_raster<R_MASS>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
                    (const double*)nullptr, (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0,
-                   (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, (float*)nullptr, (int*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+                   (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, (float*)nullptr, (int*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                   (const int*)(m->dflag.p + 0));
         FEM_LAUNCH(F_RASTER, s, k_finalize<6>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
                    m->loc.p);
         FEM_LAUNCH(F_RASTER, s, k_raster_small<R_MASS>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p,
@@ -693,7 +702,8 @@ fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s) {
     } else {
         FEM_LAUNCH(F_RASTER, s, k_raster<R_SCAT>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
                    (const double*)nullptr, (const float2*)nullptr, r, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P),
-                   m->partial.p, (float*)nullptr, (int*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+                   m->partial.p, (float*)nullptr, (int*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                   (const int*)(m->dflag.p + 0));
         FEM_LAUNCH(F_RASTER, s, k_finalize<3>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
                    m->loc.p);
         FEM_LAUNCH(F_RASTER, s, k_raster_small<R_SCAT>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p,
@@ -715,9 +725,10 @@ fem_status raster_errors_scratch(const int4* tri, const int2* vxy, int T, int N,
     FEM_LAUNCH(F_RASTER, s, k_item_expand, blocks, 256, 0, w.item_cnt, w.item_off, T, w.item_cap, w.item_tri, err);
     FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, w.grid, kRasterThreads, 0, tri, vxy, uv, (const float2*)nullptr, f, N,
                w.item_tri, w.item_off, n_items_dev, w.item_cap, item_pixels_for((long long)N * N), w.partial, (float*)nullptr,
-               (int*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+               (int*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, (const int*)err);
     FEM_LAUNCH(F_RASTER, s, k_finalize_err, std::max(1, std::min(w.grid, (T + 7) / 8)), 256, 0, w.item_cnt,
-               w.item_off, (const float2*)w.partial, T, tri, vxy, err_out, (unsigned long long*)nullptr);
+               w.item_off, (const float2*)w.partial, T, tri, vxy, err_out, (unsigned long long*)nullptr, w.item_cap,
+               (const int*)err);
     FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, std::max(1, std::min(blocks, w.grid / 2)), 256, 0, (const int*)nullptr,
                tri, vxy, uv, (const float2*)nullptr, f, N, T, err_out, (unsigned long long*)nullptr, (float*)nullptr,
                (int*)nullptr, nullptr);
@@ -869,8 +880,10 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fast(
     const int4* __restrict__ tri, const int2* __restrict__ vxy, const double* __restrict__ uv,
     const float2* __restrict__ uvf, const float* __restrict__ img, int N, const int* __restrict__ item_tri,
     const int* __restrict__ item_off, const int* __restrict__ item_cnt, const int* __restrict__ n_items_dev,
-    int item_cap, int item_px, float2* __restrict__ partial, int* __restrict__ item_done, FastOut F) {
+    int item_cap, int item_px, float2* __restrict__ partial, int* __restrict__ item_done, FastOut F,
+    const int* __restrict__ plan_err) {
     pdl_wait();
+    if (plan_err && *plan_err) return;  // an overflowing plan: as in k_raster
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1196,7 +1209,7 @@ fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, co
     note_bytes(F_RASTER, raster_err_bytes(m));
     FEM_LAUNCH(F_RASTER, s, k_raster_fast, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
                m->item_tri.p, m->item_off.p, m->item_cnt.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P),
-               (float2*)m->partial.p, m->item_done.p, F);
+               (float2*)m->partial.p, m->item_done.p, F, (const int*)(m->dflag.p + 0));
     FEM_LAUNCH(F_RASTER, s, k_raster_small_fast, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv, uvf, f,
                m->N, T, F);
     // bracket and classification
@@ -1207,7 +1220,8 @@ fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, co
     // exact float-float keys of the band
     FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv, uvf, f, m->N,
                m->item_tri.p, m->item_off.p, cnt + 2, (int)m->band_items.n, item_pixels_for(m->P), m->partial.p,
-               (float*)nullptr, (int*)nullptr, m->item_cnt.p, m->item_done.p, m->keys.p, m->keyc.p, m->band_items.p);
+               (float*)nullptr, (int*)nullptr, m->item_cnt.p, m->item_done.p, m->keys.p, m->keyc.p, m->band_items.p,
+               (const int*)(m->dflag.p + 0));
     FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, small_grid(m), 256, 0, m->band_small.p, m->tri.p, m->vxy.p, uv,
                uvf, f, m->N, T, m->keys.p, m->keyc.p, (float*)nullptr, (int*)nullptr, cnt + 3);
     return FEM_OK;
@@ -1236,7 +1250,8 @@ extern "C" fem_status fem_triangle_error_bounds(fem_mesh* m, const double* uv_de
     FastOut F{lo_dev, hi_dev, m->fast_hist.p, m->fast_hist.p + kFastBins};
     FEM_LAUNCH(F_RASTER, s, k_raster_fast, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv_dev,
                (const float2*)nullptr, f_dev, m->N, m->item_tri.p, m->item_off.p, m->item_cnt.p, m->dcount.p + 0,
-               (int)m->item_tri.n, item_pixels_for(m->P), (float2*)m->partial.p, m->item_done.p, F);
+               (int)m->item_tri.n, item_pixels_for(m->P), (float2*)m->partial.p, m->item_done.p, F,
+               (const int*)(m->dflag.p + 0));
     FEM_LAUNCH(F_RASTER, s, k_raster_small_fast, small_grid(m), 256, 0, (const int*)nullptr, m->tri.p, m->vxy.p,
                uv_dev, (const float2*)nullptr, f_dev, m->N, T, F);
     int e = 0;

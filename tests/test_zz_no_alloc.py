@@ -65,3 +65,41 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(fem):
     with pytest.raises(fem.FemError) as e:
         fem.fem_triangle_errors_noalloc(4097, xy, big[:2], uv, f2, err[:2])
     assert e.value.status == fem.FEM_E_SHAPE
+
+
+def test_noalloc_allocates_no_device_memory(oracle_mod, fem):
+    # the defining property: after the first calls (which load the library's
+    # kernels and look up the fixed array's address), a call leaves the
+    # device's free memory exactly where it was
+    m, xy, tri4, uv, f = _case(oracle_mod, fem, 257, 1, 0.03)
+    err = torch.empty((tri4.shape[0],), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        fem.fem_triangle_errors_noalloc(257, xy, tri4, uv, f, err)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        fem.fem_triangle_errors_noalloc(257, xy, tri4, uv, f, err)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_noalloc_overflow_is_reported_and_the_next_call_is_correct(oracle_mod, fem):
+    # 200 copies of the two image-sized triangles of a 2049 x 2049 image: every
+    # index is in range, but the triangles need about 410k rasterisation items,
+    # more than the fixed scratch holds (3 * 65536 + 2049^2 / 128 + 1024)
+    n = 2049
+    xy = torch.tensor([[0, 0], [n - 1, 0], [0, n - 1], [n - 1, n - 1]], dtype=torch.int32, device="cuda")
+    tri4 = torch.tensor([[0, 3, 2, 0], [3, 0, 1, 0]] * 100, dtype=torch.int32, device="cuda")
+    uv = torch.zeros(4, dtype=torch.float64, device="cuda")
+    f = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    err = torch.zeros(tri4.shape[0], dtype=torch.float64, device="cuda")
+    with pytest.raises(fem.FemError) as e:
+        fem.fem_triangle_errors_noalloc(n, xy, tri4, uv, f, err)
+    assert e.value.status == fem.FEM_E_INVALID and "items" in str(e.value)
+    # the context is still usable and a valid call after it is exact
+    m, xy2, tri2, uv2, f2 = _case(oracle_mod, fem, 257, 1, 0.03)
+    ref = m.triangle_errors(uv2, f2)
+    out = torch.full((tri2.shape[0],), -1.0, dtype=torch.float64, device="cuda")
+    fem.fem_triangle_errors_noalloc(257, xy2, tri2, uv2, f2, out)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out.cpu().numpy(), ref.cpu().numpy(), rtol=1e-12, atol=1e-300)
