@@ -222,6 +222,22 @@ FEM_API fem_status fem_tonal_opt(fem_mesh *m, const float *f_dev, float *g_dev, 
  *   gbar_dev out: nmask float32 */
 FEM_API fem_status fem_adjoint(fem_mesh *m, const float *r_dev, float *gbar_dev, const fem_params *p, void *stream);
 
+/* Tonal loss of Sec. 4 (eq. 4) and its gradient, whose zero is the normal
+ * equations (eq. 5):  loss = 1/2 ||B g - f||^2,  grad = B^T (B g - f).
+ * One inpainting solve gives the vertex values v = E g; the loss is half the
+ * sum of the per-triangle squared errors of fem_triangle_errors (float-float
+ * per pixel, FP64 per triangle and in the total); the gradient is
+ * E^T (M v - P^T f) with the pixel-mass matrix M = P^T P, so no pixel
+ * residual is formed, and takes one adjoint solve.
+ *   g_dev    in : nmask float32 mask-vertex values
+ *   f_dev    in : width*height float32 image
+ *   loss_dev out: 1 float64 (device), or NULL
+ *   grad_dev out: nmask float32, or NULL (at least one of the two is needed)
+ * The solves use p->tol / p->inner_tol and p->precision.  Synchronises
+ * `stream`. */
+FEM_API fem_status fem_tonal_loss(fem_mesh *m, const float *g_dev, const float *f_dev, double *loss_dev,
+                                  float *grad_dev, const fem_params *p, void *stream);
+
 /* ---------------------------------------------------------------------
  * Serving: continuous batching of whole data-optimisation jobs (configuration
  * 5 of the benchmarks; the paper has no serving layer).  A server owns

@@ -45,7 +45,7 @@ _STATUS = {0: "FEM_OK", 1: "FEM_E_INVALID", 2: "FEM_E_SHAPE", 3: "FEM_E_OOM", 4:
 
 EXPORTED = ["fem_params_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_info", "fem_mesh_export",
             "fem_mesh_import", "fem_mesh_curve_order", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_triangle_error_bounds", "fem_triangle_errors_noalloc", "fem_rasterize", "fem_spatial_refine",
-            "fem_tonal_opt", "fem_adjoint", "fem_mesh_stats", "fem_last_error", "fem_profile_enable",
+            "fem_tonal_opt", "fem_adjoint", "fem_tonal_loss", "fem_mesh_stats", "fem_last_error", "fem_profile_enable",
             "fem_profile_read", "fem_launch_count", "fem_selftest_wait_timeout", "fem_server_create",
             "fem_server_submit", "fem_server_wait", "fem_server_result", "fem_server_release", "fem_server_destroy"]
 
@@ -83,6 +83,7 @@ _sig = {
     "fem_spatial_refine": (_i, [_vp, _vp, ctypes.c_double, _pp, _vp]),
     "fem_tonal_opt": (_i, [_vp, _vp, _vp, _pp, _vp]),
     "fem_adjoint": (_i, [_vp, _vp, _vp, _pp, _vp]),
+    "fem_tonal_loss": (_i, [_vp, _vp, _vp, _vp, _vp, _pp, _vp]),
     "fem_mesh_stats": (_i, [_vp, ctypes.POINTER(fem_stats)]),
     "fem_last_error": (ctypes.c_char_p, []),
     "fem_profile_enable": (None, [_i]),
@@ -271,6 +272,16 @@ def fem_adjoint(h: int, r, gbar, p: fem_params | None = None, stream=None):
     torch = _torch()
     _check(_lib.fem_adjoint(h, _dev_ptr(r, torch.float32, None, "r"), _dev_ptr(gbar, torch.float32, K, "gbar"),
                             ctypes.byref(p or params()), _stream(stream)), "fem_adjoint")
+
+
+def fem_tonal_loss(h: int, g, f, loss=None, grad=None, p: fem_params | None = None, stream=None):
+    """loss (0-dim float64) = 1/2 ||B g - f||^2 and grad (nmask float32) =
+    B^T (B g - f), both written by the library into the given CUDA tensors."""
+    V, T, K = fem_mesh_info(h)
+    torch = _torch()
+    _check(_lib.fem_tonal_loss(h, _dev_ptr(g, torch.float32, K, "g"), _dev_ptr(f, torch.float32, None, "f"),
+                               _dev_ptr(loss, torch.float64, 1, "loss"), _dev_ptr(grad, torch.float32, K, "grad"),
+                               ctypes.byref(p or params()), _stream(stream)), "fem_tonal_loss")
 
 
 def fem_mesh_stats(h: int) -> dict:

@@ -4,13 +4,14 @@
 backward is the hand-written adjoint kernel path (fem_adjoint): dL/dg =
 B^T dL/du.  ``TonalLoss.apply(g, f, mesh)`` returns 1/2 ||B g - f||^2 with
 gradient B^T (B g - f), the quantity whose zero is the normal equations
-(eq. 5).  Both run entirely in the CUDA library.
+(eq. 5), both from fem_tonal_loss.  Every step of the method runs in the
+CUDA library; these classes only marshal tensors.
 """
 from __future__ import annotations
 
 import torch
 
-from . import Mesh, params
+from . import Mesh, fem_tonal_loss, params
 
 
 class FemInpaint(torch.autograd.Function):
@@ -27,19 +28,23 @@ class FemInpaint(torch.autograd.Function):
 
 
 class TonalLoss(torch.autograd.Function):
+    """The loss and its gradient both come from one library call
+    (fem_tonal_loss): the gradient B^T (B g - f) is computed in the forward
+    pass when g requires it, and the backward pass only applies the chain
+    rule's scalar factor."""
+
     @staticmethod
     def forward(ctx, g: torch.Tensor, f: torch.Tensor, mesh: Mesh, p=None):
-        u = mesh.inpaint(g.detach().contiguous(), p)
-        r = (u - f).contiguous()
-        ctx.mesh, ctx.p = mesh, p
-        ctx.save_for_backward(r)
-        return 0.5 * (r.double() ** 2).sum()
+        loss = torch.empty((), dtype=torch.float64, device=g.device)
+        grad = torch.empty(mesh.nmask, dtype=torch.float32, device=g.device) if ctx.needs_input_grad[0] else None
+        fem_tonal_loss(mesh.h, g.detach().to(torch.float32).contiguous(), f.detach().contiguous(), loss, grad, p)
+        ctx.save_for_backward(grad)
+        return loss
 
     @staticmethod
     def backward(ctx, grad_out: torch.Tensor):
-        (r,) = ctx.saved_tensors
-        gbar = ctx.mesh.adjoint(r, ctx.p)
-        return gbar * grad_out.to(gbar.dtype), None, None, None
+        (grad,) = ctx.saved_tensors
+        return grad * grad_out.to(grad.dtype), None, None, None
 
 
 __all__ = ["FemInpaint", "TonalLoss", "params"]

@@ -288,6 +288,7 @@ struct fem_mesh {
     fem::DArr<double> Moff;         // 8*V pixel-mass off-diagonal per direction
     fem::DArr<double> Mdiag;        // V
     fem::DArr<double> tv, ty, tz, tg, tr, tp, tw, tc;  // tonal work vectors
+    fem::DArr<double> lossk, lossred;  // tonal loss: per-triangle squared errors, block partial sums
 
     // host staging (pinned)
     void* host_stage = nullptr;

@@ -487,6 +487,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->inc, s); release(m->loc, s); release(m->Moff, s); release(m->Mdiag, s);
     release(m->tv, s); release(m->ty, s); release(m->tz, s); release(m->tg, s);
     release(m->tr, s); release(m->tp, s); release(m->tw, s); release(m->tc, s);
+    release(m->lossk, s); release(m->lossred, s);
     cudaStreamSynchronize(s);
     if (m->host_stage) cudaFreeHost(m->host_stage);
     if (m->round_ev) cudaEventDestroy(m->round_ev);

@@ -305,6 +305,46 @@ __global__ void k_d2f(int n, const double* __restrict__ a, float* __restrict__ b
     if (i < n) b[i] = (float)a[i];
 }
 
+// b = a - b
+__global__ void k_sub_from(int n, const double* __restrict__ a, double* __restrict__ b) {
+    pdl_wait();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i] - b[i];
+}
+
+// per-block partial sums of x (grid-stride, fixed order within a block)
+__global__ void k_sum_partial(long long n, const double* __restrict__ x, double* __restrict__ partial) {
+    pdl_wait();
+    __shared__ double sh[kVecThreads / 32];
+    double t = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        t += x[i];
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kVecThreads / 32; ++w) s += sh[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
+// *out = scale * (sum of the n partials), one block
+__global__ void k_final_sum_scaled(int n, const double* __restrict__ partial, double scale, double* __restrict__ out) {
+    pdl_wait();
+    __shared__ double sh[kVecThreads / 32];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t += partial[i];
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kVecThreads / 32; ++w) s += sh[w];
+        *out = scale * s;
+    }
+}
+
 static int vec_grid(fem_mesh* m) { return 2 * m->num_sms; }
 
 // read one device double (synchronises the stream)
@@ -523,5 +563,63 @@ extern "C" fem_status fem_adjoint(fem_mesh* m, const float* r_dev, float* gbar_d
     FEM_TRY(apply_ET(m, m->ty.p, m->tw.p, c, s));
     FEM_LAUNCH(F_TONAL, s, k_d2f, (m->nK + 255) / 256, 256, 0, m->nK, m->tw.p, gbar_dev);
     FEM_CUDA(cudaStreamSynchronize(s));
+    return FEM_OK;
+}
+
+// Tonal loss of Sec. 4 (eq. 4) and its gradient, the left side of the normal
+// equations (eq. 5):  L(g) = 1/2 ||B g - f||^2,  dL/dg = B^T (B g - f).
+// v = E g comes from one inpainting solve.  L is half the sum of the
+// per-triangle squared errors of the error pass (float-float per pixel,
+// FP64 per triangle).  The gradient never forms the pixel residual:
+// P^T (P v - f) = M v - P^T f with the pixel-mass matrix M = P^T P, then
+// E^T (one adjoint solve) maps it to the mask vertices.
+extern "C" fem_status fem_tonal_loss(fem_mesh* m, const float* g_dev, const float* f_dev, double* loss_dev,
+                                     float* grad_dev, const fem_params* p, void* stream) {
+    if (!m || !g_dev || !f_dev || (!loss_dev && !grad_dev)) {
+        set_error("fem_tonal_loss: null argument (g, f and at least one of loss, grad are required)");
+        return FEM_E_INVALID;
+    }
+    fem_params dflt;
+    fem_params_default(&dflt);
+    if (!p) p = &dflt;
+    cudaStream_t s = (cudaStream_t)stream;
+    m->last_stream = s;
+    m->stats = fem_stats{};
+    const bool fp64 = p->precision == FEM_PREC_FP64;
+    // v = E g: g at the mask vertices, the Laplace solution at the unknown ones
+    FEM_TRY(set_uv_from_g(m, g_dev, s));
+    int it = 0;
+    double rel = 0.0;
+    FEM_TRY(solve_laplace(m, fp64, p->tol, p->maxit, s, &it, &rel));
+    if (loss_dev) {
+        FEM_TRY(ensure(m->lossk, (size_t)m->T, s));
+        FEM_TRY(raster_errors(m, m->uv.p, nullptr, f_dev, m->lossk.p, s));
+        const int G = vec_grid(m);
+        FEM_TRY(ensure(m->lossred, (size_t)G, s));
+        FEM_LAUNCH(F_TONAL, s, k_sum_partial, G, kVecThreads, 0, (long long)m->T, (const double*)m->lossk.p,
+                   m->lossred.p);
+        FEM_LAUNCH(F_TONAL, s, k_final_sum_scaled, 1, kVecThreads, 0, G, (const double*)m->lossred.p, 0.5, loss_dev);
+    }
+    if (grad_dev) {
+        FEM_TRY(prepare_tonal(m, s));
+        FEM_TRY(ensure_tonal_vectors(m, s));
+        FEM_TRY(scatter_PT(m, f_dev, s));  // ty = P^T f
+        const int G = vec_grid(m);
+        FEM_LAUNCH(F_TONAL, s, k_mass_spmv, G, kVecThreads, 0, m->V, (const double*)m->Mdiag.p,
+                   (const double*)m->Moff.p, (const int*)m->nbr.p, (const double*)m->uv.p, m->tv.p, m->red.p);
+        FEM_LAUNCH(F_TONAL, s, k_sub_from, (m->V + 255) / 256, 256, 0, m->V, (const double*)m->tv.p, m->ty.p);
+        InnerCfg c{fp64, p->inner_tol, p->maxit, false};
+        FEM_TRY(apply_ET(m, m->ty.p, m->tw.p, c, s));
+        FEM_LAUNCH(F_TONAL, s, k_d2f, (m->nK + 255) / 256, 256, 0, m->nK, (const double*)m->tw.p, grad_dev);
+    }
+    int e = 0;
+    FEM_CUDA(cudaMemcpyAsync(&e, m->dflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    if (e) {
+        cudaMemsetAsync(m->dflag.p, 0, sizeof(int), s);
+        m->plan_version = -1;
+        set_error("fem_tonal_loss: rasterisation plan overflow");
+        return (fem_status)e;
+    }
     return FEM_OK;
 }

@@ -49,6 +49,7 @@ def test_defaults_and_host_checks(fem):
     assert fem._lib.fem_spatial_refine(None, None, ctypes.c_double(0.1), None, None) == fem.FEM_E_INVALID
     assert fem._lib.fem_tonal_opt(None, None, None, None, None) == fem.FEM_E_INVALID
     assert fem._lib.fem_adjoint(None, None, None, None, None) == fem.FEM_E_INVALID
+    assert fem._lib.fem_tonal_loss(None, None, None, None, None, None, None) == fem.FEM_E_INVALID
     assert b"null" in fem._lib.fem_last_error()
     h = ctypes.c_void_p()
     for bad in ((256, 256), (257, 129), (2, 2), (0, 0)):

