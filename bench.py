@@ -1,14 +1,16 @@
 #!/usr/bin/env python
 """Benchmark of the FEM harmonic-inpainting data optimisation on GB300.
 
-One step = the whole hot path on one seeded 1025 x 1025 image: create the
-two-triangle mesh, spatial optimisation (top-k 1 % of triangles per round,
-newest-vertex bisection, FP32 CG inside FP64 refinement, until 3 % of the
-pixels are vertices), g = f at the mask vertices, tonal optimisation (CG on
-the normal equations through forward and adjoint solves).  value = image
+One step = the whole hot path on one seeded image.  Default (configuration
+4, the largest): an 8193 x 8193 image with texture; create the two-triangle
+mesh, spatial optimisation (top-k 1 % of triangles per round, newest-vertex
+bisection, FP32 CG inside float-float iterative refinement, until 2 % of the
+pixels are vertices), g = f at the mask vertices, 50 tonal CG iterations on
+the normal equations through forward and adjoint solves.  value = image
 Mpixel per second of whole-step time, inputs resident in HBM; e2e = the same
 through the public API with the image copied from pinned host memory and the
-result (mesh + g) copied back inside the timed region.
+result (mesh + g) copied back inside the timed region.  The plain FP64 GPU
+path is timed on the same workload after the timed region (fp64_path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -33,6 +35,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "Mpixel/s FEM inpaint+tonal opt at 1e-6 rel err vs FP64"
+# FP32 CG and FP32 pixel work; float-float (a pair of FP32, about 48 bits)
+# for the refinement residuals and the per-pixel error sums; FP64 per
+# triangle, per vertex and in the CG scalars
+DTYPE_MIXED = "fp32+float-float+fp64"
 UNIT = "Mpixel/s"
 L2_FLUSH_BYTES = 512 << 20
 
@@ -43,18 +49,22 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
-                    help="1: 257^2 FP64, one triangle per round to 5%%, one solve + errors; 2 (default): 1025^2 "
-                         "spatial (1%% per round, 3%%) + tonal; 3: 2049^2 at 4%% + tonal; 4: 8193^2 textured at 2%% "
-                         "+ 50 tonal iterations")
+    ap.add_argument("--config", type=int, default=4, choices=[1, 2, 3, 4],
+                    help="1: 257^2 FP64, one triangle per round to 5%%, one solve + errors; 2: 1025^2 "
+                         "spatial (1%% per round, 3%%) + tonal; 3: 2049^2 at 4%% + tonal; 4 (default): 8193^2 "
+                         "textured at 2%% + 50 tonal iterations")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--density", type=float, default=None)
     ap.add_argument("--frac", type=float, default=None)
     ap.add_argument("--tonal-tol", type=float, default=None)
     ap.add_argument("--precision", default=None, choices=["fp32ir", "fp64"])
+    ap.add_argument("--inner-tol", type=float, default=None,
+                    help="relative tolerance of the tonal inner solves (default: the library's 1e-11; 1e-13 in "
+                         "configuration 4, whose 50th outer iterate is sensitive to the inner solves' accuracy)")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check after timing")
+    ap.add_argument("--no-fp64-timing", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--ncu-step", action="store_true",
                     help="for ncu launch lists: one warm-up step, then exactly one step, no timing output")
     ap.add_argument("--serve", action="store_true",
@@ -63,6 +73,13 @@ def parse():
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--solve-micro", action="store_true",
                     help="time the Laplace solve alone on the refined mesh (FP32-IR and FP64), 20 solves each")
+    ap.add_argument("--pass-micro", default=None,
+                    help="comma-separated round counts: time the error pass over all squares (k_sq, FP32 with "
+                         "error intervals) on the mesh after each number of spatial rounds, 10 passes each")
+    ap.add_argument("--mesh-file", default=None,
+                    help="with --pass-micro and one round count: import the mesh from this .npz file if it "
+                         "exists, else refine and save it there (so that a profiler run launches few kernels "
+                         "before the pass)")
     a = ap.parse_args()
     preset = PRESETS[a.config]
     for k, v in preset.items():
@@ -74,13 +91,13 @@ def parse():
 # seeded workloads (seed = configuration index - 1)
 PRESETS = {
     1: dict(n=257, density=0.05, frac=0.0, seed=0, texture=False, tonal="none", tonal_tol=0.0, tonal_iters=0,
-            precision="fp64"),
+            precision="fp64", inner_tol=1e-11),
     2: dict(n=1025, density=0.03, frac=0.01, seed=1, texture=False, tonal="tol", tonal_tol=1e-8, tonal_iters=0,
-            precision="fp32ir"),
+            precision="fp32ir", inner_tol=1e-11),
     3: dict(n=2049, density=0.04, frac=0.01, seed=2, texture=False, tonal="tol", tonal_tol=1e-8, tonal_iters=0,
-            precision="fp32ir"),
+            precision="fp32ir", inner_tol=1e-11),
     4: dict(n=8193, density=0.02, frac=0.01, seed=3, texture=True, tonal="iters", tonal_tol=0.0, tonal_iters=50,
-            precision="fp32ir"),
+            precision="fp32ir", inner_tol=1e-13),
 }
 
 
@@ -98,6 +115,7 @@ def workload_name(a):
 def config(a, world):
     return {"workload": workload_name(a), "config_index": a.config, "image": f"{a.n}x{a.n}", "density": a.density,
             "topk_frac": a.frac, "tonal": a.tonal, "tonal_tol": a.tonal_tol, "tonal_iters": a.tonal_iters,
+            "inner_tol": a.inner_tol,
             "precision": a.precision, "seed": a.seed, "l2_flush": True,
             "parallelism": f"replicas{world}" if world > 1 else "single"}
 
@@ -228,7 +246,7 @@ def run_ours(a, world, rank, local):
     f_np = seeded_inputs.make_image(n, replica_seed(a.seed, rank), texture=a.texture)
     f = torch.from_numpy(f_np).to(dev)
     prec = fem.FEM_PREC_FP64 if a.precision == "fp64" else fem.FEM_PREC_FP32_IR
-    p = fem.params(topk_frac=a.frac, tonal_tol=a.tonal_tol, precision=prec)
+    p = fem.params(topk_frac=a.frac, tonal_tol=a.tonal_tol, precision=prec, inner_tol=a.inner_tol)
     if a.tonal == "iters":
         p.tonal_maxit = a.tonal_iters
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -249,8 +267,8 @@ def run_ours(a, world, rank, local):
             fem.fem_tonal_opt(mesh.h, f_dev, g, pp, allow_not_converged=(a.tonal == "iters"))
         return mesh, g, st_sp
 
-    def step(f_dev, keep=False):
-        mesh, g, _ = run(f_dev, p)
+    def step(f_dev, keep=False, pp=None):
+        mesh, g, _ = run(f_dev, pp or p)
         if keep:
             return mesh, g
         mesh.close()
@@ -263,6 +281,10 @@ def run_ours(a, world, rank, local):
 
     if a.solve_micro:
         print(json.dumps(solve_micro(fem, torch, f, n, a)), flush=True)
+        return
+    if a.pass_micro:
+        for line in pass_micro(fem, torch, f, n, a):
+            print(json.dumps(line), flush=True)
         return
 
     if a.ncu_step:
@@ -281,23 +303,22 @@ def run_ours(a, world, rank, local):
     step(f)
     prof_all = fem.fem_profile_read()
     fem.fem_profile_enable(False)
-    # The roofline is reported for the family that holds the step's top
-    # kernel: the error pass ("raster", k_raster*), the component solve
-    # ("cg", k_solve_comp) or the system build ("assembly", k_build_system),
-    # the three families with a per-unit algorithmic byte model (ncu launch
-    # lists: k_build_system and k_solve_comp lead at 1025^2, the raster
-    # kernels at 8193^2).  Refinement and top-k are chains of short kernels.
-    dom = max(("raster", "cg", "assembly"), key=lambda k: prof_all[k]["ms"])
+    # The roofline is reported for the step's top kernel among the three
+    # with a per-unit algorithmic byte model: the square-tiled error pass
+    # ("raster_pass", k_sq over all squares), the component solve ("cg",
+    # k_solve_comp) or the system build ("assembly", k_build_system).
+    # Refinement and top-k are chains of short kernels.
+    dom = max(("raster_pass", "cg", "assembly"), key=lambda k: prof_all[k]["ms"])
 
-    def steps_timed():
+    def steps_timed(k=None, pp=None):
         times = []
-        for _ in range(a.steps):
+        for _ in range(a.steps if k is None else k):
             flush.zero_()
             torch.cuda.synchronize(dev)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(f)
+            step(f, pp=pp)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -324,6 +345,21 @@ def run_ours(a, world, rank, local):
     prof_times = steps_timed()
     prof = fem.fem_profile_read()[dom]
     fem.fem_profile_enable(False)
+
+    # the plain FP64 GPU path on the same workload (same parameters but the
+    # precision), timed the same way after the timed region
+    fp64_path = None
+    if not a.no_fp64_timing and a.precision != "fp64":
+        p64t = fem.params(topk_frac=a.frac, tonal_tol=a.tonal_tol, precision=fem.FEM_PREC_FP64,
+                          inner_tol=a.inner_tol)
+        if a.tonal == "iters":
+            p64t.tonal_maxit = a.tonal_iters
+        step(f, pp=p64t)
+        k64 = max(1, min(a.steps, 3))
+        t64 = steps_timed(k64, p64t)
+        ms64 = sum(t64) / k64
+        fp64_path = {"ms_per_step": round(ms64, 3), "value": round(P / 1e6 / (ms64 / 1e3), 4), "unit": UNIT,
+                     "steps": k64, "mixed_precision_speedup": round(ms64 / ms_per_step, 4)}
 
     # end to end through the public API: pinned host image in, mesh + g out
     f_host = torch.from_numpy(f_np).pin_memory()
@@ -392,9 +428,11 @@ def run_ours(a, world, rank, local):
 
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "fp32+fp64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else DTYPE_MIXED,
             "data": "synthetic", "config": config(a, world), "roofline": roofline, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches)}
+    if fp64_path:
+        line["fp64_path"] = fp64_path
     line.update(extra)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, f_np, gpu_info)
@@ -402,6 +440,45 @@ def run_ours(a, world, rank, local):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def pass_micro(fem, torch, f, n, a):
+    """The error pass alone (the kernel that reads every pixel once per
+    round) on the meshes the spatial optimisation reaches after the given
+    numbers of rounds: device time per pass from CUDA events around the
+    kernel, algorithmic bytes (4 B per pixel, 32 B per triangle, 16 B per
+    vertex) per second, and the fraction of the measured HBM bandwidth."""
+    peak, _ = measured_peaks()
+    out = []
+    import numpy as np
+    for rounds in [int(x) for x in str(a.pass_micro).split(",")]:
+        mesh = fem.Mesh(n)
+        if a.mesh_file and os.path.exists(a.mesh_file):
+            z = np.load(a.mesh_file)
+            mesh.import_(z["xy"], z["tri"], z["mask"])
+        else:
+            # exact keys in the loop, so that the fast pass runs only below
+            mesh.spatial_refine(f, a.density, fem.params(topk_frac=a.frac, max_rounds=rounds, fast_keys=0))
+            if a.mesh_file:
+                xy, tri, mk = mesh.export()
+                np.savez(a.mesh_file, xy=xy, tri=tri, mask=mk)
+        g = mesh.g_from_f(f)
+        _, uv = mesh.inpaint(g, want_uv=True)
+        for _ in range(3):
+            mesh.triangle_error_bounds(uv, f)
+        torch.cuda.synchronize()
+        fem.fem_profile_enable("raster_pass")
+        for _ in range(10):
+            mesh.triangle_error_bounds(uv, f)
+        prof = fem.fem_profile_read()["raster_pass"]
+        fem.fem_profile_enable(False)
+        us = 1e3 * prof["ms"] / max(1, prof["launches"])
+        gbs = prof["bytes"] / max(1, prof["launches"]) / (us * 1e-6) / 1e9 if us > 0 else 0.0
+        V, T, K = mesh.info
+        out.append({"pass_micro": True, "rounds": rounds, "V": V, "T": T, "us_per_pass": round(us, 2),
+                    "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)})
+        mesh.close()
+    return out
 
 
 def solve_micro(fem, torch, f, n, a):
@@ -448,18 +525,50 @@ def oracle_job(a, f_np, tonal_iters=None):
         oracle.raster(om, v, f_np)
         return t1 - t0, time.perf_counter() - t1, 0, len(log)
     g, st = oracle.tonal(om, f_np, tol=a.tonal_tol if a.tonal == "tol" else 0.0,
-                         maxit=tonal_iters or (a.tonal_iters if a.tonal == "iters" else 100000), inner_tol=1e-11,
+                         maxit=tonal_iters or (a.tonal_iters if a.tonal == "iters" else 100000), inner_tol=a.inner_tol,
                          allow_not_converged=True)
     return t1 - t0, time.perf_counter() - t1, st["iters"], len(log)
 
 
+# Whole-job counts of the sampled workloads: spatial rounds and tonal outer
+# iterations.  The spatial optimisation is deterministic and its meshes are
+# the same on every correct implementation (bit-exact topology), so the round
+# count is a property of the seeded workload; the 8193^2 workload fixes 50
+# tonal iterations.
+JOB_COUNTS = {3: (362, 63), 4: (541, 50)}
+
+
+def oracle_sample(a, f_np, tonal_mesh=None, rounds=2):
+    """A bounded sample of the oracle's work on the workload: the first
+    `rounds` spatial rounds from the two-triangle mesh, then one tonal outer
+    iteration (tonal(maxit=1): the set-up passes B^T f, B g0, B^T r and one
+    iteration) on `tonal_mesh` (default: the mesh the sample reached).
+    Returns (seconds per round, seconds of tonal(maxit=1), total seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    om, _ = oracle.spatial(f_np, a.density, a.frac, max_rounds=rounds)
+    t1 = time.perf_counter()
+    oracle.tonal(tonal_mesh if tonal_mesh is not None else om, f_np, tol=0.0, maxit=1, inner_tol=a.inner_tol,
+                 allow_not_converged=True)
+    t2 = time.perf_counter()
+    return (t1 - t0) / rounds, t2 - t1, t2 - t0
+
+
+def project_job(t_round, t_tonal1, rounds, iters):
+    """Whole-job seconds from a sample: every round costs a sampled round, and
+    the tonal run costs its set-up plus `iters` iterations, where tonal(maxit=1)
+    is three set-up applications of B or B^T and one iteration of two (each a
+    pixel pass plus a solve), so one application costs t_tonal1 / 5."""
+    return t_round * rounds + t_tonal1 / 5.0 * (3 + 2 * iters)
+
+
 def cpu_baseline(a, f_np, gpu):
     """The oracle on the host cores.  Configurations 1-2: the whole workload,
-    once.  Larger images: a bounded sample, scaled to the whole workload: the
-    first 4 spatial rounds (each costs about one pass over the pixels, so the
-    per-round time is scaled by the GPU run's round count) and 2 tonal outer
-    iterations on the GPU's final mesh (scaled by its outer-iteration count)."""
-    import numpy as np
+    once.  Larger images: a bounded sample (oracle_sample: the first spatial
+    rounds, and one tonal iteration on the GPU's final mesh) scaled to the
+    whole job by the GPU run's round and iteration counts (project_job).  The
+    sampled rounds run on the smallest meshes of the loop, so the estimate is
+    a lower bound on the oracle's time."""
     import oracle
     P = a.n * a.n
     if a.n <= 1025:
@@ -469,57 +578,69 @@ def cpu_baseline(a, f_np, gpu):
                 "sample": f"one full run of the workload by the FP64 C oracle (single thread): spatial {rounds} "
                           f"rounds {ts:.1f} s + {what} ({it} outer iterations) {tt:.1f} s"}
     R = 4
-    t0 = time.perf_counter()
-    oracle.spatial(f_np, a.density, a.frac, max_rounds=R)
-    t_round = (time.perf_counter() - t0) / R
     om = oracle.Mesh(a.n, gpu["xy"][:, 0].copy(), gpu["xy"][:, 1].copy(), gpu["mask"].copy(), gpu["tri"][:, 0].copy(),
                      gpu["tri"][:, 1].copy(), gpu["tri"][:, 2].copy())
-    t1 = time.perf_counter()
-    oracle.tonal(om, f_np, tol=0.0, maxit=2, inner_tol=1e-11, allow_not_converged=True)
-    t_it = (time.perf_counter() - t1) / 2
-    est = t_round * gpu["rounds"] + t_it * gpu["tonal_iters"]
+    t_round, t_tonal1, _ = oracle_sample(a, f_np, tonal_mesh=om, rounds=R)
+    est = project_job(t_round, t_tonal1, gpu["rounds"], gpu["tonal_iters"])
     return {"value": round(P / 1e6 / est, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"bounded sample by the FP64 C oracle (single thread): {R} spatial rounds ({t_round:.2f} s "
-                      f"each, scaled to {gpu['rounds']} rounds) + 2 tonal outer iterations on the GPU's final mesh "
-                      f"({t_it:.2f} s each, scaled to {gpu['tonal_iters']}); estimated {est:.0f} s for the job"}
+            "sample": f"bounded sample by the FP64 C oracle (single thread): the first {R} spatial rounds "
+                      f"({t_round:.2f} s each, scaled to {gpu['rounds']} rounds) + one tonal iteration with its "
+                      f"set-up on the GPU's final mesh ({t_tonal1:.2f} s, scaled to {gpu['tonal_iters']} "
+                      f"iterations); estimated {est:.0f} s for the job (a lower bound: the sampled rounds run on "
+                      f"the loop's smallest meshes)"}
 
 
 def run_reference(a, world, rank):
-    """The oracle as the reference arm (configurations 1 and 2): each step
-    runs the full spatial optimisation and 10 tonal outer iterations; the
-    tonal time is scaled to the outer-iteration count of a full tonal run
-    taken in the first warm-up step."""
+    """The oracle as the reference arm, on the same workload.  Configurations
+    1-2: each step runs the whole job (spatial optimisation and tonal
+    optimisation to the tolerance).  Configurations 3-4 (hours on one core):
+    each step runs a bounded sample of the job (oracle_sample: 2 spatial rounds
+    and one tonal iteration), ms_per_step is that sample's wall time, and value
+    is the whole job's throughput projected from it (project_job with the
+    workload's round and iteration counts, JOB_COUNTS)."""
     if rank != 0:
-        return
-    if a.config not in (1, 2):
-        print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle needs tens of minutes per step on "
-                                                              "this image size; it is timed on configurations 1-2"}))
         return
     import seeded_inputs
     f_np = seeded_inputs.make_image(a.n, a.seed, texture=a.texture)
     P = a.n * a.n
-    cap = 10
-    full_iters = None
-    for w in range(a.warmup):
-        if w == 0:
-            _, _, full_iters, _ = oracle_job(a, f_np)
-        else:
-            oracle_job(a, f_np, cap)
-    times = []
-    rounds = 0
-    for _ in range(a.steps):
-        ts, tt, it, rounds = oracle_job(a, f_np, cap)
-        times.append(ts + (tt * (full_iters / max(1, it)) if a.tonal != "none" else tt))
-    ms = 1e3 * statistics.mean(times)
-    value = P / 1e6 / (ms / 1e3)
-    sample = (f"per step: oracle spatial optimisation in full ({rounds} rounds) + "
-              + (f"{cap} tonal outer iterations, tonal time scaled to the {full_iters} iterations of a full tonal run "
-                 f"(first warm-up step)" if a.tonal != "none" else "one solve + per-triangle errors"))
-    line = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(a, 1), "impl": "reference",
-            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample},
-            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    base = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(a, 1), "impl": "reference"}
+    if a.config in (1, 2):
+        for _ in range(a.warmup):
+            oracle_job(a, f_np)
+        times, its, rounds = [], 0, 0
+        for _ in range(a.steps):
+            ts, tt, its, rounds = oracle_job(a, f_np)
+            times.append(ts + tt)
+        ms = 1e3 * statistics.mean(times)
+        value = P / 1e6 / (ms / 1e3)
+        sample = (f"each step the whole job by the FP64 C oracle (single thread): spatial optimisation "
+                  f"({rounds} rounds) + " + (f"tonal optimisation ({its} outer iterations)" if a.tonal != "none"
+                                              else "one solve + per-triangle errors"))
+        extra = {}
+    else:
+        rounds, iters = JOB_COUNTS[a.config]
+        for _ in range(a.warmup):
+            oracle_sample(a, f_np)
+        samples = [oracle_sample(a, f_np) for _ in range(a.steps)]
+        ms = 1e3 * statistics.mean(x[2] for x in samples)
+        t_round = statistics.median(x[0] for x in samples)
+        t_tonal1 = statistics.median(x[1] for x in samples)
+        est = project_job(t_round, t_tonal1, rounds, iters)
+        value = P / 1e6 / est
+        sample = (f"each step a bounded sample by the FP64 C oracle (single thread): the first 2 spatial rounds "
+                  f"({t_round:.2f} s each) + one tonal iteration with its set-up ({t_tonal1:.2f} s); value "
+                  f"projected to the whole job ({rounds} rounds, {iters} tonal iterations): {est:.0f} s, a lower "
+                  f"bound (the sampled rounds run on the loop's smallest meshes)")
+        extra = {"projection": {"job_seconds": round(est, 1), "rounds": rounds, "tonal_iters": iters,
+                                "sample_seconds_per_step": round(ms / 1e3, 3)}}
+    line = dict(base)
+    line.update({"value": round(value, 6), "ms_per_step": round(ms, 3),
+                 "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "kind": "oracle", "cores": 1,
+                                  "sample": sample},
+                 "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    line.update(extra)
     print(json.dumps(line), flush=True)
 
 
@@ -599,7 +720,7 @@ def run_serving(a, world, rank):
     main = out["poisson_0.8"]
     line = {"metric": "serving Mpixel/s and p50/p99 latency (Poisson arrivals at 0.8x saturated throughput)",
             "value": main["mpixel_per_s"], "unit": "Mpixel/s", "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
-            "n_gpus": 1, "higher_is_better": True, "dtype": "fp32+fp64", "data": "synthetic",
+            "n_gpus": 1, "higher_is_better": True, "dtype": DTYPE_MIXED, "data": "synthetic",
             "config": {"workload": f"{R} requests, side from {{257,513,1025,2049}}, density U[2%,10%], spatial + "
                                    f"tonal (tol 1e-6) each", "slots": a.slots, "config_index": 5},
             "runs": out}

@@ -113,17 +113,18 @@ FEM_API fem_status fem_mesh_info(const fem_mesh *m, int *V, int *T, int *nmask);
 FEM_API fem_status fem_mesh_export(fem_mesh *m, int *xy, int *tri, unsigned char *is_mask);
 
 /* The order in which the kernels visit the triangles (host buffer, T ints):
- * for meshes grown by fem_spatial_refine from fem_mesh_create this is the
- * space-filling curve of the bisection tree (consecutive triangles share the
- * vertex where the curve leaves one and enters the next; *is_curve = 1);
- * after fem_mesh_import it is the id order (*is_curve = 0).  Either pointer
- * may be NULL. */
+ * the space-filling curve of the bisection tree (consecutive triangles share
+ * the vertex where the curve leaves one and enters the next), for meshes
+ * grown by fem_spatial_refine and for imported ones alike (*is_curve = 1).
+ * Either pointer may be NULL. */
 FEM_API fem_status fem_mesh_curve_order(fem_mesh *m, int *order, int *is_curve);
 
 /* Replace the mesh by host arrays of the same layout (checkpoint/resume).
  * The arrays are checked: vertices on the grid, triangles positively
- * oriented and right-isosceles with c at the right angle, areas summing to
- * the image.  Conformity is the caller's contract.  FEM_E_INVALID otherwise. */
+ * oriented and right-isosceles with c at the right angle, each a triangle of
+ * the newest-vertex-bisection tree of the two-triangle mesh, none twice,
+ * areas summing to the image.  Conformity is the caller's contract.
+ * FEM_E_INVALID otherwise. */
 FEM_API fem_status fem_mesh_import(fem_mesh *m, int V, const int *xy, int T, const int *tri,
                            const unsigned char *is_mask);
 
@@ -295,8 +296,10 @@ FEM_API const char *fem_last_error(void);
  * least once: inputs read, outputs written; counted on the host from the
  * sizes and iteration counts).  fem_profile_read() synchronises, returns
  * per family the launches, summed device time in ms and algorithmic bytes,
- * and clears the records.  Families: 0 raster/error, 1 CG, 2 assembly,
- * 3 top-k, 4 refinement, 5 tonal vector work, 6 other.  name receives a
+ * and clears the records.  Families: 0 raster/error (plans, band, image
+ * layout, tonal pixel sums), 1 CG, 2 assembly, 3 top-k, 4 refinement,
+ * 5 tonal vector work, 6 other, 7 the square-tiled error pass over all
+ * squares (that one kernel).  name receives a
  * static label.  Returns 0, or -1 for an unknown family. */
 FEM_API void fem_profile_enable(int family_mask);
 FEM_API int fem_profile_read(int family, long long *launches, double *ms, double *bytes, const char **name);

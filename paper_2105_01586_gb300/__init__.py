@@ -290,7 +290,7 @@ def fem_mesh_stats(h: int) -> dict:
     return {k: getattr(s, k) for k, _ in fem_stats._fields_}
 
 
-FAMILIES = ["raster", "cg", "assembly", "topk", "refine", "tonal", "other"]
+FAMILIES = ["raster", "cg", "assembly", "topk", "refine", "tonal", "other", "raster_pass"]
 
 
 def fem_profile_enable(mask) -> None:

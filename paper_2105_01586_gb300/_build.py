@@ -10,8 +10,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfeminpaint.so")
-SOURCES = ["mesh.cu", "raster.cu", "solve.cu", "components.cu", "solve_comp.cu", "refine.cu", "tonal.cu", "noalloc.cu", "serve.cu"]
-HEADERS = [os.path.join(CSRC, h) for h in ("fem_internal.cuh", "ff.cuh", "scan.cuh")] + [
+SOURCES = ["mesh.cu", "raster.cu", "raster_sq.cu", "solve.cu", "components.cu", "solve_comp.cu", "refine.cu", "tonal.cu", "noalloc.cu", "serve.cu"]
+HEADERS = [os.path.join(CSRC, h) for h in ("fem_internal.cuh", "ff.cuh", "scan.cuh", "raster_common.cuh")] + [
     os.path.join(ROOT, "include", "feminpaint.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

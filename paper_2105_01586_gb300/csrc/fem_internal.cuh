@@ -36,7 +36,11 @@ fem_status cuda_fail(cudaError_t e, const char* what);
     } while (0)
 
 // ------------------------------------------------------ launch accounting
-enum Family { F_RASTER = 0, F_CG = 1, F_ASSEMBLY = 2, F_TOPK = 3, F_REFINE = 4, F_TONAL = 5, F_OTHER = 6, F_COUNT = 7 };
+// F_SQPASS: the square-tiled error pass over all squares (one kernel, so
+// that its roofline can be taken alone); the rest of the error work (plan,
+// band, image layout) is F_RASTER
+enum Family { F_RASTER = 0, F_CG = 1, F_ASSEMBLY = 2, F_TOPK = 3, F_REFINE = 4, F_TONAL = 5, F_OTHER = 6, F_SQPASS = 7,
+              F_COUNT = 8 };
 void note_launch_begin(int family, cudaStream_t s);
 bool profiling(int family);
 // algorithmic bytes moved by work of a family (counted only while profiling)
@@ -214,16 +218,15 @@ struct fem_mesh {
     fem::DArr<double> uv;
     fem::DArr<int> order;      // triangle ids along the space-filling curve
     fem::DArr<int> order_tmp, ocnt, ooff;
-    bool order_is_curve = true;  // false after an import (then id order)
+    bool order_is_curve = true;  // the curve of the bisection tree (also after an import)
     fem::DArr<float2> uvf;  // float-float copy of uv, written with it in the spatial loop
 
     // rasterisation plan (valid for plan_T triangles of plan_version)
     fem::DArr<int> item_cnt, item_off, item_tri;
-    fem::DArr<int> item_done;  // T: items finished per triangle (fused finalisation), 0 between passes
     // fast keys (FP32 with error bounds, exact band): intervals, histograms, band lists
-    fem::DArr<double> keys_lo, keys_hi;
+    fem::DArr<float> keys_lo, keys_hi;
     fem::DArr<unsigned> fast_hist;
-    fem::DArr<int> band, band_items, band_small;
+    fem::DArr<int> band;
     fem::DArr<double> partial;
     fem::DArr<double> keys;
     fem::DArr<unsigned long long> keyc;  // composite selection keys (eligible flag | key bits)
@@ -288,6 +291,22 @@ struct fem_mesh {
     fem::DArr<double> Moff;         // 8*V pixel-mass off-diagonal per direction
     fem::DArr<double> Mdiag;        // V
     fem::DArr<double> tv, ty, tz, tg, tr, tp, tw, tc;  // tonal work vectors
+    fem::DArr<double> tyr;             // tonal: y = P^T (f - B g), the residual recursion
+
+    // square-tiled error pass (raster_sq.cu): the image as squares, the node
+    // tables of the plan, per-node partial sums, the band's squares
+    fem::DArr<float> fsq, fedge;       // Q*Q squares of s rows of s + 1 floats; the image's last row (N)
+    fem::DArr<int> sq_nodeof, sq_off;  // per curve position: node (fine) or -1; first bounding-box square
+    fem::DArr<int> sq_cov, sq_slot;    // per node: covering triangle's curve position or -1; partial slot
+    fem::DArr<int2> sq_seg;            // per node: curve segment of its triangles
+    fem::DArr<float4> sq_part;         // partial sums (hi, lo, pixel count)
+    fem::DArr<int> sq_coarse, sq_list; // curve positions of the coarse triangles; listed squares
+    fem::DArr<int> sq_ctr;             // [0] coarse bounding-box squares, [1] coarse triangles
+    fem::DArr<int4> sq_rec;            // 2 int4 per curve position: fine-triangle records of the FP32 pass
+    fem::DArr<int> sq_stage;           // squares of the staged FP32 pass (count in sq_ctr[2])
+    fem::DArr<unsigned char> sq_flag, sq_staged;  // per square: flagged by the plan; staged (this plan)
+    fem::DArr<unsigned char> sq_mark, bsel;  // squares with a band triangle; band flag per triangle
+    long long sq_plan_version = -1;
     fem::DArr<double> lossk, lossred;  // tonal loss: per-triangle squared errors, block partial sums
 
     // host staging (pinned)
@@ -331,11 +350,15 @@ fem_status solve_totals_read(fem_mesh* m, cudaStream_t s);
 fem_status set_uv_from_g(fem_mesh* m, const float* g_dev, cudaStream_t s);
 fem_status set_uv_from_f(fem_mesh* m, const float* f_dev, cudaStream_t s);
 fem_status raster_plan(fem_mesh* m, cudaStream_t s);
-fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, const float* f, double* err,
-                         cudaStream_t s, unsigned long long* keyc_out = nullptr);
+// exact keys of every triangle (square-tiled pass, raster_sq.cu); the image
+// must have been laid out in squares by sq_image for the call
+fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, double* err, cudaStream_t s,
+                         unsigned long long* keyc_out = nullptr);
 fem_status raster_image(fem_mesh* m, const double* uv, float* u, int* owner, cudaStream_t s);
-fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, const float* f, double frac,
-                            long long vcap, cudaStream_t s);
+fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, double frac, long long vcap,
+                            cudaStream_t s);
+// the image f as squares for the square-tiled pass (once per call that reads f)
+fem_status sq_image(fem_mesh* m, const float* f, cudaStream_t s);
 fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s);
 fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vstar, cudaStream_t s,
                         double* margin_out, int* k_out, bool band = false);
@@ -344,7 +367,7 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
 constexpr int kFastBins = 32768;
 // ints into fem_mesh::host_stage where a refinement round leaves its counters
 constexpr int kRoundStageInts = 1024;
-enum FastCounter { FC_IN = 0, FC_BAND = 1, FC_BAND_ITEMS = 2, FC_BAND_SMALL = 3 };
+enum FastCounter { FC_IN = 0, FC_BAND = 1, FC_BAND_SQUARES = 2 };
 fem_status sync_counts(fem_mesh* m, cudaStream_t s);
 fem_status ensure_mesh_capacity(fem_mesh* m, int needV, int needT, cudaStream_t s);
 void reset_coop_state(fem_mesh* m, cudaStream_t s);

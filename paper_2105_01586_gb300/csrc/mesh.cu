@@ -1,4 +1,5 @@
 // mesh.cu -- mesh handle, import/export, errors, launch accounting, scans.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -341,7 +342,7 @@ long long fem_launch_count(void) { return g_launches.load(); }
 void fem_profile_enable(int family_mask) { g_prof_on.store(family_mask); }
 
 int fem_profile_read(int family, long long* launches, double* ms, double* bytes, const char** name) {
-    static const char* names[F_COUNT] = {"raster", "cg", "assembly", "topk", "refine", "tonal", "other"};
+    static const char* names[F_COUNT] = {"raster", "cg", "assembly", "topk", "refine", "tonal", "other", "raster_pass"};
     if (family < 0 || family >= F_COUNT) return -1;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     double tot = 0.0;
@@ -465,8 +466,8 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->vxy, s); release(m->mask, s); release(m->tri, s); release(m->uv, s); release(m->uvf, s);
     release(m->order, s); release(m->order_tmp, s); release(m->ocnt, s); release(m->ooff, s);
     release(m->item_cnt, s); release(m->item_off, s); release(m->item_tri, s); release(m->partial, s);
-    release(m->item_done, s); release(m->keys_lo, s); release(m->keys_hi, s); release(m->fast_hist, s);
-    release(m->band, s); release(m->band_items, s); release(m->band_small, s);
+    release(m->keys_lo, s); release(m->keys_hi, s); release(m->fast_hist, s);
+    release(m->band, s);
     release(m->keys, s);
     release(m->keyc, s);
     release(m->bmM, s); release(m->bmS, s); release(m->wpre, s);
@@ -487,7 +488,11 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->inc, s); release(m->loc, s); release(m->Moff, s); release(m->Mdiag, s);
     release(m->tv, s); release(m->ty, s); release(m->tz, s); release(m->tg, s);
     release(m->tr, s); release(m->tp, s); release(m->tw, s); release(m->tc, s);
-    release(m->lossk, s); release(m->lossred, s);
+    release(m->lossk, s); release(m->lossred, s); release(m->tyr, s);
+    release(m->fsq, s); release(m->fedge, s); release(m->sq_nodeof, s); release(m->sq_off, s);
+    release(m->sq_cov, s); release(m->sq_slot, s); release(m->sq_seg, s); release(m->sq_part, s);
+    release(m->sq_coarse, s); release(m->sq_ctr, s); release(m->sq_list, s); release(m->sq_rec, s);
+    release(m->sq_stage, s); release(m->sq_flag, s); release(m->sq_staged, s); release(m->sq_mark, s); release(m->bsel, s);
     cudaStreamSynchronize(s);
     if (m->host_stage) cudaFreeHost(m->host_stage);
     if (m->round_ev) cudaEventDestroy(m->round_ev);
@@ -536,6 +541,81 @@ fem_status fem_mesh_curve_order(fem_mesh* m, int* order, int* is_curve) {
     return FEM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+struct P2 {
+    long long x, y;
+};
+
+// strictly inside the positively oriented triangle (a, b, c); p has three
+// times the coordinates, the vertices are scaled here
+bool inside3_host(P2 p, P2 a, P2 b, P2 c) {
+    a = {3 * a.x, 3 * a.y};
+    b = {3 * b.x, 3 * b.y};
+    c = {3 * c.x, 3 * c.y};
+    const long long e0 = (b.x - a.x) * (p.y - a.y) - (b.y - a.y) * (p.x - a.x);
+    const long long e1 = (c.x - b.x) * (p.y - b.y) - (c.y - b.y) * (p.x - b.x);
+    const long long e2 = (a.x - c.x) * (p.y - c.y) - (a.y - c.y) * (p.x - c.x);
+    return e0 > 0 && e1 > 0 && e2 > 0;
+}
+
+// Position of a triangle (a, b, c) on the space-filling curve of the
+// bisection tree of the two-triangle mesh of an image of side D + 1: the
+// path from the root (first bit: which initial triangle; then at every
+// bisection whether the child holding the triangle comes first or second on
+// the curve), left-aligned in 64 bits, so that sorting the keys gives the
+// curve order.  The curve enters a triangle with legs along the axes at a
+// and one with diagonal legs at b; (a, b, c) is bisected into (c, a, m) and
+// (b, c, m), and the child holding the entry comes first.  False when the
+// triangle is not a node of the tree.
+bool curve_key(long long D, P2 a, P2 b, P2 c, unsigned long long* key) {
+    const P2 g{a.x + b.x + c.x, a.y + b.y + c.y};
+    P2 na{0, 0}, nb{D, D}, nc{0, D};
+    unsigned long long bits = 0;
+    int depth = 1;
+    if (!inside3_host(g, na, nb, nc)) {
+        na = {D, D};
+        nb = {0, 0};
+        nc = {D, 0};
+        bits = 1;
+        if (!inside3_host(g, na, nb, nc)) return false;
+    }
+    const long long l2 = (a.x - c.x) * (a.x - c.x) + (a.y - c.y) * (a.y - c.y);
+    for (;;) {
+        if (na.x == a.x && na.y == a.y && nb.x == b.x && nb.y == b.y && nc.x == c.x && nc.y == c.y) break;
+        const long long nl2 = (na.x - nc.x) * (na.x - nc.x) + (na.y - nc.y) * (na.y - nc.y);
+        if (nl2 <= l2 || ((na.x + nb.x) & 1) || ((na.y + nb.y) & 1) || depth >= 63) return false;
+        const P2 m{(na.x + nb.x) / 2, (na.y + nb.y) / 2};
+        const bool at_b = nc.x != na.x && nc.y != na.y;
+        int bit;
+        if (inside3_host(g, nc, na, m)) {  // (c, a, m)
+            bit = at_b ? 1 : 0;
+            const P2 o = na;
+            na = nc;
+            nb = o;
+            nc = m;
+        } else if (inside3_host(g, nb, nc, m)) {  // (b, c, m)
+            bit = at_b ? 0 : 1;
+            const P2 o = nb;
+            na = o;
+            nb = nc;
+            nc = m;
+        } else {
+            return false;
+        }
+        bits = (bits << 1) | (unsigned long long)bit;
+        ++depth;
+    }
+    *key = bits << (64 - depth);
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
 fem_status fem_mesh_import(fem_mesh* m, int V, const int* xy, int T, const int* tri, const unsigned char* is_mask) {
     FEM_TRY(check_mesh(m));
     if (V < 3 || T < 1 || !xy || !tri || !is_mask || (long long)V > m->P || (long long)T > 2LL * (m->N - 1) * (m->N - 1)) {
@@ -573,19 +653,39 @@ fem_status fem_mesh_import(fem_mesh* m, int V, const int* xy, int T, const int* 
         set_error("fem_mesh_import: triangle areas do not add up to the image");
         return FEM_E_INVALID;
     }
+    // every triangle must be a node of the bisection tree of the
+    // two-triangle mesh; the kernels visit them along the tree's curve
+    std::vector<std::pair<unsigned long long, int>> keyed(T);
+    for (int t = 0; t < T; ++t) {
+        const int a = tri[3 * t], b = tri[3 * t + 1], c = tri[3 * t + 2];
+        unsigned long long key = 0;
+        if (!curve_key(N - 1, P2{xy[2 * a], xy[2 * a + 1]}, P2{xy[2 * b], xy[2 * b + 1]},
+                       P2{xy[2 * c], xy[2 * c + 1]}, &key)) {
+            set_error("fem_mesh_import: triangle " + std::to_string(t) +
+                      " is not a newest-vertex-bisection triangle of the two-triangle mesh");
+            return FEM_E_INVALID;
+        }
+        keyed[t] = {key, t};
+    }
+    std::sort(keyed.begin(), keyed.end());
+    std::vector<int> ord(T);
+    for (int i = 0; i < T; ++i) {
+        if (i > 0 && keyed[i].first == keyed[i - 1].first) {
+            set_error("fem_mesh_import: triangles " + std::to_string(keyed[i - 1].second) + " and " +
+                      std::to_string(keyed[i].second) + " coincide");
+            return FEM_E_INVALID;
+        }
+        ord[i] = keyed[i].second;
+    }
     cudaStream_t s = m->last_stream;
     FEM_TRY(ensure_mesh_capacity(m, V, T, s));
     FEM_CUDA(cudaMemcpyAsync(m->vxy.p, xy, sizeof(int2) * V, cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemcpyAsync(m->mask.p, is_mask, V, cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemcpyAsync(m->tri.p, t4.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemsetAsync(m->uv.p, 0, sizeof(double) * V, s));
-    {
-        std::vector<int> ord(T);
-        for (int t = 0; t < T; ++t) ord[t] = t;
-        FEM_CUDA(cudaMemcpyAsync(m->order.p, ord.data(), sizeof(int) * T, cudaMemcpyHostToDevice, s));
-        FEM_CUDA(cudaStreamSynchronize(s));
-    }
-    m->order_is_curve = false;
+    FEM_CUDA(cudaMemcpyAsync(m->order.p, ord.data(), sizeof(int) * T, cudaMemcpyHostToDevice, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    m->order_is_curve = true;
     FEM_CUDA(cudaStreamSynchronize(s));
     int nk = 0;
     for (int i = 0; i < V; ++i) nk += is_mask[i] ? 1 : 0;

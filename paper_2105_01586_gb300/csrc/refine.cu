@@ -1028,6 +1028,8 @@ extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double
     // mask vertices take their image values once; vertices made by the
     // refinement get theirs when they are created (k_bisect)
     FEM_TRY(set_uv_from_f(m, f_dev, s));
+    // the error passes read the image as squares, laid out once per call
+    FEM_TRY(sq_image(m, f_dev, s));
     while ((long long)m->V < vstar && (p->max_rounds <= 0 || round < p->max_rounds)) {
         // solve_laplace builds the system of the refined mesh (with its
         // right-hand side in the same kernel)
@@ -1039,9 +1041,9 @@ extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double
         // its float-float copy (mask vertices from f, unknowns by the solve)
         bool band = p->fast_keys > 0 || (p->fast_keys < 0 && m->P >= 2049LL * 2049);
         if (band)
-            FEM_TRY(raster_keys_fast(m, m->uv.p, m->uvf.p, f_dev, p->topk_frac, vstar - m->V, s));
+            FEM_TRY(raster_keys_fast(m, m->uv.p, m->uvf.p, p->topk_frac, vstar - m->V, s));
         else
-            FEM_TRY(raster_errors(m, m->uv.p, m->uvf.p, f_dev, m->keys.p, s, m->keyc.p));
+            FEM_TRY(raster_errors(m, m->uv.p, m->uvf.p, m->keys.p, s, m->keyc.p));
         double margin = 0.0;
         int k = 0;
         FEM_TRY(refine_round(m, f_dev, p->topk_frac, vstar, s, &margin, &k, band));

@@ -8,7 +8,9 @@
 // so it is assembled once per mesh from one pass over the pixels, and each
 // outer iteration costs one forward solve, one sparse product with M and one
 // adjoint solve (E^T y = y_K - A_KU A_UU^{-1} y_U); no pixel is read inside
-// the iteration.  B itself is never formed.
+// the iteration.  B itself is never formed.  The iteration has the form of
+// CGLS: its residual recursion runs on y = P^T (f - B g), and the normal
+// residual E^T y is formed afresh each iteration.
 //
 // Per-vertex sums are gathered over the (at most 8) triangles around a
 // vertex in a fixed order of their angular sector, so results do not depend
@@ -245,7 +247,8 @@ __global__ void k_cg_update_sum(int nb, const double* __restrict__ partial, CgSc
 }
 
 // mode 0: partial of x.y; mode 1: g += a p, r -= a w, partial of r.r;
-// mode 2: p = r + b p; mode 3: r = c - w, p = r, partial r.r.
+// mode 2: p = r + b p; mode 3: r = c - w (r = c when w is null), p = r,
+// partial r.r.
 // cg (optional, the outer CG's device scalars, see CgScalars): modes 1 and
 // 2 take a = gamma / pNp and b = gamma / gamma_old from it and do nothing
 // once the iteration has stopped, so no scalar is read back per iteration.
@@ -274,8 +277,8 @@ __global__ void k_vec(int mode, int n, double a, double* __restrict__ x, double*
             dot += r * r;
         } else if (mode == 2) {  // x = p, z = r
             x[i] = z[i] + a * x[i];
-        } else {  // x = r, y = p, z = c
-            double r = z[i] - w[i];
+        } else {  // x = r, y = p, z = c (w null: r = c)
+            double r = w ? z[i] - w[i] : z[i];
             x[i] = r;
             y[i] = r;
             dot += r * r;
@@ -291,6 +294,28 @@ __global__ void k_vec(int mode, int n, double a, double* __restrict__ x, double*
         for (int w2 = 0; w2 < kVecThreads / 32; ++w2) t += sh[w2];
         partial[blockIdx.x] = t;
     }
+}
+
+// One step of the outer iteration (modes of the CgScalars): a = gamma / pNp,
+// g += a p over the nK mask values and y -= a (M E p) over the V vertices;
+// nothing once the iteration has stopped or broken down (pNp <= 0).
+__global__ void k_tonal_step(int nK, int V, double* __restrict__ g, const double* __restrict__ p,
+                             double* __restrict__ y, const double* __restrict__ My, const CgScalars* __restrict__ cg) {
+    pdl_wait();
+    if (cg->stop != 0.0 || !(cg->pNp > 0.0)) return;
+    const double a = cg->gamma / cg->pNp;
+    const int n = max(nK, V);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (i < nK) g[i] += a * p[i];
+        if (i < V) y[i] -= a * My[i];
+    }
+}
+
+// y = y - x
+__global__ void k_sub_into(int n, const double* __restrict__ x, double* __restrict__ y) {
+    pdl_wait();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] -= x[i];
 }
 
 __global__ void k_f2d(int n, const float* __restrict__ a, double* __restrict__ b) {
@@ -384,6 +409,7 @@ static fem_status ensure_tonal_vectors(fem_mesh* m, cudaStream_t s) {
     FEM_TRY(ensure(m->tp, nK, s));
     FEM_TRY(ensure(m->tw, nK, s));
     FEM_TRY(ensure(m->tc, nK, s));
+    FEM_TRY(ensure(m->tyr, V, s));
     FEM_TRY(ensure(m->red, (size_t)vec_grid(m) + 8, s));
     return FEM_OK;
 }
@@ -408,9 +434,8 @@ static fem_status apply_ET(fem_mesh* m, const double* y, double* w, const InnerC
     return FEM_OK;
 }
 
-// w = B^T B p = E^T M E p; *pNp_dev = (E p) . M (E p)
-static fem_status apply_N(fem_mesh* m, const double* p, double* w, double* pNp_dev, const InnerCfg& c,
-                          cudaStream_t s) {
+// ty = M E p (V entries) and *pNp_dev = (E p) . M (E p) = ||B p||^2
+static fem_status apply_EM(fem_mesh* m, const double* p, double* pNp_dev, const InnerCfg& c, cudaStream_t s) {
     int nU = m->nU, V = m->V;
     if (nU > 0) {
         FEM_LAUNCH(F_TONAL, s, k_fwd_rhs, (nU + 255) / 256, 256, 0, nU, V, m->urow_vertex.p, m->nbr.p, m->coefA.p,
@@ -424,7 +449,7 @@ static fem_status apply_N(fem_mesh* m, const double* p, double* w, double* pNp_d
     FEM_LAUNCH(F_TONAL, s, k_mass_spmv, G, kVecThreads, 0, V, m->Mdiag.p, m->Moff.p, m->nbr.p, m->tv.p, m->ty.p,
                m->red.p);
     FEM_LAUNCH(F_TONAL, s, k_final_sum, 1, kVecThreads, 0, G, m->red.p, pNp_dev);
-    return apply_ET(m, m->ty.p, w, c, s);
+    return FEM_OK;
 }
 
 static fem_status vec_op(fem_mesh* m, int mode, int n, double a, double* x, double* y, double* z, const double* w,
@@ -465,14 +490,23 @@ extern "C" fem_status fem_tonal_opt(fem_mesh* m, const float* f_dev, float* g_de
     FEM_TRY(solve_totals_reset(m, s));
     CgScalars* cg = (CgScalars*)(m->dscal.p + 32);
     double* sc = m->dscal.p + 32;  // [0] |c|^2 [1] pNp [2] gamma (the CgScalars layout)
-    // c = B^T f
+    // The outer iteration is CG on the normal equations in the form of CGLS:
+    // the recursion runs on y = P^T (f - B g) (the pixel residual seen through
+    // P^T, a vertex vector: y -= a M E p), and the normal residual
+    // s = B^T (f - B g) = E^T y is formed from it each iteration by the
+    // adjoint solve.  Updating s itself (s -= a B^T B p) would lose accuracy
+    // with the square of B's condition number.
+    // c = B^T f = E^T P^T f, and y = P^T f - M E g for the start g
     FEM_TRY(scatter_PT(m, f_dev, s));
+    FEM_CUDA(cudaMemcpyAsync(m->tyr.p, m->ty.p, sizeof(double) * m->V, cudaMemcpyDeviceToDevice, s));
     FEM_TRY(apply_ET(m, m->ty.p, m->tc.p, c, s));
     FEM_TRY(vec_op(m, 0, nK, 0.0, m->tc.p, m->tc.p, nullptr, nullptr, sc + 0, s));
-    // g, r = c - N g, p = r
     FEM_LAUNCH(F_TONAL, s, k_f2d, (nK + 255) / 256, 256, 0, nK, g_dev, m->tg.p);
-    FEM_TRY(apply_N(m, m->tg.p, m->tw.p, sc + 1, c, s));
-    FEM_TRY(vec_op(m, 3, nK, 0.0, m->tr.p, m->tp.p, m->tc.p, m->tw.p, sc + 2, s));
+    FEM_TRY(apply_EM(m, m->tg.p, sc + 1, c, s));
+    FEM_LAUNCH(F_TONAL, s, k_sub_into, (m->V + 255) / 256, 256, 0, m->V, (const double*)m->ty.p, m->tyr.p);
+    // s = E^T y (into tw), r = s, p = s, gamma = |s|^2
+    FEM_TRY(apply_ET(m, m->tyr.p, m->tw.p, c, s));
+    FEM_TRY(vec_op(m, 3, nK, 0.0, m->tr.p, m->tp.p, m->tw.p, nullptr, sc + 2, s));
     double cc = 0.0, gamma = 0.0;
     FEM_TRY(read_scalar(m, sc + 0, &cc, s));
     FEM_TRY(read_scalar(m, sc + 2, &gamma, s));
@@ -503,10 +537,16 @@ extern "C" fem_status fem_tonal_opt(fem_mesh* m, const float* f_dev, float* g_de
         double* slot = hs + 8;  // three pinned (stop, iters) pairs
         int G = vec_grid(m);
         for (int k = 0; lst == FEM_OK && k < p->tonal_maxit; ++k) {
-            lst = apply_N(m, m->tp.p, m->tw.p, &cg->pNp, c, s);
+            // ||B p||^2 and M E p; g += a p, y -= a M E p; r = E^T y
+            lst = apply_EM(m, m->tp.p, &cg->pNp, c, s);
             if (lst != FEM_OK) break;
             note_launch_begin(F_TONAL, s);
-            k_vec<<<G, kVecThreads, 0, s>>>(1, nK, 0.0, m->tg.p, m->tp.p, m->tr.p, m->tw.p, m->red.p, cg);
+            k_tonal_step<<<G, kVecThreads, 0, s>>>(nK, m->V, m->tg.p, m->tp.p, m->tyr.p, m->ty.p, cg);
+            note_launch_end(F_TONAL, s);
+            lst = apply_ET(m, m->tyr.p, m->tr.p, c, s);
+            if (lst != FEM_OK) break;
+            note_launch_begin(F_TONAL, s);
+            k_vec<<<G, kVecThreads, 0, s>>>(0, nK, 0.0, m->tr.p, m->tr.p, nullptr, nullptr, m->red.p, cg);
             note_launch_end(F_TONAL, s);
             note_launch_begin(F_TONAL, s);
             k_cg_update_sum<<<1, kVecThreads, 0, s>>>(G, m->red.p, cg);
@@ -593,7 +633,8 @@ extern "C" fem_status fem_tonal_loss(fem_mesh* m, const float* g_dev, const floa
     FEM_TRY(solve_laplace(m, fp64, p->tol, p->maxit, s, &it, &rel));
     if (loss_dev) {
         FEM_TRY(ensure(m->lossk, (size_t)m->T, s));
-        FEM_TRY(raster_errors(m, m->uv.p, nullptr, f_dev, m->lossk.p, s));
+        FEM_TRY(sq_image(m, f_dev, s));
+        FEM_TRY(raster_errors(m, m->uv.p, nullptr, m->lossk.p, s));
         const int G = vec_grid(m);
         FEM_TRY(ensure(m->lossred, (size_t)G, s));
         FEM_LAUNCH(F_TONAL, s, k_sum_partial, G, kVecThreads, 0, (long long)m->T, (const double*)m->lossk.p,

@@ -10,8 +10,10 @@ checked against central differences (h = 1e-4) on 32 random mask vertices.
 the spatial loop (hours), so the checks are sampled outputs it can compute
 and properties that hold at any size: bisection-mesh invariants, the
 per-triangle errors against the oracle's rasteriser on the GPU's mesh and
-vertex values, and the FEM residual of the GPU solve with the oracle's
-stiffness matrix.
+vertex values, the FEM residual of the GPU solve with the oracle's
+stiffness matrix, and after the workload's 50 tonal iterations the normal
+residual of the returned g through the oracle's B and B^T (it must match the
+residual the GPU reports) and a smaller error ||B g - f|| than at the start.
 
 Tolerances:
   * optimality: the GPU stops at ||B^T r|| <= 1e-9 ||B^T f|| and returns g in
@@ -65,6 +67,10 @@ def test_config_2049_mesh_tonal_and_gradient(oracle_mod, fem):
     c = oracle_mod.apply_BT(om, f_np.astype(np.float64))
     res = oracle_mod.apply_BT(om, oracle_mod.apply_B(om, g) - f_np)
     assert np.linalg.norm(res) <= 1e-7 * np.linalg.norm(c)
+    # g itself against the oracle's converged minimiser (the 1e-6 target)
+    g_ref, st = oracle_mod.tonal(om, f_np, tol=1e-12)
+    assert st["relres"] <= 1e-12
+    assert np.linalg.norm(g - g_ref) <= 1e-6 * np.linalg.norm(g_ref)
 
     g0 = m.g_from_f(f)
     gg = g0.clone().requires_grad_(True)
@@ -125,3 +131,19 @@ def test_config_8193_sampled(oracle_mod, fem):
     _, keys_ref, own = oracle_mod.raster(om, uvn, f_np, owner=True)
     err = m.triangle_errors(uv, f).cpu().numpy()
     assert (np.abs(err - keys_ref) <= key_err_tol(keys_ref, own, np.abs(uvn).max())).all()
+    # 50 tonal iterations (the workload's count): the oracle's B and B^T on
+    # the GPU's mesh give the normal residual of the returned g, which must
+    # match the residual the GPU reports, and the error ||B g - f|| must fall
+    p = fem.params(tonal_tol=0.0, inner_tol=1e-13)
+    p.tonal_maxit = 50
+    g50 = g.clone()
+    fem.fem_tonal_opt(m.h, f, g50, p, allow_not_converged=True)
+    st = m.stats()
+    assert st["tonal_iters"] == 50
+    g50n = g50.double().cpu().numpy()
+    c = oracle_mod.apply_BT(om, f_np.astype(np.float64))
+    r50 = oracle_mod.apply_B(om, g50n) - f_np
+    res = np.linalg.norm(oracle_mod.apply_BT(om, r50)) / np.linalg.norm(c)
+    assert abs(res - st["tonal_relres"]) <= 1e-3 * st["tonal_relres"] + 1e-7, (res, st["tonal_relres"])
+    r0 = oracle_mod.apply_B(om, g.double().cpu().numpy()) - f_np
+    assert np.linalg.norm(r50) < np.linalg.norm(r0)
