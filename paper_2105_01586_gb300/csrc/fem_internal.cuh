@@ -297,6 +297,8 @@ struct fem_mesh {
     // tables of the plan, per-node partial sums, the band's squares
     fem::DArr<float> fsq, fedge;       // Q*Q squares of s rows of s + 1 floats; the image's last row (N)
     fem::DArr<int> sq_nodeof, sq_off;  // per curve position: node (fine) or -1; first bounding-box square
+    fem::DArr<int> sq_pos;             // per triangle: its curve position
+    fem::DArr<int> sq_bcoarse;         // curve positions of the band's coarse triangles
     fem::DArr<int> sq_cov, sq_slot;    // per node: covering triangle's curve position or -1; partial slot
     fem::DArr<int2> sq_seg;            // per node: curve segment of its triangles
     fem::DArr<float4> sq_part;         // partial sums (hi, lo, pixel count)
@@ -367,7 +369,7 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
 constexpr int kFastBins = 32768;
 // ints into fem_mesh::host_stage where a refinement round leaves its counters
 constexpr int kRoundStageInts = 1024;
-enum FastCounter { FC_IN = 0, FC_BAND = 1, FC_BAND_SQUARES = 2 };
+enum FastCounter { FC_IN = 0, FC_BAND = 1, FC_BAND_SQUARES = 2, FC_BAND_COARSE = 3 };
 fem_status sync_counts(fem_mesh* m, cudaStream_t s);
 fem_status ensure_mesh_capacity(fem_mesh* m, int needV, int needT, cudaStream_t s);
 void reset_coop_state(fem_mesh* m, cudaStream_t s);

@@ -492,7 +492,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->fsq, s); release(m->fedge, s); release(m->sq_nodeof, s); release(m->sq_off, s);
     release(m->sq_cov, s); release(m->sq_slot, s); release(m->sq_seg, s); release(m->sq_part, s);
     release(m->sq_coarse, s); release(m->sq_ctr, s); release(m->sq_list, s); release(m->sq_rec, s);
-    release(m->sq_stage, s); release(m->sq_flag, s); release(m->sq_staged, s); release(m->sq_mark, s); release(m->bsel, s);
+    release(m->sq_stage, s); release(m->sq_flag, s); release(m->sq_staged, s); release(m->sq_pos, s); release(m->sq_bcoarse, s); release(m->sq_mark, s); release(m->bsel, s);
     cudaStreamSynchronize(s);
     if (m->host_stage) cudaFreeHost(m->host_stage);
     if (m->round_ev) cudaEventDestroy(m->round_ev);

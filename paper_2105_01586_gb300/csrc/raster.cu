@@ -655,7 +655,8 @@ __global__ void k_fast_classify(const int4* __restrict__ tri, const int2* __rest
                                 const double* __restrict__ tau, double* __restrict__ keys,
                                 unsigned long long* __restrict__ keyc, int* __restrict__ band,
                                 unsigned char* __restrict__ sel, unsigned char* __restrict__ sq_mark,
-                                int* __restrict__ cnt, unsigned long long* __restrict__ max_out) {
+                                const int* __restrict__ pos, int* __restrict__ band_coarse, int* __restrict__ cnt,
+                                unsigned long long* __restrict__ max_out) {
     pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned FULL = 0xffffffffu;
@@ -683,6 +684,8 @@ __global__ void k_fast_classify(const int4* __restrict__ tri, const int2* __rest
             const int2 a = make_int2(g.ax, g.ay), b = make_int2(g.bx, g.by), c = make_int2(g.cx, g.cy);
             if (leg2(a, c) <= (long long)G.s * G.s)
                 sq_mark[sq_node_at((long long)a.x + b.x + c.x, (long long)a.y + b.y + c.y, G) >> 1] = 1;
+            else
+                band_coarse[atomicAdd(cnt + FC_BAND_COARSE, 1)] = pos[t];  // its exact key needs its node sums
         }
         sel[t] = cls == 3 ? 1 : 0;
     }
@@ -723,7 +726,8 @@ fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, do
     }
     FEM_TRY(ensure(m->fast_hist, (size_t)2 * kFastBins + 8, s));
     unsigned* hist = m->fast_hist.p;
-    int* cnt = (int*)(hist + 2 * kFastBins);  // [0] in, [1] band, [2] band squares
+    int* cnt = (int*)(hist + 2 * kFastBins);  // [0] in, [1] band, [2] band squares, [3] coarse band triangles
+    FEM_TRY(ensure(m->sq_bcoarse, (size_t)T, s));
     unsigned long long* max_out = (unsigned long long*)(m->dscal.p + 18);
     double* tau = m->dscal.p + 16;
     int* kdev = m->dcount.p + 2;
@@ -734,7 +738,8 @@ fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, do
     // bracket and classification
     FEM_LAUNCH(F_TOPK, s, k_fast_bracket, 1, kBracketThreads, 0, hist, hist + kFastBins, T, frac, vcap, kdev, tau);
     FEM_LAUNCH(F_TOPK, s, k_fast_classify, (T + 255) / 256, 256, 0, m->tri.p, m->vxy.p, T, G, m->keys_lo.p,
-               m->keys_hi.p, tau, m->keys.p, m->keyc.p, m->band.p, m->bsel.p, m->sq_mark.p, cnt, max_out);
+               m->keys_hi.p, tau, m->keys.p, m->keyc.p, m->band.p, m->bsel.p, m->sq_mark.p, (const int*)m->sq_pos.p,
+               m->sq_bcoarse.p, cnt, max_out);
     // exact float-float keys of the band, over the squares that hold it
     return sq_band_exact(m, uv, uvf, cnt + 2, s);
 }

@@ -174,8 +174,11 @@ int sq_side(int N);
 SqGeo sq_geo(const fem_mesh* m);
 fem_status sq_plan(fem_mesh* m, cudaStream_t s);
 fem_status sq_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, FastOut F, cudaStream_t s);
+// coarse (optional): the coarse triangles to finish, by curve position
+// (default: all of them)
 fem_status sq_keys_exact(fem_mesh* m, const double* uv, const float2* uvf, double* keys, unsigned long long* keyc,
-                         const unsigned char* sel, const int* list, const int* n_list, int n_max, cudaStream_t s);
+                         const unsigned char* sel, const int* list, const int* n_list, int n_max, cudaStream_t s,
+                         const int* coarse = nullptr, const int* n_coarse = nullptr);
 fem_status sq_band_exact(fem_mesh* m, const double* uv, const float2* uvf, int* n_list_dev, cudaStream_t s);
 
 }  // namespace fem

@@ -117,9 +117,11 @@ struct SqCountIn {
     const int2* vxy;
     SqGeo G;
     int* nodeof;
+    int* pos;             // curve position of each triangle
     unsigned char* flag;  // squares that the staged pass takes (a fine triangle larger than small)
     __device__ __forceinline__ int operator()(long long i) const {
         const int t = order[i];
+        pos[t] = (int)i;
         const int4 tr = tri[t];
         const int2 a = vxy[tr.x], b = vxy[tr.y], c = vxy[tr.z];
         if (leg2(a, c) <= (long long)G.s * G.s) {
@@ -333,6 +335,15 @@ __device__ __forceinline__ void sq_small(const SqArgs& A, const float* img, int 
     }
 }
 
+// The warp's sum of the lanes' sums: FAST adds the FP32 sums by a butterfly
+// (five more additions in each lane's chain, within kSqChain), EXACT the
+// float-float sums.  Every lane returns the same value.
+template <int MODE>
+__device__ __forceinline__ ff sq_warp_total(float accf, ff acc) {
+    if (MODE == SQ_FAST) return ff{warp_sum(accf), 0.f};
+    return ff_warp_sum(acc);
+}
+
 // Row spans of region g for a sweep of up to 33 rows from row y (the first
 // row of the sweep): lane r holds the span of row y + r, lane 0 also of row
 // y + 32; rows outside the region's rows get an empty span.
@@ -378,8 +389,10 @@ __device__ __forceinline__ void sq_sweep2(const TriGeom& g0, bool want0, const S
     float a0 = 0.f, a1 = 0.f;
     ff e0{0.f, 0.f}, e1{0.f, 0.f};
     for (int r = 0; r < h; ++r) {
-        const int L = r < 32 ? __shfl_sync(FULL, La, r) : __shfl_sync(FULL, Lb, 0);
-        const int n = r < 32 ? __shfl_sync(FULL, na, r) : __shfl_sync(FULL, nb, 0);
+        // rows 0..31 take their span from lane r, row 32 from lane 0's second
+        const int src = r < 32 ? r : 0;
+        const int L = __shfl_sync(FULL, r < 32 ? La : Lb, src);
+        const int n = __shfl_sync(FULL, r < 32 ? na : nb, src);
         const float* rowp = img + r * pitch;
         const float u0f = fmaf(P0.gyf, fy0, P0.ucf), u1f = fmaf(P1.gyf, fy1, P1.ucf);
         ff u0{0.f, 0.f}, u1{0.f, 0.f};
@@ -404,12 +417,8 @@ __device__ __forceinline__ void sq_sweep2(const TriGeom& g0, bool want0, const S
         fy0 += 1.0f;
         fy1 += 1.0f;
     }
-    if (MODE == SQ_FAST) {
-        e0 = ff{a0, 0.f};
-        e1 = ff{a1, 0.f};
-    }
-    S0 = ff_warp_sum(e0);
-    S1 = ff_warp_sum(e1);
+    S0 = sq_warp_total<MODE>(a0, e0);
+    S1 = sq_warp_total<MODE>(a1, e1);
 }
 
 // A larger fine triangle over its bounding box (at most 33 x 33 pixels of the
@@ -432,8 +441,9 @@ __device__ __forceinline__ ff sq_bbox(const TriGeom& g, const SqPlane& P, const 
     float af = 0.f;
     ff e{0.f, 0.f};
     for (int r = 0; r < R; ++r) {
-        const int L = r < 32 ? __shfl_sync(FULL, La, r) : __shfl_sync(FULL, Lb, 0);
-        const int n = r < 32 ? __shfl_sync(FULL, na, r) : __shfl_sync(FULL, nb, 0);
+        const int src = r < 32 ? r : 0;
+        const int L = __shfl_sync(FULL, r < 32 ? La : Lb, src);
+        const int n = __shfl_sync(FULL, r < 32 ? na : nb, src);
         const float* rowp = img + (g.ytop + r - y0) * pitch - x0;
         const float uf = fmaf(P.gyf, fy, P.ucf);
         ff u{0.f, 0.f};
@@ -442,8 +452,7 @@ __device__ __forceinline__ ff sq_bbox(const TriGeom& g, const SqPlane& P, const 
         if (two && (unsigned)(xb - L) < (unsigned)n) sq_px<MODE>(P, fb, uf, u, rowp[xb], af, e);
         fy += 1.0f;
     }
-    if (MODE == SQ_FAST) e = ff{af, 0.f};
-    return ff_warp_sum(e);
+    return sq_warp_total<MODE>(af, e);
 }
 
 // A square inside one triangle: every staged pixel, lanes over columns.
@@ -479,8 +488,7 @@ __device__ __forceinline__ ff sq_full(const SqPlane& P, int pcx, int pcy, const 
             if (two) acc = ff_add(acc, ff_sqr(ff_add_f(ff_add(urow, gxb), -rowp[lane + 32])));
         }
     }
-    if (MODE == SQ_FAST) acc = ff{accf, 0.f};
-    return ff_warp_sum(acc);
+    return sq_warp_total<MODE>(accf, acc);
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -533,15 +541,15 @@ __device__ __forceinline__ void sq_issue(const SqArgs& A, int q, float* img, uns
     bulk_copy(img, A.fsq + (long long)q * s * (s + 1), bytes, bar, policy);
 }
 
-// The records of the fine triangles (nodeof >= 0) for the FP32 pass, one
-// thread per curve position; all gathers of the pass happen here, in a fully
-// parallel kernel, and the pass reads each square's records contiguously.
+// The records of the triangles for the FP32 pass, one thread per curve
+// position; all gathers of the pass happen here, in a fully parallel kernel,
+// and the pass reads each square's records contiguously (fine triangles) or
+// one record per covered node (coarse ones).
 __global__ void k_sq_records(const int* __restrict__ order, const int4* __restrict__ tri, const int2* __restrict__ vxy,
                              const double* __restrict__ uv, const float2* __restrict__ uvf,
                              const int* __restrict__ nodeof, int T, int N, SqRec* __restrict__ rec) {
     pdl_wait();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
-        if (nodeof[i] < 0) continue;
         const int t = order[i];
         const int4 tr = tri[t];
         const TriGeom g = tri_geom(tr, vxy, N);
@@ -649,6 +657,24 @@ __global__ void __launch_bounds__(256) k_sq_small(const SqRec* __restrict__ rec,
     }
 }
 
+// The plane and right-angle corner of the triangle at curve position c:
+// FAST from its record, EXACT from the mesh (float-float plane).
+template <int MODE>
+__device__ __forceinline__ void sq_plane_at(const SqArgs& A, int c, int t, SqPlane& P, int& cx, int& cy) {
+    if (MODE == SQ_FAST) {
+        const SqRec R = A.rec[c];
+        P = rec_plane(R);
+        cx = R.cx;
+        cy = R.cy;
+    } else {
+        const int4 tr = A.tri[t];
+        const TriGeom gt = tri_geom(tr, A.vxy, A.G.N);
+        P = sq_plane(gt, tr, A.uv, A.uvf);
+        cx = gt.cx;
+        cy = gt.cy;
+    }
+}
+
 // Warp w of the grid takes squares w, w + W, ... (W warps); each warp stages
 // its next square while it works on the current one, with its own two
 // buffers and mbarriers, so warps never wait for one another.
@@ -708,13 +734,13 @@ __global__ void __launch_bounds__(kSqThreads) k_sq(SqArgs A) {
         const int c0 = A.ncov[n0], c1 = A.ncov[n0 + 1];
         if (c0 >= 0 && c0 == c1) {
             // the whole square lies in one triangle
-            const int t = A.order[c0];
-            if (sq_want<MODE>(A, t)) {
-                const int4 tr = A.tri[t];
-                const TriGeom gt = tri_geom(tr, A.vxy, N);
-                const SqPlane P = sq_plane(gt, tr, A.uv, A.uvf);
+            const int t = MODE == SQ_FAST ? -1 : A.order[c0];
+            if (MODE == SQ_FAST || sq_want<MODE>(A, t)) {
+                SqPlane P;
+                int cx, cy;
+                sq_plane_at<MODE>(A, c0, t, P, cx, cy);
                 const int w = s + (J == Q - 1 ? 1 : 0), h = s + (I == Q - 1 ? 1 : 0);
-                const ff S = sq_full<MODE>(P, gt.cx, gt.cy, img, x0, y0, w, h, pitch);
+                const ff S = sq_full<MODE>(P, cx, cy, img, x0, y0, w, h, pitch);
                 if (lane == 0) {
                     const int s0 = A.nslot[n0], s1 = A.nslot[n0 + 1];
                     if (s0 >= 0 && s0 < A.part_cap) A.partial[s0] = make_float4(S.hi, S.lo, __int_as_float(w * h), 0.f);
@@ -723,25 +749,15 @@ __global__ void __launch_bounds__(kSqThreads) k_sq(SqArgs A) {
             }
         } else {
             // nodes inside coarse triangles: one sweep over the square
-            const int t0 = c0 >= 0 ? A.order[c0] : -1, t1 = c1 >= 0 ? A.order[c1] : -1;
-            const bool want0 = t0 >= 0 && sq_want<MODE>(A, t0), want1 = t1 >= 0 && sq_want<MODE>(A, t1);
+            const int t0 = c0 >= 0 && MODE == SQ_EXACT ? A.order[c0] : -1;
+            const int t1 = c1 >= 0 && MODE == SQ_EXACT ? A.order[c1] : -1;
+            const bool want0 = c0 >= 0 && (MODE == SQ_FAST || sq_want<MODE>(A, t0));
+            const bool want1 = c1 >= 0 && (MODE == SQ_FAST || sq_want<MODE>(A, t1));
             if (want0 || want1) {
                 SqPlane P0{}, P1{};
                 int cx0 = 0, cy0 = 0, cx1 = 0, cy1 = 0;
-                if (want0) {
-                    const int4 tr = A.tri[t0];
-                    const TriGeom gt = tri_geom(tr, A.vxy, N);
-                    P0 = sq_plane(gt, tr, A.uv, A.uvf);
-                    cx0 = gt.cx;
-                    cy0 = gt.cy;
-                }
-                if (want1) {
-                    const int4 tr = A.tri[t1];
-                    const TriGeom gt = tri_geom(tr, A.vxy, N);
-                    P1 = sq_plane(gt, tr, A.uv, A.uvf);
-                    cx1 = gt.cx;
-                    cy1 = gt.cy;
-                }
+                if (want0) sq_plane_at<MODE>(A, c0, t0, P0, cx0, cy0);
+                if (want1) sq_plane_at<MODE>(A, c1, t1, P1, cx1, cy1);
                 int2 na, nb, nc;
                 sq_node_tri(n0, G, na, nb, nc);
                 const int w = s + (J == Q - 1 ? 1 : 0), h = s + (I == Q - 1 ? 1 : 0);
@@ -836,10 +852,20 @@ __global__ void __launch_bounds__(256) k_sq_final(SqArgs A, const int* __restric
     const int s = A.G.s;
     for (int k = gw; k < n; k += nw) {
         const int c = coarse[k];
-        const int t = A.order[c];
-        if (MODE == SQ_EXACT && A.sel && !A.sel[t]) continue;  // the same for the whole warp
-        const int4 tr = A.tri[t];
-        const TriGeom gt = tri_geom(tr, A.vxy, A.G.N);
+        int t;
+        TriGeom gt;
+        int4 tr = make_int4(0, 0, 0, 0);
+        SqRec R{};
+        if (MODE == SQ_FAST) {
+            R = A.rec[c];
+            t = R.t;
+            gt = rec_geom(R, A.G.N);
+        } else {
+            t = A.order[c];
+            if (A.sel && !A.sel[t]) continue;  // the same for the whole warp
+            tr = A.tri[t];
+            gt = tri_geom(tr, A.vxy, A.G.N);
+        }
         const int w = (gt.maxw - 1) / s, h = (max(gt.ay, max(gt.by, gt.cy)) - gt.ytop) / s;
         const long long o = 2LL * A.sqoff[c];
         const long long cnt = o + 2LL * w * h <= A.part_cap ? 2LL * w * h : 0;
@@ -861,10 +887,7 @@ __global__ void __launch_bounds__(256) k_sq_final(SqArgs A, const int* __restric
         }
         S = ff_warp_sum(S);
         np = warp_sum(np);
-        if (lane == 0) {
-            const SqPlane P = sq_plane(gt, tr, A.uv, A.uvf);
-            sq_finish<MODE>(A, t, gt, P, S, np);
-        }
+        if (lane == 0) sq_finish<MODE>(A, t, gt, MODE == SQ_FAST ? rec_plane(R) : sq_plane(gt, tr, A.uv, A.uvf), S, np);
     }
 }
 
@@ -939,7 +962,8 @@ fem_status sq_plan(fem_mesh* m, cudaStream_t s) {
     // fine with an empty segment
     FEM_CUDA(cudaMemsetAsync(m->sq_cov.p, 0xff, sizeof(int) * nodes, s));
     FEM_CUDA(cudaMemsetAsync(m->sq_seg.p, 0xff, sizeof(int2) * nodes, s));
-    FEM_TRY(scan_fused(m, SqCountIn{m->order.p, m->tri.p, m->vxy.p, G, m->sq_nodeof.p, m->sq_flag.p},
+    FEM_TRY(ensure(m->sq_pos, (size_t)T, s));
+    FEM_TRY(scan_fused(m, SqCountIn{m->order.p, m->tri.p, m->vxy.p, G, m->sq_nodeof.p, m->sq_pos.p, m->sq_flag.p},
                        ScanStore{m->sq_off.p}, T, s, W, F_RASTER));
     // work: T curve positions, then at most 2 Q^2 bounding-box squares
     const long long work = std::max<long long>(T, 2LL * G.Q * G.Q);
@@ -1018,7 +1042,8 @@ fem_status sq_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, FastOu
 // selected triangles over the squares in list[0 .. *n_list) (n_max: the
 // list's capacity, for the grid).
 fem_status sq_keys_exact(fem_mesh* m, const double* uv, const float2* uvf, double* keys, unsigned long long* keyc,
-                         const unsigned char* sel, const int* list, const int* n_list, int n_max, cudaStream_t s) {
+                         const unsigned char* sel, const int* list, const int* n_list, int n_max, cudaStream_t s,
+                         const int* coarse, const int* n_coarse) {
     FEM_TRY(sq_plan(m, s));
     SqArgs A = sq_args(m, uv, uvf);
     A.keys = keys;
@@ -1030,8 +1055,9 @@ fem_status sq_keys_exact(fem_mesh* m, const double* uv, const float2* uvf, doubl
     const int fam = list ? F_RASTER : F_SQPASS;
     if (!list) note_bytes(F_SQPASS, sq_bytes(m, false));
     FEM_LAUNCH(fam, s, k_sq<SQ_EXACT>, sq_grid(m, list ? (long long)n_max : (long long)Q * Q), kSqThreads, 0, A);
-    FEM_LAUNCH(F_RASTER, s, k_sq_final<SQ_EXACT>, m->num_sms * 8, 256, 0, A, (const int*)m->sq_coarse.p,
-               (const int*)(m->sq_ctr.p + 1));
+    // the coarse triangles to finish: the given list, else all of them
+    FEM_LAUNCH(F_RASTER, s, k_sq_final<SQ_EXACT>, m->num_sms * 8, 256, 0, A, coarse ? coarse : (const int*)m->sq_coarse.p,
+               n_coarse ? n_coarse : (const int*)(m->sq_ctr.p + 1));
     return FEM_OK;
 }
 
@@ -1066,7 +1092,9 @@ fem_status sq_band_exact(fem_mesh* m, const double* uv, const float2* uvf, int* 
     FEM_CUDA(cudaMemsetAsync(n_list_dev, 0, sizeof(int), s));
     FEM_LAUNCH(F_TOPK, s, k_sq_band_list, (nsq + 255) / 256, 256, 0, nsq, (const int*)m->order.p,
                (const int*)m->sq_cov.p, (const unsigned char*)m->bsel.p, m->sq_mark.p, m->sq_list.p, n_list_dev);
-    return sq_keys_exact(m, uv, uvf, m->keys.p, m->keyc.p, m->bsel.p, m->sq_list.p, n_list_dev, nsq, s);
+    int* fc = (int*)(m->fast_hist.p + 2 * kFastBins);
+    return sq_keys_exact(m, uv, uvf, m->keys.p, m->keyc.p, m->bsel.p, m->sq_list.p, n_list_dev, nsq, s,
+                         (const int*)m->sq_bcoarse.p, (const int*)(fc + FC_BAND_COARSE));
 }
 
 }  // namespace fem
