@@ -31,18 +31,22 @@
 //     its columns);
 //   * fine triangles with a bounding box of at most 17 x 17 pixels are summed
 //     one per lane, walking their rows in shared memory;
-//   * larger fine triangles, and nodes inside coarse triangles (with the
-//     coarse triangle's plane), are summed by the warp: lane r finds the
-//     span of row r, then the lanes walk the rows over the columns;
-//   * the sums of coarse triangles go to per-node slots, and a second kernel
-//     adds each coarse triangle's slots in a fixed order with a block of
-//     threads.
+//   * nodes inside coarse triangles (with the coarse triangle's plane) are
+//     swept together over the square's full rows, and larger fine triangles
+//     over their bounding box: lane r finds the span of row r, then the
+//     lanes take the columns of each row;
+//   * the sums of coarse triangles go to per-node slots, and k_sq_final adds
+//     each coarse triangle's slots in a fixed order, one warp per triangle.
+// Squares that hold only small triangles are left to k_sq_small (one thread
+// per triangle along the curve, pixels from the squared image in global
+// memory); the plan lists the other squares for k_sq.
 // Every triangle's result is formed in a fixed order of operations, so the
 // pass is deterministic.
 //
 // Two modes.  FAST: FP32 sums with a rigorous error interval (the fast keys
 // of raster.cu: per-lane chains of at most kSqChain FP32 additions of
-// non-negative terms, combined in float-float).  EXACT: float-float per
+// non-negative terms, lanes added by an FP32 butterfly, nodes in
+// float-float), planes from per-triangle records.  EXACT: float-float per
 // pixel (the keys of the selection), over all triangles or only the
 // selected ones (the band of the fast keys), on all squares or a list.
 #include <algorithm>
