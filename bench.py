@@ -62,6 +62,8 @@ def parse():
                     help="relative tolerance of the tonal inner solves (default: the library's 1e-11; 1e-13 in "
                          "configuration 4, whose 50th outer iterate is sensitive to the inner solves' accuracy)")
     ap.add_argument("--seed", type=int, default=None)
+    ap.add_argument("--fast-keys", type=int, default=-1, choices=[-1, 0, 1],
+                    help="selection keys: -1 the library's choice by image size, 0 exact, 1 FP32 intervals + exact band")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check after timing")
     ap.add_argument("--no-fp64-timing", action="store_true", help="skip timing the plain FP64 GPU path")
@@ -115,7 +117,7 @@ def workload_name(a):
 def config(a, world):
     return {"workload": workload_name(a), "config_index": a.config, "image": f"{a.n}x{a.n}", "density": a.density,
             "topk_frac": a.frac, "tonal": a.tonal, "tonal_tol": a.tonal_tol, "tonal_iters": a.tonal_iters,
-            "inner_tol": a.inner_tol,
+            "inner_tol": a.inner_tol, "fast_keys": {-1: "auto", 0: "exact", 1: "fp32_band"}[getattr(a, "fast_keys", -1)],
             "precision": a.precision, "seed": a.seed, "l2_flush": True,
             "parallelism": f"replicas{world}" if world > 1 else "single"}
 
@@ -246,7 +248,8 @@ def run_ours(a, world, rank, local):
     f_np = seeded_inputs.make_image(n, replica_seed(a.seed, rank), texture=a.texture)
     f = torch.from_numpy(f_np).to(dev)
     prec = fem.FEM_PREC_FP64 if a.precision == "fp64" else fem.FEM_PREC_FP32_IR
-    p = fem.params(topk_frac=a.frac, tonal_tol=a.tonal_tol, precision=prec, inner_tol=a.inner_tol)
+    p = fem.params(topk_frac=a.frac, tonal_tol=a.tonal_tol, precision=prec, inner_tol=a.inner_tol,
+                   fast_keys=a.fast_keys)
     if a.tonal == "iters":
         p.tonal_maxit = a.tonal_iters
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -351,7 +354,7 @@ def run_ours(a, world, rank, local):
     fp64_path = None
     if not a.no_fp64_timing and a.precision != "fp64":
         p64t = fem.params(topk_frac=a.frac, tonal_tol=a.tonal_tol, precision=fem.FEM_PREC_FP64,
-                          inner_tol=a.inner_tol)
+                          inner_tol=a.inner_tol, fast_keys=a.fast_keys)
         if a.tonal == "iters":
             p64t.tonal_maxit = a.tonal_iters
         step(f, pp=p64t)
@@ -436,6 +439,7 @@ def run_ours(a, world, rank, local):
     line.update(extra)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, f_np, gpu_info)
+        line["cpu_baseline_openmp"] = cpu_baseline_openmp(a, f_np, gpu_info)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -588,6 +592,25 @@ def cpu_baseline(a, f_np, gpu):
                       f"set-up on the GPU's final mesh ({t_tonal1:.2f} s, scaled to {gpu['tonal_iters']} "
                       f"iterations); estimated {est:.0f} s for the job (a lower bound: the sampled rounds run on "
                       f"the loop's smallest meshes)"}
+
+
+def cpu_baseline_openmp(a, f_np, gpu):
+    """The same measurement as cpu_baseline with the oracle's OpenMP build on
+    all host cores (raster and A_UU x parallel, bit-identical results)."""
+    import oracle
+    try:
+        oracle.build(openmp=True)
+        cores = oracle.use_openmp(True)
+    except Exception as e:  # noqa: BLE001
+        return {"unavailable": f"OpenMP build of the oracle failed: {e}"}
+    try:
+        out = cpu_baseline(a, f_np, gpu)
+    finally:
+        oracle.use_openmp(False)
+    out["cores"] = cores
+    out["kind"] = "oracle_openmp"
+    out["sample"] = out["sample"].replace("(single thread)", f"(OpenMP build, {cores} threads)")
+    return out
 
 
 def run_reference(a, world, rank):

@@ -31,6 +31,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _SO = os.path.join(_HERE, "_liboracle.so")
+_SO_OMP = os.path.join(_HERE, "_liboracle_omp.so")
 
 OM_OK = 0
 OM_E_INVALID = 1
@@ -38,24 +39,38 @@ OM_E_OOM = 3
 OM_E_NOT_CONVERGED = 4
 LOG_COLS = 8
 
-_lib = None
+_libs = {}
+_openmp = False
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into the oracle library used by the tests (gcc, plain C11)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
-    return _SO
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile oracle.c into the oracle library used by the tests (gcc, plain
+    C11).  openmp=True builds the multi-core variant (-fopenmp) used as the
+    second CPU baseline; its results are bit-identical (see oracle.c)."""
+    so = _SO_OMP if openmp else _SO
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+        tmp = so + ".tmp.%d" % os.getpid()
+        extra = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, so)
+    return so
+
+
+def use_openmp(on: bool = True) -> int:
+    """Meshes created from now on use the OpenMP build (on=True) or the
+    single-thread build (on=False).  Returns the thread count of that build
+    (OMP_NUM_THREADS, else all host cores)."""
+    global _openmp
+    _openmp = bool(on)
+    return int(_load().om_threads())
 
 
 def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
-    build()
-    L = ctypes.CDLL(_SO)
+    L = _libs.get(_openmp)
+    if L is not None:
+        return L
+    so = build(openmp=_openmp)
+    L = ctypes.CDLL(so)
     P = ctypes.c_void_p
     ip = ctypes.POINTER(ctypes.c_int)
     dp = ctypes.POINTER(ctypes.c_double)
@@ -84,7 +99,8 @@ def _load():
     L.om_apply_B.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_int]
     L.om_apply_BT.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_int]
     L.om_tonal.argtypes = [P, fp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]
-    _lib = L
+    L.om_threads.restype = ctypes.c_int
+    _libs[_openmp] = L
     return L
 
 

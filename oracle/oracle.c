@@ -38,9 +38,20 @@
  *  R8  Top-k: k = max(1, ceil(frac*T)), capped by the number of eligible
  *      triangles and by V* - V; order by key descending, then id ascending.
  *      A triangle is eligible when its refinement-edge midpoint is a pixel.
+ *
+ * Threads.  Compiled with -fopenmp (the multi-core CPU baseline), two loops
+ * share their iterations among threads: the per-triangle raster loop and the
+ * row loop of A_UU x.  In both each output element (a pixel, a key, a row) is
+ * computed by one thread with the same operations in the same order, so the
+ * results are bit-identical to the single-thread build.  Dot products, the
+ * scatter P^T r, sorting and refinement stay serial.  Without -fopenmp the
+ * pragmas are ignored.
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -436,6 +447,7 @@ int om_stiffness_csr(const om_mesh *m, int *rowptr, int *col, double *val, int c
 /* y_U = A_UU x_U, using the vertex-indexed vector x (entries at K ignored) */
 static void apply_AUU(const om_mesh *m, const sp_rows *A, const double *x, double *y)
 {
+    #pragma omp parallel for schedule(static) if (m->V > 4096)
     for (int i = 0; i < m->V; ++i) {
         if (m->mask[i]) continue;
         double s = A->diag[i] * x[i];
@@ -603,8 +615,12 @@ static int pix_buf_fit(pix_buf *pb, const om_mesh *m, int t)
     pb->px = malloc(sizeof(int) * need); pb->py = malloc(sizeof(int) * need);
     pb->la = malloc(sizeof(double) * need); pb->lb = malloc(sizeof(double) * need);
     pb->lc = malloc(sizeof(double) * need);
+    if (!pb->px || !pb->py || !pb->la || !pb->lb || !pb->lc) {
+        free(pb->px); free(pb->py); free(pb->la); free(pb->lb); free(pb->lc);
+        memset(pb, 0, sizeof(*pb));
+        return OM_E_OOM;
+    }
     pb->cap = need;
-    if (!pb->px || !pb->py || !pb->la || !pb->lb || !pb->lc) return OM_E_OOM;
     return OM_OK;
 }
 
@@ -618,30 +634,49 @@ int om_raster(const om_mesh *m, const double *v, const float *f, double *u_img, 
 {
     long P = (long)m->N * m->N;
     int rc = OM_OK;
-    pix_buf pb;
-    memset(&pb, 0, sizeof(pb));
     if (owner) for (long p = 0; p < P; ++p) owner[p] = -1;
-    for (int t = 0; t < m->T && !rc; ++t) {
-        if (pix_buf_fit(&pb, m, t)) { rc = OM_E_OOM; break; }
-        long n = owned_pixels(m, t, pb.px, pb.py, pb.la, pb.lb, pb.lc);
-        double va = v[m->ta[t]], vb = v[m->tb[t]], vc = v[m->tc[t]];
-        double err = 0.0;
-        for (long q = 0; q < n; ++q) {
-            long p = (long)pb.py[q] * m->N + pb.px[q];
-            double u = pb.la[q] * va + pb.lb[q] * vb + pb.lc[q] * vc;
-            if (u_img) u_img[p] = u;
-            if (f) { double d = u - (double)f[p]; err += d * d; }
-            if (owner) {
-                if (owner[p] != -1) rc = OM_E_INVALID;
-                owner[p] = t;
+    /* The ownership check writes shared state, so it runs on one thread. */
+    #pragma omp parallel if (!owner && m->T > 64)
+    {
+        pix_buf pb;
+        memset(&pb, 0, sizeof(pb));
+        #pragma omp for schedule(dynamic, 16)
+        for (int t = 0; t < m->T; ++t) {
+            if (pix_buf_fit(&pb, m, t)) {
+                #pragma omp atomic write
+                rc = OM_E_OOM;
+                continue;
             }
+            long n = owned_pixels(m, t, pb.px, pb.py, pb.la, pb.lb, pb.lc);
+            double va = v[m->ta[t]], vb = v[m->tb[t]], vc = v[m->tc[t]];
+            double err = 0.0;
+            for (long q = 0; q < n; ++q) {
+                long p = (long)pb.py[q] * m->N + pb.px[q];
+                double u = pb.la[q] * va + pb.lb[q] * vb + pb.lc[q] * vc;
+                if (u_img) u_img[p] = u;
+                if (f) { double d = u - (double)f[p]; err += d * d; }
+                if (owner) {
+                    if (owner[p] != -1) rc = OM_E_INVALID;
+                    owner[p] = t;
+                }
+            }
+            if (keys) keys[t] = err;
         }
-        if (keys) keys[t] = err;
+        pix_buf_free(&pb);
     }
     if (owner && !rc)
         for (long p = 0; p < P; ++p) if (owner[p] < 0) { rc = OM_E_INVALID; break; }
-    pix_buf_free(&pb);
     return rc;
+}
+
+/* Threads the library computes with: 1 unless compiled with OpenMP. */
+int om_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* s = P^T r: each pixel's value spread onto the three vertices of its owner
