@@ -18,7 +18,9 @@
  *  - "_dev" pointers are device pointers on the current CUDA device; the
  *    caller owns them.  Host pointers are named "_host" or documented as host
  *    buffers.  The library owns the mesh and all its scratch memory, which it
- *    allocates with the stream-ordered allocator on the stream it is given.
+ *    allocates with the stream-ordered allocator on the stream it is given,
+ *    from the pool set with fem_set_mem_pool (default: the device's current
+ *    pool).
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Every call enqueues its work on that stream; calls that return
  *    sizes or convergence results synchronise that stream before returning.
@@ -53,7 +55,8 @@ typedef enum {
     FEM_E_OOM = 3,           /* device allocation failed */
     FEM_E_NOT_CONVERGED = 4, /* iteration cap reached; last iterate written */
     FEM_E_TIMEOUT = 5,       /* a bounded device-side wait ran out */
-    FEM_E_CUDA = 6           /* a CUDA runtime error (message in fem_last_error) */
+    FEM_E_CUDA = 6,          /* a CUDA runtime error (message in fem_last_error) */
+    FEM_E_CANCELLED = 7      /* a served request cancelled by fem_server_cancel */
 } fem_status;
 
 enum {
@@ -277,6 +280,17 @@ FEM_API fem_status fem_server_wait(fem_server *sv, long long id, double timeout_
 FEM_API fem_status fem_server_result(fem_server *sv, long long id, int *sizes, int *xy, int *tri,
                                      unsigned char *is_mask, float *g, double *times);
 
+/* State of a request: *state = 0 queued, 1 running, 2 finished. */
+FEM_API fem_status fem_server_state(fem_server *sv, long long id, int *state);
+
+/* Cancel a request.  A queued request is removed from the queue; a running
+ * one stops at its next spatial round or tonal iteration (its kernels in
+ * flight finish first, nothing is interrupted on the device) and frees its
+ * memory.  Either way the request then counts as finished with status
+ * FEM_E_CANCELLED (no results).  Cancelling a finished request does nothing
+ * and returns FEM_OK; an unknown id returns FEM_E_INVALID. */
+FEM_API fem_status fem_server_cancel(fem_server *sv, long long id);
+
 /* Drop a finished request's results. */
 FEM_API fem_status fem_server_release(fem_server *sv, long long id);
 
@@ -313,6 +327,25 @@ FEM_API fem_status fem_selftest_wait_timeout(void *stream);
 
 /* Number of kernels this library has launched in the process so far. */
 FEM_API long long fem_launch_count(void);
+
+/* Memory pool for the library's device allocations (the mesh, its scratch,
+ * the server's request buffers).  pool is a cudaMemPool_t passed as void*;
+ * allocations from now on are made with cudaMallocFromPoolAsync on that
+ * pool, on the stream of the call.  NULL returns to the current device's
+ * current pool (cudaMallocAsync).  The setting is process-wide; memory
+ * already allocated stays where it is and is freed in stream order as usual.
+ * The caller keeps the pool alive until every mesh and server created while
+ * it was set has been destroyed. */
+FEM_API fem_status fem_set_mem_pool(void *pool);
+
+/* Test hook for the library's handling of a full device (no counterpart in
+ * the paper).  *calls_out (may be NULL) receives the number of device
+ * allocations the library has attempted in this process so far.  With
+ * fail_after >= 0 the allocation that comes fail_after attempts from now
+ * (0: the next one) fails as if the device were full: it makes no CUDA call
+ * and the operation that needed it returns FEM_E_OOM.  fail_after < 0
+ * disarms the hook.  Host-side only: nothing runs on the device. */
+FEM_API fem_status fem_debug_alloc_fault(long long fail_after, long long *calls_out);
 
 #ifdef __cplusplus
 }

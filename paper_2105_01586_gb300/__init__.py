@@ -38,16 +38,18 @@ FEM_E_OOM = 3
 FEM_E_NOT_CONVERGED = 4
 FEM_E_TIMEOUT = 5
 FEM_E_CUDA = 6
+FEM_E_CANCELLED = 7
 FEM_PREC_FP32_IR = 0
 FEM_PREC_FP64 = 1
 _STATUS = {0: "FEM_OK", 1: "FEM_E_INVALID", 2: "FEM_E_SHAPE", 3: "FEM_E_OOM", 4: "FEM_E_NOT_CONVERGED",
-           5: "FEM_E_TIMEOUT", 6: "FEM_E_CUDA"}
+           5: "FEM_E_TIMEOUT", 6: "FEM_E_CUDA", 7: "FEM_E_CANCELLED"}
 
 EXPORTED = ["fem_params_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_info", "fem_mesh_export",
             "fem_mesh_import", "fem_mesh_curve_order", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_triangle_error_bounds", "fem_triangle_errors_noalloc", "fem_rasterize", "fem_spatial_refine",
             "fem_tonal_opt", "fem_adjoint", "fem_tonal_loss", "fem_mesh_stats", "fem_last_error", "fem_profile_enable",
             "fem_profile_read", "fem_launch_count", "fem_selftest_wait_timeout", "fem_server_create",
-            "fem_server_submit", "fem_server_wait", "fem_server_result", "fem_server_release", "fem_server_destroy"]
+            "fem_server_submit", "fem_server_wait", "fem_server_result", "fem_server_state", "fem_server_cancel", "fem_server_release",
+            "fem_server_destroy", "fem_set_mem_pool", "fem_debug_alloc_fault"]
 
 
 class fem_params(ctypes.Structure):
@@ -95,7 +97,11 @@ _sig = {
     "fem_server_submit": (_i, [_vp, _i, _vp, ctypes.c_double, _pp, ctypes.POINTER(ctypes.c_longlong)]),
     "fem_server_wait": (_i, [_vp, ctypes.c_longlong, ctypes.c_double, _ip]),
     "fem_server_result": (_i, [_vp, ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "fem_server_cancel": (_i, [_vp, ctypes.c_longlong]),
+    "fem_server_state": (_i, [_vp, ctypes.c_longlong, _ip]),
     "fem_server_release": (_i, [_vp, ctypes.c_longlong]),
+    "fem_set_mem_pool": (_i, [_vp]),
+    "fem_debug_alloc_fault": (_i, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
     "fem_server_destroy": (_i, [_vp]),
 }
 for _n, (_r, _a) in _sig.items():
@@ -321,6 +327,20 @@ def fem_selftest_wait_timeout(stream=None) -> int:
 
 def fem_launch_count() -> int:
     return int(_lib.fem_launch_count())
+
+
+def fem_set_mem_pool(pool) -> None:
+    """Device allocations from now on come from `pool` (a cudaMemPool_t as an
+    int or c_void_p); None returns to the device's current pool."""
+    _check(_lib.fem_set_mem_pool(pool), "fem_set_mem_pool")
+
+
+def fem_debug_alloc_fault(fail_after: int) -> int:
+    """Arm (fail_after >= 0) or disarm (< 0) the injected allocation failure;
+    returns the device allocations attempted so far."""
+    n = ctypes.c_longlong()
+    _check(_lib.fem_debug_alloc_fault(int(fail_after), ctypes.byref(n)), "fem_debug_alloc_fault")
+    return int(n.value)
 
 
 # ------------------------------------------------------------- convenience

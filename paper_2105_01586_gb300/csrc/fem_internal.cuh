@@ -8,6 +8,7 @@
 //                   between rounds as the warm start
 // Per-round scratch is sized by capacity and reused.
 #pragma once
+#include <atomic>
 #include <utility>
 
 #include <cuda_runtime.h>
@@ -16,11 +17,22 @@
 #include <string>
 
 #include "../../include/feminpaint.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace fem {
 
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
+
+// NVTX range for the lifetime of a scope: API calls, spatial rounds, Laplace
+// solves and tonal iterations show up by name in Nsight timelines (a no-op
+// unless a tool is attached).
+struct Nvtx {
+    explicit Nvtx(const char* name) { nvtxRangePushA(name); }
+    ~Nvtx() { nvtxRangePop(); }
+    Nvtx(const Nvtx&) = delete;
+    Nvtx& operator=(const Nvtx&) = delete;
+};
 fem_status cuda_fail(cudaError_t e, const char* what);
 
 #define FEM_CUDA(call)                                              \
@@ -210,6 +222,9 @@ struct fem_mesh {
     int V = 0, T = 0, nK = 0, nU = 0;
     int dev = 0, num_sms = 0;
     cudaStream_t last_stream = nullptr;
+    // set by the server for a running request: the spatial rounds and the
+    // tonal iterations stop with FEM_E_CANCELLED once it reads nonzero
+    const std::atomic<int>* cancel = nullptr;
 
     // mesh proper
     fem::DArr<int2> vxy;
@@ -303,10 +318,12 @@ struct fem_mesh {
     fem::DArr<int2> sq_seg;            // per node: curve segment of its triangles
     fem::DArr<float4> sq_part;         // partial sums (hi, lo, pixel count)
     fem::DArr<int> sq_coarse, sq_list; // curve positions of the coarse triangles; listed squares
+    fem::DArr<int4> sq_long;           // long coarse triangles (curve position, first piece, pieces, slots)
+    fem::DArr<int2> sq_piece;          // pieces of the long ones (triangle, index)
+    fem::DArr<float4> sq_psum;         // their sums
+    fem::DArr<int> sq_pdone;           // finished pieces per long triangle
     fem::DArr<int> sq_ctr;             // [0] coarse bounding-box squares, [1] coarse triangles
     fem::DArr<int4> sq_rec;            // 2 int4 per curve position: fine-triangle records of the FP32 pass
-    fem::DArr<int> sq_stage;           // squares of the staged FP32 pass (count in sq_ctr[2])
-    fem::DArr<unsigned char> sq_flag, sq_staged;  // per square: flagged by the plan; staged (this plan)
     fem::DArr<unsigned char> sq_mark, bsel;  // squares with a band triangle; band flag per triangle
     long long sq_plan_version = -1;
     fem::DArr<double> lossk, lossred;  // tonal loss: per-triangle squared errors, block partial sums
@@ -320,6 +337,15 @@ struct fem_mesh {
 };
 
 namespace fem {
+// A cancelled request stops between spatial rounds and tonal iterations.
+inline fem_status check_cancel(const fem_mesh* m) {
+    if (m->cancel && m->cancel->load(std::memory_order_relaxed) != 0) {
+        set_error("request cancelled");
+        return FEM_E_CANCELLED;
+    }
+    return FEM_OK;
+}
+
 // component sizes: up to kWarpComp rows a warp solves the component, up to
 // kBlockComp a block; a larger component sends the whole system to the
 // grid-wide solver

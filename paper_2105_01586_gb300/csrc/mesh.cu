@@ -124,9 +124,23 @@ void reset_coop_state(fem_mesh* m, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ memory
+// Every device allocation of the library comes through dalloc_raw: from the
+// caller's pool when one is set, else from the device's current pool.  The
+// attempt counter and the armed failure index serve fem_debug_alloc_fault.
+static std::atomic<long long> g_alloc_calls{0};
+static std::atomic<long long> g_alloc_fail_at{-1};
+static std::atomic<cudaMemPool_t> g_pool{nullptr};
+
 fem_status dalloc_raw(void** p, size_t bytes, cudaStream_t s) {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    long long k = g_alloc_calls.fetch_add(1);
+    if (k == g_alloc_fail_at.load()) {
+        *p = nullptr;
+        set_error("device allocation of " + std::to_string(bytes) + " bytes failed: injected by fem_debug_alloc_fault");
+        return FEM_E_OOM;
+    }
+    cudaMemPool_t pool = g_pool.load();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
@@ -339,6 +353,18 @@ const char* fem_last_error(void) { return g_last_error.c_str(); }
 
 long long fem_launch_count(void) { return g_launches.load(); }
 
+fem_status fem_set_mem_pool(void* pool) {
+    g_pool.store((cudaMemPool_t)pool);
+    return FEM_OK;
+}
+
+fem_status fem_debug_alloc_fault(long long fail_after, long long* calls_out) {
+    long long now = g_alloc_calls.load();
+    if (calls_out) *calls_out = now;
+    g_alloc_fail_at.store(fail_after >= 0 ? now + fail_after : -1);
+    return FEM_OK;
+}
+
 void fem_profile_enable(int family_mask) { g_prof_on.store(family_mask); }
 
 int fem_profile_read(int family, long long* launches, double* ms, double* bytes, const char** name) {
@@ -491,8 +517,9 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->lossk, s); release(m->lossred, s); release(m->tyr, s);
     release(m->fsq, s); release(m->fedge, s); release(m->sq_nodeof, s); release(m->sq_off, s);
     release(m->sq_cov, s); release(m->sq_slot, s); release(m->sq_seg, s); release(m->sq_part, s);
-    release(m->sq_coarse, s); release(m->sq_ctr, s); release(m->sq_list, s); release(m->sq_rec, s);
-    release(m->sq_stage, s); release(m->sq_flag, s); release(m->sq_staged, s); release(m->sq_pos, s); release(m->sq_bcoarse, s); release(m->sq_mark, s); release(m->bsel, s);
+    release(m->sq_coarse, s); release(m->sq_long, s); release(m->sq_piece, s); release(m->sq_psum, s);
+    release(m->sq_pdone, s); release(m->sq_ctr, s); release(m->sq_list, s); release(m->sq_rec, s);
+    release(m->sq_pos, s); release(m->sq_bcoarse, s); release(m->sq_mark, s); release(m->bsel, s);
     cudaStreamSynchronize(s);
     if (m->host_stage) cudaFreeHost(m->host_stage);
     if (m->round_ev) cudaEventDestroy(m->round_ev);

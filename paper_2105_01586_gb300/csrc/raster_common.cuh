@@ -53,6 +53,41 @@ __device__ __forceinline__ void row_span(const TriGeom& g, int y, int N, int& L,
     len = n > 0 ? n : 0;
 }
 
+// Row spans in closed form.  Every edge of the mesh's triangles is
+// horizontal, vertical or diagonal, so with the corners sorted by y (v0, v1,
+// v2) row y meets the long edge v0-v2 at x0 + (y - y0) s02 and the short
+// edges at x0 + (y - y0) s01 (y < y1) or x1 + (y - y1) s12, where s is the
+// edge's step in x per row (0 or +-1).  The span [min, max) of the two, with
+// the image's last column added as in row_span, equals row_span's for every
+// owned row, at a few operations per row instead of three edge tests.
+struct RowGeo {
+    int y0, y1, x0, x1;
+    int sl;  // (s02 + 1) | (s01 + 1) << 2 | (s12 + 1) << 4
+};
+
+__device__ __forceinline__ int step_sign(int d) { return (d > 0) - (d < 0); }
+
+__device__ __forceinline__ RowGeo row_geo(const TriGeom& g) {
+    int ax = g.ax, ay = g.ay, bx = g.bx, by = g.by, cx = g.cx, cy = g.cy, t;
+    if (by < ay) { t = ax; ax = bx; bx = t; t = ay; ay = by; by = t; }
+    if (cy < by) { t = bx; bx = cx; cx = t; t = by; by = cy; cy = t; }
+    if (by < ay) { t = ax; ax = bx; bx = t; t = ay; ay = by; by = t; }
+    RowGeo r;
+    r.y0 = ay; r.y1 = by; r.x0 = ax; r.x1 = bx;
+    r.sl = (step_sign(cx - ax) + 1) | ((step_sign(bx - ax) + 1) << 2) | ((step_sign(cx - bx) + 1) << 4);
+    return r;
+}
+
+__device__ __forceinline__ void row_span_geo(const RowGeo& r, int y, int N, int& L, int& len) {
+    const int s02 = (r.sl & 3) - 1, s01 = ((r.sl >> 2) & 3) - 1, s12 = ((r.sl >> 4) & 3) - 1;
+    const int xl = r.x0 + (y - r.y0) * s02;
+    const int xs = y < r.y1 ? r.x0 + (y - r.y0) * s01 : r.x1 + (y - r.y1) * s12;
+    const int l = min(xl, xs), rr = max(xl, xs);
+    const int n = rr - l + ((rr == N - 1 && l < rr) ? 1 : 0);
+    L = l;
+    len = n > 0 ? n : 0;
+}
+
 // Small triangles (bounding box at most kSmallSide pixels each way, at most
 // 153 pixels) are rasterised one per thread along the space-filling curve
 // (k_raster_small); only the larger ones are cut into warp items.

@@ -29,17 +29,17 @@
 // last row is loaded by the last row of squares.  In a square:
 //   * a square inside one triangle is summed as a dense block (lanes over
 //     its columns);
-//   * fine triangles with a bounding box of at most 17 x 17 pixels are summed
-//     one per lane, walking their rows in shared memory;
 //   * nodes inside coarse triangles (with the coarse triangle's plane) are
-//     swept together over the square's full rows, and larger fine triangles
-//     over their bounding box: lane r finds the span of row r, then the
-//     lanes take the columns of each row;
+//     swept together over the square's full rows: lane r finds the span of
+//     row r, then the lanes take the columns of each row;
+//   * fine triangles, FAST mode: one triangle row per lane (sq_fine_rows),
+//     rows of a triangle combined by a segmented warp scan, so the lanes
+//     stay busy for any mix of sizes;
+//   * fine triangles, EXACT mode: those with a bounding box of at most
+//     17 x 17 pixels one per lane, larger ones over their bounding box with
+//     the lanes over the columns;
 //   * the sums of coarse triangles go to per-node slots, and k_sq_final adds
 //     each coarse triangle's slots in a fixed order, one warp per triangle.
-// Squares that hold only small triangles are left to k_sq_small (one thread
-// per triangle along the curve, pixels from the squared image in global
-// memory); the plan lists the other squares for k_sq.
 // Every triangle's result is formed in a fixed order of operations, so the
 // pass is deterministic.
 //
@@ -68,10 +68,12 @@ constexpr int kSqWarps = kSqThreads / 32;
 // larger fine triangles of one square: a bounding box above 17 pixels means
 // at least 81 pixels, so at most 1089 / 81 = 13
 constexpr int kSqBigCap = 32;
-// Longest FP32 addition chain of one lane in the FAST mode: a small triangle
-// summed by one lane has at most 153 pixels; with the lanes over the columns
-// a lane takes at most 2 pixels in each of at most 33 rows.  Lanes are
-// combined in float-float.
+// Bound on the FP32 additions any term of a FAST sum passes through: a row
+// of a fine triangle is one lane's chain of at most 33 additions, then at
+// most 5 levels of the segmented scan and 3 batches (41 in all); with the
+// lanes over the columns of a coarse node a lane takes at most 2 pixels in
+// each of at most 33 rows, then 5 levels of the butterfly.  Kept at the
+// 153-pixel chain of a triangle summed by one lane, which covers both.
 constexpr float kSqChain = 153.0f + 7.0f;
 constexpr unsigned long long kSqWaitLimitNs = 1000000000ull;
 
@@ -122,7 +124,6 @@ struct SqCountIn {
     SqGeo G;
     int* nodeof;
     int* pos;             // curve position of each triangle
-    unsigned char* flag;  // squares that the staged pass takes (a fine triangle larger than small)
     __device__ __forceinline__ int operator()(long long i) const {
         const int t = order[i];
         pos[t] = (int)i;
@@ -131,7 +132,6 @@ struct SqCountIn {
         if (leg2(a, c) <= (long long)G.s * G.s) {
             const int n = sq_node_at((long long)a.x + b.x + c.x, (long long)a.y + b.y + c.y, G);
             nodeof[i] = n;
-            if (!is_small(geom_xy(a, b, c, G.N))) flag[n >> 1] = 1;
             return 0;
         }
         nodeof[i] = -1;
@@ -139,6 +139,24 @@ struct SqCountIn {
         const int h = max(a.y, max(b.y, c.y)) - min(a.y, min(b.y, c.y));
         return (w / G.s) * (h / G.s);
     }
+};
+
+// Coarse triangles with more than kSqPiece node slots ("long": the large
+// triangles of the early rounds) are summed in pieces of kSqPiece slots, one
+// block per piece, so that no single warp reads a large triangle's slots
+// alone.  longs[L] = (curve position, first piece, pieces, slots); piece[p] =
+// (L, index of the piece in its triangle); psum[p] the piece's sum; pdone[L]
+// counts the finished pieces (the block that finishes the last one adds them
+// up and resets it to zero).
+constexpr int kSqPiece = 4096;
+struct SqLong {
+    int4* longs;
+    int2* piece;
+    float4* psum;
+    int* pdone;
+    int* n_long;
+    int* n_pieces;
+    int cap_long, cap_pieces;
 };
 
 // Node tables: a fine node gets its curve segment [start, end) and ncov =
@@ -150,10 +168,11 @@ __global__ void k_sq_nodes(const int* __restrict__ order, const int4* __restrict
                            const int* __restrict__ nodeof, const int* __restrict__ sqoff, const int* __restrict__ W_dev,
                            int T, SqGeo G, int* __restrict__ ncov, int2* __restrict__ nseg, int* __restrict__ nslot,
                            float4* __restrict__ partial, long long part_cap, int* __restrict__ err,
-                           int* __restrict__ coarse, int* __restrict__ n_coarse, unsigned char* __restrict__ flag) {
+                           int* __restrict__ coarse, int* __restrict__ n_coarse, SqLong LG) {
     pdl_wait();
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int W = *W_dev;
     // every thread of the grid runs the same number of iterations of this
     // loop (the bound is rounded up to the grid), so the warp-aggregated
     // append below sees full warps
@@ -165,7 +184,22 @@ __global__ void k_sq_nodes(const int* __restrict__ order, const int4* __restrict
         int base = 0;
         if ((threadIdx.x & 31) == 0 && bal) base = atomicAdd(n_coarse, __popc(bal));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (is_coarse) coarse[base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = (int)i;
+        if (is_coarse) {
+            coarse[base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = (int)i;
+            // a long triangle is also listed with its pieces
+            const int cnt = 2 * ((i + 1 < T ? sqoff[i + 1] : W) - sqoff[i]);
+            if (cnt > kSqPiece) {
+                const int np = (cnt + kSqPiece - 1) / kSqPiece;
+                const int L = atomicAdd(LG.n_long, 1);
+                const int pb = atomicAdd(LG.n_pieces, np);
+                if (L < LG.cap_long && pb + np <= LG.cap_pieces) {
+                    LG.longs[L] = make_int4((int)i, pb, np, cnt);
+                    for (int j = 0; j < np; ++j) LG.piece[pb + j] = make_int2(L, j);
+                } else {
+                    atomicCAS(err, 0, (int)FEM_E_INVALID);
+                }
+            }
+        }
         if (i >= T || n < 0) continue;
         if (i == 0 || nodeof[i - 1] != n) {
             nseg[n].x = (int)i;
@@ -173,7 +207,6 @@ __global__ void k_sq_nodes(const int* __restrict__ order, const int4* __restrict
         }
         if (i == T - 1 || nodeof[i + 1] != n) nseg[n].y = (int)i + 1;
     }
-    const int W = *W_dev;
     if (2LL * W > part_cap) {
         // more bounding-box squares than a conforming mesh can have: nothing
         // is written past the slots, the call reports the mesh as invalid
@@ -204,7 +237,6 @@ __global__ void k_sq_nodes(const int* __restrict__ order, const int4* __restrict
             if (inside3((long long)na.x + nb.x + nc.x, (long long)na.y + nb.y + nc.y, a, b, cc)) {
                 ncov[n] = c;
                 nslot[n] = (int)(2 * w + h);
-                flag[n >> 1] = 1;
             } else {
                 partial[2 * w + h] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
@@ -237,6 +269,7 @@ struct SqArgs {
     const unsigned char* sel;   // SQ_EXACT: only triangles with sel[t] != 0 (null: all)
     const int* sq_list;         // squares to process (null: all Q*Q)
     const int* n_sq;            // their number (device)
+    SqLong LG;                  // long coarse triangles and their pieces
     int* err;
 };
 
@@ -284,59 +317,28 @@ __device__ __forceinline__ void sq_finish(const SqArgs& A, int t, const TriGeom&
     }
 }
 
-// One lane, one small fine triangle, pixels from the staged square.  Along a
-// row u = g_x k + u_row is evaluated afresh per pixel (FAST; k counted in
-// floats, exact) or advanced by the exact float-float g_x (EXACT).  FAST
-// returns the histogram bins (0xffffffff: none) for warp aggregation.
-template <int MODE>
+// EXACT: one lane, one small fine triangle, pixels from the staged square;
+// along a row u is advanced by the exact float-float g_x.
 __device__ __forceinline__ void sq_small(const SqArgs& A, const float* img, int x0, int y0, int pitch, int t,
-                                         const TriGeom& g, const SqPlane& P, unsigned& blo, unsigned& bhi) {
+                                         const TriGeom& g, const SqPlane& P) {
     const int N = A.G.N;
-    if (MODE == SQ_FAST) {
-        float acc = 0.f;
-        int n = 0;
-        for (int y = g.ytop; y <= g.yend; ++y) {
-            int L, len;
-            row_span(g, y, N, L, len);
-            if (len <= 0) continue;
-            const float* rowp = img + (y - y0) * pitch + (L - x0);
-            const float urow = fmaf(P.gyf, (float)(y - g.cy), fmaf(P.gxf, (float)(L - g.cx), P.ucf));
-            float fk = 0.f;
+    ff acc{0.f, 0.f};
+    for (int y = g.ytop; y <= g.yend; ++y) {
+        int L, len;
+        row_span(g, y, N, L, len);
+        if (len <= 0) continue;
+        const float* rowp = img + (y - y0) * pitch + (L - x0);
+        ff u = ff_add(ff_add(P.uc, ff_mul_f(P.gx, (float)(L - g.cx))), ff_mul_f(P.gy, (float)(y - g.cy)));
 #pragma unroll 4
-            for (int k = 0; k < len; ++k) {
-                const float d = fmaf(P.gxf, fk, urow) - rowp[k];
-                acc = fmaf(d, d, acc);
-                fk += 1.0f;
-            }
-            n += len;
+        for (int k = 0; k < len; ++k) {
+            const ff d = ff_add_f(u, -rowp[k]);
+            acc = ff_add(acc, ff_sqr(d));
+            u = ff_add(u, P.gx);
         }
-        float lo, hi;
-        fast_interval(ff{acc, 0.f}, (float)n, fast_M(g, P.ucf, P.gxf, P.gyf), kSqChain, lo, hi);
-        A.F.lo[t] = lo;
-        A.F.hi[t] = hi;
-        if (tri_eligible(g)) {
-            blo = fast_bin(lo);
-            bhi = fast_bin(hi);
-        }
-    } else {
-        ff acc{0.f, 0.f};
-        for (int y = g.ytop; y <= g.yend; ++y) {
-            int L, len;
-            row_span(g, y, N, L, len);
-            if (len <= 0) continue;
-            const float* rowp = img + (y - y0) * pitch + (L - x0);
-            ff u = ff_add(ff_add(P.uc, ff_mul_f(P.gx, (float)(L - g.cx))), ff_mul_f(P.gy, (float)(y - g.cy)));
-#pragma unroll 4
-            for (int k = 0; k < len; ++k) {
-                const ff d = ff_add_f(u, -rowp[k]);
-                acc = ff_add(acc, ff_sqr(d));
-                u = ff_add(u, P.gx);
-            }
-        }
-        const double key = ff_to_double(acc);
-        A.keys[t] = key;
-        if (A.keyc) A.keyc[t] = sq_keyc(g, key);
     }
+    const double key = ff_to_double(acc);
+    A.keys[t] = key;
+    if (A.keyc) A.keyc[t] = sq_keyc(g, key);
 }
 
 // The warp's sum of the lanes' sums: FAST adds the FP32 sums by a butterfly
@@ -572,26 +574,6 @@ __global__ void k_sq_records(const int* __restrict__ order, const int4* __restri
     }
 }
 
-// Squares for the staged pass: those flagged by the plan (a node inside a
-// coarse triangle, or a fine triangle larger than small); staged[q] records
-// the decision for the small-triangle kernel, and the flags are cleared.
-__global__ void k_sq_stage_list(int nsq, unsigned char* __restrict__ flag, unsigned char* __restrict__ staged,
-                                int* __restrict__ list, int* __restrict__ n_list) {
-    pdl_wait();
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    bool on = false;
-    if (q < nsq) {
-        on = flag[q] != 0;
-        flag[q] = 0;
-        staged[q] = on ? 1 : 0;
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, on);
-    int base = 0;
-    if ((threadIdx.x & 31) == 0 && bal) base = atomicAdd(n_list, __popc(bal));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (on) list[base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = q;
-}
-
 __device__ __forceinline__ TriGeom rec_geom(const SqRec& r, int N) {
     return geom_xy(make_int2(r.ax, r.ay), make_int2(r.bx, r.by), make_int2(r.cx, r.cy), N);
 }
@@ -604,60 +586,159 @@ __device__ __forceinline__ SqPlane rec_plane(const SqRec& r) {
     return P;
 }
 
-// The FP32 pass over the squares that hold only small triangles: one thread
-// per triangle along the curve (neighbouring threads read neighbouring
-// pixels), each walking its rows in the image laid out in squares (global
-// memory).  The triangles of staged squares are left to k_sq.
-__global__ void __launch_bounds__(256) k_sq_small(const SqRec* __restrict__ rec, const int* __restrict__ nodeof,
-                                                  const unsigned char* __restrict__ staged, int T, SqGeo G,
-                                                  const float* __restrict__ fsq, const float* __restrict__ frow,
-                                                  FastOut F) {
-    pdl_wait();
-    const int N = G.N, s = G.s, Q = G.Q, pitch = s + 1;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
-        const int n = nodeof[i];
-        unsigned blo = 0xffffffffu, bhi = 0xffffffffu;
-        if (n >= 0 && !staged[n >> 1]) {
-            const SqRec R = rec[i];
-            const TriGeom g = rec_geom(R, N);
-            const int q = n >> 1, I = q / Q, J = q - I * Q;
-            const int x0 = J * s, y0 = I * s;
-            const float* sqp = fsq + (long long)q * s * pitch;
+// FAST: the interval of each lane's triangle from its FP32 sum and pixel
+// count, and the histograms (one atomic per distinct bin).  Whole warp.
+__device__ __forceinline__ void sq_fine_finish(const SqArgs& A, bool have, const SqRec& R, const TriGeom& g, float sum,
+                                               int n) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    unsigned blo = 0xffffffffu, bhi = 0xffffffffu;
+    if (have) {
+        float lo, hi;
+        fast_interval(ff{sum, 0.f}, (float)n, fast_M(g, R.ucf, R.gxf, R.gyf), kSqChain, lo, hi);
+        A.F.lo[R.t] = lo;
+        A.F.hi[R.t] = hi;
+        if (tri_eligible(g)) {
+            blo = fast_bin(lo);
+            bhi = fast_bin(hi);
+        }
+    }
+    unsigned peers = __match_any_sync(FULL, blo);
+    if (blo != 0xffffffffu && (__ffs(peers) - 1) == lane) atomicAdd(A.F.hlo + blo, (unsigned)__popc(peers));
+    peers = __match_any_sync(FULL, bhi);
+    if (bhi != 0xffffffffu && (__ffs(peers) - 1) == lane) atomicAdd(A.F.hhi + bhi, (unsigned)__popc(peers));
+}
+
+// FAST: the fine triangles of a square, one triangle row per lane.  The
+// square's fine triangles (the curve segments of its two nodes) are taken
+// 32 at a time in curve order, lane k holding triangle k of the chunk.  Their
+// rows are numbered by an exclusive warp scan of the row counts, and in each
+// batch lane i takes row item j0 + i: it finds its triangle from the batch's
+// start bits, takes the triangle's corners and plane from that lane by
+// shuffles, and sums the row's pixels from the staged square (one FP32 chain,
+// at most 33 pixels).  A segmented scan over the lanes adds the rows of each
+// triangle within the batch (5 levels), and the triangle's lane adds its
+// batches in order (at most 3 for the at most 33 rows of a fine triangle).
+// Every term thus passes through at most 33 + 5 + 3 additions of non-negative
+// values, within kSqChain, and the order is fixed, so the pass stays
+// deterministic.  Lanes take rows, not triangles, so a warp stays busy
+// whatever the mix of triangle sizes in the square.  A chunk whose triangles
+// are all small (bounding box at most 17 x 17) is summed one triangle per
+// lane instead: there the exchanges of the row scheme would cost more than
+// the lanes' uneven loads.
+__device__ __forceinline__ void sq_fine_rows(const SqArgs& A, const float* img, int x0, int y0, int pitch, int2 sg0,
+                                             int len0, int2 sg1, int len1) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int N = A.G.N;
+    const int nf = len0 + len1;
+    for (int e0 = 0; e0 < nf; e0 += 32) {
+        const int e = e0 + lane;
+        const bool have = e < nf;
+        SqRec R{};
+        TriGeom g{};
+        int h = 0;
+        if (have) {
+            R = A.rec[e < len0 ? sg0.x + e : sg1.x + (e - len0)];
+            g = rec_geom(R, N);
+            h = g.yend - g.ytop + 1;
+        }
+        if (__all_sync(FULL, !have || is_small(g))) {
+            // a chunk of small triangles: one lane each (a chain of at most
+            // 153 pixels), no exchange between lanes
             float acc = 0.f;
-            int cnt = 0;
-            for (int y = g.ytop; y <= g.yend; ++y) {
-                int L, len;
-                row_span(g, y, N, L, len);
-                if (len <= 0) continue;
-                // rows of the square, or the image's last row
-                const float* rowp = (y - y0 < s ? sqp + (y - y0) * pitch - x0 : frow) + L;
-                const float urow = fmaf(R.gyf, (float)(y - g.cy), fmaf(R.gxf, (float)(L - g.cx), R.ucf));
-                float fk = 0.f;
+            int n = 0;
+            if (have) {
+                const RowGeo rg = row_geo(g);
+                for (int y = g.ytop; y <= g.yend; ++y) {
+                    int L, len;
+                    row_span_geo(rg, y, N, L, len);
+                    if (len <= 0) continue;
+                    const float* rowp = img + (y - y0) * pitch + (L - x0);
+                    const float urow = fmaf(R.gyf, (float)(y - g.cy), fmaf(R.gxf, (float)(L - g.cx), R.ucf));
+                    float fk = 0.f;
 #pragma unroll 4
-                for (int k = 0; k < len; ++k) {
-                    const float d = fmaf(R.gxf, fk, urow) - rowp[k];
-                    acc = fmaf(d, d, acc);
-                    fk += 1.0f;
+                    for (int q = 0; q < len; ++q) {
+                        const float d = fmaf(R.gxf, fk, urow) - rowp[q];
+                        acc = fmaf(d, d, acc);
+                        fk += 1.0f;
+                    }
+                    n += len;
                 }
-                cnt += len;
             }
-            float lo, hi;
-            fast_interval(ff{acc, 0.f}, (float)cnt, fast_M(g, R.ucf, R.gxf, R.gyf), kSqChain, lo, hi);
-            F.lo[R.t] = lo;
-            F.hi[R.t] = hi;
-            if (tri_eligible(g)) {
-                blo = fast_bin(lo);
-                bhi = fast_bin(hi);
+            sq_fine_finish(A, have, R, g, acc, n);
+            continue;
+        }
+        // exclusive scan of the row counts: rows H .. Hn - 1 are triangle k's
+        int Hn = h;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, Hn, o);
+            if (lane >= o) Hn += v;
+        }
+        const int H = Hn - h;
+        const int total = __shfl_sync(FULL, Hn, 31);
+        const RowGeo rg = row_geo(g);
+        float tot = 0.f;
+        int cnt = 0;
+        for (int j0 = 0; j0 < total; j0 += 32) {
+            // triangle of item j0 + lane: the one holding item j0, plus the
+            // triangles that start in (j0, j0 + lane]
+            const unsigned starts = __reduce_or_sync(FULL, (have && H > j0 && H < j0 + 32) ? 1u << (H - j0) : 0u);
+            const int k0 = __popc(__ballot_sync(FULL, have && H <= j0)) - 1;
+            const int j = j0 + lane;
+            const bool valid = j < total;
+            const int k = valid ? k0 + __popc(starts & (FULL >> (31 - lane))) : 0;
+            // triangle k's rows (its top row is y0 of its sorted corners), corner and plane
+            RowGeo rk;
+            rk.y0 = __shfl_sync(FULL, rg.y0, k); rk.y1 = __shfl_sync(FULL, rg.y1, k);
+            rk.x0 = __shfl_sync(FULL, rg.x0, k); rk.x1 = __shfl_sync(FULL, rg.x1, k);
+            rk.sl = __shfl_sync(FULL, rg.sl, k);
+            const int Hk = __shfl_sync(FULL, H, k);
+            const int ckx = __shfl_sync(FULL, g.cx, k), cky = __shfl_sync(FULL, g.cy, k);
+            const float ucf = __shfl_sync(FULL, R.ucf, k), gxf = __shfl_sync(FULL, R.gxf, k);
+            const float gyf = __shfl_sync(FULL, R.gyf, k);
+            float acc = 0.f;
+            int n = 0;
+            if (valid) {
+                const int y = rk.y0 + (j - Hk);
+                int L, len;
+                row_span_geo(rk, y, N, L, len);
+                if (len > 0) {
+                    const float* rowp = img + (y - y0) * pitch + (L - x0);
+                    const float urow = fmaf(gyf, (float)(y - cky), fmaf(gxf, (float)(L - ckx), ucf));
+                    float fk = 0.f;
+#pragma unroll 4
+                    for (int q = 0; q < len; ++q) {
+                        const float d = fmaf(gxf, fk, urow) - rowp[q];
+                        acc = fmaf(d, d, acc);
+                        fk += 1.0f;
+                    }
+                    n = len;
+                }
+            }
+            // the rows of one triangle are consecutive lanes: segmented scan
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float a = __shfl_up_sync(FULL, acc, o);
+                const int m = __shfl_up_sync(FULL, n, o);
+                const int ko = __shfl_up_sync(FULL, k, o);
+                if (lane >= o && ko == k) {
+                    acc += a;
+                    n += m;
+                }
+            }
+            // lane k takes its rows' total from the last of them in the batch
+            const bool part = have && H < j0 + 32 && Hn > j0;
+            const int last = part ? min(Hn, j0 + 32) - 1 - j0 : lane;
+            const float a = __shfl_sync(FULL, acc, last);
+            const int m = __shfl_sync(FULL, n, last);
+            if (part) {
+                tot += a;
+                cnt += m;
             }
         }
-        // histogram: one atomic per distinct bin among the converged lanes
-        const unsigned act = __activemask();
-        unsigned peers = __match_any_sync(act, blo);
-        if (blo != 0xffffffffu && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
-            atomicAdd(F.hlo + blo, (unsigned)__popc(peers));
-        peers = __match_any_sync(act, bhi);
-        if (bhi != 0xffffffffu && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
-            atomicAdd(F.hhi + bhi, (unsigned)__popc(peers));
+        sq_fine_finish(A, have, R, g, tot, cnt);
     }
 }
 
@@ -777,62 +858,40 @@ __global__ void __launch_bounds__(kSqThreads) k_sq(SqArgs A) {
                         A.partial[s1] = make_float4(S1.hi, S1.lo, __int_as_float(w * h - (int)np0), 0.f);
                 }
             }
-            // fine triangles: small ones by one lane each, larger ones listed
+            // fine triangles.  FAST: one row per lane.  EXACT: small ones by
+            // one lane each, larger ones listed
             const int2 sg0 = A.nseg[n0], sg1 = A.nseg[n0 + 1];
             const int len0 = c0 < 0 ? sg0.y - sg0.x : 0, len1 = c1 < 0 ? sg1.y - sg1.x : 0;
+            if (MODE == SQ_FAST) {
+                sq_fine_rows(A, img, x0, y0, pitch, sg0, len0, sg1, len1);
+                __syncwarp();
+                continue;
+            }
             if (lane == 0) s_nbig[wb] = 0;
             __syncwarp();
             for (int e = lane; e < len0 + len1; e += 32) {
                 const int c = e < len0 ? sg0.x + e : sg1.x + (e - len0);
-                unsigned blo = 0xffffffffu, bhi = 0xffffffffu;
-                bool big = false;
-                if (MODE == SQ_FAST) {
-                    const SqRec R = A.rec[c];
-                    const TriGeom g = rec_geom(R, N);
-                    if (is_small(g)) sq_small<MODE>(A, img, x0, y0, pitch, R.t, g, rec_plane(R), blo, bhi);
-                    else big = true;
+                const int t = A.order[c];
+                if (!sq_want<MODE>(A, t)) continue;
+                const int4 tr = A.tri[t];
+                const TriGeom g = tri_geom(tr, A.vxy, N);
+                if (is_small(g)) {
+                    sq_small(A, img, x0, y0, pitch, t, g, sq_plane(g, tr, A.uv, A.uvf));
                 } else {
-                    const int t = A.order[c];
-                    if (sq_want<MODE>(A, t)) {
-                        const int4 tr = A.tri[t];
-                        const TriGeom g = tri_geom(tr, A.vxy, N);
-                        if (is_small(g)) sq_small<MODE>(A, img, x0, y0, pitch, t, g, sq_plane(g, tr, A.uv, A.uvf), blo, bhi);
-                        else big = true;
-                    }
-                }
-                if (big) {
                     // listed by curve position
                     const int slot = atomicAdd(&s_nbig[wb], 1);
                     if (slot < kSqBigCap) s_big[wb][slot] = c;
                     else atomicCAS(A.err, 0, (int)FEM_E_INVALID);
-                }
-                if (MODE == SQ_FAST) {
-                    // histogram: one atomic per distinct bin among the converged lanes
-                    const unsigned act = __activemask();
-                    unsigned peers = __match_any_sync(act, blo);
-                    if (blo != 0xffffffffu && (__ffs(peers) - 1) == lane) atomicAdd(A.F.hlo + blo, (unsigned)__popc(peers));
-                    peers = __match_any_sync(act, bhi);
-                    if (bhi != 0xffffffffu && (__ffs(peers) - 1) == lane) atomicAdd(A.F.hhi + bhi, (unsigned)__popc(peers));
                 }
             }
             __syncwarp();
             const int nbig = min(s_nbig[wb], kSqBigCap);
             for (int e = 0; e < nbig; ++e) {
                 const int c = s_big[wb][e];
-                int t;
-                TriGeom g;
-                SqPlane P;
-                if (MODE == SQ_FAST) {
-                    const SqRec R = A.rec[c];
-                    t = R.t;
-                    g = rec_geom(R, N);
-                    P = rec_plane(R);
-                } else {
-                    t = A.order[c];
-                    const int4 tr = A.tri[t];
-                    g = tri_geom(tr, A.vxy, N);
-                    P = sq_plane(g, tr, A.uv, A.uvf);
-                }
+                const int t = A.order[c];
+                const int4 tr = A.tri[t];
+                const TriGeom g = tri_geom(tr, A.vxy, N);
+                const SqPlane P = sq_plane(g, tr, A.uv, A.uvf);
                 long long np = 0;
                 const ff S = sq_bbox<MODE>(g, P, img, x0, y0, pitch, N, np);
                 if (lane == 0) sq_finish<MODE>(A, t, g, P, S, np);
@@ -842,35 +901,120 @@ __global__ void __launch_bounds__(kSqThreads) k_sq(SqArgs A) {
     }
 }
 
-// The coarse triangles: one warp each adds the triangle's node slots (all
-// of its bounding-box slots; those outside it hold zero) in a fixed order
-// and finishes its interval (FAST) or key (EXACT).  coarse[0 .. *n_coarse)
-// are curve positions; many warps in flight hide the loads of each.
+// Finish coarse triangle c (curve position) from the sum S of its node slots
+// and its pixel count: FAST interval or EXACT key.  One thread.
+template <int MODE>
+__device__ __forceinline__ void sq_coarse_finish(const SqArgs& A, int c, ff S, int np) {
+    if (MODE == SQ_FAST) {
+        const SqRec R = A.rec[c];
+        sq_finish<MODE>(A, R.t, rec_geom(R, A.G.N), rec_plane(R), S, np);
+    } else {
+        const int t = A.order[c];
+        const int4 tr = A.tri[t];
+        const TriGeom gt = tri_geom(tr, A.vxy, A.G.N);
+        sq_finish<MODE>(A, t, gt, sq_plane(gt, tr, A.uv, A.uvf), S, np);
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ bool sq_coarse_wanted(const SqArgs& A, int c) {
+    return MODE == SQ_FAST || !A.sel || A.sel[A.order[c]];
+}
+
+// The coarse triangles.  First the pieces of the long ones, one block per
+// piece: the block adds the piece's slots in a fixed order (each thread a
+// strided share, then the warps' butterflies, then the eight warps in
+// order) and stores the piece's sum; the block that stores a triangle's last
+// piece (counted by an atomic after a fence) adds its pieces in order and
+// finishes the triangle.  Nothing waits.  Then the other coarse triangles,
+// coarse[0 .. *n_coarse) (curve positions), one warp each: the triangle's
+// node slots (all of its bounding-box slots; those outside it hold zero)
+// added in a fixed order.  Both give the same sums on every run.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_sq_final(SqArgs A, const int* __restrict__ coarse,
                                                   const int* __restrict__ n_coarse) {
     pdl_wait();
-    const int lane = threadIdx.x & 31;
+    __shared__ float2 s_sum[8];
+    __shared__ int s_cnt[8];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    const int s = A.G.s;
+    // after an overflow of the lists (only in a mesh the plan reported as
+    // invalid) some entries were never written: no piece is read then
+    const int nlong = *A.LG.n_long, npieces_all = *A.LG.n_pieces;
+    const int npieces = (nlong <= A.LG.cap_long && npieces_all <= A.LG.cap_pieces) ? npieces_all : 0;
+    for (int p = blockIdx.x; p < npieces; p += gridDim.x) {
+        const int2 pc = A.LG.piece[p];
+        const int4 L = A.LG.longs[pc.x];  // (curve position, first piece, pieces, slots)
+        if (!sq_coarse_wanted<MODE>(A, L.x)) continue;  // the same for the whole block
+        const long long o = 2LL * A.sqoff[L.x] + (long long)pc.y * kSqPiece;
+        int len = min(kSqPiece, L.w - pc.y * kSqPiece);
+        if (o + len > A.part_cap) len = 0;  // only in a mesh already reported invalid
+        ff S{0.f, 0.f};
+        int np = 0;
+        for (int e0 = threadIdx.x; e0 < len; e0 += 4 * 256) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + 256 * u;
+                v[u] = e < len ? A.partial[o + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                S = ff_add(S, ff{v[u].x, v[u].y});
+                np += __float_as_int(v[u].z);
+            }
+        }
+        S = ff_warp_sum(S);
+        np = warp_sum(np);
+        if (lane == 0) {
+            s_sum[wb] = make_float2(S.hi, S.lo);
+            s_cnt[wb] = np;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ff T{0.f, 0.f};
+            int n = 0;
+            for (int w = 0; w < 8; ++w) {
+                T = ff_add(T, ff{s_sum[w].x, s_sum[w].y});
+                n += s_cnt[w];
+            }
+            A.LG.psum[p] = make_float4(T.hi, T.lo, __int_as_float(n), 0.f);
+            __threadfence();
+            s_last = atomicAdd(A.LG.pdone + pc.x, 1) == L.z - 1;
+        }
+        __syncthreads();
+        if (s_last && wb == 0) {
+            __threadfence();
+            ff U{0.f, 0.f};
+            int n = 0;
+            for (int j = lane; j < L.z; j += 32) {
+                const float4 v = __ldcg(A.LG.psum + L.y + j);
+                U = ff_add(U, ff{v.x, v.y});
+                n += __float_as_int(v.z);
+            }
+            U = ff_warp_sum(U);
+            n = warp_sum(n);
+            if (lane == 0) {
+                A.LG.pdone[pc.x] = 0;
+                sq_coarse_finish<MODE>(A, L.x, U, n);
+            }
+        }
+        __syncthreads();
+    }
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     const int n = *n_coarse;
-    const int s = A.G.s;
     for (int k = gw; k < n; k += nw) {
         const int c = coarse[k];
-        int t;
+        if (!sq_coarse_wanted<MODE>(A, c)) continue;  // the same for the whole warp
         TriGeom gt;
-        int4 tr = make_int4(0, 0, 0, 0);
-        SqRec R{};
         if (MODE == SQ_FAST) {
-            R = A.rec[c];
-            t = R.t;
-            gt = rec_geom(R, A.G.N);
+            gt = rec_geom(A.rec[c], A.G.N);
         } else {
-            t = A.order[c];
-            if (A.sel && !A.sel[t]) continue;  // the same for the whole warp
-            tr = A.tri[t];
-            gt = tri_geom(tr, A.vxy, A.G.N);
+            gt = tri_geom(A.tri[A.order[c]], A.vxy, A.G.N);
         }
         const int w = (gt.maxw - 1) / s, h = (max(gt.ay, max(gt.by, gt.cy)) - gt.ytop) / s;
+        if (2 * w * h > kSqPiece) continue;  // long: summed in pieces above
         const long long o = 2LL * A.sqoff[c];
         const long long cnt = o + 2LL * w * h <= A.part_cap ? 2LL * w * h : 0;
         ff S{0.f, 0.f};
@@ -891,7 +1035,7 @@ __global__ void __launch_bounds__(256) k_sq_final(SqArgs A, const int* __restric
         }
         S = ff_warp_sum(S);
         np = warp_sum(np);
-        if (lane == 0) sq_finish<MODE>(A, t, gt, MODE == SQ_FAST ? rec_plane(R) : sq_plane(gt, tr, A.uv, A.uvf), S, np);
+        if (lane == 0) sq_coarse_finish<MODE>(A, c, S, np);
     }
 }
 
@@ -937,6 +1081,19 @@ fem_status sq_image(fem_mesh* m, const float* f, cudaStream_t s) {
     return FEM_OK;
 }
 
+static SqLong sq_long_args(fem_mesh* m) {
+    SqLong LG;
+    LG.longs = m->sq_long.p;
+    LG.piece = m->sq_piece.p;
+    LG.psum = m->sq_psum.p;
+    LG.pdone = m->sq_pdone.p;
+    LG.n_long = m->sq_ctr.p + 2;
+    LG.n_pieces = m->sq_ctr.p + 3;
+    LG.cap_long = (int)m->sq_long.n;
+    LG.cap_pieces = (int)m->sq_piece.n;
+    return LG;
+}
+
 fem_status sq_plan(fem_mesh* m, cudaStream_t s) {
     if (m->sq_plan_version == m->mesh_version) return FEM_OK;
     const SqGeo G = sq_geo(m);
@@ -952,32 +1109,31 @@ fem_status sq_plan(fem_mesh* m, cudaStream_t s) {
     FEM_TRY(ensure(m->sq_part, (size_t)4 * G.Q * G.Q + 8, s));
     FEM_TRY(ensure(m->sq_coarse, (size_t)T, s));
     FEM_TRY(ensure(m->sq_ctr, 8, s));
-    const int nsq = G.Q * G.Q;
-    FEM_TRY(ensure(m->sq_stage, (size_t)nsq, s));
-    FEM_TRY(ensure(m->sq_staged, (size_t)nsq, s));
-    if (!m->sq_flag.p || m->sq_flag.n < (size_t)nsq) {
-        FEM_TRY(ensure(m->sq_flag, (size_t)nsq, s));
-        FEM_CUDA(cudaMemsetAsync(m->sq_flag.p, 0, m->sq_flag.n, s));  // cleared by each plan's stage list after
-    }
+    // long coarse triangles: each has more than kSqPiece of the at most
+    // 4 Q^2 + 8 slots, and at most one piece more than its slots fill
+    const int cap_long = (int)((4LL * G.Q * G.Q + 8) / kSqPiece + 2);
+    FEM_TRY(ensure(m->sq_long, (size_t)cap_long, s));
+    FEM_TRY(ensure(m->sq_pdone, (size_t)cap_long, s));
+    FEM_TRY(ensure(m->sq_piece, (size_t)2 * cap_long, s));
+    FEM_TRY(ensure(m->sq_psum, (size_t)2 * cap_long, s));
+    FEM_CUDA(cudaMemsetAsync(m->sq_pdone.p, 0, sizeof(int) * cap_long, s));
     int* W = m->sq_ctr.p + 0;         // bounding-box squares of the coarse triangles
     int* n_coarse = m->sq_ctr.p + 1;  // coarse triangles listed
-    FEM_CUDA(cudaMemsetAsync(n_coarse, 0, sizeof(int), s));
+    // [1] coarse triangles, [2] long ones, [3] their pieces
+    FEM_CUDA(cudaMemsetAsync(n_coarse, 0, 3 * sizeof(int), s));
     // nodes that no triangle claims (only in a mesh with holes) read as
     // fine with an empty segment
     FEM_CUDA(cudaMemsetAsync(m->sq_cov.p, 0xff, sizeof(int) * nodes, s));
     FEM_CUDA(cudaMemsetAsync(m->sq_seg.p, 0xff, sizeof(int2) * nodes, s));
     FEM_TRY(ensure(m->sq_pos, (size_t)T, s));
-    FEM_TRY(scan_fused(m, SqCountIn{m->order.p, m->tri.p, m->vxy.p, G, m->sq_nodeof.p, m->sq_pos.p, m->sq_flag.p},
+    FEM_TRY(scan_fused(m, SqCountIn{m->order.p, m->tri.p, m->vxy.p, G, m->sq_nodeof.p, m->sq_pos.p},
                        ScanStore{m->sq_off.p}, T, s, W, F_RASTER));
     // work: T curve positions, then at most 2 Q^2 bounding-box squares
     const long long work = std::max<long long>(T, 2LL * G.Q * G.Q);
     const int grid = (int)std::max<long long>(1, std::min<long long>((work + 255) / 256, (long long)m->num_sms * 8));
     FEM_LAUNCH(F_RASTER, s, k_sq_nodes, grid, 256, 0, m->order.p, m->tri.p, m->vxy.p, (const int*)m->sq_nodeof.p,
                (const int*)m->sq_off.p, (const int*)W, T, G, m->sq_cov.p, m->sq_seg.p, m->sq_slot.p, m->sq_part.p,
-               (long long)m->sq_part.n, m->dflag.p + 0, m->sq_coarse.p, n_coarse, m->sq_flag.p);
-    FEM_CUDA(cudaMemsetAsync(m->sq_ctr.p + 2, 0, sizeof(int), s));
-    FEM_LAUNCH(F_RASTER, s, k_sq_stage_list, (nsq + 255) / 256, 256, 0, nsq, m->sq_flag.p, m->sq_staged.p,
-               m->sq_stage.p, m->sq_ctr.p + 2);
+               (long long)m->sq_part.n, m->dflag.p + 0, m->sq_coarse.p, n_coarse, sq_long_args(m));
     m->sq_plan_version = m->mesh_version;
     return FEM_OK;
 }
@@ -1007,6 +1163,7 @@ static SqArgs sq_args(fem_mesh* m, const double* uv, const float2* uvf) {
     A.sqoff = m->sq_off.p;
     A.partial = m->sq_part.p;
     A.part_cap = (long long)m->sq_part.n;
+    A.LG = sq_long_args(m);
     A.err = m->dflag.p + 0;
     return A;
 }
@@ -1027,16 +1184,9 @@ fem_status sq_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, FastOu
     SqArgs A = sq_args(m, uv, uvf);
     A.F = F;
     A.rec = (const SqRec*)m->sq_rec.p;
-    A.sq_list = m->sq_stage.p;
-    A.n_sq = m->sq_ctr.p + 2;
     const int Q = A.G.Q;
-    // the pass is two kernels that each read their share of the pixels once:
-    // the staged squares (k_sq), then the small triangles of the others
     note_bytes(F_SQPASS, sq_bytes(m, true));
     FEM_LAUNCH(F_SQPASS, s, k_sq<SQ_FAST>, sq_grid(m, (long long)Q * Q), kSqThreads, 0, A);
-    FEM_LAUNCH(F_SQPASS, s, k_sq_small, std::max(1, std::min((m->T + 255) / 256, m->num_sms * 16)), 256, 0,
-               (const SqRec*)m->sq_rec.p, (const int*)m->sq_nodeof.p, (const unsigned char*)m->sq_staged.p, m->T,
-               A.G, (const float*)m->fsq.p, (const float*)m->fedge.p, F);
     FEM_LAUNCH(F_RASTER, s, k_sq_final<SQ_FAST>, m->num_sms * 8, 256, 0, A, (const int*)m->sq_coarse.p,
                (const int*)(m->sq_ctr.p + 1));
     return FEM_OK;

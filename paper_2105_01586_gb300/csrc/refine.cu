@@ -1009,6 +1009,7 @@ using namespace fem;
 
 extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double density, const fem_params* p,
                                          void* stream) {
+    Nvtx range("fem_spatial_refine");
     if (!m || !f_dev || !(density > 0.0) || density > 1.0) {
         set_error("fem_spatial_refine: null argument or density outside (0, 1]");
         return FEM_E_INVALID;
@@ -1031,6 +1032,8 @@ extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double
     // the error passes read the image as squares, laid out once per call
     FEM_TRY(sq_image(m, f_dev, s));
     while ((long long)m->V < vstar && (p->max_rounds <= 0 || round < p->max_rounds)) {
+        Nvtx round_range("spatial round");
+        FEM_TRY(check_cancel(m));
         // solve_laplace builds the system of the refined mesh (with its
         // right-hand side in the same kernel)
         fem_status st = solve_laplace(m, p->precision == FEM_PREC_FP64, p->tol, p->maxit, s, nullptr, nullptr, true);
@@ -1040,13 +1043,19 @@ extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double
         // in the spatial loop every vertex value was just written together with
         // its float-float copy (mask vertices from f, unknowns by the solve)
         bool band = p->fast_keys > 0 || (p->fast_keys < 0 && m->P >= 2049LL * 2049);
-        if (band)
-            FEM_TRY(raster_keys_fast(m, m->uv.p, m->uvf.p, p->topk_frac, vstar - m->V, s));
-        else
-            FEM_TRY(raster_errors(m, m->uv.p, m->uvf.p, m->keys.p, s, m->keyc.p));
+        {
+            Nvtx pass_range("error pass");
+            if (band)
+                FEM_TRY(raster_keys_fast(m, m->uv.p, m->uvf.p, p->topk_frac, vstar - m->V, s));
+            else
+                FEM_TRY(raster_errors(m, m->uv.p, m->uvf.p, m->keys.p, s, m->keyc.p));
+        }
         double margin = 0.0;
         int k = 0;
-        FEM_TRY(refine_round(m, f_dev, p->topk_frac, vstar, s, &margin, &k, band));
+        {
+            Nvtx refine_range("top-k and refinement");
+            FEM_TRY(refine_round(m, f_dev, p->topk_frac, vstar, s, &margin, &k, band));
+        }
         if (k == 0) break;
         if (margin < m->stats.min_margin) m->stats.min_margin = margin;
         round++;

@@ -50,6 +50,8 @@ struct Request {
     std::vector<float> g;
     fem_stats spatial{}, tonal{};
     bool done = false;
+    bool running = false;
+    std::atomic<int> cancel{0};  // fem_server_cancel: the mesh loops stop at their next check
 };
 
 }  // namespace
@@ -92,7 +94,10 @@ fem_status run_request(Request& r, cudaStream_t s) {
     size_t P = (size_t)r.width * r.width;
     fem_status st = fem_mesh_create(r.width, r.width, s, &m);
     if (st != FEM_OK) return st;
+    m->cancel = &r.cancel;
     do {
+        st = check_cancel(m);
+        if (st != FEM_OK) break;
         st = dalloc_raw((void**)&f_dev, sizeof(float) * P, s);
         if (st != FEM_OK) break;
         cudaError_t e = cudaMemcpyAsync(f_dev, r.f.data(), sizeof(float) * P, cudaMemcpyHostToDevice, s);
@@ -151,6 +156,7 @@ void worker_main(fem_server* sv) {
             sv->queue.pop_front();
             sv->in_use += r->mem_estimate;
             sv->running++;
+            r->running = true;
             r->t_start = now_s();
         }
         fem_status st = run_request(*r, s);
@@ -160,6 +166,7 @@ void worker_main(fem_server* sv) {
             if (st != FEM_OK) r->error = fem_last_error();
             r->t_end = now_s();
             r->done = true;
+            r->running = false;
             r->f.clear();
             r->f.shrink_to_fit();
             sv->in_use -= r->mem_estimate;
@@ -278,6 +285,58 @@ fem_status fem_server_result(fem_server* sv, long long id, int* sizes, int* xy, 
     }
     if (r->status != FEM_OK && r->status != FEM_E_NOT_CONVERGED) set_error(r->error);
     return r->status;
+}
+
+fem_status fem_server_state(fem_server* sv, long long id, int* state) {
+    if (!sv || !state) {
+        set_error("fem_server_state: null argument");
+        return FEM_E_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(id);
+    if (it == sv->all.end()) {
+        set_error("fem_server_state: unknown request id");
+        return FEM_E_INVALID;
+    }
+    *state = it->second->done ? 2 : (it->second->running ? 1 : 0);
+    return FEM_OK;
+}
+
+fem_status fem_server_cancel(fem_server* sv, long long id) {
+    if (!sv) {
+        set_error("fem_server_cancel: null server");
+        return FEM_E_INVALID;
+    }
+    bool dequeued = false;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->all.find(id);
+        if (it == sv->all.end()) {
+            set_error("fem_server_cancel: unknown request id");
+            return FEM_E_INVALID;
+        }
+        auto r = it->second;
+        if (r->done) return FEM_OK;
+        r->cancel.store(1);
+        for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q) {
+            if (*q != r) continue;
+            sv->queue.erase(q);
+            r->status = FEM_E_CANCELLED;
+            r->error = "request cancelled";
+            r->t_start = r->t_end = now_s();
+            r->f.clear();
+            r->f.shrink_to_fit();
+            r->done = true;
+            dequeued = true;
+            break;
+        }
+    }
+    // a running request finishes through its worker, which notifies as usual
+    if (dequeued) {
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();
+    }
+    return FEM_OK;
 }
 
 fem_status fem_server_release(fem_server* sv, long long id) {

@@ -1094,6 +1094,7 @@ fem_status solve_totals_read(fem_mesh* m, cudaStream_t s) {
 // the Dirichlet data, those at U the start; the solution is written back.
 fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cudaStream_t s, int* iters_out,
                          double* relres_out, bool deferred) {
+    Nvtx range("laplace solve");
     bool rhs_done = true;  // filled by the ELL kernel when the system is rebuilt here
     FEM_TRY(build_system_rhs(m, s, &rhs_done));
     int nU = m->nU;
@@ -1171,6 +1172,7 @@ extern "C" fem_status fem_gather_mask(fem_mesh* m, const float* f_dev, float* g_
 
 extern "C" fem_status fem_inpaint(fem_mesh* m, const float* g_dev, float* u_dev, double* uv_dev, const fem_params* p,
                                   void* stream) {
+    Nvtx range("fem_inpaint");
     if (!m || !g_dev) {
         set_error("fem_inpaint: null argument");
         return FEM_E_INVALID;

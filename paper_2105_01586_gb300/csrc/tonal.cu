@@ -472,6 +472,7 @@ static fem_status scatter_PT(fem_mesh* m, const float* r, cudaStream_t s) {
 using namespace fem;
 
 extern "C" fem_status fem_tonal_opt(fem_mesh* m, const float* f_dev, float* g_dev, const fem_params* p, void* stream) {
+    Nvtx range("fem_tonal_opt");
     if (!m || !f_dev || !g_dev) {
         set_error("fem_tonal_opt: null argument");
         return FEM_E_INVALID;
@@ -537,6 +538,9 @@ extern "C" fem_status fem_tonal_opt(fem_mesh* m, const float* f_dev, float* g_de
         double* slot = hs + 8;  // three pinned (stop, iters) pairs
         int G = vec_grid(m);
         for (int k = 0; lst == FEM_OK && k < p->tonal_maxit; ++k) {
+            Nvtx it_range("tonal iteration");
+            lst = check_cancel(m);
+            if (lst != FEM_OK) break;
             // ||B p||^2 and M E p; g += a p, y -= a M E p; r = E^T y
             lst = apply_EM(m, m->tp.p, &cg->pNp, c, s);
             if (lst != FEM_OK) break;
@@ -586,6 +590,7 @@ extern "C" fem_status fem_tonal_opt(fem_mesh* m, const float* f_dev, float* g_de
 }
 
 extern "C" fem_status fem_adjoint(fem_mesh* m, const float* r_dev, float* gbar_dev, const fem_params* p, void* stream) {
+    Nvtx range("fem_adjoint");
     if (!m || !r_dev || !gbar_dev) {
         set_error("fem_adjoint: null argument");
         return FEM_E_INVALID;
@@ -615,6 +620,7 @@ extern "C" fem_status fem_adjoint(fem_mesh* m, const float* r_dev, float* gbar_d
 // E^T (one adjoint solve) maps it to the mask vertices.
 extern "C" fem_status fem_tonal_loss(fem_mesh* m, const float* g_dev, const float* f_dev, double* loss_dev,
                                      float* grad_dev, const fem_params* p, void* stream) {
+    Nvtx range("fem_tonal_loss");
     if (!m || !g_dev || !f_dev || (!loss_dev && !grad_dev)) {
         set_error("fem_tonal_loss: null argument (g, f and at least one of loss, grad are required)");
         return FEM_E_INVALID;

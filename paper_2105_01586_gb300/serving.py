@@ -48,6 +48,23 @@ class Server:
                 "cg_iters": int(times[4]), "tonal_iters": int(times[5]), "tonal_relres": float(times[6]),
                 "mem_estimate": int(times[7])}
 
+    def state(self, rid: int) -> str:
+        """"queued", "running" or "finished" (fem_server_state)."""
+        st = ctypes.c_int()
+        _check(_lib.fem_server_state(self.h, rid, ctypes.byref(st)), "fem_server_state")
+        return ("queued", "running", "finished")[st.value]
+
+    def cancel(self, rid: int) -> None:
+        """Cancel a queued or running request (fem_server_cancel); it then
+        finishes with status FEM_E_CANCELLED."""
+        _check(_lib.fem_server_cancel(self.h, rid), "fem_server_cancel")
+
+    def status(self, rid: int) -> int:
+        """Status of a finished request (FEM_OK, FEM_E_NOT_CONVERGED,
+        FEM_E_CANCELLED, ...)."""
+        sizes = np.zeros(4, np.int32)
+        return int(_lib.fem_server_result(self.h, rid, sizes.ctypes.data, None, None, None, None, None))
+
     def release(self, rid: int) -> None:
         _check(_lib.fem_server_release(self.h, rid), "fem_server_release")
 

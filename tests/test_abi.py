@@ -79,6 +79,8 @@ def test_server_entry_points_reject_bad_handles_on_the_host(fem):
     assert fem._lib.fem_server_wait(None, 1, 0.0, ctypes.byref(done)) == fem.FEM_E_INVALID
     assert fem._lib.fem_server_result(None, 1, sizes.ctypes.data, None, None, None, None, None) == fem.FEM_E_INVALID
     assert fem._lib.fem_server_release(None, 1) == fem.FEM_E_INVALID
+    assert fem._lib.fem_server_cancel(None, 1) == fem.FEM_E_INVALID
+    assert fem._lib.fem_server_state(None, 1, ctypes.byref(done)) == fem.FEM_E_INVALID
     assert fem._lib.fem_server_destroy(None) == fem.FEM_OK
     out = ctypes.c_void_p()
     assert fem._lib.fem_server_create(0, 0, ctypes.byref(out)) == fem.FEM_E_INVALID
@@ -99,3 +101,13 @@ def test_noalloc_entry_point_checks_sizes_on_the_host(fem):
     assert b"null" in L.fem_last_error()
     assert L.fem_triangle_errors_noalloc(*args(129, 4, 2, tri=ok_ptr + 4)) == fem.FEM_E_INVALID
     assert b"aligned" in L.fem_last_error()
+
+
+def test_allocation_fault_hook_and_pool_setting_are_host_only(fem):
+    """fem_debug_alloc_fault counts and arms on the host; fem_set_mem_pool(NULL)
+    selects the device's current pool.  Neither touches a device."""
+    n0 = fem.fem_debug_alloc_fault(-1)
+    assert n0 >= 0
+    assert fem.fem_debug_alloc_fault(5) == n0   # armed five attempts ahead; nothing allocated here
+    assert fem.fem_debug_alloc_fault(-1) == n0  # disarmed
+    fem.fem_set_mem_pool(None)
