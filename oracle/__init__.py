@@ -18,6 +18,10 @@ Functions and the paper passages they follow:
   select_topk descending-error order of Sec. 3, ties by triangle id
   spatial     the spatial optimisation loop (Sec. 3, adapted)
   apply_B, apply_BT, tonal   u = B g and the normal equations of Sec. 4
+
+Images are H x W arrays.  A W x H image that is not square with side
+2^L + 1 lies at the top-left of the smallest such square domain, which
+carries the mesh; only image pixels are data (reading R9 of oracle.c).
 """
 from __future__ import annotations
 
@@ -78,10 +82,13 @@ def _load():
     up = ctypes.POINTER(ctypes.c_ubyte)
     L.om_mesh_new.restype = P
     L.om_mesh_new.argtypes = [ctypes.c_int]
+    L.om_mesh_new_image.restype = P
+    L.om_mesh_new_image.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.om_mesh_set_image.argtypes = [P, ctypes.c_int, ctypes.c_int]
     L.om_mesh_from.restype = P
     L.om_mesh_from.argtypes = [ctypes.c_int, ctypes.c_int, ip, ip, up, ctypes.c_int, ip, ip, ip]
     L.om_mesh_free.argtypes = [P]
-    for n in ("om_mesh_V", "om_mesh_T", "om_mesh_N"):
+    for n in ("om_mesh_V", "om_mesh_T", "om_mesh_N", "om_mesh_W", "om_mesh_H"):
         getattr(L, n).argtypes = [P]
         getattr(L, n).restype = ctypes.c_int
     L.om_mesh_get.argtypes = [P, ip, ip, up, ip, ip, ip]
@@ -119,7 +126,8 @@ def _check(rc, what):
 
 @dataclass
 class Mesh:
-    """A triangle mesh on the pixel grid of an N x N image.  Triangle t is
+    """A triangle mesh on the pixel grid of the N x N domain (N = 2^L + 1)
+    that holds a W x H image (W = H = N unless given).  Triangle t is
     (ta[t], tb[t], tc[t]): refinement edge (ta, tb), newest vertex tc."""
     N: int
     vx: np.ndarray
@@ -128,6 +136,12 @@ class Mesh:
     ta: np.ndarray
     tb: np.ndarray
     tc: np.ndarray
+    W: int = 0
+    H: int = 0
+
+    def __post_init__(self):
+        self.W = int(self.W) or int(self.N)
+        self.H = int(self.H) or int(self.N)
 
     @property
     def V(self) -> int:
@@ -147,7 +161,7 @@ class Mesh:
 
     def copy(self) -> "Mesh":
         return Mesh(self.N, self.vx.copy(), self.vy.copy(), self.mask.copy(),
-                    self.ta.copy(), self.tb.copy(), self.tc.copy())
+                    self.ta.copy(), self.tb.copy(), self.tc.copy(), self.W, self.H)
 
     def with_mask(self, mask) -> "Mesh":
         m = self.copy()
@@ -156,9 +170,13 @@ class Mesh:
 
 
 class _CMesh:
-    def __init__(self, mesh: Mesh | None = None, N: int | None = None):
+    def __init__(self, mesh: Mesh | None = None, N: int | None = None, W: int | None = None, H: int | None = None):
         L = _load()
-        if mesh is None:
+        if mesh is None and W is not None:
+            self.p = L.om_mesh_new_image(int(W), int(H))
+            if not self.p:
+                raise OracleError("image sides must be at least 2")
+        elif mesh is None:
             self.p = L.om_mesh_new(int(N))
             if not self.p:
                 raise OracleError("image side must be 2^L + 1")
@@ -168,16 +186,19 @@ class _CMesh:
             self.p = L.om_mesh_from(int(mesh.N), len(c[0]), _ptr(c[0], ctypes.c_int), _ptr(c[1], ctypes.c_int),
                                     _ptr(mk, ctypes.c_ubyte), len(c[2]), _ptr(c[2], ctypes.c_int),
                                     _ptr(c[3], ctypes.c_int), _ptr(c[4], ctypes.c_int))
+            if self.p and (mesh.W, mesh.H) != (mesh.N, mesh.N):
+                _check(L.om_mesh_set_image(self.p, int(mesh.W), int(mesh.H)), "set_image")
         self.L = L
 
     def to_mesh(self) -> Mesh:
         L = self.L
         V, T, N = L.om_mesh_V(self.p), L.om_mesh_T(self.p), L.om_mesh_N(self.p)
+        W, H = L.om_mesh_W(self.p), L.om_mesh_H(self.p)
         vx = np.empty(V, np.int32); vy = np.empty(V, np.int32); mk = np.empty(V, np.uint8)
         ta = np.empty(T, np.int32); tb = np.empty(T, np.int32); tc = np.empty(T, np.int32)
         L.om_mesh_get(self.p, _ptr(vx, ctypes.c_int), _ptr(vy, ctypes.c_int), _ptr(mk, ctypes.c_ubyte),
                       _ptr(ta, ctypes.c_int), _ptr(tb, ctypes.c_int), _ptr(tc, ctypes.c_int))
-        return Mesh(N, vx, vy, mk, ta, tb, tc)
+        return Mesh(N, vx, vy, mk, ta, tb, tc, W, H)
 
     def __del__(self):
         if getattr(self, "p", None):
@@ -185,9 +206,13 @@ class _CMesh:
             self.p = None
 
 
-def mesh_init(N: int) -> Mesh:
-    """Two triangles on the corners of an N x N image (N = 2^L + 1)."""
-    return _CMesh(N=N).to_mesh()
+def mesh_init(N: int, H: int | None = None) -> Mesh:
+    """Two triangles on the corners of the domain: of an N x N image
+    (N = 2^L + 1), or with H given of an N x H (width x height) image in the
+    smallest domain that holds it."""
+    if H is None:
+        return _CMesh(N=N).to_mesh()
+    return _CMesh(W=N, H=H).to_mesh()
 
 
 def refine(mesh: Mesh, selected) -> tuple[Mesh, dict]:
@@ -216,9 +241,10 @@ def stiffness(mesh: Mesh):
 
 
 def g_from_f(mesh: Mesh, f: np.ndarray) -> np.ndarray:
-    """Dirichlet data g = f at the mask vertices, in ascending vertex id."""
+    """Dirichlet data g = f at the mask vertices, in ascending vertex id (a
+    vertex outside the image takes the nearest image pixel)."""
     k = mesh.mask.astype(bool)
-    return f[mesh.vy[k], mesh.vx[k]].astype(np.float64)
+    return f[np.minimum(mesh.vy[k], mesh.H - 1), np.minimum(mesh.vx[k], mesh.W - 1)].astype(np.float64)
 
 
 def vertex_values(mesh: Mesh, g: np.ndarray, start: np.ndarray | None = None) -> np.ndarray:
@@ -240,14 +266,14 @@ def solve(mesh: Mesh, g: np.ndarray, start: np.ndarray | None = None, tol: float
 
 
 def raster(mesh: Mesh, v: np.ndarray, f: np.ndarray | None = None, owner: bool = False):
-    """Interpolate vertex values v to all pixels.  Returns (u image (N x N),
-    per-triangle squared errors against f (or None), owner map (or None))."""
+    """Interpolate vertex values v to all image pixels.  Returns (u image
+    (H x W), per-triangle squared errors against f (or None), owner map (or
+    None))."""
     cm = _CMesh(mesh)
-    N = mesh.N
     vv = np.ascontiguousarray(v, dtype=np.float64)
-    u = np.zeros((N, N), np.float64)
+    u = np.zeros((mesh.H, mesh.W), np.float64)
     keys = np.zeros(mesh.T, np.float64) if f is not None else None
-    own = np.zeros((N, N), np.int32) if owner else None
+    own = np.zeros((mesh.H, mesh.W), np.int32) if owner else None
     ff = np.ascontiguousarray(f, dtype=np.float32) if f is not None else None
     rc = cm.L.om_raster(cm.p, _ptr(vv, ctypes.c_double),
                         _ptr(ff, ctypes.c_float) if ff is not None else None,
@@ -268,10 +294,10 @@ def scatter(mesh: Mesh, r: np.ndarray) -> np.ndarray:
 
 
 def eligible(mesh: Mesh) -> np.ndarray:
-    """Triangles whose refinement-edge midpoint is a pixel."""
+    """Triangles whose refinement-edge midpoint is a pixel of the image."""
     sx = mesh.vx[mesh.ta] + mesh.vx[mesh.tb]
     sy = mesh.vy[mesh.ta] + mesh.vy[mesh.tb]
-    return ((sx % 2) == 0) & ((sy % 2) == 0)
+    return ((sx % 2) == 0) & ((sy % 2) == 0) & (sx // 2 < mesh.W) & (sy // 2 < mesh.H)
 
 
 def topk_count(T: int, frac: float, n_eligible: int, vcap: int) -> int:
@@ -289,19 +315,20 @@ def select_topk(mesh: Mesh, keys: np.ndarray, k: int) -> tuple[np.ndarray, float
     return sel[:n].copy(), marg.value
 
 
-def vstar(N: int, density: float) -> int:
+def vstar(N: int, density: float, H: int | None = None) -> int:
+    """ceil(density * pixels) of an N x N image, or of an N x H one."""
     import math
-    return int(math.ceil(density * float(N * N)))
+    return int(math.ceil(density * float(N * (N if H is None else H))))
 
 
 def spatial(f: np.ndarray, density: float, frac: float, max_rounds: int = 0, tol: float = 1e-13,
             maxit: int = 1_000_000, mesh: Mesh | None = None, log_cap: int = 100_000):
     """Spatial optimisation: refine from the two-triangle mesh (or `mesh`)
-    until V >= ceil(density * N^2) or max_rounds rounds (> 0).
+    until V >= ceil(density * W H) or max_rounds rounds (> 0); f is H x W.
     Returns (mesh, log) with log columns V, T, k, margin, CG iterations,
     relres, new vertices, new mask vertices (one row per round)."""
-    N = f.shape[0]
-    cm = _CMesh(mesh) if mesh is not None else _CMesh(N=N)
+    H, W = f.shape
+    cm = _CMesh(mesh) if mesh is not None else _CMesh(W=W, H=H)
     ff = np.ascontiguousarray(f, dtype=np.float32)
     log = np.zeros((log_cap, LOG_COLS), np.float64)
     rounds = ctypes.c_int(0)
@@ -314,7 +341,7 @@ def spatial(f: np.ndarray, density: float, frac: float, max_rounds: int = 0, tol
 def apply_B(mesh: Mesh, g: np.ndarray, tol: float = 1e-14, maxit: int = 1_000_000) -> np.ndarray:
     cm = _CMesh(mesh)
     gg = np.ascontiguousarray(g, dtype=np.float64)
-    u = np.zeros((mesh.N, mesh.N), np.float64)
+    u = np.zeros((mesh.H, mesh.W), np.float64)
     _check(cm.L.om_apply_B(cm.p, _ptr(gg, ctypes.c_double), _ptr(u, ctypes.c_double), tol, maxit), "apply_B")
     return u
 

@@ -37,7 +37,19 @@
  *      squared L2 error of Sec. 3 (same order as the L2 norm).
  *  R8  Top-k: k = max(1, ceil(frac*T)), capped by the number of eligible
  *      triangles and by V* - V; order by key descending, then id ascending.
- *      A triangle is eligible when its refinement-edge midpoint is a pixel.
+ *      A triangle is eligible when its refinement-edge midpoint is a pixel
+ *      of the image.
+ *  R9  Image sizes other than 2^L + 1 (the paper's 2^k images and its
+ *      4896 x 3264 photograph, Sec. 5): a W x H image lies at the top-left
+ *      of the domain [0, N-1]^2, N = 2^L + 1 >= max(W, H), which carries the
+ *      mesh exactly as for a square image.  Only image pixels are data: a
+ *      triangle owns the pixels of R6 that lie in the image, so P has one
+ *      row per image pixel, the keys and the data term of the tonal
+ *      optimisation run over image pixels, and V* = ceil(density W H).  A
+ *      mask vertex outside the image (only the initial corners can be: a
+ *      selected midpoint is an image pixel by R8) takes the value of the
+ *      nearest image pixel (f at the clamped position).  With W = H = N
+ *      everything reduces to the square case.
  *
  * Threads.  Compiled with -fopenmp (the multi-core CPU baseline), two loops
  * share their iterations among threads: the per-triangle raster loop and the
@@ -62,6 +74,7 @@
 
 typedef struct {
     int N;
+    int W, H;  /* image size (R9); W = H = N for a square image */
     int V, T;
     int capV, capT;
     int *vx, *vy;
@@ -141,6 +154,8 @@ om_mesh *om_mesh_new(int N)
     om_mesh *m = calloc(1, sizeof(om_mesh));
     if (!m) return NULL;
     m->N = N;
+    m->W = N;
+    m->H = N;
     add_vertex(m, 0, 0, 1);
     add_vertex(m, N - 1, 0, 1);
     add_vertex(m, 0, N - 1, 1);
@@ -157,6 +172,8 @@ om_mesh *om_mesh_from(int N, int V, const int *vx, const int *vy, const unsigned
     om_mesh *m = calloc(1, sizeof(om_mesh));
     if (!m) return NULL;
     m->N = N;
+    m->W = N;
+    m->H = N;
     if (grow_vertices(m, V > 0 ? V : 1) || grow_triangles(m, T > 0 ? T : 1)) { om_mesh_free(m); return NULL; }
     memcpy(m->vx, vx, sizeof(int) * V);
     memcpy(m->vy, vy, sizeof(int) * V);
@@ -168,6 +185,29 @@ om_mesh *om_mesh_from(int N, int V, const int *vx, const int *vy, const unsigned
     return m;
 }
 
+/* R9: the image W x H inside the domain of side N (2 <= W, H <= N). */
+int om_mesh_set_image(om_mesh *m, int W, int H)
+{
+    if (W < 2 || H < 2 || W > m->N || H > m->N) return OM_E_INVALID;
+    m->W = W;
+    m->H = H;
+    return OM_OK;
+}
+
+/* The initial mesh for a W x H image: the smallest domain N = 2^L + 1 that
+ * holds it (R1, R9). */
+om_mesh *om_mesh_new_image(int W, int H)
+{
+    if (W < 2 || H < 2) return NULL;
+    int N = 3;
+    while (N < W || N < H) N = 2 * N - 1;
+    om_mesh *m = om_mesh_new(N);
+    if (m && om_mesh_set_image(m, W, H)) { om_mesh_free(m); return NULL; }
+    return m;
+}
+
+int om_mesh_W(const om_mesh *m) { return m->W; }
+int om_mesh_H(const om_mesh *m) { return m->H; }
 int om_mesh_V(const om_mesh *m) { return m->V; }
 int om_mesh_T(const om_mesh *m) { return m->T; }
 int om_mesh_N(const om_mesh *m) { return m->N; }
@@ -255,10 +295,18 @@ static long eset_insert(edge_set *s, uint64_t k, int *fresh)
 /* R2-R5: one refinement round by newest-vertex bisection              */
 /* ------------------------------------------------------------------ */
 
-int om_eligible(const om_mesh *m, int t)
+/* the refinement-edge midpoint is a lattice point (the edge can be bisected) */
+static int lattice_mid(const om_mesh *m, int t)
 {
     int a = m->ta[t], b = m->tb[t];
     return ((m->vx[a] + m->vx[b]) % 2 == 0) && ((m->vy[a] + m->vy[b]) % 2 == 0);
+}
+
+/* R8, R9: selectable when the midpoint is a pixel of the image */
+int om_eligible(const om_mesh *m, int t)
+{
+    int a = m->ta[t], b = m->tb[t];
+    return lattice_mid(m, t) && (m->vx[a] + m->vx[b]) / 2 < m->W && (m->vy[a] + m->vy[b]) / 2 < m->H;
 }
 
 typedef struct { long pix; long slot; } pix_slot;
@@ -270,8 +318,13 @@ static int cmp_pix(const void *p, const void *q)
 }
 
 /* info[0] = new vertices, info[1] = new triangles, info[2] = generations,
- * info[3] = new mask vertices */
-int om_refine(om_mesh *m, const int *sel, int nsel, int *info)
+ * info[3] = new mask vertices; par (optional, 2 per possible new vertex):
+ * the ends of the edge each new vertex bisects, in new-vertex order */
+static int refine_par(om_mesh *m, const int *sel, int nsel, int *info, int *par);
+
+int om_refine(om_mesh *m, const int *sel, int nsel, int *info) { return refine_par(m, sel, nsel, info, NULL); }
+
+static int refine_par(om_mesh *m, const int *sel, int nsel, int *info, int *par)
 {
     int rc = OM_OK;
     edge_set E;
@@ -296,7 +349,7 @@ int om_refine(om_mesh *m, const int *sel, int nsel, int *info)
             uint64_t kref = edge_key(a, b);
             if (eset_find(&E, kref) >= 0) continue;
             if (eset_find(&E, edge_key(b, c)) >= 0 || eset_find(&E, edge_key(c, a)) >= 0) {
-                if (!om_eligible(m, t)) { eset_free(&E); return OM_E_INVALID; } /* never happens on valid meshes */
+                if (!lattice_mid(m, t)) { eset_free(&E); return OM_E_INVALID; } /* never happens on valid meshes */
                 int fresh;
                 if (eset_insert(&E, kref, &fresh) < 0) { eset_free(&E); return OM_E_OOM; }
                 changed = 1;
@@ -326,6 +379,10 @@ int om_refine(om_mesh *m, const int *sel, int nsel, int *info)
         int id = add_vertex(m, x, y, E.sel[h]);
         if (id < 0) { free(order); eset_free(&E); return OM_E_OOM; }
         E.vid[h] = id;
+        if (par) {
+            par[2 * (id - V0)] = (int)(E.key[h] >> 32);
+            par[2 * (id - V0) + 1] = (int)(E.key[h] & 0xffffffffu);
+        }
         nmask += E.sel[h];
     }
     free(order);
@@ -564,7 +621,8 @@ static int inner_side(long w, long gx, long gy, int sx, int sy)
 }
 
 /* Enumerate the pixels owned by triangle t with their barycentric
- * coordinates (lambda_a, lambda_b, lambda_c).  Returns the count. */
+ * coordinates (lambda_a, lambda_b, lambda_c): those of R6 that lie in the
+ * image (R9).  Returns the count. */
 static long owned_pixels(const om_mesh *m, int t, int *px, int *py, double *la, double *lb, double *lc)
 {
     int N = m->N;
@@ -575,6 +633,8 @@ static long owned_pixels(const om_mesh *m, int t, int *px, int *py, double *la, 
     long x1 = ax > bx ? ax : bx; if (cx > x1) x1 = cx;
     long y0 = ay < by ? ay : by; if (cy < y0) y0 = cy;
     long y1 = ay > by ? ay : by; if (cy > y1) y1 = cy;
+    if (x1 > m->W - 1) x1 = m->W - 1;
+    if (y1 > m->H - 1) y1 = m->H - 1;
     long n = 0;
     for (long y = y0; y <= y1; ++y) {
         int sy = (y < N - 1) ? 1 : -1;
@@ -627,12 +687,13 @@ static int pix_buf_fit(pix_buf *pb, const om_mesh *m, int t)
 static void pix_buf_free(pix_buf *pb) { free(pb->px); free(pb->py); free(pb->la); free(pb->lb); free(pb->lc); }
 
 /* u = P v: the piecewise-linear interpolant of the vertex values v at every
- * pixel (Sec. 2.2, last step), and optionally the per-triangle squared
- * errors against f (Sec. 3) and the owner of each pixel.  When owner is
- * given, every pixel must be owned exactly once or OM_E_INVALID is returned. */
+ * image pixel (Sec. 2.2, last step), and optionally the per-triangle squared
+ * errors against f (Sec. 3) and the owner of each pixel.  Images are W x H,
+ * row-major.  When owner is given, every image pixel must be owned exactly
+ * once or OM_E_INVALID is returned. */
 int om_raster(const om_mesh *m, const double *v, const float *f, double *u_img, double *keys, int *owner)
 {
-    long P = (long)m->N * m->N;
+    long P = (long)m->W * m->H;
     int rc = OM_OK;
     if (owner) for (long p = 0; p < P; ++p) owner[p] = -1;
     /* The ownership check writes shared state, so it runs on one thread. */
@@ -651,7 +712,7 @@ int om_raster(const om_mesh *m, const double *v, const float *f, double *u_img, 
             double va = v[m->ta[t]], vb = v[m->tb[t]], vc = v[m->tc[t]];
             double err = 0.0;
             for (long q = 0; q < n; ++q) {
-                long p = (long)pb.py[q] * m->N + pb.px[q];
+                long p = (long)pb.py[q] * m->W + pb.px[q];
                 double u = pb.la[q] * va + pb.lb[q] * vb + pb.lc[q] * vc;
                 if (u_img) u_img[p] = u;
                 if (f) { double d = u - (double)f[p]; err += d * d; }
@@ -690,7 +751,7 @@ static int scatter_PT(const om_mesh *m, const double *r_img, double *s)
         if (pix_buf_fit(&pb, m, t)) { pix_buf_free(&pb); return OM_E_OOM; }
         long n = owned_pixels(m, t, pb.px, pb.py, pb.la, pb.lb, pb.lc);
         for (long q = 0; q < n; ++q) {
-            double r = r_img[(long)pb.py[q] * m->N + pb.px[q]];
+            double r = r_img[(long)pb.py[q] * m->W + pb.px[q]];
             s[m->ta[t]] += pb.la[q] * r;
             s[m->tb[t]] += pb.lb[q] * r;
             s[m->tc[t]] += pb.lc[q] * r;
@@ -764,18 +825,26 @@ int om_select_topk(const om_mesh *m, const double *keys, int k, int *sel, double
 
 #define LOG_COLS 8
 
-/* Refines m until it has at least ceil(density*N*N) vertices (or max_rounds
+/* f at pixel (x, y) of the domain: the nearest image pixel (R9) */
+static double f_at(const om_mesh *m, const float *f, int x, int y)
+{
+    if (x > m->W - 1) x = m->W - 1;
+    if (y > m->H - 1) y = m->H - 1;
+    return (double)f[(long)y * m->W + x];
+}
+
+/* Refines m until it has at least ceil(density*W*H) vertices (or max_rounds
  * rounds when > 0).  Each round: g = f at the mask vertices, Laplace solve
  * (warm-started), per-triangle squared errors, top-k, one refinement.
  * log rows: V, T, k, margin, CG iterations, relres, new vertices, new mask. */
 int om_spatial(om_mesh *m, const float *f, double density, double frac, int max_rounds,
                double tol, int maxit, double *log, int log_cap, int *rounds_out)
 {
-    long P = (long)m->N * m->N;
+    long P = (long)m->W * m->H;
     long Vstar = (long)ceil(density * (double)P);
     int rc = OM_OK, round = 0;
     double *uv = NULL, *keys = NULL, *u_img = malloc(sizeof(double) * P);
-    int *sel = NULL;
+    int *sel = NULL, *par = NULL;
     if (!u_img) return OM_E_OOM;
     int capV = 0;
     while (m->V < Vstar && (max_rounds <= 0 || round < max_rounds)) {
@@ -787,7 +856,7 @@ int om_spatial(om_mesh *m, const float *f, double density, double frac, int max_
         }
         if (round == 0) for (int i = 0; i < m->V; ++i) uv[i] = 0.0;
         for (int i = 0; i < m->V; ++i)
-            if (m->mask[i]) uv[i] = (double)f[(long)m->vy[i] * m->N + m->vx[i]];
+            if (m->mask[i]) uv[i] = f_at(m, f, m->vx[i], m->vy[i]);
         int iters = 0; double relres = 0.0;
         rc = om_solve(m, uv, tol, maxit, &iters, &relres);
         if (rc) break;
@@ -803,16 +872,21 @@ int om_spatial(om_mesh *m, const float *f, double density, double frac, int max_
         double margin = 0.0;
         k = om_select_topk(m, keys, k, sel, &margin);
         int V0 = m->V, T0 = m->T, info[4];
-        rc = om_refine(m, sel, k, info);
+        /* at most one new vertex per edge: V + T - 1 edges */
+        int *np = realloc(par, sizeof(int) * 2 * (size_t)(m->V + m->T));
+        if (!np) { rc = OM_E_OOM; break; }
+        par = np;
+        rc = refine_par(m, sel, k, info, par);
         if (rc) break;
-        /* warm start: the previous interpolant at the new vertices */
+        /* warm start: the previous interpolant at the new vertices, i.e. the
+         * mean of the ends of the edge each one bisects */
         if (capV < m->V) {
             capV = m->capV;
             double *nu = realloc(uv, sizeof(double) * capV);
             if (!nu) { rc = OM_E_OOM; break; }
             uv = nu;
         }
-        for (int i = V0; i < m->V; ++i) uv[i] = u_img[(long)m->vy[i] * m->N + m->vx[i]];
+        for (int i = V0; i < m->V; ++i) uv[i] = 0.5 * (uv[par[2 * (i - V0)]] + uv[par[2 * (i - V0) + 1]]);
         if (log && round < log_cap) {
             double *row = log + (long)round * LOG_COLS;
             row[0] = V0; row[1] = T0; row[2] = k; row[3] = margin;
@@ -821,7 +895,7 @@ int om_spatial(om_mesh *m, const float *f, double density, double frac, int max_
         round++;
     }
     if (rounds_out) *rounds_out = round;
-    free(uv); free(keys); free(sel); free(u_img);
+    free(uv); free(keys); free(sel); free(u_img); free(par);
     return rc;
 }
 
@@ -927,7 +1001,7 @@ static double dotn(const double *x, const double *y, long n)
 int om_tonal(const om_mesh *m, const float *f, double *g, double tol, int maxit,
              double inner_tol, int inner_maxit, double *stats)
 {
-    long P = (long)m->N * m->N;
+    long P = (long)m->W * m->H;
     tonal_ctx c;
     int rc = ctx_init(&c, m, inner_tol, inner_maxit);
     int nK = c.nK;
