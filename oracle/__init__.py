@@ -93,6 +93,7 @@ def _load():
         getattr(L, n).restype = ctypes.c_int
     L.om_mesh_get.argtypes = [P, ip, ip, up, ip, ip, ip]
     L.om_refine.argtypes = [P, ip, ctypes.c_int, ip]
+    L.om_refine_par.argtypes = [P, ip, ctypes.c_int, ip, ip]
     L.om_stiffness_csr.argtypes = [P, ip, ip, dp, ctypes.c_int]
     L.om_solve.argtypes = [P, dp, ctypes.c_double, ctypes.c_int, ip, dp]
     L.om_raster.argtypes = [P, dp, fp, dp, dp, ip]
@@ -217,13 +218,17 @@ def mesh_init(N: int, H: int | None = None) -> Mesh:
 
 def refine(mesh: Mesh, selected) -> tuple[Mesh, dict]:
     """One NVB round with the given selected triangles (their refinement-edge
-    midpoints become mask vertices; closure-only midpoints are unknowns)."""
+    midpoints become mask vertices; closure-only midpoints are unknowns).
+    info["parents"][i] holds the ends of the edge new vertex V + i bisects."""
     cm = _CMesh(mesh)
     sel = np.ascontiguousarray(selected, dtype=np.int32)
     info = np.zeros(4, np.int32)
-    _check(cm.L.om_refine(cm.p, _ptr(sel, ctypes.c_int), len(sel), _ptr(info, ctypes.c_int)), "refine")
+    par = np.zeros(2 * (mesh.V + mesh.T), np.int32)
+    _check(cm.L.om_refine_par(cm.p, _ptr(sel, ctypes.c_int), len(sel), _ptr(info, ctypes.c_int),
+                              _ptr(par, ctypes.c_int)), "refine")
     return cm.to_mesh(), {"new_vertices": int(info[0]), "new_triangles": int(info[1]),
-                          "generations": int(info[2]), "new_mask": int(info[3])}
+                          "generations": int(info[2]), "new_mask": int(info[3]),
+                          "parents": par[: 2 * int(info[0])].reshape(-1, 2).copy()}
 
 
 def stiffness(mesh: Mesh):

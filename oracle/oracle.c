@@ -323,6 +323,10 @@ static int cmp_pix(const void *p, const void *q)
 static int refine_par(om_mesh *m, const int *sel, int nsel, int *info, int *par);
 
 int om_refine(om_mesh *m, const int *sel, int nsel, int *info) { return refine_par(m, sel, nsel, info, NULL); }
+int om_refine_par(om_mesh *m, const int *sel, int nsel, int *info, int *par)
+{
+    return refine_par(m, sel, nsel, info, par);
+}
 
 static int refine_par(om_mesh *m, const int *sel, int nsel, int *info, int *par)
 {

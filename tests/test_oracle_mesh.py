@@ -188,3 +188,25 @@ def test_topk_against_lexsort(oracle_mod):
     assert oracle_mod.topk_count(1000, 0.0, 50, 1000) == 1
     assert oracle_mod.topk_count(1000, 0.5, 50, 1000) == 50
     assert oracle_mod.topk_count(1000, 0.5, 500, 7) == 7
+
+
+def test_refinement_records_the_bisected_edge_of_each_new_vertex(oracle_mod):
+    """info["parents"] gives, for every new vertex, the two vertices of the
+    edge it bisects: the new vertex is their midpoint, and both existed
+    before the round."""
+    import seeded_inputs as S
+    f = S.make_image(65, 4)
+    m = oracle_mod.mesh_init(65)
+    for _ in range(8):
+        v, _, _ = oracle_mod.solve(m, oracle_mod.g_from_f(m, f))
+        _, keys, _ = oracle_mod.raster(m, v, f)
+        k = oracle_mod.topk_count(m.T, 0.05, int(oracle_mod.eligible(m).sum()), 10 ** 6)
+        sel, _ = oracle_mod.select_topk(m, keys, k)
+        V0 = m.V
+        m, info = oracle_mod.refine(m, sel)
+        par = info["parents"]
+        assert par.shape == (m.V - V0, 2)
+        assert par.max() < V0 and par.min() >= 0
+        new = np.arange(V0, m.V)
+        assert np.array_equal(2 * m.vx[new], m.vx[par[:, 0]] + m.vx[par[:, 1]])
+        assert np.array_equal(2 * m.vy[new], m.vy[par[:, 0]] + m.vy[par[:, 1]])
