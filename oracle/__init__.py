@@ -104,6 +104,8 @@ def _load():
     L.om_select_topk.restype = ctypes.c_int
     L.om_spatial.argtypes = [P, fp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                              ctypes.c_int, dp, ctypes.c_int, ip]
+    L.om_spatial_channels.argtypes = [P, fp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, dp, ctypes.c_int, ip]
     L.om_apply_B.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_int]
     L.om_apply_BT.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_int]
     L.om_tonal.argtypes = [P, fp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]
@@ -299,10 +301,13 @@ def scatter(mesh: Mesh, r: np.ndarray) -> np.ndarray:
 
 
 def eligible(mesh: Mesh) -> np.ndarray:
-    """Triangles whose refinement-edge midpoint is a pixel of the image."""
+    """Triangles whose refinement-edge midpoint is a pixel and whose
+    bounding box meets the image."""
     sx = mesh.vx[mesh.ta] + mesh.vx[mesh.tb]
     sy = mesh.vy[mesh.ta] + mesh.vy[mesh.tb]
-    return ((sx % 2) == 0) & ((sy % 2) == 0) & (sx // 2 < mesh.W) & (sy // 2 < mesh.H)
+    xmin = np.minimum(np.minimum(mesh.vx[mesh.ta], mesh.vx[mesh.tb]), mesh.vx[mesh.tc])
+    ymin = np.minimum(np.minimum(mesh.vy[mesh.ta], mesh.vy[mesh.tb]), mesh.vy[mesh.tc])
+    return ((sx % 2) == 0) & ((sy % 2) == 0) & (xmin < mesh.W) & (ymin < mesh.H)
 
 
 def topk_count(T: int, frac: float, n_eligible: int, vcap: int) -> int:
@@ -329,16 +334,24 @@ def vstar(N: int, density: float, H: int | None = None) -> int:
 def spatial(f: np.ndarray, density: float, frac: float, max_rounds: int = 0, tol: float = 1e-13,
             maxit: int = 1_000_000, mesh: Mesh | None = None, log_cap: int = 100_000):
     """Spatial optimisation: refine from the two-triangle mesh (or `mesh`)
-    until V >= ceil(density * W H) or max_rounds rounds (> 0); f is H x W.
+    until V >= ceil(density * W H) or max_rounds rounds (> 0); f is H x W,
+    or C x H x W for C channels (colour: the channels share the mesh, each
+    has its own solve, a triangle's error is the sum over the channels).
     Returns (mesh, log) with log columns V, T, k, margin, CG iterations,
     relres, new vertices, new mask vertices (one row per round)."""
-    H, W = f.shape
+    C = 1 if f.ndim == 2 else f.shape[0]
+    H, W = f.shape[-2:]
     cm = _CMesh(mesh) if mesh is not None else _CMesh(W=W, H=H)
     ff = np.ascontiguousarray(f, dtype=np.float32)
     log = np.zeros((log_cap, LOG_COLS), np.float64)
     rounds = ctypes.c_int(0)
-    rc = cm.L.om_spatial(cm.p, _ptr(ff, ctypes.c_float), float(density), float(frac), int(max_rounds), tol, maxit,
-                         _ptr(log, ctypes.c_double), log_cap, ctypes.byref(rounds))
+    if f.ndim == 2:
+        rc = cm.L.om_spatial(cm.p, _ptr(ff, ctypes.c_float), float(density), float(frac), int(max_rounds), tol,
+                             maxit, _ptr(log, ctypes.c_double), log_cap, ctypes.byref(rounds))
+    else:
+        rc = cm.L.om_spatial_channels(cm.p, _ptr(ff, ctypes.c_float), C, float(density), float(frac),
+                                      int(max_rounds), tol, maxit, _ptr(log, ctypes.c_double), log_cap,
+                                      ctypes.byref(rounds))
     _check(rc, "spatial")
     return cm.to_mesh(), log[: min(rounds.value, log_cap)].copy()
 

@@ -38,7 +38,7 @@
  *  R8  Top-k: k = max(1, ceil(frac*T)), capped by the number of eligible
  *      triangles and by V* - V; order by key descending, then id ascending.
  *      A triangle is eligible when its refinement-edge midpoint is a pixel
- *      of the image.
+ *      and its bounding box meets the image (R9).
  *  R9  Image sizes other than 2^L + 1 (the paper's 2^k images and its
  *      4896 x 3264 photograph, Sec. 5): a W x H image lies at the top-left
  *      of the domain [0, N-1]^2, N = 2^L + 1 >= max(W, H), which carries the
@@ -46,10 +46,14 @@
  *      triangle owns the pixels of R6 that lie in the image, so P has one
  *      row per image pixel, the keys and the data term of the tonal
  *      optimisation run over image pixels, and V* = ceil(density W H).  A
- *      mask vertex outside the image (only the initial corners can be: a
- *      selected midpoint is an image pixel by R8) takes the value of the
- *      nearest image pixel (f at the clamped position).  With W = H = N
- *      everything reduces to the square case.
+ *      selected triangle's midpoint becomes a mask vertex when it is an
+ *      image pixel and an unknown vertex otherwise (it has no data); the
+ *      selection may need such midpoints, e.g. when the image is less than
+ *      half the domain high, the two initial triangles bisect outside it.
+ *      Triangles whose bounding box misses the image are not eligible.  A
+ *      mask vertex outside the image (only the initial corners can be)
+ *      takes the value of the nearest image pixel (f at the clamped
+ *      position).  With W = H = N everything reduces to the square case.
  *
  * Threads.  Compiled with -fopenmp (the multi-core CPU baseline), two loops
  * share their iterations among threads: the per-triangle raster loop and the
@@ -302,11 +306,16 @@ static int lattice_mid(const om_mesh *m, int t)
     return ((m->vx[a] + m->vx[b]) % 2 == 0) && ((m->vy[a] + m->vy[b]) % 2 == 0);
 }
 
-/* R8, R9: selectable when the midpoint is a pixel of the image */
+/* R8, R9: selectable when the edge can be bisected and the triangle's
+ * bounding box meets the image (its smallest x and y lie in the image) */
 int om_eligible(const om_mesh *m, int t)
 {
-    int a = m->ta[t], b = m->tb[t];
-    return lattice_mid(m, t) && (m->vx[a] + m->vx[b]) / 2 < m->W && (m->vy[a] + m->vy[b]) / 2 < m->H;
+    int a = m->ta[t], b = m->tb[t], c = m->tc[t];
+    int xmin = m->vx[a] < m->vx[b] ? m->vx[a] : m->vx[b];
+    int ymin = m->vy[a] < m->vy[b] ? m->vy[a] : m->vy[b];
+    if (m->vx[c] < xmin) xmin = m->vx[c];
+    if (m->vy[c] < ymin) ymin = m->vy[c];
+    return lattice_mid(m, t) && xmin < m->W && ymin < m->H;
 }
 
 typedef struct { long pix; long slot; } pix_slot;
@@ -341,7 +350,9 @@ static int refine_par(om_mesh *m, const int *sel, int nsel, int *info, int *par)
         int fresh;
         long h = eset_insert(&E, edge_key(m->ta[t], m->tb[t]), &fresh);
         if (h < 0) { eset_free(&E); return OM_E_OOM; }
-        E.sel[h] = 1;
+        /* R5, R9: a mask vertex when the midpoint is an image pixel */
+        int a = m->ta[t], b = m->tb[t];
+        E.sel[h] = (m->vx[a] + m->vx[b]) / 2 < m->W && (m->vy[a] + m->vy[b]) / 2 < m->H;
     }
 
     /* closure: a triangle with any marked edge must bisect its refinement edge */
@@ -840,35 +851,59 @@ static double f_at(const om_mesh *m, const float *f, int x, int y)
 /* Refines m until it has at least ceil(density*W*H) vertices (or max_rounds
  * rounds when > 0).  Each round: g = f at the mask vertices, Laplace solve
  * (warm-started), per-triangle squared errors, top-k, one refinement.
- * log rows: V, T, k, margin, CG iterations, relres, new vertices, new mask. */
-int om_spatial(om_mesh *m, const float *f, double density, double frac, int max_rounds,
-               double tol, int maxit, double *log, int log_cap, int *rounds_out)
+ * log rows: V, T, k, margin, CG iterations, relres, new vertices, new mask.
+ *
+ * R10 colour (Sec. 5: the extension to colour images is straightforward):
+ * with C channels (f holds C planes of W x H, one after the other) the
+ * channels share the mesh, the mask set and A_UU; each channel has its own
+ * mask values and its own Laplace solve, and a triangle's error is the sum
+ * over the channels of its squared errors (channel 0 first).  C = 1 is the
+ * grey case.  CG iterations and relres in the log are channel 0's. */
+int om_spatial_channels(om_mesh *m, const float *f, int C, double density, double frac, int max_rounds,
+                        double tol, int maxit, double *log, int log_cap, int *rounds_out)
 {
+    if (C < 1) return OM_E_INVALID;
     long P = (long)m->W * m->H;
     long Vstar = (long)ceil(density * (double)P);
     int rc = OM_OK, round = 0;
-    double *uv = NULL, *keys = NULL, *u_img = malloc(sizeof(double) * P);
+    double *uv = NULL, *keys = NULL, *keys_c = NULL, *u_img = malloc(sizeof(double) * P);
     int *sel = NULL, *par = NULL;
     if (!u_img) return OM_E_OOM;
     int capV = 0;
-    while (m->V < Vstar && (max_rounds <= 0 || round < max_rounds)) {
-        if (capV < m->V) {
-            capV = m->capV;
-            double *nu = realloc(uv, sizeof(double) * capV);
-            if (!nu) { rc = OM_E_OOM; break; }
-            uv = nu;
+    /* channel c's vertex values are uv[c * capV ...]; grow keeps them */
+    #define GROW_UV()                                                                  \
+        if (capV < m->V) {                                                             \
+            int nc = m->capV;                                                          \
+            double *nu = malloc(sizeof(double) * (size_t)nc * C);                      \
+            if (!nu) { rc = OM_E_OOM; break; }                                         \
+            for (int c_ = 0; c_ < C; ++c_)                                             \
+                for (int i_ = 0; i_ < capV; ++i_) nu[(size_t)c_ * nc + i_] = uv[(size_t)c_ * capV + i_]; \
+            free(uv); uv = nu; capV = nc;                                              \
         }
-        if (round == 0) for (int i = 0; i < m->V; ++i) uv[i] = 0.0;
-        for (int i = 0; i < m->V; ++i)
-            if (m->mask[i]) uv[i] = f_at(m, f, m->vx[i], m->vy[i]);
+    while (m->V < Vstar && (max_rounds <= 0 || round < max_rounds)) {
+        GROW_UV();
         int iters = 0; double relres = 0.0;
-        rc = om_solve(m, uv, tol, maxit, &iters, &relres);
-        if (rc) break;
         double *nk = realloc(keys, sizeof(double) * m->T);
+        double *nkc = realloc(keys_c, sizeof(double) * m->T);
         int *ns = realloc(sel, sizeof(int) * m->T);
-        if (!nk || !ns) { free(nk ? nk : keys); free(ns ? ns : sel); keys = NULL; sel = NULL; rc = OM_E_OOM; break; }
-        keys = nk; sel = ns;
-        rc = om_raster(m, uv, f, u_img, keys, NULL);
+        if (nk) keys = nk;
+        if (nkc) keys_c = nkc;
+        if (ns) sel = ns;
+        if (!nk || !nkc || !ns) { rc = OM_E_OOM; break; }
+        for (int c = 0; c < C && !rc; ++c) {
+            double *v = uv + (size_t)c * capV;
+            const float *fc = f + (size_t)c * P;
+            if (round == 0) for (int i = 0; i < m->V; ++i) v[i] = 0.0;
+            for (int i = 0; i < m->V; ++i)
+                if (m->mask[i]) v[i] = f_at(m, fc, m->vx[i], m->vy[i]);
+            int it_c = 0; double rr_c = 0.0;
+            rc = om_solve(m, v, tol, maxit, &it_c, &rr_c);
+            if (rc) break;
+            if (c == 0) { iters = it_c; relres = rr_c; }
+            rc = om_raster(m, v, fc, u_img, c == 0 ? keys : keys_c, NULL);
+            if (rc) break;
+            if (c > 0) for (int t = 0; t < m->T; ++t) keys[t] += keys_c[t];
+        }
         if (rc) break;
         int ne = om_count_eligible(m);
         int k = om_topk_count(m->T, frac, ne, Vstar - m->V);
@@ -884,13 +919,11 @@ int om_spatial(om_mesh *m, const float *f, double density, double frac, int max_
         if (rc) break;
         /* warm start: the previous interpolant at the new vertices, i.e. the
          * mean of the ends of the edge each one bisects */
-        if (capV < m->V) {
-            capV = m->capV;
-            double *nu = realloc(uv, sizeof(double) * capV);
-            if (!nu) { rc = OM_E_OOM; break; }
-            uv = nu;
+        GROW_UV();
+        for (int c = 0; c < C; ++c) {
+            double *v = uv + (size_t)c * capV;
+            for (int i = V0; i < m->V; ++i) v[i] = 0.5 * (v[par[2 * (i - V0)]] + v[par[2 * (i - V0) + 1]]);
         }
-        for (int i = V0; i < m->V; ++i) uv[i] = 0.5 * (uv[par[2 * (i - V0)]] + uv[par[2 * (i - V0) + 1]]);
         if (log && round < log_cap) {
             double *row = log + (long)round * LOG_COLS;
             row[0] = V0; row[1] = T0; row[2] = k; row[3] = margin;
@@ -898,9 +931,16 @@ int om_spatial(om_mesh *m, const float *f, double density, double frac, int max_
         }
         round++;
     }
+    #undef GROW_UV
     if (rounds_out) *rounds_out = round;
-    free(uv); free(keys); free(sel); free(u_img); free(par);
+    free(uv); free(keys); free(keys_c); free(sel); free(u_img); free(par);
     return rc;
+}
+
+int om_spatial(om_mesh *m, const float *f, double density, double frac, int max_rounds,
+               double tol, int maxit, double *log, int log_cap, int *rounds_out)
+{
+    return om_spatial_channels(m, f, 1, density, frac, max_rounds, tol, maxit, log, log_cap, rounds_out);
 }
 
 /* ------------------------------------------------------------------ */
