@@ -109,6 +109,8 @@ def _load():
     L.om_apply_B.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_int]
     L.om_apply_BT.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_int]
     L.om_tonal.argtypes = [P, fp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]
+    L.om_tonal_l1.argtypes = [P, fp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                              ctypes.c_double, ctypes.c_int, dp]
     L.om_threads.restype = ctypes.c_int
     _libs[_openmp] = L
     return L
@@ -386,3 +388,20 @@ def tonal(mesh: Mesh, f: np.ndarray, g0: np.ndarray | None = None, tol: float = 
         _check(rc, "tonal")
     return g, {"iters": int(st[0]), "relres": float(st[1]), "inner_iters": int(st[2]), "sse": float(st[3]),
                "status": int(rc)}
+
+
+def tonal_l1(mesh: Mesh, f: np.ndarray, g0: np.ndarray | None = None, irls: int = 10, eps: float = 1e-3,
+             tol: float = 1e-12, maxit: int = 10_000, inner_tol: float = 1e-14, inner_maxit: int = 1_000_000):
+    """The L1 data term (Sec. 5): min_g sum |B g - f| by IRLS, `irls` steps of
+    weighted least squares with weights 1 / max(|B g - f|, eps), each from the
+    current g (start g0, default f at the mask).  Returns (g, stats) with the
+    CG iterations, the last step's relative residual, inner iterations, the
+    L1 objective and the Huber objective at the end."""
+    cm = _CMesh(mesh)
+    ff = np.ascontiguousarray(f, dtype=np.float32)
+    g = np.ascontiguousarray(g_from_f(mesh, f) if g0 is None else g0, dtype=np.float64).copy()
+    st = np.zeros(5, np.float64)
+    _check(cm.L.om_tonal_l1(cm.p, _ptr(ff, ctypes.c_float), _ptr(g, ctypes.c_double), int(irls), float(eps), tol,
+                            maxit, inner_tol, inner_maxit, _ptr(st, ctypes.c_double)), "tonal_l1")
+    return g, {"iters": int(st[0]), "relres": float(st[1]), "inner_iters": int(st[2]), "l1": float(st[3]),
+               "huber": float(st[4])}

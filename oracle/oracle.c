@@ -45,15 +45,16 @@
  *      mesh exactly as for a square image.  Only image pixels are data: a
  *      triangle owns the pixels of R6 that lie in the image, so P has one
  *      row per image pixel, the keys and the data term of the tonal
- *      optimisation run over image pixels, and V* = ceil(density W H).  A
- *      selected triangle's midpoint becomes a mask vertex when it is an
- *      image pixel and an unknown vertex otherwise (it has no data); the
- *      selection may need such midpoints, e.g. when the image is less than
- *      half the domain high, the two initial triangles bisect outside it.
- *      Triangles whose bounding box misses the image are not eligible.  A
- *      mask vertex outside the image (only the initial corners can be)
- *      takes the value of the nearest image pixel (f at the clamped
- *      position).  With W = H = N everything reduces to the square case.
+ *      optimisation run over image pixels, and V* = ceil(density W H).
+ *      Triangles whose bounding box misses the image are not eligible; a
+ *      selected midpoint may still lie outside the image (when the image is
+ *      less than half the domain high, the two initial triangles bisect
+ *      below it).  Every vertex outside the image is a mask vertex with the
+ *      value of the nearest image pixel (f at the clamped position): the
+ *      method runs on the image padded with its edge values, with the data
+ *      term restricted to the image, and the padding holds no unknowns
+ *      (with no data there, they would form large badly conditioned
+ *      blocks).  With W = H = N everything reduces to the square case.
  *
  * Threads.  Compiled with -fopenmp (the multi-core CPU baseline), two loops
  * share their iterations among threads: the per-triangle raster loop and the
@@ -350,9 +351,7 @@ static int refine_par(om_mesh *m, const int *sel, int nsel, int *info, int *par)
         int fresh;
         long h = eset_insert(&E, edge_key(m->ta[t], m->tb[t]), &fresh);
         if (h < 0) { eset_free(&E); return OM_E_OOM; }
-        /* R5, R9: a mask vertex when the midpoint is an image pixel */
-        int a = m->ta[t], b = m->tb[t];
-        E.sel[h] = (m->vx[a] + m->vx[b]) / 2 < m->W && (m->vy[a] + m->vy[b]) / 2 < m->H;
+        E.sel[h] = 1;
     }
 
     /* closure: a triangle with any marked edge must bisect its refinement edge */
@@ -391,14 +390,16 @@ static int refine_par(om_mesh *m, const int *sel, int nsel, int *info, int *par)
     for (size_t r = 0; r < nn; ++r) {
         long h = order[r].slot;
         int x = (int)(order[r].pix % m->N), y = (int)(order[r].pix / m->N);
-        int id = add_vertex(m, x, y, E.sel[h]);
+        /* R5, R9: selected midpoints, and every vertex outside the image */
+        int is_mask = E.sel[h] || x >= m->W || y >= m->H;
+        int id = add_vertex(m, x, y, is_mask);
         if (id < 0) { free(order); eset_free(&E); return OM_E_OOM; }
         E.vid[h] = id;
         if (par) {
             par[2 * (id - V0)] = (int)(E.key[h] >> 32);
             par[2 * (id - V0) + 1] = (int)(E.key[h] & 0xffffffffu);
         }
-        nmask += E.sel[h];
+        nmask += is_mask;
     }
     free(order);
 
@@ -1042,8 +1043,13 @@ static double dotn(const double *x, const double *y, long n)
  * ||B^T (f - B g)|| <= tol ||B^T f|| or after maxit outer iterations.
  * stats: [0] outer iterations, [1] final relative normal residual,
  *        [2] inner CG iterations, [3] ||B g - f||^2 at the end. */
-int om_tonal(const om_mesh *m, const float *f, double *g, double tol, int maxit,
-             double inner_tol, int inner_maxit, double *stats)
+/* Weighted least squares min_g sum_p w_p ((B g)_p - f_p)^2 by CGLS on the
+ * matrix W^(1/2) B (w = NULL: all weights 1, the tonal optimisation of
+ * eq. 4).  The residual r = f - B g is kept unweighted and the weights enter
+ * where W^(1/2) appears twice: s = B^T W r and |W^(1/2) q|^2.  Stops when
+ * ||B^T W (f - B g)|| <= tol ||B^T W f|| or after maxit iterations. */
+int om_tonal_weighted(const om_mesh *m, const float *f, const double *w, double *g, double tol, int maxit,
+                      double inner_tol, int inner_maxit, double *stats)
 {
     long P = (long)m->W * m->H;
     tonal_ctx c;
@@ -1051,16 +1057,18 @@ int om_tonal(const om_mesh *m, const float *f, double *g, double tol, int maxit,
     int nK = c.nK;
     double *r = malloc(sizeof(double) * P), *q = malloc(sizeof(double) * P);
     double *s = malloc(sizeof(double) * nK), *p = malloc(sizeof(double) * nK);
-    double *fd = malloc(sizeof(double) * P);
-    if (rc || !r || !q || !s || !p || !fd) { rc = rc ? rc : OM_E_OOM; goto out; }
+    double *fd = malloc(sizeof(double) * P), *wr = malloc(sizeof(double) * P);
+    if (rc || !r || !q || !s || !p || !fd || !wr) { rc = rc ? rc : OM_E_OOM; goto out; }
     for (long i = 0; i < P; ++i) fd[i] = f[i];
-    rc = apply_BT(&c, fd, s);                /* B^T f, for the stopping test */
+    for (long i = 0; i < P; ++i) wr[i] = w ? w[i] * fd[i] : fd[i];
+    rc = apply_BT(&c, wr, s);                /* B^T W f, for the stopping test */
     if (rc) goto out;
     double cnorm = sqrt(dotn(s, s, nK));
     rc = apply_B(&c, g, q);
     if (rc) goto out;
     for (long i = 0; i < P; ++i) r[i] = fd[i] - q[i];
-    rc = apply_BT(&c, r, s);
+    for (long i = 0; i < P; ++i) wr[i] = w ? w[i] * r[i] : r[i];
+    rc = apply_BT(&c, wr, s);
     if (rc) goto out;
     for (int i = 0; i < nK; ++i) p[i] = s[i];
     double gamma = dotn(s, s, nK);
@@ -1071,12 +1079,15 @@ int om_tonal(const om_mesh *m, const float *f, double *g, double tol, int maxit,
         if (it >= maxit) break;
         int e = apply_B(&c, p, q);
         if (e) { rc = e; break; }
-        double qq = dotn(q, q, P);
+        double qq = 0.0;
+        if (w) { for (long i = 0; i < P; ++i) qq += w[i] * q[i] * q[i]; }
+        else qq = dotn(q, q, P);
         if (qq == 0.0) { rc = OM_OK; break; }
         double alpha = gamma / qq;
         for (int i = 0; i < nK; ++i) g[i] += alpha * p[i];
         for (long i = 0; i < P; ++i) r[i] -= alpha * q[i];
-        e = apply_BT(&c, r, s);
+        for (long i = 0; i < P; ++i) wr[i] = w ? w[i] * r[i] : r[i];
+        e = apply_BT(&c, wr, s);
         if (e) { rc = e; break; }
         double gamma1 = dotn(s, s, nK);
         double beta = gamma1 / gamma;
@@ -1094,7 +1105,59 @@ int om_tonal(const om_mesh *m, const float *f, double *g, double tol, int maxit,
         stats[3] = e ? NAN : sse;
     }
 out:
-    free(r); free(q); free(s); free(p); free(fd);
+    free(r); free(q); free(s); free(p); free(fd); free(wr);
     ctx_free(&c);
+    return rc;
+}
+
+/* CG on the normal equations of eq. 4 in least-squares form (CGLS): the
+ * inner solves are the inpainting problems.  g holds the start on entry and
+ * the result on exit.  Stops when ||B^T (f - B g)|| <= tol ||B^T f|| or
+ * after maxit outer iterations.  stats: [0] outer iterations, [1] final
+ * relative normal residual, [2] inner CG iterations, [3] ||B g - f||^2. */
+int om_tonal(const om_mesh *m, const float *f, double *g, double tol, int maxit,
+             double inner_tol, int inner_maxit, double *stats)
+{
+    return om_tonal_weighted(m, f, NULL, g, tol, maxit, inner_tol, inner_maxit, stats);
+}
+
+/* R11, the L1 data term of Sec. 5 (after the cited work, the L1 error
+ * instead of the L2 one): min_g sum_p |(B g)_p - f_p| by iteratively
+ * reweighted least squares.  Each of the `irls` steps sets the weights
+ * w_p = 1 / max(|(B g)_p - f_p|, eps) from the current g and solves the
+ * weighted least-squares problem from the current g (om_tonal_weighted to
+ * tol).  stats: [0] CG iterations over all steps, [1] the last step's
+ * relative residual, [2] inner CG iterations, [3] sum_p |(B g)_p - f_p| at
+ * the end, [4] the smoothed objective sum_p min(r^2 / (2 eps), |r| - eps/2)
+ * at the end (Huber, which the iteration does not increase). */
+int om_tonal_l1(const om_mesh *m, const float *f, double *g, int irls, double eps, double tol, int maxit,
+                double inner_tol, int inner_maxit, double *stats)
+{
+    long P = (long)m->W * m->H;
+    double *u = malloc(sizeof(double) * P), *w = malloc(sizeof(double) * P);
+    int rc = (u && w && eps > 0.0 && irls >= 0) ? OM_OK : (eps > 0.0 && irls >= 0 ? OM_E_OOM : OM_E_INVALID);
+    double its = 0.0, inner = 0.0, rel = 0.0;
+    for (int k = 0; k < irls && !rc; ++k) {
+        rc = om_apply_B(m, g, u, inner_tol, inner_maxit);
+        if (rc) break;
+        for (long i = 0; i < P; ++i) {
+            double a = fabs(u[i] - (double)f[i]);
+            w[i] = 1.0 / (a > eps ? a : eps);
+        }
+        double st[4];
+        rc = om_tonal_weighted(m, f, w, g, tol, maxit, inner_tol, inner_maxit, st);
+        its += st[0]; inner += st[2]; rel = st[1];
+    }
+    if (!rc && stats) {
+        rc = om_apply_B(m, g, u, inner_tol, inner_maxit);
+        double l1 = 0.0, hub = 0.0;
+        for (long i = 0; i < P && !rc; ++i) {
+            double a = fabs(u[i] - (double)f[i]);
+            l1 += a;
+            hub += a <= eps ? a * a / (2.0 * eps) : a - eps / 2.0;
+        }
+        stats[0] = its; stats[1] = rel; stats[2] = inner; stats[3] = l1; stats[4] = hub;
+    }
+    free(u); free(w);
     return rc;
 }
