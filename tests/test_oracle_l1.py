@@ -56,3 +56,24 @@ def test_zero_steps_leave_g_unchanged(oracle_mod):
     g, st = oracle_mod.tonal_l1(m, f, irls=0)
     np.testing.assert_array_equal(g, g0)
     assert st["l1"] == pytest.approx(np.abs(oracle_mod.apply_B(m, g0) - f.astype(np.float64)).sum(), rel=1e-12)
+
+
+def test_irls_reaches_the_linear_programming_l1_minimum(oracle_mod):
+    """min_g sum_p |(B g)_p - f_p| is a linear program (g free, t >= |B g - f|);
+    the Huber minimiser's L1 objective is within P eps / 2 of its optimum, since
+    |r| - eps/2 <= huber(r) <= |r|."""
+    linprog = pytest.importorskip("scipy.optimize").linprog
+    f, m = _case(oracle_mod, N=17, seed=5, density=0.3)
+    B = _dense_B(oracle_mod, m)
+    fd = f.astype(np.float64).ravel()
+    P, nK = B.shape
+    c = np.concatenate([np.zeros(nK), np.ones(P)])
+    I = np.eye(P)
+    A = np.block([[B, -I], [-B, -I]])
+    b = np.concatenate([fd, -fd])
+    lp = linprog(c, A_ub=A, b_ub=b, bounds=[(None, None)] * nK + [(0, None)] * P, method="highs")
+    assert lp.status == 0
+    eps = 1e-4
+    _, st = oracle_mod.tonal_l1(m, f, irls=80, eps=eps, tol=1e-12)
+    assert st["l1"] >= lp.fun - 1e-9
+    assert st["l1"] <= lp.fun + P * eps / 2, (st["l1"], lp.fun)
