@@ -49,10 +49,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=4, choices=[1, 2, 3, 4],
+    ap.add_argument("--config", type=int, default=4, choices=[1, 2, 3, 4, 6, 7],
                     help="1: 257^2 FP64, one triangle per round to 5%%, one solve + errors; 2: 1025^2 "
                          "spatial (1%% per round, 3%%) + tonal; 3: 2049^2 at 4%% + tonal; 4 (default): 8193^2 "
-                         "textured at 2%% + 50 tonal iterations")
+                         "textured at 2%% + 50 tonal iterations; 6: 1024^2 at 4%% + tonal (Table 2's size); "
+                         "7: 4896 x 3264 textured at 2%% + 50 tonal iterations (Fig. 3's size); the serving "
+                         "workload (5) is --serve")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--density", type=float, default=None)
     ap.add_argument("--frac", type=float, default=None)
@@ -100,11 +102,34 @@ PRESETS = {
             precision="fp32ir", inner_tol=1e-11),
     4: dict(n=8193, density=0.02, frac=0.01, seed=3, texture=True, tonal="iters", tonal_tol=0.0, tonal_iters=50,
             precision="fp32ir", inner_tol=1e-13),
+    # (5 is the serving workload, bench.py --serve)
+    # the paper's own image sizes (general sizes in the smallest (2^L+1)^2
+    # domain): Table 2's largest, 1024 x 1024 at 4 %, and the 4896 x 3264
+    # photograph size of Fig. 3 (textured synthetic stand-in) at 2 %
+    6: dict(n=1024, h=1024, density=0.04, frac=0.01, seed=4, texture=False, tonal="tol", tonal_tol=1e-8,
+            tonal_iters=0, precision="fp32ir", inner_tol=1e-11),
+    7: dict(n=4896, h=3264, density=0.02, frac=0.01, seed=5, texture=True, tonal="iters", tonal_tol=0.0,
+            tonal_iters=50, precision="fp32ir", inner_tol=1e-13),
 }
 
 
+def image_hw(a):
+    """(height, width) of the workload's image."""
+    return (getattr(a, "h", None) or a.n), a.n
+
+
+def make_workload_image(a, seed):
+    import numpy as np
+    import seeded_inputs
+    H, W = image_hw(a)
+    if H == W:
+        return seeded_inputs.make_image(W, seed, texture=a.texture)
+    return np.ascontiguousarray(seeded_inputs.make_image(max(W, H), seed, texture=a.texture)[:H, :W])
+
+
 def workload_name(a):
-    sp = (f"{a.n}x{a.n} seeded image{' with texture' if a.texture else ''}: spatial optimisation "
+    H, W = image_hw(a)
+    sp = (f"{W}x{H} seeded image{' with texture' if a.texture else ''}: spatial optimisation "
           f"({'one triangle' if a.frac == 0 else f'top-k {a.frac:.0%} of triangles'} per round, NVB, to "
           f"{a.density:.0%} vertex density)")
     if a.tonal == "none":
@@ -115,7 +140,8 @@ def workload_name(a):
 
 
 def config(a, world):
-    return {"workload": workload_name(a), "config_index": a.config, "image": f"{a.n}x{a.n}", "density": a.density,
+    H, W = image_hw(a)
+    return {"workload": workload_name(a), "config_index": a.config, "image": f"{W}x{H}", "density": a.density,
             "topk_frac": a.frac, "tonal": a.tonal, "tonal_tol": a.tonal_tol, "tonal_iters": a.tonal_iters,
             "inner_tol": a.inner_tol, "fast_keys": {-1: "auto", 0: "exact", 1: "fp32_band"}[getattr(a, "fast_keys", -1)],
             "precision": a.precision, "seed": a.seed, "l2_flush": True,
@@ -244,8 +270,9 @@ def run_ours(a, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = a.n
-    P = n * n
-    f_np = seeded_inputs.make_image(n, replica_seed(a.seed, rank), texture=a.texture)
+    H, W = image_hw(a)
+    P = W * H
+    f_np = make_workload_image(a, replica_seed(a.seed, rank))
     f = torch.from_numpy(f_np).to(dev)
     prec = fem.FEM_PREC_FP64 if a.precision == "fp64" else fem.FEM_PREC_FP32_IR
     p = fem.params(topk_frac=a.frac, tonal_tol=a.tonal_tol, precision=prec, inner_tol=a.inner_tol,
@@ -256,7 +283,7 @@ def run_ours(a, world, rank, local):
     stream = torch.cuda.current_stream(dev)
 
     def run(f_dev, pp):
-        mesh = fem.Mesh(n)
+        mesh = fem.Mesh(W, H)
         mesh.spatial_refine(f_dev, a.density, pp)
         st_sp = mesh.stats()
         g = mesh.g_from_f(f_dev)
@@ -574,16 +601,20 @@ def cpu_baseline(a, f_np, gpu):
     sampled rounds run on the smallest meshes of the loop, so the estimate is
     a lower bound on the oracle's time."""
     import oracle
-    P = a.n * a.n
-    if a.n <= 1025:
+    H, W = image_hw(a)
+    P = W * H
+    if max(W, H) <= 1025:
         ts, tt, it, rounds = oracle_job(a, f_np)
         what = "tonal" if a.tonal != "none" else "solve + errors"
         return {"value": round(P / 1e6 / (ts + tt), 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": f"one full run of the workload by the FP64 C oracle (single thread): spatial {rounds} "
                           f"rounds {ts:.1f} s + {what} ({it} outer iterations) {tt:.1f} s"}
     R = 4
-    om = oracle.Mesh(a.n, gpu["xy"][:, 0].copy(), gpu["xy"][:, 1].copy(), gpu["mask"].copy(), gpu["tri"][:, 0].copy(),
-                     gpu["tri"][:, 1].copy(), gpu["tri"][:, 2].copy())
+    N = 3
+    while N < max(W, H):
+        N = 2 * N - 1
+    om = oracle.Mesh(N, gpu["xy"][:, 0].copy(), gpu["xy"][:, 1].copy(), gpu["mask"].copy(), gpu["tri"][:, 0].copy(),
+                     gpu["tri"][:, 1].copy(), gpu["tri"][:, 2].copy(), W, H)
     t_round, t_tonal1, _ = oracle_sample(a, f_np, tonal_mesh=om, rounds=R)
     est = project_job(t_round, t_tonal1, gpu["rounds"], gpu["tonal_iters"])
     return {"value": round(P / 1e6 / est, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -623,13 +654,13 @@ def run_reference(a, world, rank):
     workload's round and iteration counts, JOB_COUNTS)."""
     if rank != 0:
         return
-    import seeded_inputs
-    f_np = seeded_inputs.make_image(a.n, a.seed, texture=a.texture)
-    P = a.n * a.n
+    H, W = image_hw(a)
+    f_np = make_workload_image(a, a.seed)
+    P = W * H
     base = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config(a, 1), "impl": "reference"}
-    if a.config in (1, 2):
+    if a.config in (1, 2, 6):
         for _ in range(a.warmup):
             oracle_job(a, f_np)
         times, its, rounds = [], 0, 0
@@ -643,6 +674,9 @@ def run_reference(a, world, rank):
                                               else "one solve + per-triangle errors"))
         extra = {}
     else:
+        if a.config not in JOB_COUNTS:
+            print(json.dumps({"impl": "reference", "unavailable": f"no recorded round count for configuration {a.config}"}))
+            return
         rounds, iters = JOB_COUNTS[a.config]
         for _ in range(a.warmup):
             oracle_sample(a, f_np)

@@ -6,8 +6,16 @@
  *
  * Conventions shared by every call
  *  - Images are width x height float32, row-major, y pointing down; pixel
- *    (x, y) is at offset y*width + x.  width == height == 2^L + 1 (L >= 1), so
- *    that every edge midpoint created by bisection is a pixel.
+ *    (x, y) is at offset y*width + x.  The mesh lives on the domain
+ *    [0, N-1]^2 with N = 2^L + 1 the smallest such side >= max(width,
+ *    height), so that every edge midpoint created by bisection is a pixel of
+ *    the domain; the image lies at the domain's top-left.  Only image pixels
+ *    are data: a triangle owns the pixels of the ownership rule that lie in
+ *    the image, and the per-triangle errors and the tonal data term sum
+ *    over image pixels.  A triangle can be selected when its bounding box
+ *    meets the image.  Every vertex outside the image is a mask vertex and
+ *    takes the value of the nearest image pixel.  For width == height ==
+ *    2^L + 1 the domain is the image.
  *  - A mesh has V vertices (integer pixel positions) and T triangles.  A
  *    triangle is stored as (a, b, c): (a, b) is its refinement edge and c its
  *    newest vertex (the right-angle corner).  Vertices are either mask
@@ -51,7 +59,7 @@ typedef struct fem_server fem_server;
 typedef enum {
     FEM_OK = 0,
     FEM_E_INVALID = 1,       /* bad argument or malformed mesh */
-    FEM_E_SHAPE = 2,         /* image side is not 2^L + 1, or width != height */
+    FEM_E_SHAPE = 2,         /* image size out of range (see fem_mesh_create) */
     FEM_E_OOM = 3,           /* device allocation failed */
     FEM_E_NOT_CONVERGED = 4, /* iteration cap reached; last iterate written */
     FEM_E_TIMEOUT = 5,       /* a bounded device-side wait ran out */
@@ -97,11 +105,12 @@ typedef struct {
 FEM_API void fem_params_default(fem_params *p);
 
 /* Create the initial mesh for a width x height image (Sec. 2.2's mesh,
- * replaced by the two triangles of the image square split along the diagonal
- * (0,0)-(N-1,N-1)): vertices 0..3 at the corners (0,0), (N-1,0), (0,N-1),
- * (N-1,N-1), all mask vertices, and triangles (v0,v3,v2), (v3,v0,v1).
- * *out receives a library-owned handle.  FEM_E_SHAPE unless width == height
- * == 2^L + 1 with 2 <= 2^L <= 2^15. */
+ * replaced by the two triangles of the domain square split along the
+ * diagonal (0,0)-(N-1,N-1)): vertices 0..3 at the corners (0,0), (N-1,0),
+ * (0,N-1), (N-1,N-1), all mask vertices, and triangles (v0,v3,v2),
+ * (v3,v0,v1).  N is the smallest 2^L + 1 >= max(width, height) (and >= 3).
+ * *out receives a library-owned handle.  FEM_E_SHAPE unless
+ * 2 <= width, height <= 32769. */
 FEM_API fem_status fem_mesh_create(int width, int height, void *stream, fem_mesh **out);
 
 /* Free the mesh and its device memory (after the work on its streams ends). */
@@ -109,6 +118,10 @@ FEM_API fem_status fem_mesh_destroy(fem_mesh *m);
 
 /* Sizes of the mesh: vertices, triangles, mask vertices (any pointer may be NULL). */
 FEM_API fem_status fem_mesh_info(const fem_mesh *m, int *V, int *T, int *nmask);
+
+/* The image width and height of the mesh and its domain side N (any
+ * pointer may be NULL). */
+FEM_API fem_status fem_mesh_size(const fem_mesh *m, int *width, int *height, int *domain);
 
 /* Copy the mesh to host buffers: xy (2V ints: x0,y0,x1,y1,...), tri (3T ints:
  * a,b,c per triangle), is_mask (V bytes, 1 = mask vertex).  Any may be NULL.
@@ -187,7 +200,7 @@ FEM_API fem_status fem_triangle_errors_noalloc(int width, int V, const int *xy_d
  * fem_triangle_errors (u linear on t from the vertex values uv_dev, f the
  * image).  The FP32 sum carries a rigorous bound from the number of
  * roundings of the plane evaluation, the difference and the summation,
- * widened by 1 %.  uv_dev: V doubles; f_dev: N*N floats; lo_dev, hi_dev: T
+ * widened by 1 %.  uv_dev: V doubles; f_dev: the width x height image; lo_dev, hi_dev: T
  * doubles (device, caller-owned).  FEM_E_INVALID on null pointers. */
 FEM_API fem_status fem_triangle_error_bounds(fem_mesh *m, const double *uv_dev, const float *f_dev, double *lo_dev,
                                              double *hi_dev, void *stream);
@@ -202,15 +215,31 @@ FEM_API fem_status fem_rasterize(fem_mesh *m, const double *uv_dev, float *u_dev
  * V >= ceil(density * width*height) (or p->max_rounds rounds), each round
  * sets g = f at the mask vertices, solves (warm-started), computes the
  * per-triangle errors, selects the top k = max(1, ceil(topk_frac*T))
- * eligible triangles (error descending, id ascending; eligible = refinement
- * edge midpoint is a pixel; k capped by the vertex target) and refines them
- * by newest-vertex bisection.  Midpoints of selected refinement edges become
+ * eligible triangles (error descending, id ascending; eligible = the
+ * refinement-edge midpoint is a pixel and the triangle's bounding box meets
+ * the image; k capped by the vertex target) and refines them by
+ * newest-vertex bisection.  Midpoints of selected refinement edges become
  * mask vertices; midpoints created only to keep the mesh conforming become
- * unknown vertices.  New vertices are numbered by ascending pixel index, new
+ * unknown vertices.  New vertices are numbered by
+ * ascending pixel index of the domain (y N + x), new
  * triangles by ascending (generation, parent id).
  *   f_dev in: width*height float32 image */
 FEM_API fem_status fem_spatial_refine(fem_mesh *m, const float *f_dev, double density, const fem_params *p,
                               void *stream);
+
+/* Spatial optimisation of a colour image (Sec. 5 notes that the extension
+ * to colour is straightforward; this is its reading): f_dev holds
+ * `channels` planes of width*height float32, plane c at offset
+ * c*width*height.  The channels share the mesh and the mask vertices, each
+ * has its own mask values and Laplace solve, and a triangle's error is the
+ * sum over the channels of its squared errors.  channels = 1 is
+ * fem_spatial_refine.  1 <= channels <= 4, else FEM_E_INVALID.  With more
+ * than one channel every key is the exact (float-float) one; the fast keys
+ * serve one channel.  After the call the mesh's vertex values are channel
+ * 0's; for each channel, fem_gather_mask and fem_tonal_opt on its plane give
+ * its mask values and tonally optimised values (B is the same for all). */
+FEM_API fem_status fem_spatial_refine_channels(fem_mesh *m, const float *f_dev, int channels, double density,
+                                               const fem_params *p, void *stream);
 
 /* Tonal optimisation (Sec. 4, eqs. 4-5): g* = argmin ||B g - f||^2 by CG on
  * the normal equations B^T B g = B^T f, applying B and B^T through inner
@@ -218,6 +247,23 @@ FEM_API fem_status fem_spatial_refine(fem_mesh *m, const float *f_dev, double de
  *   f_dev in : width*height float32 image
  *   g_dev in : nmask float32 start values; out: the optimised values */
 FEM_API fem_status fem_tonal_opt(fem_mesh *m, const float *f_dev, float *g_dev, const fem_params *p, void *stream);
+
+/* Tonal optimisation with the L1 data term (Sec. 5, after the cited work,
+ * the L1 error instead of the L2 one): min_g sum over image pixels of
+ * |(B g)_p - f_p| by iteratively reweighted least squares.  Each of the
+ * `irls` steps sets the weights w_p = 1 / max(|(B g)_p - f_p|, eps) from the
+ * current g and runs the tonal CG on the weighted problem
+ * min_g sum_p w_p ((B g)_p - f_p)^2 from the current g, with p->tonal_tol and
+ * p->tonal_maxit per step (B^T W B g = B^T W f, the pixel-mass matrix
+ * P^T W P built by a weighted pixel pass).  The steps majorise the Huber
+ * function with threshold eps, which therefore does not increase.
+ *   f_dev    in : width*height float32 image
+ *   g_dev    in : start (nmask float32); out: the result
+ *   irls     steps (>= 0); eps > 0 (grey values in [0, 1]: 1e-3, say)
+ * Returns FEM_E_NOT_CONVERGED when the last step hit tonal_maxit;
+ * fem_mesh_stats' tonal_iters counts the CG iterations of all steps. */
+FEM_API fem_status fem_tonal_opt_l1(fem_mesh *m, const float *f_dev, float *g_dev, int irls, double eps,
+                                    const fem_params *p, void *stream);
 
 /* Adjoint of u = B g (Sec. 4): gbar = B^T r = (P^T r)_K - A_KU A_UU^{-1} (P^T r)_U,
  * with P the pixel interpolation matrix.  This is the gradient of

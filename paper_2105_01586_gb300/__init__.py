@@ -44,9 +44,10 @@ FEM_PREC_FP64 = 1
 _STATUS = {0: "FEM_OK", 1: "FEM_E_INVALID", 2: "FEM_E_SHAPE", 3: "FEM_E_OOM", 4: "FEM_E_NOT_CONVERGED",
            5: "FEM_E_TIMEOUT", 6: "FEM_E_CUDA", 7: "FEM_E_CANCELLED"}
 
-EXPORTED = ["fem_params_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_info", "fem_mesh_export",
-            "fem_mesh_import", "fem_mesh_curve_order", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_triangle_error_bounds", "fem_triangle_errors_noalloc", "fem_rasterize", "fem_spatial_refine",
-            "fem_tonal_opt", "fem_adjoint", "fem_tonal_loss", "fem_mesh_stats", "fem_last_error", "fem_profile_enable",
+EXPORTED = ["fem_params_default", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_info", "fem_mesh_size",
+            "fem_mesh_export",
+            "fem_mesh_import", "fem_mesh_curve_order", "fem_gather_mask", "fem_inpaint", "fem_triangle_errors", "fem_triangle_error_bounds", "fem_triangle_errors_noalloc", "fem_rasterize", "fem_spatial_refine", "fem_spatial_refine_channels",
+            "fem_tonal_opt", "fem_tonal_opt_l1", "fem_adjoint", "fem_tonal_loss", "fem_mesh_stats", "fem_last_error", "fem_profile_enable",
             "fem_profile_read", "fem_launch_count", "fem_selftest_wait_timeout", "fem_server_create",
             "fem_server_submit", "fem_server_wait", "fem_server_result", "fem_server_state", "fem_server_cancel", "fem_server_release",
             "fem_server_destroy", "fem_set_mem_pool", "fem_debug_alloc_fault"]
@@ -73,6 +74,7 @@ _sig = {
     "fem_mesh_create": (_i, [_i, _i, _vp, ctypes.POINTER(_vp)]),
     "fem_mesh_destroy": (_i, [_vp]),
     "fem_mesh_info": (_i, [_vp, _ip, _ip, _ip]),
+    "fem_mesh_size": (_i, [_vp, _ip, _ip, _ip]),
     "fem_mesh_export": (_i, [_vp, _vp, _vp, _vp]),
     "fem_mesh_import": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
     "fem_gather_mask": (_i, [_vp, _vp, _vp, _vp]),
@@ -83,7 +85,9 @@ _sig = {
     "fem_triangle_errors_noalloc": (_i, [_i, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "fem_rasterize": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "fem_spatial_refine": (_i, [_vp, _vp, ctypes.c_double, _pp, _vp]),
+    "fem_spatial_refine_channels": (_i, [_vp, _vp, _i, ctypes.c_double, _pp, _vp]),
     "fem_tonal_opt": (_i, [_vp, _vp, _vp, _pp, _vp]),
+    "fem_tonal_opt_l1": (_i, [_vp, _vp, _vp, _i, ctypes.c_double, _pp, _vp]),
     "fem_adjoint": (_i, [_vp, _vp, _vp, _pp, _vp]),
     "fem_tonal_loss": (_i, [_vp, _vp, _vp, _vp, _vp, _pp, _vp]),
     "fem_mesh_stats": (_i, [_vp, ctypes.POINTER(fem_stats)]),
@@ -180,6 +184,18 @@ def fem_mesh_info(h: int) -> tuple[int, int, int]:
     return V.value, T.value, K.value
 
 
+def fem_mesh_size(h: int) -> tuple[int, int, int]:
+    """(width, height, domain side N) of the mesh's image."""
+    W, H, N = _i(), _i(), _i()
+    _check(_lib.fem_mesh_size(h, ctypes.byref(W), ctypes.byref(H), ctypes.byref(N)), "fem_mesh_size")
+    return W.value, H.value, N.value
+
+
+def _pixels(h: int) -> int:
+    W, H, _ = fem_mesh_size(h)
+    return W * H
+
+
 def fem_mesh_export(h: int):
     V, T, _ = fem_mesh_info(h)
     xy = np.zeros((V, 2), np.int32)
@@ -209,13 +225,13 @@ def fem_mesh_curve_order(h: int):
 def fem_gather_mask(h: int, f, g, stream=None):
     V, T, K = fem_mesh_info(h)
     torch = _torch()
-    _check(_lib.fem_gather_mask(h, _dev_ptr(f, torch.float32, None, "f"), _dev_ptr(g, torch.float32, K, "g"),
+    _check(_lib.fem_gather_mask(h, _dev_ptr(f, torch.float32, _pixels(h), "f"), _dev_ptr(g, torch.float32, K, "g"),
                                 _stream(stream)), "fem_gather_mask")
 
 
 def fem_inpaint(h: int, g, u=None, uv=None, p: fem_params | None = None, stream=None, allow_not_converged=False):
     V, T, K = fem_mesh_info(h)
-    st = _lib.fem_inpaint(h, _dev_ptr(g, _torch().float32, K, "g"), _dev_ptr(u, _torch().float32, None, "u"),
+    st = _lib.fem_inpaint(h, _dev_ptr(g, _torch().float32, K, "g"), _dev_ptr(u, _torch().float32, _pixels(h) if u is not None else None, "u"),
                           _dev_ptr(uv, _torch().float64, V, "uv"), ctypes.byref(p or params()), _stream(stream))
     return _check(st, "fem_inpaint", (FEM_E_NOT_CONVERGED,) if allow_not_converged else ())
 
@@ -223,7 +239,7 @@ def fem_inpaint(h: int, g, u=None, uv=None, p: fem_params | None = None, stream=
 def fem_triangle_errors(h: int, uv, f, err, stream=None):
     V, T, K = fem_mesh_info(h)
     torch = _torch()
-    _check(_lib.fem_triangle_errors(h, _dev_ptr(uv, torch.float64, V, "uv"), _dev_ptr(f, torch.float32, None, "f"),
+    _check(_lib.fem_triangle_errors(h, _dev_ptr(uv, torch.float64, V, "uv"), _dev_ptr(f, torch.float32, _pixels(h), "f"),
                                     _dev_ptr(err, torch.float64, T, "err"), _stream(stream)), "fem_triangle_errors")
 
 
@@ -231,7 +247,7 @@ def fem_triangle_error_bounds(h: int, uv, f, lo, hi, stream=None):
     V, T, K = fem_mesh_info(h)
     torch = _torch()
     _check(_lib.fem_triangle_error_bounds(h, _dev_ptr(uv, torch.float64, V, "uv"),
-                                          _dev_ptr(f, torch.float32, None, "f"), _dev_ptr(lo, torch.float64, T, "lo"),
+                                          _dev_ptr(f, torch.float32, _pixels(h), "f"), _dev_ptr(lo, torch.float64, T, "lo"),
                                           _dev_ptr(hi, torch.float64, T, "hi"), _stream(stream)),
            "fem_triangle_error_bounds")
 
@@ -248,7 +264,8 @@ def fem_triangle_errors_noalloc(width: int, xy, tri4, uv, f, err, stream=None):
         raise ValueError("xy must be (V, 2) and tri4 (T, 4)")
     _check(_lib.fem_triangle_errors_noalloc(int(width), V, _dev_ptr(xy, torch.int32, 2 * V, "xy"), T,
                                             _dev_ptr(tri4, torch.int32, 4 * T, "tri4"),
-                                            _dev_ptr(uv, torch.float64, V, "uv"), _dev_ptr(f, torch.float32, None, "f"),
+                                            _dev_ptr(uv, torch.float64, V, "uv"),
+                                            _dev_ptr(f, torch.float32, int(width) * int(width), "f"),
                                             _dev_ptr(err, torch.float64, T, "err"), _stream(stream)),
            "fem_triangle_errors_noalloc")
 
@@ -256,27 +273,45 @@ def fem_triangle_errors_noalloc(width: int, xy, tri4, uv, f, err, stream=None):
 def fem_rasterize(h: int, uv, u=None, owner=None, stream=None):
     V, T, K = fem_mesh_info(h)
     torch = _torch()
-    _check(_lib.fem_rasterize(h, _dev_ptr(uv, torch.float64, V, "uv"), _dev_ptr(u, torch.float32, None, "u"),
-                              _dev_ptr(owner, torch.int32, None, "owner"), _stream(stream)), "fem_rasterize")
+    _check(_lib.fem_rasterize(h, _dev_ptr(uv, torch.float64, V, "uv"), _dev_ptr(u, torch.float32, _pixels(h) if u is not None else None, "u"),
+                              _dev_ptr(owner, torch.int32, _pixels(h) if owner is not None else None, "owner"), _stream(stream)), "fem_rasterize")
 
 
 def fem_spatial_refine(h: int, f, density: float, p: fem_params | None = None, stream=None):
-    _check(_lib.fem_spatial_refine(h, _dev_ptr(f, _torch().float32, None, "f"), float(density),
+    _check(_lib.fem_spatial_refine(h, _dev_ptr(f, _torch().float32, _pixels(h), "f"), float(density),
                                    ctypes.byref(p or params()), _stream(stream)), "fem_spatial_refine")
+
+
+def fem_spatial_refine_channels(h: int, f, density: float, p: fem_params | None = None, stream=None):
+    """Colour spatial optimisation: f is (C, H, W) float32 on the device."""
+    C = int(f.shape[0]) if f.dim() == 3 else 1
+    _check(_lib.fem_spatial_refine_channels(h, _dev_ptr(f, _torch().float32, C * _pixels(h), "f"), C,
+                                            float(density), ctypes.byref(p or params()), _stream(stream)),
+           "fem_spatial_refine_channels")
 
 
 def fem_tonal_opt(h: int, f, g, p: fem_params | None = None, stream=None, allow_not_converged=False):
     V, T, K = fem_mesh_info(h)
     torch = _torch()
-    st = _lib.fem_tonal_opt(h, _dev_ptr(f, torch.float32, None, "f"), _dev_ptr(g, torch.float32, K, "g"),
+    st = _lib.fem_tonal_opt(h, _dev_ptr(f, torch.float32, _pixels(h), "f"), _dev_ptr(g, torch.float32, K, "g"),
                             ctypes.byref(p or params()), _stream(stream))
     return _check(st, "fem_tonal_opt", (FEM_E_NOT_CONVERGED,) if allow_not_converged else ())
+
+
+def fem_tonal_opt_l1(h: int, f, g, irls: int = 10, eps: float = 1e-3, p: fem_params | None = None, stream=None,
+                     allow_not_converged=False):
+    """L1 data term by IRLS (see include/feminpaint.h); g: start and result."""
+    V, T, K = fem_mesh_info(h)
+    torch = _torch()
+    st = _lib.fem_tonal_opt_l1(h, _dev_ptr(f, torch.float32, _pixels(h), "f"), _dev_ptr(g, torch.float32, K, "g"),
+                               int(irls), float(eps), ctypes.byref(p or params()), _stream(stream))
+    return _check(st, "fem_tonal_opt_l1", (FEM_E_NOT_CONVERGED,) if allow_not_converged else ())
 
 
 def fem_adjoint(h: int, r, gbar, p: fem_params | None = None, stream=None):
     V, T, K = fem_mesh_info(h)
     torch = _torch()
-    _check(_lib.fem_adjoint(h, _dev_ptr(r, torch.float32, None, "r"), _dev_ptr(gbar, torch.float32, K, "gbar"),
+    _check(_lib.fem_adjoint(h, _dev_ptr(r, torch.float32, _pixels(h), "r"), _dev_ptr(gbar, torch.float32, K, "gbar"),
                             ctypes.byref(p or params()), _stream(stream)), "fem_adjoint")
 
 
@@ -285,7 +320,7 @@ def fem_tonal_loss(h: int, g, f, loss=None, grad=None, p: fem_params | None = No
     B^T (B g - f), both written by the library into the given CUDA tensors."""
     V, T, K = fem_mesh_info(h)
     torch = _torch()
-    _check(_lib.fem_tonal_loss(h, _dev_ptr(g, torch.float32, K, "g"), _dev_ptr(f, torch.float32, None, "f"),
+    _check(_lib.fem_tonal_loss(h, _dev_ptr(g, torch.float32, K, "g"), _dev_ptr(f, torch.float32, _pixels(h), "f"),
                                _dev_ptr(loss, torch.float64, 1, "loss"), _dev_ptr(grad, torch.float32, K, "grad"),
                                ctypes.byref(p or params()), _stream(stream)), "fem_tonal_loss")
 
@@ -345,11 +380,15 @@ def fem_debug_alloc_fault(fail_after: int) -> int:
 
 # ------------------------------------------------------------- convenience
 class Mesh:
-    """Owning wrapper of a mesh handle for an N x N image (N = 2^L + 1)."""
+    """Owning wrapper of a mesh handle for a width x height image (height
+    defaults to width).  The mesh lives on the smallest (2^L + 1)^2 domain
+    that holds the image; only image pixels are data."""
 
-    def __init__(self, n: int, stream=None):
-        self.n = n
-        self.h = fem_mesh_create(n, n, stream)
+    def __init__(self, width: int, height: int | None = None, stream=None):
+        self.width = int(width)
+        self.height = int(width if height is None else height)
+        self.h = fem_mesh_create(self.width, self.height, stream)
+        self.n = fem_mesh_size(self.h)[2]  # the domain side N
 
     def close(self):
         if getattr(self, "h", None):
@@ -389,7 +428,7 @@ class Mesh:
 
     def inpaint(self, g, p=None, want_uv=False, stream=None, allow_not_converged=False):
         torch = _torch()
-        u = torch.empty((self.n, self.n), dtype=torch.float32, device=g.device)
+        u = torch.empty((self.height, self.width), dtype=torch.float32, device=g.device)
         uv = torch.empty(self.V, dtype=torch.float64, device=g.device) if want_uv else None
         fem_inpaint(self.h, g, u, uv, p, stream, allow_not_converged)
         return (u, uv) if want_uv else u
@@ -410,13 +449,17 @@ class Mesh:
 
     def rasterize(self, uv, want_owner=False, stream=None):
         torch = _torch()
-        u = torch.empty((self.n, self.n), dtype=torch.float32, device=uv.device)
-        own = torch.empty((self.n, self.n), dtype=torch.int32, device=uv.device) if want_owner else None
+        u = torch.empty((self.height, self.width), dtype=torch.float32, device=uv.device)
+        own = torch.empty((self.height, self.width), dtype=torch.int32, device=uv.device) if want_owner else None
         fem_rasterize(self.h, uv, u, own, stream)
         return (u, own) if want_owner else u
 
     def spatial_refine(self, f, density, p=None, stream=None):
-        fem_spatial_refine(self.h, f, density, p, stream)
+        """f: (H, W) grey, or (C, H, W) colour (C <= 4)."""
+        if f.dim() == 3:
+            fem_spatial_refine_channels(self.h, f, density, p, stream)
+        else:
+            fem_spatial_refine(self.h, f, density, p, stream)
 
     def g_from_f(self, f, stream=None):
         """g = f at the mask vertices (fem_gather_mask)."""
@@ -428,6 +471,11 @@ class Mesh:
     def tonal_opt(self, f, g0=None, p=None, stream=None, allow_not_converged=False):
         g = (self.g_from_f(f) if g0 is None else g0).clone()
         fem_tonal_opt(self.h, f, g, p, stream, allow_not_converged)
+        return g
+
+    def tonal_opt_l1(self, f, g0=None, irls=10, eps=1e-3, p=None, stream=None, allow_not_converged=False):
+        g = (self.g_from_f(f) if g0 is None else g0).clone()
+        fem_tonal_opt_l1(self.h, f, g, irls, eps, p, stream, allow_not_converged)
         return g
 
     def adjoint(self, r, p=None, stream=None):

@@ -169,6 +169,21 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
     return s_ok != 0;
 }
 
+// The pixel domain of a mesh: side N = 2^L + 1, and the W x H image at its
+// top-left whose pixels alone are data (W = H = N for a square image).  A
+// triangle owns the pixels of the ownership rule that lie in the image.  It
+// can be selected when its refinement edge (a, b) can be bisected (the
+// midpoint is a pixel) and its bounding box meets the image.
+struct Dom {
+    int N, W, H;
+};
+
+constexpr int kMaxChannels = 4;  // channels of a colour image in the spatial optimisation
+
+__host__ __device__ __forceinline__ bool dom_eligible(int ax, int ay, int bx, int by, int cx, int cy, const Dom& D) {
+    return (((ax + bx) | (ay + by)) & 1) == 0 && min(ax, min(bx, cx)) < D.W && min(ay, min(by, cy)) < D.H;
+}
+
 // Direction index (0..7) of a nonzero lattice step whose components are each
 // -1, 0 or +1 after taking signs: E, NE(+x,+y), N(+y), NW, W, SW, S, SE.
 __host__ __device__ __forceinline__ int dir_index(int dx, int dy) {
@@ -217,8 +232,10 @@ void release(DArr<T>& a, cudaStream_t s) {
 
 // ------------------------------------------------------------------ mesh
 struct fem_mesh {
-    int N = 0;          // image side (2^L + 1)
-    long long P = 0;    // pixels
+    int N = 0;          // domain side (2^L + 1): the mesh lives on [0, N-1]^2
+    long long P = 0;    // domain pixels N^2
+    int W = 0, H = 0;   // the image, at the domain's top-left (W = H = N: square image)
+    long long PI = 0;   // image pixels W H
     int V = 0, T = 0, nK = 0, nU = 0;
     int dev = 0, num_sms = 0;
     cudaStream_t last_stream = nullptr;
@@ -311,6 +328,14 @@ struct fem_mesh {
     // square-tiled error pass (raster_sq.cu): the image as squares, the node
     // tables of the plan, per-node partial sums, the band's squares
     fem::DArr<float> fsq, fedge;       // Q*Q squares of s rows of s + 1 floats; the image's last row (N)
+    fem::DArr<float> fpad;             // a W x H input image padded to the domain with its edge values
+    // channels 1..3 of a colour image in the spatial optimisation (channel 0
+    // uses uv, uvf, fsq, fedge, fpad), and the keys of one channel
+    fem::DArr<double> uvc[3];
+    fem::DArr<float2> uvfc[3];
+    fem::DArr<float> fsqc[3], fedgec[3], fpadc[3];
+    fem::DArr<double> keys_acc;
+    fem::DArr<float> wimg, wfimg;      // IRLS weights w and w f of the L1 data term (domain layout)
     fem::DArr<int> sq_nodeof, sq_off;  // per curve position: node (fine) or -1; first bounding-box square
     fem::DArr<int> sq_pos;             // per triangle: its curve position
     fem::DArr<int> sq_bcoarse;         // curve positions of the band's coarse triangles
@@ -338,6 +363,15 @@ struct fem_mesh {
 
 namespace fem {
 // A cancelled request stops between spatial rounds and tonal iterations.
+inline Dom dom_of(const fem_mesh* m) { return Dom{m->N, m->W, m->H}; }
+
+// The image the kernels read, indexed over the domain (pixel (x, y) at
+// y N + x): f itself for a square image, else a copy of the W x H image f
+// padded to N x N with the values of its nearest pixels (fem_mesh::fpad).
+// Pixels outside the image are only ever read as the values of mask
+// vertices there, never as data.
+fem_status domain_image(fem_mesh* m, const float* f, cudaStream_t s, const float** out);
+
 inline fem_status check_cancel(const fem_mesh* m) {
     if (m->cancel && m->cancel->load(std::memory_order_relaxed) != 0) {
         set_error("request cancelled");
@@ -388,6 +422,8 @@ fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, do
 // the image f as squares for the square-tiled pass (once per call that reads f)
 fem_status sq_image(fem_mesh* m, const float* f, cudaStream_t s);
 fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s);
+fem_status raster_weights(fem_mesh* m, const double* uv, const float* f, float eps, float* w_dom, float* wf_dom,
+                          cudaStream_t s);
 fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vstar, cudaStream_t s,
                         double* margin_out, int* k_out, bool band = false);
 // fast keys: histogram bins (top 16 bits of a non-negative float) and the

@@ -123,6 +123,29 @@ void reset_coop_state(fem_mesh* m, cudaStream_t s) {
     cudaMemsetAsync(m->dflag.p + 2, 0, sizeof(int), s);
 }
 
+// ------------------------------------------------------------ domain image
+__global__ void k_pad_image(const float* __restrict__ f, int W, int H, int N, float* __restrict__ out) {
+    pdl_wait();
+    const long long n = (long long)N * N;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(p / N), x = (int)(p - (long long)y * N);
+        out[p] = f[(long long)min(y, H - 1) * W + min(x, W - 1)];
+    }
+}
+
+fem_status domain_image(fem_mesh* m, const float* f, cudaStream_t s, const float** out) {
+    if (m->W == m->N && m->H == m->N) {
+        *out = f;
+        return FEM_OK;
+    }
+    FEM_TRY(ensure(m->fpad, (size_t)m->P, s));
+    const int grid = (int)std::min<long long>((m->P + 255) / 256, (long long)m->num_sms * 16);
+    note_bytes(F_OTHER, 4.0 * (double)m->PI + 4.0 * (double)m->P);
+    FEM_LAUNCH(F_OTHER, s, k_pad_image, grid, 256, 0, f, m->W, m->H, m->N, m->fpad.p);
+    *out = m->fpad.p;
+    return FEM_OK;
+}
+
 // ------------------------------------------------------------------ memory
 // Every device allocation of the library comes through dalloc_raw: from the
 // caller's pool when one is set, else from the device's current pool.  The
@@ -396,15 +419,20 @@ fem_status fem_mesh_create(int width, int height, void* stream, fem_mesh** out) 
         return FEM_E_INVALID;
     }
     *out = nullptr;
-    int L = width - 1;
-    if (width != height || width < 3 || width > 32769 || (L & (L - 1)) != 0) {
-        set_error("fem_mesh_create: width == height == 2^L + 1 (3..32769) required");
+    if (width < 2 || height < 2 || width > 32769 || height > 32769) {
+        set_error("fem_mesh_create: width and height must be 2..32769");
         return FEM_E_SHAPE;
     }
+    // the smallest domain side 2^L + 1 that holds the image
+    int n = 3;
+    while (n < width || n < height) n = 2 * n - 1;
     cudaStream_t s = (cudaStream_t)stream;
     fem_mesh* m = new fem_mesh();
-    m->N = width;
-    m->P = (long long)width * width;
+    m->N = n;
+    m->P = (long long)n * n;
+    m->W = width;
+    m->H = height;
+    m->PI = (long long)width * height;
     cudaGetDevice(&m->dev);
     m->num_sms = sm_count();
     m->last_stream = s;
@@ -435,7 +463,7 @@ fem_status fem_mesh_create(int width, int height, void* stream, fem_mesh** out) 
         if (e == cudaSuccess) e = cudaMemsetAsync(m->dflag.p, 0, 64 * sizeof(int), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(m->dcount.p, 0, 64 * sizeof(int), s);
         if (e != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
-        int n1 = width - 1;
+        int n1 = n - 1;
         int2 xy[4] = {{0, 0}, {n1, 0}, {0, n1}, {n1, n1}};
         unsigned char mk[4] = {1, 1, 1, 1};
         int4 tr[2] = {{0, 3, 2, 0}, {3, 0, 1, 0}};
@@ -515,7 +543,12 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->tv, s); release(m->ty, s); release(m->tz, s); release(m->tg, s);
     release(m->tr, s); release(m->tp, s); release(m->tw, s); release(m->tc, s);
     release(m->lossk, s); release(m->lossred, s); release(m->tyr, s);
-    release(m->fsq, s); release(m->fedge, s); release(m->sq_nodeof, s); release(m->sq_off, s);
+    release(m->fsq, s); release(m->fedge, s); release(m->fpad, s);
+    for (int c = 0; c < 3; ++c) {
+        release(m->uvc[c], s); release(m->uvfc[c], s); release(m->fsqc[c], s); release(m->fedgec[c], s);
+        release(m->fpadc[c], s);
+    }
+    release(m->keys_acc, s); release(m->wimg, s); release(m->wfimg, s); release(m->sq_nodeof, s); release(m->sq_off, s);
     release(m->sq_cov, s); release(m->sq_slot, s); release(m->sq_seg, s); release(m->sq_part, s);
     release(m->sq_coarse, s); release(m->sq_long, s); release(m->sq_piece, s); release(m->sq_psum, s);
     release(m->sq_pdone, s); release(m->sq_ctr, s); release(m->sq_list, s); release(m->sq_rec, s);
@@ -533,6 +566,14 @@ fem_status fem_mesh_info(const fem_mesh* m, int* V, int* T, int* nmask) {
     if (V) *V = m->V;
     if (T) *T = m->T;
     if (nmask) *nmask = m->nK;
+    return FEM_OK;
+}
+
+fem_status fem_mesh_size(const fem_mesh* m, int* width, int* height, int* domain) {
+    FEM_TRY(check_mesh(m));
+    if (width) *width = m->W;
+    if (height) *height = m->H;
+    if (domain) *domain = m->N;
     return FEM_OK;
 }
 

@@ -26,7 +26,11 @@
 
 namespace fem {
 
-enum RasterMode { R_ERR = 0, R_IMG = 1, R_MASS = 2, R_SCAT = 3 };
+// R_WMASS: the mass entries with a pixel weight (P^T W P of a weighted least
+// squares step); R_WGT: the weights of an IRLS step of the L1 data term,
+// w = 1 / max(|u - f|, eps), and w f, written per image pixel in domain
+// layout (u in float-float, as in the error mode)
+enum RasterMode { R_ERR = 0, R_IMG = 1, R_MASS = 2, R_SCAT = 3, R_WMASS = 4, R_WGT = 5 };
 // Pixels per item (about 1024): fewer items mean less fixed cost per pixel.
 // 256-pixel items at 1025^2, meant to shorten the longest item, measured
 // slower (the fixed cost of four times as many items), so every size uses
@@ -99,7 +103,7 @@ __global__ void k_item_expand(const int* __restrict__ cnt, const int* __restrict
 
 template <int MODE>
 struct NAcc {
-    static constexpr int n = MODE == R_ERR ? 1 : (MODE == R_MASS ? 6 : (MODE == R_SCAT ? 3 : 0));
+    static constexpr int n = MODE == R_ERR ? 1 : ((MODE == R_MASS || MODE == R_WMASS) ? 6 : (MODE == R_SCAT ? 3 : 0));
 };
 
 // Sum of a triangle's item partials (float-float) by one warp in a fixed
@@ -123,17 +127,17 @@ __device__ __forceinline__ ff warp_sum_partials(const float2* partial, int o, in
 template <int MODE>
 __global__ void __launch_bounds__(kRasterThreads) k_raster(
     const int4* __restrict__ tri, const int2* __restrict__ vxy, const double* __restrict__ uv,
-    const float2* __restrict__ uvf, const float* __restrict__ img, int N, const int* __restrict__ item_tri,
+    const float2* __restrict__ uvf, const float* __restrict__ img, Dom D, const int* __restrict__ item_tri,
     const int* __restrict__ item_off, const int* __restrict__ n_items_dev, int item_cap, int item_px,
     double* __restrict__ partial, float* __restrict__ u_out, int* __restrict__ owner_out,
-    const int* __restrict__ plan_err) {
+    const int* __restrict__ plan_err, float* __restrict__ wf_out, float eps) {
     pdl_wait();
     // An overflowing plan left item slots unwritten (they may hold another
     // mesh's triangle ids): read none of them.  Every thread reads the same
     // word, so the whole grid returns or none of it does.
     if (plan_err && *plan_err) return;
     constexpr int NA = NAcc<MODE>::n;
-    constexpr bool FF = (MODE == R_ERR || MODE == R_IMG);
+    constexpr bool FF = (MODE == R_ERR || MODE == R_IMG || MODE == R_WGT);
     const unsigned FULL = 0xffffffffu;
     int lane = threadIdx.x & 31;
     long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -143,12 +147,12 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
         int t = item_tri[it];
         int j = (int)(it - item_off[t]);
         int4 tr = tri[t];
-        TriGeom g = tri_geom(tr, vxy, N);
+        TriGeom g = tri_geom(tr, vxy, D.N);
         int rpi = rows_per_item(g.maxw, item_px);
         int r0 = g.ytop + j * rpi;
         int nr = min(rpi, g.yend + 1 - r0);
         int L = 0, len = 0;
-        if (lane < nr) row_span(g, r0 + lane, N, L, len);
+        if (lane < nr) row_span(g, r0 + lane, D, L, len);
 
         int dax = g.ax - g.cx, day = g.ay - g.cy, dbx = g.bx - g.cx, dby = g.by - g.cy;
         long long l2 = (long long)dax * dax + (long long)day * day;
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
         const int coff = cinc - ccnt;
         const int nchunks = __shfl_sync(FULL, cinc, 31);
         constexpr int kPre = 4;
-        constexpr bool READS = (MODE == R_ERR || MODE == R_SCAT);
+        constexpr bool READS = (MODE == R_ERR || MODE == R_SCAT || MODE == R_WMASS || MODE == R_WGT);
         for (int q0 = 0; q0 < nchunks; q0 += kPre) {
             int px[kPre], py[kPre];
             float fv[kPre];
@@ -208,19 +212,25 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
                 const bool ok = q < nchunks && c < lr;
                 px[u] = ok ? Lr + c : -1;
                 py[u] = r0 + r;
-                fv[u] = (READS && ok) ? img[(long long)py[u] * N + px[u]] : 0.f;
+                fv[u] = (READS && ok) ? img[(long long)py[u] * D.N + px[u]] : 0.f;
             }
 #pragma unroll
             for (int u = 0; u < kPre; ++u) {
             if (px[u] >= 0) {
                 int x = px[u], y = py[u];
-                long long p = (long long)y * N + x;
+                long long p = (long long)y * D.W + x;  // outputs are W x H
                 if (FF) {
                     float dx = (float)(x - g.cx), dy = (float)(y - g.cy);
                     ff u_ = ff_add(ff_add(uc, ff_mul_f(gx, dx)), ff_mul_f(gy, dy));
                     if (MODE == R_ERR) {
                         ff d = ff_add_f(u_, -fv[u]);
                         acc_ff = ff_add(acc_ff, ff_sqr(d));
+                    } else if (MODE == R_WGT) {
+                        const ff d = ff_add_f(u_, -fv[u]);
+                        const float w = 1.0f / fmaxf(fabsf(__fadd_rn(d.hi, d.lo)), eps);
+                        const long long pd = (long long)y * D.N + x;  // domain layout
+                        u_out[pd] = w;
+                        wf_out[pd] = w * fv[u];
                     } else {
                         if (u_out) u_out[p] = __fadd_rn(u_.hi, u_.lo);
                         if (owner_out) owner_out[p] = t;
@@ -230,13 +240,15 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
                     double la = (double)(dxp * dax + dyp * day) * inv_l2;
                     double lb = (double)(dxp * dbx + dyp * dby) * inv_l2;
                     double lc = 1.0 - la - lb;
-                    if (MODE == R_MASS) {
-                        acc[0] = fma(la, la, acc[0]);
-                        acc[1] = fma(lb, lb, acc[1]);
-                        acc[2] = fma(lc, lc, acc[2]);
-                        acc[3] = fma(la, lb, acc[3]);
-                        acc[4] = fma(lb, lc, acc[4]);
-                        acc[5] = fma(lc, la, acc[5]);
+                    if (MODE == R_MASS || MODE == R_WMASS) {
+                        const double wt = MODE == R_WMASS ? (double)fv[u] : 1.0;
+                        const double wa = wt * la, wb = wt * lb, wc = wt * lc;
+                        acc[0] = fma(wa, la, acc[0]);
+                        acc[1] = fma(wb, lb, acc[1]);
+                        acc[2] = fma(wc, lc, acc[2]);
+                        acc[3] = fma(wa, lb, acc[3]);
+                        acc[4] = fma(wb, lc, acc[4]);
+                        acc[5] = fma(wc, la, acc[5]);
                     } else if (MODE == R_SCAT) {
                         double r = (double)fv[u];
                         acc[0] = fma(la, r, acc[0]);
@@ -268,7 +280,8 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(
 __global__ void k_finalize_err(const int* __restrict__ cnt, const int* __restrict__ off,
                                const float2* __restrict__ partial, int T, const int4* __restrict__ tri,
                                const int2* __restrict__ vxy, double* __restrict__ out,
-                               unsigned long long* __restrict__ keyc, int item_cap, const int* __restrict__ plan_err) {
+                               unsigned long long* __restrict__ keyc, int item_cap, const int* __restrict__ plan_err,
+                               Dom D) {
     pdl_wait();
     if (plan_err && *plan_err) return;  // the plan overflowed: no partial is valid
     long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -284,8 +297,8 @@ __global__ void k_finalize_err(const int* __restrict__ cnt, const int* __restric
             out[t] = key;
             if (keyc) {
                 int4 tr = tri[t];
-                int2 a = vxy[tr.x], b = vxy[tr.y];
-                bool eligible = (((a.x + b.x) | (a.y + b.y)) & 1) == 0;
+                int2 a = vxy[tr.x], b = vxy[tr.y], c = vxy[tr.z];
+                bool eligible = dom_eligible(a.x, a.y, b.x, b.y, c.x, c.y, D);
                 keyc[t] = eligible ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
             }
         }
@@ -318,22 +331,23 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_raster_small(const int* __restrict__ order, const int4* __restrict__ tri,
                                                       const int2* __restrict__ vxy, const double* __restrict__ uv,
                                                       const float2* __restrict__ uvf, const float* __restrict__ img,
-                                                      int N, int T, double* __restrict__ out,
+                                                      Dom D, int T, double* __restrict__ out,
                                                       unsigned long long* __restrict__ keyc,
                                                       float* __restrict__ u_out, int* __restrict__ owner_out,
-                                                      const int* __restrict__ n_dev = nullptr) {
+                                                      const int* __restrict__ n_dev, float* __restrict__ wf_out,
+                                                      float eps) {
     pdl_wait();
     // n_dev: the order list has *n_dev entries (a device-side count, at most T)
     const int Tn = n_dev ? min(*n_dev, T) : T;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Tn; i += gridDim.x * blockDim.x) {
         int t = order ? order[i] : i;
         int4 tr = tri[t];
-        TriGeom g = tri_geom(tr, vxy, N);
+        TriGeom g = tri_geom(tr, vxy, D.N);
         if (!is_small(g)) continue;
         int dax = g.ax - g.cx, day = g.ay - g.cy, dbx = g.bx - g.cx, dby = g.by - g.cy;
         long long l2 = (long long)dax * dax + (long long)day * day;
         bool pow2 = (l2 & (l2 - 1)) == 0;
-        if (MODE == R_ERR || MODE == R_IMG) {
+        if (MODE == R_ERR || MODE == R_IMG || MODE == R_WGT) {
             ff va = vertex_ff(uv, uvf, tr.x), vb = vertex_ff(uv, uvf, tr.y), uc = vertex_ff(uv, uvf, tr.z);
             ff da = ff_sub(va, uc), db = ff_sub(vb, uc);
             ff gx = ff_add(ff_mul_f(da, (float)dax), ff_mul_f(db, (float)dbx));
@@ -350,18 +364,25 @@ __global__ void __launch_bounds__(256) k_raster_small(const int* __restrict__ or
             ff acc{0.f, 0.f};
             for (int y = g.ytop; y <= g.yend; ++y) {
                 int L, len;
-                row_span(g, y, N, L, len);
+                row_span(g, y, D, L, len);
                 if (len <= 0) continue;
                 ff u = ff_add(ff_add(uc, ff_mul_f(gx, (float)(L - g.cx))), ff_mul_f(gy, (float)(y - g.cy)));
-                long long p0 = (long long)y * N + L;
+                const long long p0 = (long long)y * D.N + L;  // the domain image
+                const long long q0 = (long long)y * D.W + L;  // the W x H outputs
 #pragma unroll 4
                 for (int k = 0; k < len; ++k) {
                     if (MODE == R_ERR) {
                         ff d = ff_add_f(u, -img[p0 + k]);
                         acc = ff_add(acc, ff_sqr(d));
+                    } else if (MODE == R_WGT) {
+                        const float fv = img[p0 + k];
+                        const ff d = ff_add_f(u, -fv);
+                        const float w = 1.0f / fmaxf(fabsf(__fadd_rn(d.hi, d.lo)), eps);
+                        u_out[p0 + k] = w;  // domain layout
+                        wf_out[p0 + k] = w * fv;
                     } else {
-                        if (u_out) u_out[p0 + k] = __fadd_rn(u.hi, u.lo);
-                        if (owner_out) owner_out[p0 + k] = t;
+                        if (u_out) u_out[q0 + k] = __fadd_rn(u.hi, u.lo);
+                        if (owner_out) owner_out[q0 + k] = t;
                     }
                     u = ff_add(u, gx);
                 }
@@ -370,7 +391,7 @@ __global__ void __launch_bounds__(256) k_raster_small(const int* __restrict__ or
                 double key = ff_to_double(acc);
                 out[t] = key;
                 if (keyc) {
-                    bool eligible = (((g.ax + g.bx) | (g.ay + g.by)) & 1) == 0;
+                    bool eligible = tri_eligible(g, D);
                     keyc[t] = eligible ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
                 }
             }
@@ -379,29 +400,31 @@ __global__ void __launch_bounds__(256) k_raster_small(const int* __restrict__ or
             double acc[6] = {0, 0, 0, 0, 0, 0};
             for (int y = g.ytop; y <= g.yend; ++y) {
                 int L, len;
-                row_span(g, y, N, L, len);
+                row_span(g, y, D, L, len);
                 for (int k = 0; k < len; ++k) {
                     int x = L + k;
                     long long dxp = x - g.cx, dyp = y - g.cy;
                     double la = (double)(dxp * dax + dyp * day) * inv_l2;
                     double lb = (double)(dxp * dbx + dyp * dby) * inv_l2;
                     double lc = 1.0 - la - lb;
-                    if (MODE == R_MASS) {
-                        acc[0] = fma(la, la, acc[0]);
-                        acc[1] = fma(lb, lb, acc[1]);
-                        acc[2] = fma(lc, lc, acc[2]);
-                        acc[3] = fma(la, lb, acc[3]);
-                        acc[4] = fma(lb, lc, acc[4]);
-                        acc[5] = fma(lc, la, acc[5]);
+                    if (MODE == R_MASS || MODE == R_WMASS) {
+                        const double wt = MODE == R_WMASS ? (double)img[(long long)y * D.N + x] : 1.0;
+                        const double wa = wt * la, wb = wt * lb, wc = wt * lc;
+                        acc[0] = fma(wa, la, acc[0]);
+                        acc[1] = fma(wb, lb, acc[1]);
+                        acc[2] = fma(wc, lc, acc[2]);
+                        acc[3] = fma(wa, lb, acc[3]);
+                        acc[4] = fma(wb, lc, acc[4]);
+                        acc[5] = fma(wc, la, acc[5]);
                     } else {
-                        double r = (double)img[(long long)y * N + x];
+                        double r = (double)img[(long long)y * D.N + x];
                         acc[0] = fma(la, r, acc[0]);
                         acc[1] = fma(lb, r, acc[1]);
                         acc[2] = fma(lc, r, acc[2]);
                     }
                 }
             }
-            constexpr int NA = MODE == R_MASS ? 6 : 3;
+            constexpr int NA = (MODE == R_MASS || MODE == R_WMASS) ? 6 : 3;
 #pragma unroll
             for (int q = 0; q < NA; ++q) out[(long long)t * NA + q] = acc[q];
         }
@@ -442,11 +465,11 @@ fem_status raster_image(fem_mesh* m, const double* uv, float* u, int* owner, cud
     note_bytes(F_RASTER, (u ? 4.0 * (double)m->P : 0.0) + (owner ? 4.0 * (double)m->P : 0.0) + 16.0 * m->T +
                              16.0 * m->V);
     FEM_LAUNCH(F_RASTER, s, k_raster<R_IMG>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv,
-               (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, u, owner,
-               (const int*)(m->dflag.p + 0));
+               (const float2*)nullptr, (const float*)nullptr, dom_of(m), m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, u, owner,
+               (const int*)(m->dflag.p + 0), (float*)nullptr, 0.0f);
     FEM_LAUNCH(F_RASTER, s, k_raster_small<R_IMG>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv,
-               (const float2*)nullptr, (const float*)nullptr, m->N, m->T, (double*)nullptr,
-               (unsigned long long*)nullptr, u, owner, nullptr);
+               (const float2*)nullptr, (const float*)nullptr, dom_of(m), m->T, (double*)nullptr,
+               (unsigned long long*)nullptr, u, owner, nullptr, (float*)nullptr, 0.0f);
     return FEM_OK;
 }
 
@@ -459,25 +482,54 @@ fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s) {
     note_bytes(F_RASTER, (mode == R_MASS ? 64.0 * m->T : 4.0 * (double)m->P + 40.0 * m->T) + 8.0 * m->V);
     if (mode == R_MASS) {
         FEM_LAUNCH(F_RASTER, s, k_raster<R_MASS>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
-                   (const double*)nullptr, (const float2*)nullptr, (const float*)nullptr, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0,
+                   (const double*)nullptr, (const float2*)nullptr, (const float*)nullptr, dom_of(m), m->item_tri.p, m->item_off.p, m->dcount.p + 0,
                    (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, (float*)nullptr, (int*)nullptr,
-                   (const int*)(m->dflag.p + 0));
+                   (const int*)(m->dflag.p + 0), (float*)nullptr, 0.0f);
         FEM_LAUNCH(F_RASTER, s, k_finalize<6>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
                    m->loc.p);
         FEM_LAUNCH(F_RASTER, s, k_raster_small<R_MASS>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p,
-                   (const double*)nullptr, (const float2*)nullptr, (const float*)nullptr, m->N, m->T, m->loc.p,
-                   (unsigned long long*)nullptr, (float*)nullptr, (int*)nullptr, nullptr);
+                   (const double*)nullptr, (const float2*)nullptr, (const float*)nullptr, dom_of(m), m->T, m->loc.p,
+                   (unsigned long long*)nullptr, (float*)nullptr, (int*)nullptr, nullptr, (float*)nullptr, 0.0f);
+    } else if (mode == R_WMASS) {
+        // r: the pixel weights (domain layout)
+        FEM_LAUNCH(F_RASTER, s, k_raster<R_WMASS>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
+                   (const double*)nullptr, (const float2*)nullptr, r, dom_of(m), m->item_tri.p, m->item_off.p,
+                   m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, (float*)nullptr,
+                   (int*)nullptr, (const int*)(m->dflag.p + 0), (float*)nullptr, 0.0f);
+        FEM_LAUNCH(F_RASTER, s, k_finalize<6>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
+                   m->loc.p);
+        FEM_LAUNCH(F_RASTER, s, k_raster_small<R_WMASS>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p,
+                   (const double*)nullptr, (const float2*)nullptr, r, dom_of(m), m->T, m->loc.p,
+                   (unsigned long long*)nullptr, (float*)nullptr, (int*)nullptr, nullptr, (float*)nullptr, 0.0f);
     } else {
         FEM_LAUNCH(F_RASTER, s, k_raster<R_SCAT>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p,
-                   (const double*)nullptr, (const float2*)nullptr, r, m->N, m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P),
+                   (const double*)nullptr, (const float2*)nullptr, r, dom_of(m), m->item_tri.p, m->item_off.p, m->dcount.p + 0, (int)m->item_tri.n, item_pixels_for(m->P),
                    m->partial.p, (float*)nullptr, (int*)nullptr,
-                   (const int*)(m->dflag.p + 0));
+                   (const int*)(m->dflag.p + 0), (float*)nullptr, 0.0f);
         FEM_LAUNCH(F_RASTER, s, k_finalize<3>, blocks, 256, 0, m->item_cnt.p, m->item_off.p, m->partial.p, m->T,
                    m->loc.p);
         FEM_LAUNCH(F_RASTER, s, k_raster_small<R_SCAT>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p,
-                   (const double*)nullptr, (const float2*)nullptr, r, m->N, m->T, m->loc.p,
-                   (unsigned long long*)nullptr, (float*)nullptr, (int*)nullptr, nullptr);
+                   (const double*)nullptr, (const float2*)nullptr, r, dom_of(m), m->T, m->loc.p,
+                   (unsigned long long*)nullptr, (float*)nullptr, (int*)nullptr, nullptr, (float*)nullptr, 0.0f);
     }
+    return FEM_OK;
+}
+
+// The weights of an IRLS step of the L1 data term from the vertex values uv
+// and the domain image f: w = 1 / max(|u - f|, eps) and w f at every image
+// pixel, in domain layout (w_dom, wf_dom: N^2 floats; other pixels are not
+// written and never read).
+fem_status raster_weights(fem_mesh* m, const double* uv, const float* f, float eps, float* w_dom, float* wf_dom,
+                          cudaStream_t s) {
+    FEM_TRY(raster_plan(m, s));
+    note_bytes(F_RASTER, 12.0 * (double)m->PI + 16.0 * m->T + 8.0 * m->V);
+    FEM_LAUNCH(F_RASTER, s, k_raster<R_WGT>, raster_grid(m), kRasterThreads, 0, m->tri.p, m->vxy.p, uv,
+               (const float2*)nullptr, f, dom_of(m), m->item_tri.p, m->item_off.p, m->dcount.p + 0,
+               (int)m->item_tri.n, item_pixels_for(m->P), m->partial.p, w_dom, (int*)nullptr,
+               (const int*)(m->dflag.p + 0), wf_dom, eps);
+    FEM_LAUNCH(F_RASTER, s, k_raster_small<R_WGT>, small_grid(m), 256, 0, m->order.p, m->tri.p, m->vxy.p, uv,
+               (const float2*)nullptr, f, dom_of(m), m->T, (double*)nullptr, (unsigned long long*)nullptr, w_dom,
+               (int*)nullptr, nullptr, wf_dom, eps);
     return FEM_OK;
 }
 
@@ -491,15 +543,16 @@ fem_status raster_errors_scratch(const int4* tri, const int2* vxy, int T, int N,
     FEM_LAUNCH(F_RASTER, s, k_item_count, blocks, 256, 0, tri, vxy, T, N, w.item_cnt, item_pixels_for((long long)N * N));
     FEM_TRY(exclusive_scan_i32_scratch(w.item_cnt, w.item_off, T, s, n_items_dev, w.scan_tmp, w.scan_tmp_n));
     FEM_LAUNCH(F_RASTER, s, k_item_expand, blocks, 256, 0, w.item_cnt, w.item_off, T, w.item_cap, w.item_tri, err);
-    FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, w.grid, kRasterThreads, 0, tri, vxy, uv, (const float2*)nullptr, f, N,
+    const Dom D{N, N, N};  // the allocation-free pass takes square images only
+    FEM_LAUNCH(F_RASTER, s, k_raster<R_ERR>, w.grid, kRasterThreads, 0, tri, vxy, uv, (const float2*)nullptr, f, D,
                w.item_tri, w.item_off, n_items_dev, w.item_cap, item_pixels_for((long long)N * N), w.partial, (float*)nullptr,
-               (int*)nullptr, (const int*)err);
+               (int*)nullptr, (const int*)err, (float*)nullptr, 0.0f);
     FEM_LAUNCH(F_RASTER, s, k_finalize_err, std::max(1, std::min(w.grid, (T + 7) / 8)), 256, 0, w.item_cnt,
                w.item_off, (const float2*)w.partial, T, tri, vxy, err_out, (unsigned long long*)nullptr, w.item_cap,
-               (const int*)err);
+               (const int*)err, D);
     FEM_LAUNCH(F_RASTER, s, k_raster_small<R_ERR>, std::max(1, std::min(blocks, w.grid / 2)), 256, 0, (const int*)nullptr,
-               tri, vxy, uv, (const float2*)nullptr, f, N, T, err_out, (unsigned long long*)nullptr, (float*)nullptr,
-               (int*)nullptr, nullptr);
+               tri, vxy, uv, (const float2*)nullptr, f, D, T, err_out, (unsigned long long*)nullptr, (float*)nullptr,
+               (int*)nullptr, nullptr, (float*)nullptr, 0.0f);
     return FEM_OK;
 }
 
@@ -516,7 +569,9 @@ fem_status fem_triangle_errors(fem_mesh* m, const double* uv_dev, const float* f
     }
     cudaStream_t s = (cudaStream_t)stream;
     m->last_stream = s;
-    FEM_TRY(sq_image(m, f_dev, s));
+    const float* fd = nullptr;
+    FEM_TRY(domain_image(m, f_dev, s, &fd));
+    FEM_TRY(sq_image(m, fd, s));
     FEM_TRY(raster_errors(m, uv_dev, nullptr, err_dev, s));
     int e = 0;
     FEM_CUDA(cudaMemcpyAsync(&e, m->dflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -667,7 +722,7 @@ __global__ void k_fast_classify(const int4* __restrict__ tri, const int2* __rest
         const int4 tr = tri[t];
         TriGeom g = tri_geom(tr, vxy, G.N);
         const double l = (double)lo[t], h = (double)hi[t];
-        if (!tri_eligible(g)) {
+        if (!tri_eligible(g, sq_dom(G))) {
             keys[t] = l;
             keyc[t] = 0ull;
         } else if (l > tau[1]) {
@@ -767,7 +822,9 @@ extern "C" fem_status fem_triangle_error_bounds(fem_mesh* m, const double* uv_de
     }
     cudaStream_t s = (cudaStream_t)stream;
     m->last_stream = s;
-    FEM_TRY(sq_image(m, f_dev, s));
+    const float* fd = nullptr;
+    FEM_TRY(domain_image(m, f_dev, s, &fd));
+    FEM_TRY(sq_image(m, fd, s));
     FEM_TRY(ensure(m->fast_hist, (size_t)2 * kFastBins + 8, s));
     FEM_TRY(ensure(m->keys_lo, (size_t)m->T, s));
     FEM_TRY(ensure(m->keys_hi, (size_t)m->T, s));

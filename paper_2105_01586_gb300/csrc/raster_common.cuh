@@ -42,15 +42,22 @@ __device__ __forceinline__ void edge_x(int px, int py, int qx, int qy, int y, in
     R = max(R, x);
 }
 
-// owned columns of row y: [L, L + len)
-__device__ __forceinline__ void row_span(const TriGeom& g, int y, int N, int& L, int& len) {
+// the part of a row's span [L, L + len) inside the image (nothing below it)
+__device__ __forceinline__ void clip_span(int y, const Dom& D, int L, int& len) {
+    const int e = min(L + len, D.W);
+    len = (y < D.H && e > L) ? e - L : 0;
+}
+
+// owned columns of row y: [L, L + len), within the image
+__device__ __forceinline__ void row_span(const TriGeom& g, int y, const Dom& D, int& L, int& len) {
     int l = INT_MAX, r = INT_MIN;
     edge_x(g.ax, g.ay, g.bx, g.by, y, l, r);
     edge_x(g.bx, g.by, g.cx, g.cy, y, l, r);
     edge_x(g.cx, g.cy, g.ax, g.ay, y, l, r);
-    int n = r - l + ((r == N - 1 && l < r) ? 1 : 0);
+    int n = r - l + ((r == D.N - 1 && l < r) ? 1 : 0);
     L = l;
     len = n > 0 ? n : 0;
+    clip_span(y, D, L, len);
 }
 
 // Row spans in closed form.  Every edge of the mesh's triangles is
@@ -78,14 +85,15 @@ __device__ __forceinline__ RowGeo row_geo(const TriGeom& g) {
     return r;
 }
 
-__device__ __forceinline__ void row_span_geo(const RowGeo& r, int y, int N, int& L, int& len) {
+__device__ __forceinline__ void row_span_geo(const RowGeo& r, int y, const Dom& D, int& L, int& len) {
     const int s02 = (r.sl & 3) - 1, s01 = ((r.sl >> 2) & 3) - 1, s12 = ((r.sl >> 4) & 3) - 1;
     const int xl = r.x0 + (y - r.y0) * s02;
     const int xs = y < r.y1 ? r.x0 + (y - r.y0) * s01 : r.x1 + (y - r.y1) * s12;
     const int l = min(xl, xs), rr = max(xl, xs);
-    const int n = rr - l + ((rr == N - 1 && l < rr) ? 1 : 0);
+    const int n = rr - l + ((rr == D.N - 1 && l < rr) ? 1 : 0);
     L = l;
     len = n > 0 ? n : 0;
+    clip_span(y, D, L, len);
 }
 
 // Small triangles (bounding box at most kSmallSide pixels each way, at most
@@ -170,13 +178,19 @@ __device__ __forceinline__ void tri_plane(const TriGeom& g, int4 tr, const doubl
     }
 }
 
-__device__ __forceinline__ bool tri_eligible(const TriGeom& g) { return (((g.ax + g.bx) | (g.ay + g.by)) & 1) == 0; }
+// eligible for selection (dom_eligible)
+__device__ __forceinline__ bool tri_eligible(const TriGeom& g, const Dom& D) {
+    return dom_eligible(g.ax, g.ay, g.bx, g.by, g.cx, g.cy, D);
+}
 
 // Squares of the image for the square-tiled pass (raster_sq.cu): side s =
 // min(64, N - 1), Q x Q of them; node 2q + h is half h of square q.
 struct SqGeo {
     int N, s, Q;
+    int W, H;  // the image within the domain
 };
+
+__device__ __forceinline__ Dom sq_dom(const SqGeo& G) { return Dom{G.N, G.W, G.H}; }
 
 // node of the point with three times the coordinates (X3, Y3), a point
 // strictly inside a node (the centroid of a triangle below the node level):

@@ -104,6 +104,12 @@ __device__ __forceinline__ void sq_node_tri(int n, const SqGeo& G, int2& a, int2
     }
 }
 
+// columns (rows) of square J (I) that hold image pixels: s, one more for the
+// domain's last column (row), clipped to the image (0 outside it)
+__device__ __forceinline__ int sq_extent(int s, int J, int Q, int x0, int W) {
+    return max(0, min(s + (J == Q - 1 ? 1 : 0), W - x0));
+}
+
 // strictly inside the positively oriented triangle (a, b, c) (3x coordinates)
 __device__ __forceinline__ bool inside3(long long px, long long py, int2 a, int2 b, int2 c) {
     const long long ax = 3LL * a.x, ay = 3LL * a.y, bx = 3LL * b.x, by = 3LL * b.y, cx = 3LL * c.x, cy = 3LL * c.y;
@@ -293,8 +299,8 @@ __device__ __forceinline__ bool sq_want(const SqArgs& A, int t) {
 }
 
 // the selection key of an eligible triangle (flag bit over the FP64 key bits)
-__device__ __forceinline__ unsigned long long sq_keyc(const TriGeom& g, double key) {
-    return tri_eligible(g) ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
+__device__ __forceinline__ unsigned long long sq_keyc(const Dom& D, const TriGeom& g, double key) {
+    return tri_eligible(g, D) ? ((unsigned long long)__double_as_longlong(key) | (1ull << 63)) : 0ull;
 }
 
 // FAST: interval and histogram of triangle t from its sum S and pixel
@@ -306,14 +312,14 @@ __device__ __forceinline__ void sq_finish(const SqArgs& A, int t, const TriGeom&
         fast_interval(S, (float)n, fast_M(g, P.ucf, P.gxf, P.gyf), kSqChain, lo, hi);
         A.F.lo[t] = lo;
         A.F.hi[t] = hi;
-        if (tri_eligible(g)) {
+        if (tri_eligible(g, sq_dom(A.G))) {
             atomicAdd(A.F.hlo + fast_bin(lo), 1u);
             atomicAdd(A.F.hhi + fast_bin(hi), 1u);
         }
     } else {
         const double key = ff_to_double(S);
         A.keys[t] = key;
-        if (A.keyc) A.keyc[t] = sq_keyc(g, key);
+        if (A.keyc) A.keyc[t] = sq_keyc(sq_dom(A.G), g, key);
     }
 }
 
@@ -321,11 +327,11 @@ __device__ __forceinline__ void sq_finish(const SqArgs& A, int t, const TriGeom&
 // along a row u is advanced by the exact float-float g_x.
 __device__ __forceinline__ void sq_small(const SqArgs& A, const float* img, int x0, int y0, int pitch, int t,
                                          const TriGeom& g, const SqPlane& P) {
-    const int N = A.G.N;
+    const Dom D = sq_dom(A.G);
     ff acc{0.f, 0.f};
     for (int y = g.ytop; y <= g.yend; ++y) {
         int L, len;
-        row_span(g, y, N, L, len);
+        row_span(g, y, D, L, len);
         if (len <= 0) continue;
         const float* rowp = img + (y - y0) * pitch + (L - x0);
         ff u = ff_add(ff_add(P.uc, ff_mul_f(P.gx, (float)(L - g.cx))), ff_mul_f(P.gy, (float)(y - g.cy)));
@@ -338,7 +344,7 @@ __device__ __forceinline__ void sq_small(const SqArgs& A, const float* img, int 
     }
     const double key = ff_to_double(acc);
     A.keys[t] = key;
-    if (A.keyc) A.keyc[t] = sq_keyc(g, key);
+    if (A.keyc) A.keyc[t] = sq_keyc(sq_dom(A.G), g, key);
 }
 
 // The warp's sum of the lanes' sums: FAST adds the FP32 sums by a butterfly
@@ -353,12 +359,13 @@ __device__ __forceinline__ ff sq_warp_total(float accf, ff acc) {
 // Row spans of region g for a sweep of up to 33 rows from row y (the first
 // row of the sweep): lane r holds the span of row y + r, lane 0 also of row
 // y + 32; rows outside the region's rows get an empty span.
-__device__ __forceinline__ void sq_spans(const TriGeom& g, int y, int R, int N, int& La, int& na, int& Lb, int& nb) {
+__device__ __forceinline__ void sq_spans(const TriGeom& g, int y, int R, const Dom& D, int& La, int& na, int& Lb,
+                                         int& nb) {
     const int lane = threadIdx.x & 31;
     La = 0; na = 0; Lb = 0; nb = 0;
     const int ya = y + lane, yb = y + 32;
-    if (lane < R && ya >= g.ytop && ya <= g.yend) row_span(g, ya, N, La, na);
-    if (lane == 0 && R > 32 && yb >= g.ytop && yb <= g.yend) row_span(g, yb, N, Lb, nb);
+    if (lane < R && ya >= g.ytop && ya <= g.yend) row_span(g, ya, D, La, na);
+    if (lane == 0 && R > 32 && yb >= g.ytop && yb <= g.yend) row_span(g, yb, D, Lb, nb);
 }
 
 // A pixel's contribution: FAST adds d^2 to an FP32 sum, EXACT to a float-float
@@ -382,11 +389,12 @@ __device__ __forceinline__ void sq_px(const SqPlane& P, float fx, float urowf, c
 template <int MODE>
 __device__ __forceinline__ void sq_sweep2(const TriGeom& g0, bool want0, const SqPlane& P0, int cx0, int cy0,
                                           bool want1, const SqPlane& P1, int cx1, int cy1, const float* img, int x0,
-                                          int y0, int w, int h, int pitch, int N, ff& S0, ff& S1, long long& n0) {
+                                          int y0, int w, int h, int pitch, const Dom& D, ff& S0, ff& S1,
+                                          long long& n0) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     int La, na, Lb, nb;
-    sq_spans(g0, y0, h, N, La, na, Lb, nb);
+    sq_spans(g0, y0, h, D, La, na, Lb, nb);
     n0 = (long long)warp_sum(na) + __shfl_sync(FULL, nb, 0);
     const bool two = lane + 32 < w, one = lane < w;
     const int xa = x0 + lane, xb = xa + 32;
@@ -432,12 +440,12 @@ __device__ __forceinline__ void sq_sweep2(const TriGeom& g0, bool want0, const S
 // row's span.  Returns the warp's sum (every lane) and the pixel count.
 template <int MODE>
 __device__ __forceinline__ ff sq_bbox(const TriGeom& g, const SqPlane& P, const float* img, int x0, int y0, int pitch,
-                                      int N, long long& npix) {
+                                      const Dom& D, long long& npix) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int R = g.yend - g.ytop + 1;
     int La, na, Lb, nb;
-    sq_spans(g, g.ytop, R, N, La, na, Lb, nb);
+    sq_spans(g, g.ytop, R, D, La, na, Lb, nb);
     npix = (long long)warp_sum(na) + __shfl_sync(FULL, nb, 0);
     const int xmin = min(g.ax, min(g.bx, g.cx));
     const bool two = lane + 32 < g.maxw, one = lane < g.maxw;
@@ -538,13 +546,18 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
 // Issue the copy of square q into buffer `img` (one lane).  A bulk copy
 // needs a size that is a multiple of 16 bytes: 4 s (s + 1) is for s >= 4;
 // smaller images are loaded by the warp when the square is processed.
+// A square with no image pixel (only where the image is smaller than the
+// domain) is not copied: its arrival expects no bytes, so the phase
+// completes at once, and its clamped extents read none of its pixels.
 __device__ __forceinline__ void sq_issue(const SqArgs& A, int q, float* img, unsigned long long* bar,
                                          unsigned long long policy) {
     const int s = A.G.s;
-    const unsigned bytes = (unsigned)(4 * s * (s + 1));
+    const int I = q / A.G.Q, J = q - I * A.G.Q;
+    const bool outside = J * s >= A.G.W || I * s >= A.G.H;
+    const unsigned bytes = outside ? 0u : (unsigned)(4 * s * (s + 1));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, bytes);
-    bulk_copy(img, A.fsq + (long long)q * s * (s + 1), bytes, bar, policy);
+    if (!outside) bulk_copy(img, A.fsq + (long long)q * s * (s + 1), bytes, bar, policy);
 }
 
 // The records of the triangles for the FP32 pass, one thread per curve
@@ -598,7 +611,7 @@ __device__ __forceinline__ void sq_fine_finish(const SqArgs& A, bool have, const
         fast_interval(ff{sum, 0.f}, (float)n, fast_M(g, R.ucf, R.gxf, R.gyf), kSqChain, lo, hi);
         A.F.lo[R.t] = lo;
         A.F.hi[R.t] = hi;
-        if (tri_eligible(g)) {
+        if (tri_eligible(g, sq_dom(A.G))) {
             blo = fast_bin(lo);
             bhi = fast_bin(hi);
         }
@@ -631,6 +644,7 @@ __device__ __forceinline__ void sq_fine_rows(const SqArgs& A, const float* img, 
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int N = A.G.N;
+    const Dom D = sq_dom(A.G);
     const int nf = len0 + len1;
     for (int e0 = 0; e0 < nf; e0 += 32) {
         const int e = e0 + lane;
@@ -652,7 +666,7 @@ __device__ __forceinline__ void sq_fine_rows(const SqArgs& A, const float* img, 
                 const RowGeo rg = row_geo(g);
                 for (int y = g.ytop; y <= g.yend; ++y) {
                     int L, len;
-                    row_span_geo(rg, y, N, L, len);
+                    row_span_geo(rg, y, D, L, len);
                     if (len <= 0) continue;
                     const float* rowp = img + (y - y0) * pitch + (L - x0);
                     const float urow = fmaf(R.gyf, (float)(y - g.cy), fmaf(R.gxf, (float)(L - g.cx), R.ucf));
@@ -703,7 +717,7 @@ __device__ __forceinline__ void sq_fine_rows(const SqArgs& A, const float* img, 
             if (valid) {
                 const int y = rk.y0 + (j - Hk);
                 int L, len;
-                row_span_geo(rk, y, N, L, len);
+                row_span_geo(rk, y, D, L, len);
                 if (len > 0) {
                     const float* rowp = img + (y - y0) * pitch + (L - x0);
                     const float urow = fmaf(gyf, (float)(y - cky), fmaf(gxf, (float)(L - ckx), ucf));
@@ -824,7 +838,7 @@ __global__ void __launch_bounds__(kSqThreads) k_sq(SqArgs A) {
                 SqPlane P;
                 int cx, cy;
                 sq_plane_at<MODE>(A, c0, t, P, cx, cy);
-                const int w = s + (J == Q - 1 ? 1 : 0), h = s + (I == Q - 1 ? 1 : 0);
+                const int w = sq_extent(s, J, Q, x0, G.W), h = sq_extent(s, I, Q, y0, G.H);
                 const ff S = sq_full<MODE>(P, cx, cy, img, x0, y0, w, h, pitch);
                 if (lane == 0) {
                     const int s0 = A.nslot[n0], s1 = A.nslot[n0 + 1];
@@ -845,11 +859,11 @@ __global__ void __launch_bounds__(kSqThreads) k_sq(SqArgs A) {
                 if (want1) sq_plane_at<MODE>(A, c1, t1, P1, cx1, cy1);
                 int2 na, nb, nc;
                 sq_node_tri(n0, G, na, nb, nc);
-                const int w = s + (J == Q - 1 ? 1 : 0), h = s + (I == Q - 1 ? 1 : 0);
+                const int w = sq_extent(s, J, Q, x0, G.W), h = sq_extent(s, I, Q, y0, G.H);
                 ff S0, S1;
                 long long np0 = 0;
                 sq_sweep2<MODE>(geom_xy(na, nb, nc, N), want0, P0, cx0, cy0, want1, P1, cx1, cy1, img, x0, y0, w, h,
-                                pitch, N, S0, S1, np0);
+                                pitch, sq_dom(G), S0, S1, np0);
                 if (lane == 0) {
                     const int s0 = A.nslot[n0], s1 = A.nslot[n0 + 1];
                     if (want0 && s0 >= 0 && s0 < A.part_cap)
@@ -893,7 +907,7 @@ __global__ void __launch_bounds__(kSqThreads) k_sq(SqArgs A) {
                 const TriGeom g = tri_geom(tr, A.vxy, N);
                 const SqPlane P = sq_plane(g, tr, A.uv, A.uvf);
                 long long np = 0;
-                const ff S = sq_bbox<MODE>(g, P, img, x0, y0, pitch, N, np);
+                const ff S = sq_bbox<MODE>(g, P, img, x0, y0, pitch, sq_dom(G), np);
                 if (lane == 0) sq_finish<MODE>(A, t, g, P, S, np);
             }
         }
@@ -1066,6 +1080,8 @@ SqGeo sq_geo(const fem_mesh* m) {
     G.N = m->N;
     G.s = sq_side(m->N);
     G.Q = (m->N - 1) / G.s;
+    G.W = m->W;
+    G.H = m->H;
     return G;
 }
 
@@ -1172,7 +1188,7 @@ static SqArgs sq_args(fem_mesh* m, const double* uv, const float2* uvf) {
 // the triangles (16 B) and their keys or intervals out (8 or 16 B), vertex
 // positions and values (8 + 8 B)
 static double sq_bytes(const fem_mesh* m, bool fast) {
-    return 4.0 * (double)m->P + (fast ? 32.0 : 24.0) * m->T + 16.0 * m->V;
+    return 4.0 * (double)m->PI + (fast ? 32.0 : 24.0) * m->T + 16.0 * m->V;
 }
 
 fem_status sq_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, FastOut F, cudaStream_t s) {

@@ -50,12 +50,13 @@ struct TopkArgs {
     unsigned long long* out_thr;    // [0] hi, [1] lo of the k-th composite key
     double* red;
     double* out_margin;
+    Dom D;  // the image within the domain (eligibility)
 };
 
 __device__ __forceinline__ unsigned long long comp_hi(const TopkArgs& A, int t) {
     int4 tr = A.tri[t];
-    int2 a = A.vxy[tr.x], b = A.vxy[tr.y];
-    if (!lattice_mid(a, b)) return 0ull;
+    int2 a = A.vxy[tr.x], b = A.vxy[tr.y], c = A.vxy[tr.z];
+    if (!dom_eligible(a.x, a.y, b.x, b.y, c.x, c.y, A.D)) return 0ull;
     return (unsigned long long)__double_as_longlong(A.keys[t]) | (1ull << 63);
 }
 
@@ -548,14 +549,15 @@ __global__ void __launch_bounds__(kTopkBlockThreads) k_topk_block(const unsigned
 
 // mark the refinement edges of the selected triangles in bmM and bmS
 __global__ void k_mark_selected(const double* __restrict__ keys, const int4* __restrict__ tri,
-                                const int2* __restrict__ vxy, int T, int N, const unsigned long long* __restrict__ thr,
+                                const int2* __restrict__ vxy, int T, Dom D, const unsigned long long* __restrict__ thr,
                                 const int* __restrict__ kdev, unsigned* __restrict__ bmM, unsigned* __restrict__ bmS) {
     pdl_wait();
+    const int N = D.N;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T || *kdev == 0) return;
     int4 tr = tri[t];
-    int2 a = vxy[tr.x], b = vxy[tr.y];
-    if (!lattice_mid(a, b)) return;
+    int2 a = vxy[tr.x], b = vxy[tr.y], c = vxy[tr.z];
+    if (!dom_eligible(a.x, a.y, b.x, b.y, c.x, c.y, D)) return;
     unsigned long long hi = (unsigned long long)__double_as_longlong(keys[t]) | (1ull << 63);
     unsigned lo = ~(unsigned)t;
     unsigned long long th = thr[0];
@@ -631,22 +633,26 @@ struct NewVertexOut {
     const unsigned* bmS;
     int* wpre;
     int N, V0;
+    int W, H;  // the image: every vertex outside it is a mask vertex
     int2* vxy;
     unsigned char* mask;
     int* n_new_mask;
     __device__ __forceinline__ void operator()(long long w, int pre, int) const {
         wpre[w] = pre;
         unsigned bits = bmM[w], sbits = bmS[w];
-        if (sbits & bits) atomicAdd(n_new_mask, __popc(sbits & bits));
-        int id = V0 + pre;
+        int id = V0 + pre, nm = 0;
         while (bits) {
             int b = __ffs(bits) - 1;
             bits &= bits - 1u;
             long long p = w * 32 + b;
-            vxy[id] = make_int2((int)(p % N), (int)(p / N));
-            mask[id] = (unsigned char)((sbits >> b) & 1u);
+            const int x = (int)(p % N), y = (int)(p / N);
+            vxy[id] = make_int2(x, y);
+            const int mk = (int)((sbits >> b) & 1u) | (x >= W || y >= H);
+            mask[id] = (unsigned char)mk;
+            nm += mk;
             id++;
         }
+        if (nm) atomicAdd(n_new_mask, nm);
     }
 };
 
@@ -885,6 +891,7 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
     A.out_thr = thr;
     A.red = m->red.p;
     A.out_margin = margin;
+    A.D = dom_of(m);
     // set once per process (thread-safe static initialisation); a failure shows at the launch
     static const bool attr_set = [] {
         return cudaFuncSetAttribute(k_topk_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -909,7 +916,8 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
         FEM_TRY(launch_coop(F_TOPK, (const void*)k_topk, grid, kTopkThreads, 0, s, args, "k_topk"));
     }
     int tb = (T + 255) / 256;
-    FEM_LAUNCH(F_REFINE, s, k_mark_selected, tb, 256, 0, m->keys.p, m->tri.p, m->vxy.p, T, N, thr, kdev, bmM, bmS);
+    FEM_LAUNCH(F_REFINE, s, k_mark_selected, tb, 256, 0, m->keys.p, m->tri.p, m->vxy.p, T, dom_of(m), thr, kdev, bmM,
+               bmS);
     {
         int max_sweeps = 48;
         void* args[] = {(void*)&m->tri.p, (void*)&m->vxy.p, (void*)&T, (void*)&N, (void*)&bmM,
@@ -920,7 +928,7 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
     int Wi = (int)W;
     int* stage_dev = m->host_stage_dev ? (int*)m->host_stage_dev + kRoundStageInts : nullptr;
     FEM_TRY(scan_fused(m, WordIn{bmM, bmM_other, bmS_other},
-                       NewVertexOut{bmM, bmS, (int*)m->wpre.p, N, V, m->vxy.p, m->mask.p, nmask_new}, Wi, s, nnew,
+                       NewVertexOut{bmM, bmS, (int*)m->wpre.p, N, V, m->W, m->H, m->vxy.p, m->mask.p, nmask_new}, Wi, s, nnew,
                        F_REFINE));
     m->bm_parity ^= 1;
     FEM_TRY(scan_fused(m, BisectFlagIn{m->tri.p, m->vxy.p, bmM, T, N, m->flags.p}, ScanStore{m->fscan.p}, 3 * T, s,
@@ -1007,54 +1015,131 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
 
 using namespace fem;
 
-extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double density, const fem_params* p,
-                                         void* stream) {
-    Nvtx range("fem_spatial_refine");
-    if (!m || !f_dev || !(density > 0.0) || density > 1.0) {
-        set_error("fem_spatial_refine: null argument or density outside (0, 1]");
-        return FEM_E_INVALID;
-    }
-    fem_params d;
-    fem_params_default(&d);
-    if (!p) p = &d;
-    cudaStream_t s = (cudaStream_t)stream;
+// keys summed over the channels -> composite selection keys (eligible
+// triangles: the FP64 key bits under the top bit; the others 0)
+__global__ void k_add_keys(int T, const double* __restrict__ add, double* __restrict__ keys) {
+    pdl_wait();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T) keys[t] += add[t];
+}
+
+__global__ void k_keyc_from_keys(int T, const int4* __restrict__ tri, const int2* __restrict__ vxy, Dom D,
+                                 const double* __restrict__ keys, unsigned long long* __restrict__ keyc) {
+    pdl_wait();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const int4 tr = tri[t];
+    const int2 a = vxy[tr.x], b = vxy[tr.y], c = vxy[tr.z];
+    keyc[t] = dom_eligible(a.x, a.y, b.x, b.y, c.x, c.y, D)
+                  ? ((unsigned long long)__double_as_longlong(keys[t]) | (1ull << 63))
+                  : 0ull;
+}
+
+// Channel c >= 1 of a colour image in the mesh's working arrays: its vertex
+// values (with their float-float copies), its squared image and its padded
+// image are swapped with channel 0's, so that the solver and the error pass
+// run on it unchanged; a second call swaps them back.
+static void swap_channel(fem_mesh* m, int c) {
+    std::swap(m->uv, m->uvc[c - 1]);
+    std::swap(m->uvf, m->uvfc[c - 1]);
+    std::swap(m->fsq, m->fsqc[c - 1]);
+    std::swap(m->fedge, m->fedgec[c - 1]);
+    std::swap(m->fpad, m->fpadc[c - 1]);
+}
+
+// The spatial optimisation of Sec. 3 (adapted) on C channels of W x H
+// images (plane c of f at c W H).  C = 1 is the grey case; with more
+// channels (reading R10) each channel has its own mask values and Laplace
+// solve, and a triangle's error is the sum of its channels' exact errors.
+static fem_status spatial_refine(fem_mesh* m, const float* f_dev, int C, double density, const fem_params* p,
+                                 cudaStream_t s) {
     m->last_stream = s;
     m->stats = fem_stats{};
     m->stats.min_margin = INFINITY;
-    long long vstar = (long long)ceil(density * (double)m->P);
+    long long vstar = (long long)ceil(density * (double)m->PI);  // vertices per image pixel
     int round = 0;
     // solve results are accumulated on the device and read once at the end
     FEM_TRY(solve_totals_reset(m, s));
     FEM_CUDA(cudaMemsetAsync(m->dflag.p + 8, 0, sizeof(int), s));  // scan wait flag
-    // mask vertices take their image values once; vertices made by the
-    // refinement get theirs when they are created (k_bisect)
-    FEM_TRY(set_uv_from_f(m, f_dev, s));
-    // the error passes read the image as squares, laid out once per call
-    FEM_TRY(sq_image(m, f_dev, s));
+    // a W x H image is padded to the domain (the values of mask vertices
+    // outside it); only its own pixels are data.  The error passes read each
+    // channel's image as squares, laid out once per call.
+    const float* fc[kMaxChannels] = {};
+    int valid[kMaxChannels] = {};  // vertices with a value, per extra channel
+    for (int c = C - 1; c >= 0; --c) {
+        if (c > 0) swap_channel(m, c);
+        FEM_TRY(domain_image(m, f_dev + (size_t)c * m->PI, s, &fc[c]));
+        FEM_TRY(sq_image(m, fc[c], s));
+        if (c > 0) {
+            FEM_TRY(ensure(m->uv, (size_t)m->V, s));
+            FEM_TRY(ensure(m->uvf, (size_t)m->V, s));
+            FEM_CUDA(cudaMemsetAsync(m->uv.p, 0, sizeof(double) * m->V, s));
+            FEM_CUDA(cudaMemsetAsync(m->uvf.p, 0, sizeof(float2) * m->V, s));
+            valid[c] = m->V;
+            swap_channel(m, c);
+        }
+    }
+    // channel 0's mask vertices take their image values once; vertices made
+    // by the refinement get theirs when they are created (k_bisect)
+    FEM_TRY(set_uv_from_f(m, fc[0], s));
+    const bool fp64 = p->precision == FEM_PREC_FP64;
     while ((long long)m->V < vstar && (p->max_rounds <= 0 || round < p->max_rounds)) {
         Nvtx round_range("spatial round");
         FEM_TRY(check_cancel(m));
         // solve_laplace builds the system of the refined mesh (with its
         // right-hand side in the same kernel)
-        fem_status st = solve_laplace(m, p->precision == FEM_PREC_FP64, p->tol, p->maxit, s, nullptr, nullptr, true);
+        fem_status st = solve_laplace(m, fp64, p->tol, p->maxit, s, nullptr, nullptr, true);
         if (st != FEM_OK) return st;
         FEM_TRY(ensure(m->keys, (size_t)m->T, s));
         FEM_TRY(ensure(m->keyc, (size_t)m->T, s));
         // in the spatial loop every vertex value was just written together with
-        // its float-float copy (mask vertices from f, unknowns by the solve)
-        bool band = p->fast_keys > 0 || (p->fast_keys < 0 && m->P >= 2049LL * 2049);
+        // its float-float copy (mask vertices from f, unknowns by the solve);
+        // the fast keys serve one channel
+        bool band = C == 1 && (p->fast_keys > 0 || (p->fast_keys < 0 && m->PI >= 2049LL * 2049));
         {
             Nvtx pass_range("error pass");
             if (band)
                 FEM_TRY(raster_keys_fast(m, m->uv.p, m->uvf.p, p->topk_frac, vstar - m->V, s));
             else
-                FEM_TRY(raster_errors(m, m->uv.p, m->uvf.p, m->keys.p, s, m->keyc.p));
+                FEM_TRY(raster_errors(m, m->uv.p, m->uvf.p, m->keys.p, s, C == 1 ? m->keyc.p : nullptr));
+        }
+        if (C > 1) {
+            Nvtx ch_range("other channels");
+            FEM_TRY(ensure(m->keys_acc, (size_t)m->T, s));
+            const int tb = (m->T + 255) / 256;
+            for (int c = 1; c < C; ++c) {
+                swap_channel(m, c);
+                fem_status cs = FEM_OK;
+                do {
+                    // vertices made since the channel's last solve start at 0
+                    // (the solve warm-starts from the others)
+                    cs = ensure(m->uv, (size_t)m->V, s, (size_t)valid[c]);
+                    if (cs) break;
+                    cs = ensure(m->uvf, (size_t)m->V, s, (size_t)valid[c]);
+                    if (cs) break;
+                    if (m->V > valid[c]) {
+                        cudaMemsetAsync(m->uv.p + valid[c], 0, sizeof(double) * (m->V - valid[c]), s);
+                        cudaMemsetAsync(m->uvf.p + valid[c], 0, sizeof(float2) * (m->V - valid[c]), s);
+                        valid[c] = m->V;
+                    }
+                    cs = set_uv_from_f(m, fc[c], s);
+                    if (cs) break;
+                    cs = solve_laplace(m, fp64, p->tol, p->maxit, s, nullptr, nullptr, true);
+                    if (cs) break;
+                    cs = raster_errors(m, m->uv.p, m->uvf.p, m->keys_acc.p, s, nullptr);
+                } while (0);
+                swap_channel(m, c);
+                FEM_TRY(cs);
+                FEM_LAUNCH(F_RASTER, s, k_add_keys, tb, 256, 0, m->T, (const double*)m->keys_acc.p, m->keys.p);
+            }
+            FEM_LAUNCH(F_RASTER, s, k_keyc_from_keys, tb, 256, 0, m->T, m->tri.p, m->vxy.p, dom_of(m),
+                       (const double*)m->keys.p, m->keyc.p);
         }
         double margin = 0.0;
         int k = 0;
         {
             Nvtx refine_range("top-k and refinement");
-            FEM_TRY(refine_round(m, f_dev, p->topk_frac, vstar, s, &margin, &k, band));
+            FEM_TRY(refine_round(m, fc[0], p->topk_frac, vstar, s, &margin, &k, band));
         }
         if (k == 0) break;
         if (margin < m->stats.min_margin) m->stats.min_margin = margin;
@@ -1064,4 +1149,28 @@ extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double
     fem_status st = solve_totals_read(m, s);
     m->stats.rounds = round;
     return st;
+}
+
+extern "C" fem_status fem_spatial_refine(fem_mesh* m, const float* f_dev, double density, const fem_params* p,
+                                         void* stream) {
+    Nvtx range("fem_spatial_refine");
+    if (!m || !f_dev || !(density > 0.0) || density > 1.0) {
+        set_error("fem_spatial_refine: null argument or density outside (0, 1]");
+        return FEM_E_INVALID;
+    }
+    fem_params d;
+    fem_params_default(&d);
+    return spatial_refine(m, f_dev, 1, density, p ? p : &d, (cudaStream_t)stream);
+}
+
+extern "C" fem_status fem_spatial_refine_channels(fem_mesh* m, const float* f_dev, int channels, double density,
+                                                  const fem_params* p, void* stream) {
+    Nvtx range("fem_spatial_refine_channels");
+    if (!m || !f_dev || !(density > 0.0) || density > 1.0 || channels < 1 || channels > kMaxChannels) {
+        set_error("fem_spatial_refine_channels: null argument, density outside (0, 1] or channels outside 1..4");
+        return FEM_E_INVALID;
+    }
+    fem_params d;
+    fem_params_default(&d);
+    return spatial_refine(m, f_dev, channels, density, p ? p : &d, (cudaStream_t)stream);
 }

@@ -1164,6 +1164,7 @@ extern "C" fem_status fem_gather_mask(fem_mesh* m, const float* f_dev, float* g_
     cudaStream_t s = (cudaStream_t)stream;
     m->last_stream = s;
     FEM_TRY(build_system(m, s));
+    FEM_TRY(domain_image(m, f_dev, s, &f_dev));
     if (m->nK > 0)
         FEM_LAUNCH(F_OTHER, s, k_gather_mask, (m->nK + 255) / 256, 256, 0, m->kvert.p, m->vxy.p, m->nK, m->N, f_dev,
                    g_dev);

@@ -471,19 +471,15 @@ static fem_status scatter_PT(fem_mesh* m, const float* r, cudaStream_t s) {
 
 using namespace fem;
 
-extern "C" fem_status fem_tonal_opt(fem_mesh* m, const float* f_dev, float* g_dev, const fem_params* p, void* stream) {
-    Nvtx range("fem_tonal_opt");
-    if (!m || !f_dev || !g_dev) {
-        set_error("fem_tonal_opt: null argument");
-        return FEM_E_INVALID;
-    }
-    fem_params dflt;
-    fem_params_default(&dflt);
-    if (!p) p = &dflt;
-    cudaStream_t s = (cudaStream_t)stream;
-    m->last_stream = s;
+// The tonal optimisation's CG (below) on the least-squares problem
+// min_g |B g - f|^2, or with `weighted` the weighted one
+// min_g sum_p w_p ((B g)_p - f_p)^2: then the caller has put P^T W P into the
+// pixel-mass matrix (prepare_weighted) and passes rhs = W f.  rhs is a
+// domain image.  g_dev holds the start and receives the result.
+static fem_status tonal_cg(fem_mesh* m, const float* rhs, float* g_dev, const fem_params* p, cudaStream_t s,
+                           bool weighted) {
     m->stats = fem_stats{};
-    FEM_TRY(prepare_tonal(m, s));
+    if (!weighted) FEM_TRY(prepare_tonal(m, s));
     FEM_TRY(ensure_tonal_vectors(m, s));
     int nK = m->nK;
     // inner solves keep their statistics on the device (read once at the end)
@@ -498,7 +494,7 @@ extern "C" fem_status fem_tonal_opt(fem_mesh* m, const float* f_dev, float* g_de
     // adjoint solve.  Updating s itself (s -= a B^T B p) would lose accuracy
     // with the square of B's condition number.
     // c = B^T f = E^T P^T f, and y = P^T f - M E g for the start g
-    FEM_TRY(scatter_PT(m, f_dev, s));
+    FEM_TRY(scatter_PT(m, rhs, s));
     FEM_CUDA(cudaMemcpyAsync(m->tyr.p, m->ty.p, sizeof(double) * m->V, cudaMemcpyDeviceToDevice, s));
     FEM_TRY(apply_ET(m, m->ty.p, m->tc.p, c, s));
     FEM_TRY(vec_op(m, 0, nK, 0.0, m->tc.p, m->tc.p, nullptr, nullptr, sc + 0, s));
@@ -589,6 +585,67 @@ extern "C" fem_status fem_tonal_opt(fem_mesh* m, const float* f_dev, float* g_de
     return st;
 }
 
+extern "C" fem_status fem_tonal_opt(fem_mesh* m, const float* f_dev, float* g_dev, const fem_params* p, void* stream) {
+    Nvtx range("fem_tonal_opt");
+    if (!m || !f_dev || !g_dev) {
+        set_error("fem_tonal_opt: null argument");
+        return FEM_E_INVALID;
+    }
+    fem_params dflt;
+    fem_params_default(&dflt);
+    if (!p) p = &dflt;
+    cudaStream_t s = (cudaStream_t)stream;
+    m->last_stream = s;
+    FEM_TRY(domain_image(m, f_dev, s, &f_dev));
+    return tonal_cg(m, f_dev, g_dev, p, s, false);
+}
+
+// P^T W P from the pixel weights w (domain layout) into the pixel-mass
+// matrix; the unweighted one is rebuilt by the next unweighted call.
+static fem_status prepare_weighted(fem_mesh* m, const float* w, cudaStream_t s) {
+    FEM_TRY(prepare_tonal(m, s));  // system and incidence
+    FEM_TRY(raster_local(m, 4 /*R_WMASS*/, w, s));
+    FEM_LAUNCH(F_TONAL, s, k_gather_mass, (m->V + 255) / 256, 256, 0, m->V, m->inc.p, m->tri.p, m->vxy.p, m->loc.p,
+               m->Mdiag.p, m->Moff.p);
+    m->tonal_version = -1;
+    return FEM_OK;
+}
+
+extern "C" fem_status fem_tonal_opt_l1(fem_mesh* m, const float* f_dev, float* g_dev, int irls, double eps,
+                                       const fem_params* p, void* stream) {
+    Nvtx range("fem_tonal_opt_l1");
+    if (!m || !f_dev || !g_dev || irls < 0 || !(eps > 0.0)) {
+        set_error("fem_tonal_opt_l1: null argument, irls < 0 or eps <= 0");
+        return FEM_E_INVALID;
+    }
+    fem_params dflt;
+    fem_params_default(&dflt);
+    if (!p) p = &dflt;
+    cudaStream_t s = (cudaStream_t)stream;
+    m->last_stream = s;
+    FEM_TRY(domain_image(m, f_dev, s, &f_dev));
+    FEM_TRY(build_system(m, s));
+    FEM_TRY(ensure(m->wimg, (size_t)m->P, s));
+    FEM_TRY(ensure(m->wfimg, (size_t)m->P, s));
+    const bool fp64 = p->precision == FEM_PREC_FP64;
+    int iters = 0;
+    fem_status st = FEM_OK;
+    for (int k = 0; k < irls; ++k) {
+        Nvtx step_range("IRLS step");
+        FEM_TRY(check_cancel(m));
+        // the weights from u = B g: g at the mask, the Laplace solve
+        FEM_TRY(set_uv_from_g(m, g_dev, s));
+        FEM_TRY(solve_laplace(m, fp64, p->tol, p->maxit, s, nullptr, nullptr));
+        FEM_TRY(raster_weights(m, m->uv.p, f_dev, (float)eps, m->wimg.p, m->wfimg.p, s));
+        FEM_TRY(prepare_weighted(m, m->wimg.p, s));
+        st = tonal_cg(m, m->wfimg.p, g_dev, p, s, true);
+        iters += m->stats.tonal_iters;
+        if (st != FEM_OK && st != FEM_E_NOT_CONVERGED) return st;
+    }
+    m->stats.tonal_iters = iters;
+    return st;
+}
+
 extern "C" fem_status fem_adjoint(fem_mesh* m, const float* r_dev, float* gbar_dev, const fem_params* p, void* stream) {
     Nvtx range("fem_adjoint");
     if (!m || !r_dev || !gbar_dev) {
@@ -604,6 +661,7 @@ extern "C" fem_status fem_adjoint(fem_mesh* m, const float* r_dev, float* gbar_d
     FEM_TRY(prepare_tonal(m, s));
     FEM_TRY(ensure_tonal_vectors(m, s));
     InnerCfg c{p->precision == FEM_PREC_FP64, p->inner_tol, p->maxit, false};
+    FEM_TRY(domain_image(m, r_dev, s, &r_dev));
     FEM_TRY(scatter_PT(m, r_dev, s));
     FEM_TRY(apply_ET(m, m->ty.p, m->tw.p, c, s));
     FEM_LAUNCH(F_TONAL, s, k_d2f, (m->nK + 255) / 256, 256, 0, m->nK, m->tw.p, gbar_dev);
@@ -632,6 +690,7 @@ extern "C" fem_status fem_tonal_loss(fem_mesh* m, const float* g_dev, const floa
     m->last_stream = s;
     m->stats = fem_stats{};
     const bool fp64 = p->precision == FEM_PREC_FP64;
+    FEM_TRY(domain_image(m, f_dev, s, &f_dev));
     // v = E g: g at the mask vertices, the Laplace solution at the unknown ones
     FEM_TRY(set_uv_from_g(m, g_dev, s));
     int it = 0;

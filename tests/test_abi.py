@@ -47,12 +47,14 @@ def test_defaults_and_host_checks(fem):
     assert fem._lib.fem_mesh_info(None, None, None, None) == fem.FEM_E_INVALID
     assert fem._lib.fem_inpaint(None, None, None, None, None, None) == fem.FEM_E_INVALID
     assert fem._lib.fem_spatial_refine(None, None, ctypes.c_double(0.1), None, None) == fem.FEM_E_INVALID
+    assert fem._lib.fem_spatial_refine_channels(None, None, 3, ctypes.c_double(0.1), None, None) == fem.FEM_E_INVALID
+    assert fem._lib.fem_mesh_size(None, None, None, None) == fem.FEM_E_INVALID
     assert fem._lib.fem_tonal_opt(None, None, None, None, None) == fem.FEM_E_INVALID
     assert fem._lib.fem_adjoint(None, None, None, None, None) == fem.FEM_E_INVALID
     assert fem._lib.fem_tonal_loss(None, None, None, None, None, None, None) == fem.FEM_E_INVALID
     assert b"null" in fem._lib.fem_last_error()
     h = ctypes.c_void_p()
-    for bad in ((256, 256), (257, 129), (2, 2), (0, 0)):
+    for bad in ((1, 5), (5, 1), (0, 0), (-3, 9), (40000, 3), (3, 40000)):  # sides must be 2..32769
         assert fem._lib.fem_mesh_create(bad[0], bad[1], None, ctypes.byref(h)) == fem.FEM_E_SHAPE
     assert fem.fem_launch_count() == 0
 

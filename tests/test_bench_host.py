@@ -20,13 +20,16 @@ def _bench(root=ROOT):
 
 def test_presets_name_their_workload():
     b = _bench()
-    for cfg in (1, 2, 3, 4):
+    for cfg in (1, 2, 3, 4, 6, 7):
         a = type("A", (), dict(b.PRESETS[cfg]))()
         a.config = cfg
         c = b.config(a, 1)
-        assert c["image"] == f"{a.n}x{a.n}" and c["l2_flush"] is True
+        hw = f"{a.n}x{getattr(a, 'h', a.n)}"
+        assert c["image"] == hw and c["l2_flush"] is True
         assert c["parallelism"] == "single"
-        assert f"{a.n}x{a.n}" in c["workload"]
+        assert hw in c["workload"]
+    a = type("A", (), dict(b.PRESETS[7]))()
+    assert b.image_hw(a) == (3264, 4896)
     a = type("A", (), dict(b.PRESETS[2]))()
     a.config = 2
     assert b.config(a, 4)["parallelism"] == "replicas4"

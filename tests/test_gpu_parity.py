@@ -264,8 +264,10 @@ def test_errors_are_reported(fem):
     with pytest.raises(fem.FemError) as e:
         m.import_(np.array([[0, 0], [32, 0], [0, 32]]), np.array([[0, 2, 1]]), np.ones(3))
     assert e.value.status == fem.FEM_E_INVALID
-    with pytest.raises(fem.FemError):
-        fem.Mesh(100)
+    for w, h in ((1, 5), (5, 1), (40000, 5)):  # image sides must be 2..32769
+        with pytest.raises(fem.FemError) as e:
+            fem.Mesh(w, h)
+        assert e.value.status == fem.FEM_E_SHAPE
 
 
 @pytest.mark.parametrize("prec", [0, 1])

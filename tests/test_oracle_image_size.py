@@ -15,7 +15,7 @@ import pytest
 
 import seeded_inputs as S
 
-SIZES = [(50, 37), (37, 50), (64, 64), (65, 40), (33, 65)]
+SIZES = [(50, 37), (37, 50), (64, 64), (65, 40), (33, 65), (100, 61), (61, 100)]
 
 
 def _image(W, H, seed):
@@ -69,12 +69,12 @@ def test_loop_invariants(oracle_mod, W, H):
     vstar = math.ceil(density * W * H)
     assert vstar == oracle_mod.vstar(W, density, H)
     assert m.V >= vstar and log[-1, 0] < vstar
-    # selected midpoints are image pixels: every mask vertex but the
-    # initial corners lies in the image
-    k = np.flatnonzero(m.mask)
-    inside = (m.vx[k] < W) & (m.vy[k] < H)
-    assert np.all(inside | (k < 4))
-    assert np.all(oracle_mod.eligible(m) <= ((m.vx[m.ta] + m.vx[m.tb]) // 2 < W))
+    # the padding holds no unknowns: every vertex outside the image is a mask vertex
+    assert np.all(m.mask[(m.vx >= W) | (m.vy >= H)] == 1)
+    # triangles whose bounding box misses the image are never eligible
+    xmin = np.minimum(np.minimum(m.vx[m.ta], m.vx[m.tb]), m.vx[m.tc])
+    ymin = np.minimum(np.minimum(m.vy[m.ta], m.vy[m.tb]), m.vy[m.tc])
+    assert not np.any(oracle_mod.eligible(m) & ((xmin >= W) | (ymin >= H)))
     # every image pixel has exactly one owner
     g = oracle_mod.g_from_f(m, f)
     v, _, _ = oracle_mod.solve(m, g)
@@ -152,3 +152,18 @@ def test_loop_equals_steps_on_an_image_of_any_size(oracle_mod, W, H):
     np.testing.assert_array_equal(m.tri, m_loop.tri)
     np.testing.assert_array_equal(m.xy, m_loop.xy)
     np.testing.assert_array_equal(m.mask, m_loop.mask)
+
+
+
+def test_images_less_than_half_the_domain_high_refine(oracle_mod):
+    """100 x 61 in the 129 x 129 domain: both initial triangles bisect at
+    (64, 64), below the image.  The selected midpoint becomes a mask vertex
+    with the nearest image pixel's value, and the loop goes on to the vertex
+    target."""
+    W, H = 100, 61
+    f = _image(W, H, 3)
+    m, log = oracle_mod.spatial(f, 0.1, 0.02)
+    assert m.V >= oracle_mod.vstar(W, 0.1, H) and len(log) > 10
+    first = oracle_mod.refine(oracle_mod.mesh_init(W, H), [0])[0]
+    assert first.V == 5 and first.mask[4] == 1 and (first.vx[4], first.vy[4]) == (64, 64)
+    np.testing.assert_array_equal(oracle_mod.g_from_f(first, f)[-1], f[60, 64])
