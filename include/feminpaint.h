@@ -177,8 +177,9 @@ FEM_API fem_status fem_triangle_errors(fem_mesh *m, const double *uv_dev, const 
  * output; the scratch it needs is a fixed 3.4 MB device array inside the
  * library, present on every GPU that loads the library until the process
  * exits.  The first call on a device looks up that array's address (once
- * per device, with the device current); make that first call before any
- * stream capture.  The array is shared by all calls and keeps the last
+ * per device, with the device current).  Every call synchronises `stream`
+ * (it reads the item count back), so no call can be captured into a CUDA
+ * graph.  The array is shared by all calls and keeps the last
  * call's contents (the call clears what must start at zero), so calls that
  * overlap on the GPU, on any stream, race: serialise them.
  *   width      image side, 2^L + 1, at most 2049
