@@ -455,6 +455,14 @@ def run_ours(a, world, rank, local):
                 "launches_in_region": prof["launches"], "ms_in_region": round(prof["ms"], 3),
                 "share_of_step": round(prof["ms"] / sum(prof_times), 4),
                 "family_ms_one_step": {k: round(v["ms"], 3) for k, v in prof_all.items()}}
+    # the three families with a byte model, from the one profiled step
+    fams = {}
+    for k in ("raster_pass", "cg", "assembly"):
+        v = prof_all[k]
+        gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else 0.0
+        fams[k] = {"ms": round(v["ms"], 3), "launches": v["launches"], "achieved": round(gbs, 2),
+                   "frac": round(gbs / peak, 4)}
+    roofline["families_one_step"] = fams
 
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,

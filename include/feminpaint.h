@@ -87,7 +87,11 @@ typedef struct {
     int fast_keys;      /* spatial: how the selection keys are computed (the selected set is
                            the same either way): 0 = float-float for every triangle; 1 = FP32
                            with a rigorous error bound for every triangle and float-float only
-                           for the triangles whose bound straddles the k-th key; -1 = 1 from
+                           for the triangles whose bound straddles the k-th key; after a
+                           call's first round the FP32 pass covers only the squares that
+                           hold a triangle the last round bisected or whose vertex values
+                           changed (the other bounds are kept: a full pass gives the same
+                           bits); 2 = as 1 with a full FP32 pass every round; -1 = 1 from
                            2049 x 2049 pixels on, else 0 */
 } fem_params;
 

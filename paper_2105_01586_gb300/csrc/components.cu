@@ -229,6 +229,9 @@ struct BuildArgs {
     const int* dT;
     const int* guard;
     int Vcap, Tcap;
+    // only the rows of unknown vertices (nbr, coef, diag): all that the
+    // Laplace solve reads; the adjoint also reads the mask vertices' rows
+    bool unknown_rows;
 };
 
 struct UnknownFlagIn {
@@ -283,11 +286,21 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
     }
     const long long V8 = 8LL * V;
     // 0. clear; union-find forest of singletons; mask counts per chunk
-    for (long long i = tid0; i < V8; i += stride) {
-        A.nbr[i] = -1;
-        A.coef[i] = 0.0f;
+    if (!A.unknown_rows) {
+        for (long long i = tid0; i < V8; i += stride) {
+            A.nbr[i] = -1;
+            A.coef[i] = 0.0f;
+        }
     }
     for (int i = tid0; i < V; i += stride) {
+        if (A.unknown_rows) {
+            if (A.mask[i]) continue;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                A.nbr[(size_t)d * V + i] = -1;
+                A.coef[(size_t)d * V + i] = 0.0f;
+            }
+        }
         A.diag[i] = 0.0f;
         A.parent[i] = i;
         A.size[i] = 0;
@@ -299,28 +312,42 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
     // 1. assemble: legs (c,a) and (c,b) carry -1/2 each, the hypotenuse is
     //    adjacency only; K_cc = 1, K_aa = K_bb = 1/2 on the diagonal.
     //    Mask vertices are numbered by the count of mask vertices before them.
+    //    With unknown_rows a triangle writes only its unknown corners' rows
+    //    (and none when all three are mask vertices).
     for (int t = tid0; t < T; t += stride) {
         int4 tr = A.tri[t];
         int a = tr.x, b = tr.y, c = tr.z;
+        const bool ra = !A.unknown_rows || !A.mask[a];
+        const bool rb = !A.unknown_rows || !A.mask[b];
+        const bool rc = !A.unknown_rows || !A.mask[c];
+        if (!(ra || rb || rc)) continue;
         int2 pa = A.vxy[a], pb = A.vxy[b], pc = A.vxy[c];
         int d = dir_index(pa.x - pc.x, pa.y - pc.y);
-        A.nbr[(size_t)d * V + c] = a;
-        atomicAdd(A.coef + (size_t)d * V + c, -0.5f);
+        if (rc) {
+            A.nbr[(size_t)d * V + c] = a;
+            atomicAdd(A.coef + (size_t)d * V + c, -0.5f);
+        }
         d = (d + 4) & 7;
-        A.nbr[(size_t)d * V + a] = c;
-        atomicAdd(A.coef + (size_t)d * V + a, -0.5f);
+        if (ra) {
+            A.nbr[(size_t)d * V + a] = c;
+            atomicAdd(A.coef + (size_t)d * V + a, -0.5f);
+        }
         d = dir_index(pb.x - pc.x, pb.y - pc.y);
-        A.nbr[(size_t)d * V + c] = b;
-        atomicAdd(A.coef + (size_t)d * V + c, -0.5f);
+        if (rc) {
+            A.nbr[(size_t)d * V + c] = b;
+            atomicAdd(A.coef + (size_t)d * V + c, -0.5f);
+        }
         d = (d + 4) & 7;
-        A.nbr[(size_t)d * V + b] = c;
-        atomicAdd(A.coef + (size_t)d * V + b, -0.5f);
+        if (rb) {
+            A.nbr[(size_t)d * V + b] = c;
+            atomicAdd(A.coef + (size_t)d * V + b, -0.5f);
+        }
         d = dir_index(pb.x - pa.x, pb.y - pa.y);
-        A.nbr[(size_t)d * V + a] = b;
-        A.nbr[(size_t)((d + 4) & 7) * V + b] = a;
-        atomicAdd(A.diag + c, 1.0f);
-        atomicAdd(A.diag + a, 0.5f);
-        atomicAdd(A.diag + b, 0.5f);
+        if (ra) A.nbr[(size_t)d * V + a] = b;
+        if (rb) A.nbr[(size_t)((d + 4) & 7) * V + b] = a;
+        if (rc) atomicAdd(A.diag + c, 1.0f);
+        if (ra) atomicAdd(A.diag + a, 0.5f);
+        if (rb) atomicAdd(A.diag + b, 0.5f);
     }
     scan_emit(UnknownFlagIn{A.mask}, IndexMapOut{&A}, V, A.tsum, A.nU_dev);
     if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
@@ -475,7 +502,14 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
 // diagonals, row counts, vertex and component of each row (92 B per
 // unknown); with the right-hand side, 8 B per vertex read and 16 B per
 // unknown written.  The union-find forest is working state, not counted.
-double build_bytes(long long T, long long V, long long nU, bool rhs) {
+// With the unknown vertices' rows only: the triangles (16 B) and the mask
+// (1 B per vertex) read, the index maps written (4 B per vertex, 4 B per
+// mask vertex), the stencil rows of the unknowns (68 B) with their ELL
+// rows (92 B), and for the right-hand side the values of the at most 8
+// neighbours and the own vertex read (72 B) and 16 B written per unknown.
+double build_bytes(long long T, long long V, long long nU, bool rhs, bool unknown_rows) {
+    if (unknown_rows)
+        return 16.0 * T + 5.0 * V + 4.0 * (V - nU) + 160.0 * nU + (rhs ? 88.0 * nU : 0.0);
     return 16.0 * T + 85.0 * V + 4.0 * (V - nU) + 92.0 * nU + (rhs ? 8.0 * V + 16.0 * nU : 0.0);
 }
 
@@ -485,7 +519,7 @@ namespace {
 // launch k_build_system on the mesh counts V, T (host) or, ahead of the
 // host, on the counts of the round in flight (dV, dT, guard; then nU < 0).
 fem_status launch_build(fem_mesh* m, cudaStream_t s, int V, int T, int nU, size_t nv, size_t nu, bool rhs,
-                        const int* dV, const int* dT, const int* guard, int Vcap, int Tcap) {
+                        const int* dV, const int* dT, const int* guard, int Vcap, int Tcap, bool unknown_rows) {
     const size_t n = nu > 0 ? nu : 1, nr = n + 1;
     FEM_TRY(ensure(m->nbr, (size_t)8 * nv, s));
     FEM_TRY(ensure(m->coefA, (size_t)8 * nv, s));
@@ -564,6 +598,7 @@ fem_status launch_build(fem_mesh* m, cudaStream_t s, int V, int T, int nU, size_
     A.guard = guard;
     A.Vcap = Vcap;
     A.Tcap = Tcap;
+    A.unknown_rows = unknown_rows;
     // *A.err is zero: cleared at creation, left at zero by every completed
     // launch, and cleared again after a failed one (reset_coop_state)
     void* args[] = {&A};
@@ -579,7 +614,7 @@ fem_status launch_build(fem_mesh* m, cudaStream_t s, int V, int T, int nU, size_
 fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
     bool want = with_rhs && *with_rhs;
     if (with_rhs) *with_rhs = false;
-    if (m->sys_version == m->mesh_version) {
+    if (m->sys_version == m->mesh_version && (m->sys_full || m->unknown_rows_ok)) {
         if (want && m->rhs_fresh) *with_rhs = true;
         m->rhs_fresh = false;
         return FEM_OK;
@@ -591,12 +626,15 @@ fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs) {
     const int nU = V - m->nK;
     m->nU = nU;
     const bool rhs = want && nU > 0;
-    FEM_TRY(launch_build(m, s, V, T, nU, (size_t)V, (size_t)(nU > 0 ? nU : 1), rhs, nullptr, nullptr, nullptr, 0, 0));
+    FEM_TRY(launch_build(m, s, V, T, nU, (size_t)V, (size_t)(nU > 0 ? nU : 1), rhs, nullptr, nullptr, nullptr, 0, 0,
+                         false));
     note_bytes(F_ASSEMBLY, build_bytes(T, V, nU, rhs));
     if (rhs) *with_rhs = true;
     m->sys_version = m->mesh_version;
+    m->sys_full = true;
     return FEM_OK;
 }
+
 
 // The system of the mesh that the refinement round in flight produces,
 // launched behind that round's last kernel before the host has read the
@@ -612,7 +650,7 @@ fem_status build_system_ahead(fem_mesh* m, cudaStream_t s, int V, int T, const i
     long long tc = (long long)m->tri.n;
     *Vcap = (int)std::min<long long>(vc, INT_MAX);
     *Tcap = (int)std::min<long long>(tc, INT_MAX);
-    return launch_build(m, s, V, T, -1, nv, nv, true, m->dcount.p + 4, m->dcount.p + 5, guard, *Vcap, *Tcap);
+    return launch_build(m, s, V, T, -1, nv, nv, true, m->dcount.p + 4, m->dcount.p + 5, guard, *Vcap, *Tcap, true);
 }
 
 fem_status build_system(fem_mesh* m, cudaStream_t s) { return build_system_rhs(m, s, nullptr); }

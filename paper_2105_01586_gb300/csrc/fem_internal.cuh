@@ -48,7 +48,7 @@ fem_status cuda_fail(cudaError_t e, const char* what);
     } while (0)
 
 // ------------------------------------------------------ launch accounting
-// F_SQPASS: the square-tiled error pass over all squares (one kernel, so
+// F_SQPASS: the square-tiled FP32 error pass (one kernel, so
 // that its roofline can be taken alone); the rest of the error work (plan,
 // band, image layout) is F_RASTER
 enum Family { F_RASTER = 0, F_CG = 1, F_ASSEMBLY = 2, F_TOPK = 3, F_REFINE = 4, F_TONAL = 5, F_OTHER = 6, F_SQPASS = 7,
@@ -57,6 +57,9 @@ void note_launch_begin(int family, cudaStream_t s);
 bool profiling(int family);
 // algorithmic bytes moved by work of a family (counted only while profiling)
 void note_bytes(int family, double bytes);
+// algorithmic bytes of the incremental FP32 passes since the last call,
+// counted on the device while F_SQPASS is profiled (raster_sq.cu)
+double sq_inc_bytes_take();
 void note_launch_end(int family, cudaStream_t s);
 
 // Launch a kernel with accounting; returns FEM_E_CUDA on a launch error.
@@ -274,6 +277,8 @@ struct fem_mesh {
 
     // Laplace system on U
     long long sys_version = -1;
+    bool sys_full = false;          // the built system has every vertex's stiffness row
+    bool unknown_rows_ok = false;   // set by the spatial loop: the unknowns' rows suffice
     bool rhs_fresh = false;         // b64/x64 hold the right-hand side and start of the built system
     cudaEvent_t round_ev = nullptr; // end of a refinement round's last kernel
     fem::DArr<int> uidx;            // vertex -> U row or -1
@@ -351,6 +356,16 @@ struct fem_mesh {
     fem::DArr<int4> sq_rec;            // 2 int4 per curve position: fine-triangle records of the FP32 pass
     fem::DArr<unsigned char> sq_mark, bsel;  // squares with a band triangle; band flag per triangle
     long long sq_plan_version = -1;
+    // Incremental FP32 pass (spatial rounds after a call's first): the vertex
+    // values the kept intervals were formed with, the triangles rewritten by
+    // the last bisection, and the counts at that pass.
+    fem::DArr<double> uvk;
+    fem::DArr<float2> uvfk;
+    fem::DArr<unsigned char> vchg, tchg, tdirty, sq_dmark;  // per vertex, triangle, triangle, square
+    fem::DArr<unsigned char> hcnt;     // per triangle: its interval is counted in the histograms
+    fem::DArr<int> sq_dlist;           // squares of the incremental pass
+    int inc_V = 0, inc_T = 0;
+    bool inc_ok = false;               // keys_lo/hi and uvk/uvfk belong to the current mesh
     fem::DArr<double> lossk, lossred;  // tonal loss: per-triangle squared errors, block partial sums
 
     // host staging (pinned)
@@ -393,15 +408,22 @@ fem_status solve_components(fem_mesh* m, const double* b, double* x, bool use_fp
 
 // helpers implemented in the .cu files
 fem_status exclusive_scan_i32(const int* in, int* out, int n, cudaStream_t s, int* total_dev);
+// the system of the current mesh, with every vertex's stiffness row (the
+// tonal step's adjoint and pixel-mass products read the mask vertices'
+// rows); inside the spatial loop (m->unknown_rows_ok) a system built ahead
+// with the unknown vertices' rows only, all that a Laplace solve reads, is
+// kept
 fem_status build_system(fem_mesh* m, cudaStream_t s);
 // with_rhs (optional): on input asks for b64/x64 of a solve on the current
 // vertex values; on output true when the build filled them
 fem_status build_system_rhs(fem_mesh* m, cudaStream_t s, bool* with_rhs);
 // the system of the mesh the refinement round in flight produces, launched
-// before the host reads the round's counts (components.cu)
+// before the host reads the round's counts, with the unknown vertices' rows
+// only (components.cu)
 fem_status build_system_ahead(fem_mesh* m, cudaStream_t s, int V, int T, const int* guard, int* Vcap, int* Tcap);
-// algorithmic bytes of one system build
-double build_bytes(long long T, long long V, long long nU, bool rhs);
+// algorithmic bytes of one system build (unknown_rows: of the unknown
+// vertices' stiffness rows only)
+double build_bytes(long long T, long long V, long long nU, bool rhs, bool unknown_rows = false);
 fem_status solve_laplace(fem_mesh* m, bool use_fp64, double tol, int maxit, cudaStream_t s,
                          int* iters_out, double* relres_out, bool deferred = false);
 // scatter: the solution also goes to m->uv / m->uvf at the rows' vertices
@@ -418,7 +440,7 @@ fem_status raster_errors(fem_mesh* m, const double* uv, const float2* uvf, doubl
                          unsigned long long* keyc_out = nullptr);
 fem_status raster_image(fem_mesh* m, const double* uv, float* u, int* owner, cudaStream_t s);
 fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, double frac, long long vcap,
-                            cudaStream_t s);
+                            cudaStream_t s, bool incremental = false);
 // the image f as squares for the square-tiled pass (once per call that reads f)
 fem_status sq_image(fem_mesh* m, const float* f, cudaStream_t s);
 fem_status raster_local(fem_mesh* m, int mode, const float* r, cudaStream_t s);

@@ -407,6 +407,7 @@ int fem_profile_read(int family, long long* launches, double* ms, double* bytes,
     if (launches) *launches = g_prof_launches[family];
     if (ms) *ms = tot;
     if (name) *name = names[family];
+    if (family == F_SQPASS) g_prof_bytes[family] += sq_inc_bytes_take();
     if (bytes) *bytes = g_prof_bytes[family];
     g_prof_launches[family] = 0;
     g_prof_bytes[family] = 0.0;
@@ -553,6 +554,8 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->sq_coarse, s); release(m->sq_long, s); release(m->sq_piece, s); release(m->sq_psum, s);
     release(m->sq_pdone, s); release(m->sq_ctr, s); release(m->sq_list, s); release(m->sq_rec, s);
     release(m->sq_pos, s); release(m->sq_bcoarse, s); release(m->sq_mark, s); release(m->bsel, s);
+    release(m->uvk, s); release(m->uvfk, s); release(m->vchg, s); release(m->tchg, s); release(m->tdirty, s);
+    release(m->sq_dmark, s); release(m->sq_dlist, s); release(m->hcnt, s);
     cudaStreamSynchronize(s);
     if (m->host_stage) cudaFreeHost(m->host_stage);
     if (m->round_ev) cudaEventDestroy(m->round_ev);

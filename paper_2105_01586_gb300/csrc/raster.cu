@@ -765,14 +765,17 @@ __global__ void k_fast_classify(const int4* __restrict__ tri, const int2* __rest
 // keyc[] hold, for every triangle, the exact key (band) or the substituted
 // bound (outside the band), kdev the total k, and the band list with its
 // counts for the selection (refine_round).  The image must have been laid
-// out in squares (sq_image) for this call.
+// out in squares (sq_image) for this call.  incremental: the mesh is the
+// previous call's refined by one round on the same image (the FP32 pass
+// then recomputes only what the round can have changed).
 fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, double frac, long long vcap,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool incremental) {
     FEM_TRY(sq_plan(m, s));
     const int T = m->T;
     const SqGeo G = sq_geo(m);
-    FEM_TRY(ensure(m->keys_lo, (size_t)T, s));
-    FEM_TRY(ensure(m->keys_hi, (size_t)T, s));
+    const size_t keep = incremental && m->inc_ok ? (size_t)m->inc_T : 0;
+    FEM_TRY(ensure(m->keys_lo, (size_t)T, s, keep));
+    FEM_TRY(ensure(m->keys_hi, (size_t)T, s, keep));
     FEM_TRY(ensure(m->band, (size_t)T, s));
     FEM_TRY(ensure(m->bsel, (size_t)T, s));
     if (!m->sq_mark.p || m->sq_mark.n < (size_t)G.Q * G.Q) {
@@ -786,10 +789,11 @@ fem_status raster_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, do
     unsigned long long* max_out = (unsigned long long*)(m->dscal.p + 18);
     double* tau = m->dscal.p + 16;
     int* kdev = m->dcount.p + 2;
-    FEM_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned) * (2 * kFastBins + 8), s));
+    // the histograms are cleared (full pass) or kept up to date by the pass
+    FEM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 8, s));
     FEM_CUDA(cudaMemsetAsync(max_out, 0, sizeof(unsigned long long), s));
     // all pixels in FP32 with error intervals
-    FEM_TRY(sq_keys_fast(m, uv, uvf, FastOut{m->keys_lo.p, m->keys_hi.p, hist, hist + kFastBins}, s));
+    FEM_TRY(sq_keys_fast(m, uv, uvf, FastOut{m->keys_lo.p, m->keys_hi.p, hist, hist + kFastBins}, s, incremental));
     // bracket and classification
     FEM_LAUNCH(F_TOPK, s, k_fast_bracket, 1, kBracketThreads, 0, hist, hist + kFastBins, T, frac, vcap, kdev, tau);
     FEM_LAUNCH(F_TOPK, s, k_fast_classify, (T + 255) / 256, 256, 0, m->tri.p, m->vxy.p, T, G, m->keys_lo.p,

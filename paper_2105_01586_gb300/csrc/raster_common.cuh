@@ -222,7 +222,8 @@ struct __align__(16) SqRec {
 int sq_side(int N);
 SqGeo sq_geo(const fem_mesh* m);
 fem_status sq_plan(fem_mesh* m, cudaStream_t s);
-fem_status sq_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, FastOut F, cudaStream_t s);
+fem_status sq_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, FastOut F, cudaStream_t s,
+                        bool incremental = false);
 // coarse (optional): the coarse triangles to finish, by curve position
 // (default: all of them)
 fem_status sq_keys_exact(fem_mesh* m, const double* uv, const float2* uvf, double* keys, unsigned long long* keyc,

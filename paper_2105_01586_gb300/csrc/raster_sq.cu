@@ -275,6 +275,8 @@ struct SqArgs {
     const unsigned char* sel;   // SQ_EXACT: only triangles with sel[t] != 0 (null: all)
     const int* sq_list;         // squares to process (null: all Q*Q)
     const int* n_sq;            // their number (device)
+    const unsigned char* tdirty;  // SQ_FAST: finish only triangles with tdirty[t] != 0 (null: all)
+    unsigned char* hcnt;          // SQ_FAST: per finished triangle, 1 when counted in the histograms
     SqLong LG;                  // long coarse triangles and their pieces
     int* err;
 };
@@ -312,10 +314,12 @@ __device__ __forceinline__ void sq_finish(const SqArgs& A, int t, const TriGeom&
         fast_interval(S, (float)n, fast_M(g, P.ucf, P.gxf, P.gyf), kSqChain, lo, hi);
         A.F.lo[t] = lo;
         A.F.hi[t] = hi;
-        if (tri_eligible(g, sq_dom(A.G))) {
+        const bool el = tri_eligible(g, sq_dom(A.G));
+        if (el) {
             atomicAdd(A.F.hlo + fast_bin(lo), 1u);
             atomicAdd(A.F.hhi + fast_bin(hi), 1u);
         }
+        A.hcnt[t] = el ? 1 : 0;
     } else {
         const double key = ff_to_double(S);
         A.keys[t] = key;
@@ -560,30 +564,153 @@ __device__ __forceinline__ void sq_issue(const SqArgs& A, int q, float* img, uns
     if (!outside) bulk_copy(img, A.fsq + (long long)q * s * (s + 1), bytes, bar, policy);
 }
 
+// Incremental FP32 pass.  A triangle's interval depends only on its
+// corners, its vertex values, the image and the fine triangles that share
+// its square (they fix the order of the FP32 additions), and the pass forms
+// it in a fixed order.  So after a refinement round only the intervals of
+// "dirty" triangles can change: those the bisection made or rewrote, and
+// those with a vertex whose value changed (new vertices, re-solved
+// unknowns).  Only the squares that hold a dirty triangle are passed over;
+// there every fine triangle comes out as a full pass would give it, the
+// dirty ones are stored, and every other triangle keeps its interval, which
+// a full pass would reproduce bit for bit.  The histograms of the intervals
+// are kept too: a dirty triangle that was counted takes its old bins out
+// (here) and the pass counts its new ones.
+struct SqInc {
+    const unsigned char* vchg;  // per vertex: value changed since the kept intervals (null: full pass)
+    unsigned char* tchg;        // per triangle: rewritten by the bisection since (cleared here)
+    int Tk;                     // triangles at the kept intervals: ids >= Tk are new
+    unsigned char* tdirty;      // out: per triangle
+    unsigned char* dmark;       // out: per square, holds a dirty fine triangle
+    const float* lo;            // the kept intervals
+    const float* hi;
+    const unsigned char* hcnt;  // per triangle below Tk: its kept interval is counted
+    unsigned* hlo;              // histograms
+    unsigned* hhi;
+};
+
 // The records of the triangles for the FP32 pass, one thread per curve
 // position; all gathers of the pass happen here, in a fully parallel kernel,
 // and the pass reads each square's records contiguously (fine triangles) or
-// one record per covered node (coarse ones).
+// one record per covered node (coarse ones).  With I.vchg the kernel also
+// classifies every triangle dirty or clean (above), marks the squares of the
+// dirty fine ones, and takes the old bins of the counted dirty ones out of
+// the histograms (one atomic per distinct bin and warp).  The loop is
+// warp-uniform, so the whole warp takes part in the bin matching.
 __global__ void k_sq_records(const int* __restrict__ order, const int4* __restrict__ tri, const int2* __restrict__ vxy,
                              const double* __restrict__ uv, const float2* __restrict__ uvf,
-                             const int* __restrict__ nodeof, int T, int N, SqRec* __restrict__ rec) {
+                             const int* __restrict__ nodeof, int T, int N, SqRec* __restrict__ rec, SqInc I) {
     pdl_wait();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
-        const int t = order[i];
-        const int4 tr = tri[t];
-        const TriGeom g = tri_geom(tr, vxy, N);
-        ff uc, gx, gy;
-        tri_plane(g, tr, uv, uvf, uc, gx, gy);
-        SqRec r;
-        r.ax = (unsigned short)g.ax; r.ay = (unsigned short)g.ay;
-        r.bx = (unsigned short)g.bx; r.by = (unsigned short)g.by;
-        r.cx = (unsigned short)g.cx; r.cy = (unsigned short)g.cy;
-        r.t = t;
-        r.ucf = __fadd_rn(uc.hi, uc.lo);
-        r.gxf = __fadd_rn(gx.hi, gx.lo);
-        r.gyf = __fadd_rn(gy.hi, gy.lo);
-        r.pad = 0.f;
-        rec[i] = r;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < T; i0 += stride) {
+        const int i = i0 + lane;
+        unsigned blo = 0xffffffffu, bhi = 0xffffffffu;
+        if (i < T) {
+            const int t = order[i];
+            const int4 tr = tri[t];
+            const TriGeom g = tri_geom(tr, vxy, N);
+            ff uc, gx, gy;
+            tri_plane(g, tr, uv, uvf, uc, gx, gy);
+            SqRec r;
+            r.ax = (unsigned short)g.ax; r.ay = (unsigned short)g.ay;
+            r.bx = (unsigned short)g.bx; r.by = (unsigned short)g.by;
+            r.cx = (unsigned short)g.cx; r.cy = (unsigned short)g.cy;
+            r.t = t;
+            r.ucf = __fadd_rn(uc.hi, uc.lo);
+            r.gxf = __fadd_rn(gx.hi, gx.lo);
+            r.gyf = __fadd_rn(gy.hi, gy.lo);
+            r.pad = 0.f;
+            rec[i] = r;
+            if (I.vchg) {
+                const bool d = t >= I.Tk || I.tchg[t] || I.vchg[tr.x] || I.vchg[tr.y] || I.vchg[tr.z];
+                I.tdirty[t] = d ? 1 : 0;
+                if (d) {
+                    const int nd = nodeof[i];
+                    if (nd >= 0) I.dmark[nd >> 1] = 1;
+                    if (t < I.Tk && I.hcnt[t]) {
+                        blo = fast_bin(I.lo[t]);
+                        bhi = fast_bin(I.hi[t]);
+                    }
+                }
+            }
+            if (I.tchg) I.tchg[t] = 0;
+        }
+        if (I.vchg) {
+            unsigned peers = __match_any_sync(FULL, blo);
+            if (blo != 0xffffffffu && (__ffs(peers) - 1) == lane) atomicSub(I.hlo + blo, (unsigned)__popc(peers));
+            peers = __match_any_sync(FULL, bhi);
+            if (bhi != 0xffffffffu && (__ffs(peers) - 1) == lane) atomicSub(I.hhi + bhi, (unsigned)__popc(peers));
+        }
+    }
+}
+
+// Per vertex: has the value (FP64 and float-float copy) changed since the
+// kept intervals were formed?  Vertices from Vk on are new.  The kept copy
+// follows the current values.
+__global__ void k_vchanged(int V, int Vk, const double* __restrict__ uv, const float2* __restrict__ uvf,
+                           double* __restrict__ uvk, float2* __restrict__ uvfk, unsigned char* __restrict__ vchg) {
+    pdl_wait();
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        const double x = uv[v];
+        bool c = v >= Vk || __double_as_longlong(x) != __double_as_longlong(uvk[v]);
+        float2 y = make_float2(0.f, 0.f);
+        if (uvf) {
+            y = uvf[v];
+            if (!c) {
+                const float2 z = uvfk[v];
+                c = __float_as_uint(y.x) != __float_as_uint(z.x) || __float_as_uint(y.y) != __float_as_uint(z.y);
+            }
+        }
+        vchg[v] = c ? 1 : 0;
+        if (c) {
+            uvk[v] = x;
+            if (uvf) uvfk[v] = y;
+        }
+    }
+}
+
+// Algorithmic bytes of the incremental passes, when asked for (profiling):
+// per listed square its image block (4 B per pixel), its two node entries
+// (32 B), the record of each fine triangle in it (32 B) with its interval
+// (8 B), and the record of each covering coarse triangle (32 B).
+__device__ unsigned long long g_sq_inc_bytes;
+
+// The squares of the incremental pass: a square is listed when one of its
+// fine triangles is dirty (marked by k_sq_records) or one of its nodes lies
+// in a dirty coarse triangle.  The marks are cleared for the next round.
+__global__ void k_sq_dirty_list(int nsq, const int* __restrict__ order, const int* __restrict__ ncov,
+                                const int2* __restrict__ nseg, const unsigned char* __restrict__ tdirty,
+                                unsigned char* __restrict__ mark, int* __restrict__ list, int* __restrict__ n_list,
+                                SqGeo G, bool count_bytes) {
+    pdl_wait();
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    bool on = false;
+    unsigned long long bytes = 0;
+    if (q < nsq) {
+        on = mark[q] != 0;
+        mark[q] = 0;
+        const int c0 = ncov[2 * q], c1 = ncov[2 * q + 1];
+        if (c0 >= 0 && tdirty[order[c0]]) on = true;
+        if (c1 >= 0 && tdirty[order[c1]]) on = true;
+        if (on && count_bytes) {
+            const int I = q / G.Q, J = q - I * G.Q;
+            const long long px = (long long)sq_extent(G.s, J, G.Q, J * G.s, G.W) * sq_extent(G.s, I, G.Q, I * G.s, G.H);
+            long long fine = 0;
+            if (c0 < 0) { const int2 sg = nseg[2 * q]; fine += max(0, sg.y - sg.x); }
+            if (c1 < 0) { const int2 sg = nseg[2 * q + 1]; fine += max(0, sg.y - sg.x); }
+            bytes = (unsigned long long)(4 * px + 32 + 40 * fine + 32 * ((c0 >= 0) + (c1 >= 0)));
+        }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, on);
+    int base = 0;
+    if ((threadIdx.x & 31) == 0 && bal) base = atomicAdd(n_list, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (on) list[base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = q;
+    if (count_bytes) {
+        bytes = warp_sum(bytes);
+        if ((threadIdx.x & 31) == 0 && bytes) atomicAdd(&g_sq_inc_bytes, bytes);
     }
 }
 
@@ -606,15 +733,17 @@ __device__ __forceinline__ void sq_fine_finish(const SqArgs& A, bool have, const
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     unsigned blo = 0xffffffffu, bhi = 0xffffffffu;
-    if (have) {
+    if (have && (!A.tdirty || A.tdirty[R.t])) {
         float lo, hi;
         fast_interval(ff{sum, 0.f}, (float)n, fast_M(g, R.ucf, R.gxf, R.gyf), kSqChain, lo, hi);
         A.F.lo[R.t] = lo;
         A.F.hi[R.t] = hi;
-        if (tri_eligible(g, sq_dom(A.G))) {
+        const bool el = tri_eligible(g, sq_dom(A.G));
+        if (el) {
             blo = fast_bin(lo);
             bhi = fast_bin(hi);
         }
+        A.hcnt[R.t] = el ? 1 : 0;
     }
     unsigned peers = __match_any_sync(FULL, blo);
     if (blo != 0xffffffffu && (__ffs(peers) - 1) == lane) atomicAdd(A.F.hlo + blo, (unsigned)__popc(peers));
@@ -932,7 +1061,8 @@ __device__ __forceinline__ void sq_coarse_finish(const SqArgs& A, int c, ff S, i
 
 template <int MODE>
 __device__ __forceinline__ bool sq_coarse_wanted(const SqArgs& A, int c) {
-    return MODE == SQ_FAST || !A.sel || A.sel[A.order[c]];
+    if (MODE == SQ_FAST) return !A.tdirty || A.tdirty[A.order[c]];
+    return !A.sel || A.sel[A.order[c]];
 }
 
 // The coarse triangles.  First the pieces of the long ones, one block per
@@ -1191,20 +1321,91 @@ static double sq_bytes(const fem_mesh* m, bool fast) {
     return 4.0 * (double)m->PI + (fast ? 32.0 : 24.0) * m->T + 16.0 * m->V;
 }
 
-fem_status sq_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, FastOut F, cudaStream_t s) {
+double sq_inc_bytes_take() {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_sq_inc_bytes, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0;
+    }
+    const unsigned long long z = 0;
+    cudaMemcpyToSymbol(g_sq_inc_bytes, &z, sizeof(z));
+    cudaGetLastError();
+    return (double)v;
+}
+
+// incremental: the caller's intervals F.lo / F.hi and histograms F.hlo /
+// F.hhi are those of the last pass on this mesh before the refinement round
+// that made it (the spatial loop's rounds after its first); the pass then
+// covers only the dirty triangles' squares.  Otherwise every square, with
+// the histograms cleared first, and the kept state starts afresh.
+fem_status sq_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, FastOut F, cudaStream_t s,
+                        bool incremental) {
     FEM_TRY(sq_plan(m, s));
-    FEM_TRY(ensure(m->sq_rec, (size_t)2 * m->T, s));
-    const int grid = std::max(1, std::min((m->T + 255) / 256, m->num_sms * 16));
+    const int T = m->T, V = m->V;
+    const SqGeo G = sq_geo(m);
+    const int nsq = G.Q * G.Q;
+    const bool inc = incremental && m->inc_ok && m->inc_T <= T && m->inc_V <= V;
+    FEM_TRY(ensure(m->sq_rec, (size_t)2 * T, s));
+    FEM_TRY(ensure(m->tchg, (size_t)T, s, inc ? (size_t)m->inc_T : 0));
+    FEM_TRY(ensure(m->uvk, (size_t)V, s, inc ? (size_t)m->inc_V : 0));
+    FEM_TRY(ensure(m->uvfk, (size_t)V, s, inc ? (size_t)m->inc_V : 0));
+    FEM_TRY(ensure(m->hcnt, (size_t)T, s, inc ? (size_t)m->inc_T : 0));
+    if (!inc) {
+        FEM_CUDA(cudaMemsetAsync(F.hlo, 0, sizeof(unsigned) * kFastBins, s));
+        FEM_CUDA(cudaMemsetAsync(F.hhi, 0, sizeof(unsigned) * kFastBins, s));
+    }
+    SqInc I{};
+    I.tchg = m->tchg.p;
+    if (inc) {
+        FEM_TRY(ensure(m->vchg, (size_t)V, s));
+        FEM_TRY(ensure(m->tdirty, (size_t)T, s));
+        FEM_TRY(ensure(m->sq_dlist, (size_t)nsq + 1, s));
+        if (!m->sq_dmark.p || m->sq_dmark.n < (size_t)nsq) {
+            FEM_TRY(ensure(m->sq_dmark, (size_t)nsq, s));
+            FEM_CUDA(cudaMemsetAsync(m->sq_dmark.p, 0, m->sq_dmark.n, s));  // cleared by each list after
+        }
+        const int vg = std::max(1, std::min((V + 255) / 256, m->num_sms * 8));
+        FEM_LAUNCH(F_RASTER, s, k_vchanged, vg, 256, 0, V, m->inc_V, uv, uvf, m->uvk.p, uvf ? m->uvfk.p : nullptr,
+                   m->vchg.p);
+        I.vchg = m->vchg.p;
+        I.Tk = m->inc_T;
+        I.tdirty = m->tdirty.p;
+        I.dmark = m->sq_dmark.p;
+        I.lo = F.lo;
+        I.hi = F.hi;
+        I.hcnt = m->hcnt.p;
+        I.hlo = F.hlo;
+        I.hhi = F.hhi;
+    }
+    const int grid = std::max(1, std::min((T + 255) / 256, m->num_sms * 16));
     FEM_LAUNCH(F_RASTER, s, k_sq_records, grid, 256, 0, m->order.p, m->tri.p, m->vxy.p, uv, uvf,
-               (const int*)m->sq_nodeof.p, m->T, m->N, (SqRec*)m->sq_rec.p);
+               (const int*)m->sq_nodeof.p, T, m->N, (SqRec*)m->sq_rec.p, I);
     SqArgs A = sq_args(m, uv, uvf);
     A.F = F;
     A.rec = (const SqRec*)m->sq_rec.p;
-    const int Q = A.G.Q;
-    note_bytes(F_SQPASS, sq_bytes(m, true));
-    FEM_LAUNCH(F_SQPASS, s, k_sq<SQ_FAST>, sq_grid(m, (long long)Q * Q), kSqThreads, 0, A);
+    A.hcnt = m->hcnt.p;
+    if (inc) {
+        int* n_list = m->sq_dlist.p + nsq;
+        FEM_CUDA(cudaMemsetAsync(n_list, 0, sizeof(int), s));
+        FEM_LAUNCH(F_RASTER, s, k_sq_dirty_list, (nsq + 255) / 256, 256, 0, nsq, (const int*)m->order.p,
+                   (const int*)m->sq_cov.p, (const int2*)m->sq_seg.p, (const unsigned char*)m->tdirty.p,
+                   m->sq_dmark.p, m->sq_dlist.p, n_list, G, profiling(F_SQPASS));
+        A.sq_list = m->sq_dlist.p;
+        A.n_sq = n_list;
+        A.tdirty = m->tdirty.p;
+    } else {
+        note_bytes(F_SQPASS, sq_bytes(m, true));
+    }
+    FEM_LAUNCH(F_SQPASS, s, k_sq<SQ_FAST>, sq_grid(m, (long long)nsq), kSqThreads, 0, A);
     FEM_LAUNCH(F_RASTER, s, k_sq_final<SQ_FAST>, m->num_sms * 8, 256, 0, A, (const int*)m->sq_coarse.p,
                (const int*)(m->sq_ctr.p + 1));
+    if (!inc) {
+        FEM_CUDA(cudaMemcpyAsync(m->uvk.p, uv, sizeof(double) * V, cudaMemcpyDeviceToDevice, s));
+        if (uvf) FEM_CUDA(cudaMemcpyAsync(m->uvfk.p, uvf, sizeof(float2) * V, cudaMemcpyDeviceToDevice, s));
+    }
+    m->inc_ok = true;
+    m->inc_V = V;
+    m->inc_T = T;
     return FEM_OK;
 }
 

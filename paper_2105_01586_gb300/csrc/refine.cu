@@ -699,7 +699,7 @@ __global__ void k_bisect(int4* __restrict__ tri, const int2* __restrict__ vxy, i
                          const unsigned char* __restrict__ mask, const float* __restrict__ f, double* __restrict__ uv,
                          float2* __restrict__ uvf, const int* __restrict__ cnt, const int* __restrict__ scan_err,
                          const double* __restrict__ margin, int* __restrict__ stage, int* __restrict__ plan_err,
-                         int* __restrict__ clear) {
+                         int* __restrict__ clear, unsigned char* __restrict__ tchg) {
     pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
@@ -746,6 +746,7 @@ __global__ void k_bisect(int4* __restrict__ tri, const int2* __restrict__ vxy, i
     }
     tri[t] = kept;
     tri[id1] = fresh;
+    if (tchg) tchg[t] = 1;  // id t now names the kept child (the other ids are new)
 }
 
 // Space-filling (Sierpinski) order of the triangles.  A newest-vertex
@@ -941,7 +942,8 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
     FEM_LAUNCH(F_REFINE, s, k_bisect, tb, 256, 0, m->tri.p, m->vxy.p, T, N, bmM, (const int*)m->wpre.p, V,
                m->flags.p, m->fscan.p, m->mask.p, f, m->uv.p, m->uvf.p, (const int*)m->dcount.p,
                (const int*)(m->dflag.p + 8), (const double*)margin, m->host_stage_dev ? stage_dev : nullptr,
-               m->dflag.p + 0, m->host_stage_dev ? m->dcount.p : nullptr);
+               m->dflag.p + 0, m->host_stage_dev ? m->dcount.p : nullptr,
+               m->inc_ok && m->tchg.n >= (size_t)T ? m->tchg.p : nullptr);
     // k, sweeps, new counts, margin, errors: written by k_bisect into mapped
     // pinned memory, else copied (and the counters cleared here)
     int* hs = (int*)m->host_stage + kRoundStageInts;
@@ -1004,8 +1006,9 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
         // start (from the vertex values k_bisect completed) are in place
         if (ahead && m->V <= Vcap && m->T <= Tcap) {
             m->sys_version = m->mesh_version;
+            m->sys_full = false;  // the unknowns' rows only
             m->rhs_fresh = m->nU > 0;
-            note_bytes(F_ASSEMBLY, build_bytes(m->T, m->V, m->nU, m->nU > 0));
+            note_bytes(F_ASSEMBLY, build_bytes(m->T, m->V, m->nU, m->nU > 0, true));
         }
     }
     return FEM_OK;
@@ -1053,6 +1056,13 @@ static void swap_channel(fem_mesh* m, int c) {
 // solve, and a triangle's error is the sum of its channels' exact errors.
 static fem_status spatial_refine(fem_mesh* m, const float* f_dev, int C, double density, const fem_params* p,
                                  cudaStream_t s) {
+    // within the loop only Laplace solves read the system, so the systems
+    // built ahead of the host hold the unknown vertices' rows only
+    struct UnknownRowsScope {
+        fem_mesh* m;
+        explicit UnknownRowsScope(fem_mesh* mm) : m(mm) { m->unknown_rows_ok = true; }
+        ~UnknownRowsScope() { m->unknown_rows_ok = false; }
+    } rows_scope(m);
     m->last_stream = s;
     m->stats = fem_stats{};
     m->stats.min_margin = INFINITY;
@@ -1099,7 +1109,8 @@ static fem_status spatial_refine(fem_mesh* m, const float* f_dev, int C, double 
         {
             Nvtx pass_range("error pass");
             if (band)
-                FEM_TRY(raster_keys_fast(m, m->uv.p, m->uvf.p, p->topk_frac, vstar - m->V, s));
+                FEM_TRY(raster_keys_fast(m, m->uv.p, m->uvf.p, p->topk_frac, vstar - m->V, s,
+                                         round > 0 && p->fast_keys != 2));
             else
                 FEM_TRY(raster_errors(m, m->uv.p, m->uvf.p, m->keys.p, s, C == 1 ? m->keyc.p : nullptr));
         }

@@ -155,6 +155,28 @@ def test_spatial_fast_keys_bit_exact(oracle_mod, fem, N, seed, density, frac):
     assert _same_mesh(m, om), "fast-key mesh differs from the oracle mesh"
 
 
+@pytest.mark.parametrize("W,H,seed,texture,density", [(2049, 2049, 3, True, 0.02), (1025, 1025, 1, False, 0.03),
+                                                       (1500, 1100, 5, True, 0.03), (700, 1300, 2, False, 0.05)])
+def test_incremental_pass_equals_full_pass(fem, W, H, seed, texture, density):
+    """After a call's first round the FP32 pass covers only the squares of
+    the triangles a round can have changed and keeps the other intervals
+    (fast_keys 1); a full pass every round (fast_keys 2) must give the same
+    rounds, the same selection margins and the same mesh, bit for bit."""
+    f_np = np.ascontiguousarray(S.make_image(max(W, H), seed, texture=texture)[:H, :W])
+    f = torch.from_numpy(f_np).cuda()
+    out = []
+    for fast in (1, 2):
+        m = fem.Mesh(W, H)
+        m.spatial_refine(f, density, fem.params(topk_frac=0.01, fast_keys=fast))
+        st = m.stats()
+        out.append((m.export(), st["rounds"], st["min_margin"], st["cg_iters"]))
+        m.close()
+    (inc, r1, mm1, cg1), (full, r2, mm2, cg2) = out
+    assert r1 == r2 and r1 > 100
+    assert mm1 == mm2 and cg1 == cg2
+    assert all(np.array_equal(a, b) for a, b in zip(inc, full))
+
+
 @pytest.mark.parametrize("fast", [0, 1])
 @pytest.mark.parametrize("N,value", [(65, 0.5), (257, 0.3)])
 def test_spatial_constant_image_ties_by_id(oracle_mod, fem, N, value, fast):
