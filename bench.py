@@ -64,8 +64,9 @@ def parse():
                     help="relative tolerance of the tonal inner solves (default: the library's 1e-11; 1e-13 in "
                          "configuration 4, whose 50th outer iterate is sensitive to the inner solves' accuracy)")
     ap.add_argument("--seed", type=int, default=None)
-    ap.add_argument("--fast-keys", type=int, default=-1, choices=[-1, 0, 1],
-                    help="selection keys: -1 the library's choice by image size, 0 exact, 1 FP32 intervals + exact band")
+    ap.add_argument("--fast-keys", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="selection keys: -1 the library's choice by image size, 0 exact, 1 FP32 intervals + exact "
+                         "band (incremental FP32 pass after the first round), 2 as 1 with a full FP32 pass every round")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check after timing")
     ap.add_argument("--no-fp64-timing", action="store_true", help="skip timing the plain FP64 GPU path")
@@ -143,7 +144,7 @@ def config(a, world):
     H, W = image_hw(a)
     return {"workload": workload_name(a), "config_index": a.config, "image": f"{W}x{H}", "density": a.density,
             "topk_frac": a.frac, "tonal": a.tonal, "tonal_tol": a.tonal_tol, "tonal_iters": a.tonal_iters,
-            "inner_tol": a.inner_tol, "fast_keys": {-1: "auto", 0: "exact", 1: "fp32_band"}[getattr(a, "fast_keys", -1)],
+            "inner_tol": a.inner_tol, "fast_keys": {-1: "auto", 0: "exact", 1: "fp32_band", 2: "fp32_band_full_pass"}[getattr(a, "fast_keys", -1)],
             "precision": a.precision, "seed": a.seed, "l2_flush": True,
             "parallelism": f"replicas{world}" if world > 1 else "single"}
 

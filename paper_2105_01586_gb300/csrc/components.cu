@@ -202,6 +202,7 @@ struct BuildArgs {
     int* kidx;
     int* kvert;
     int* members;  // urow_vertex: vertex of each row
+    int* ulist;    // the unknown vertices in ascending id (phase 1)
     int* rowcomp;
     int* blk_list;
     int* warp_list;
@@ -250,21 +251,28 @@ struct IndexMapOut {
             a.uidx[i] = -1;
         } else {
             a.kidx[i] = -1;
+            a.ulist[u] = i;
         }
     }
 };
 
+// over the unknown list: the component size at a root, else 0
 struct RootSizeIn {
     const BuildArgs* A;
-    __device__ __forceinline__ int operator()(int v) const {
+    __device__ __forceinline__ int operator()(int k) const {
         const BuildArgs& a = *A;
-        return (!a.mask[v] && __ldcg(a.root + v) == v) ? __ldcg(a.size + v) : 0;
+        const int v = __ldcg(a.ulist + k);
+        return __ldcg(a.root + v) == v ? __ldcg(a.size + v) : 0;
     }
 };
 
-struct StoreOut {
-    int* dst;
-    __device__ __forceinline__ void operator()(int i, int pre, int) const { dst[i] = pre; }
+// the first row of the component at root ulist[k]
+struct CStartOut {
+    const BuildArgs* A;
+    __device__ __forceinline__ void operator()(int k, int pre, int) const {
+        const BuildArgs& a = *A;
+        a.cstart[__ldcg(a.ulist + k)] = pre;
+    }
 };
 
 // the kernel stops at a failed barrier; the solve then reports the code
@@ -354,9 +362,12 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
     const int nU = A.nU >= 0 ? A.nU : __ldcg(A.nU_dev);
     if (nU == 0) return;  // uniform: no unknowns, no components
     // 2. union-find over the edges of A_UU, each from its larger endpoint;
-    //    the 8 slots of a vertex are loaded together
-    for (int v = tid0; v < V; v += stride) {
-        if (A.mask[v]) continue;
+    //    the 8 slots of a vertex are loaded together.  Phases 2-6 run over
+    //    the list of unknowns (a few per cent of the vertices), in ascending
+    //    vertex id, which keeps the numbering of the vertex-order loops.
+    const int nUl = __ldcg(A.nU_dev);
+    for (int k = tid0; k < nUl; k += stride) {
+        const int v = __ldcg(A.ulist + k);
         int nb[8];
         float cf[8];
 #pragma unroll
@@ -387,8 +398,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
     if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
     // 3. final roots (into a separate array: the forest no longer changes)
     //    and component sizes
-    for (int v = tid0; v < V; v += stride) {
-        if (A.mask[v]) continue;
+    for (int k = tid0; k < nUl; k += stride) {
+        const int v = __ldcg(A.ulist + k);
         int r = v;
         for (int p = __ldcg(A.parent + r); p != r; p = __ldcg(A.parent + r)) r = p;
         A.root[v] = r;
@@ -396,13 +407,13 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_system(BuildArgs A) {
     }
     if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
     // 4.-5. first row of each component: scan of the sizes at the roots
-    scan_count(RootSizeIn{&A}, V, A.tsum);
+    scan_count(RootSizeIn{&A}, nUl, A.tsum);
     if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
-    scan_emit(RootSizeIn{&A}, StoreOut{A.cstart}, V, A.tsum, A.cnt + CC_NROWS);
+    scan_emit(RootSizeIn{&A}, CStartOut{&A}, nUl, A.tsum, A.cnt + CC_NROWS);
     if (!grid_barrier(A.bar, A.err)) { build_fail(A); return; }
     // 6. members into their ranges; a one-row component needs no sort
-    for (int v = tid0; v < V; v += stride) {
-        if (A.mask[v]) continue;
+    for (int k = tid0; k < nUl; k += stride) {
+        const int v = __ldcg(A.ulist + k);
         int r = __ldcg(A.root + v), sz = __ldcg(A.size + r), st = __ldcg(A.cstart + r);
         int slot = st + atomicAdd(A.fill + r, 1);
         if (slot >= nU || st + sz > nU) {  // more unknowns than rows: a malformed mesh count
@@ -527,6 +538,7 @@ fem_status launch_build(fem_mesh* m, cudaStream_t s, int V, int T, int nU, size_
     FEM_TRY(ensure(m->uidx, nv, s));
     FEM_TRY(ensure(m->kidx, nv, s));
     FEM_TRY(ensure(m->urow_vertex, nv, s));
+    FEM_TRY(ensure(m->ulist, nv, s));
     FEM_TRY(ensure(m->kvert, nv, s));
     FEM_TRY(ensure(m->cc_parent, nv, s));
     FEM_TRY(ensure(m->cc_root, nv, s));
@@ -576,6 +588,7 @@ fem_status launch_build(fem_mesh* m, cudaStream_t s, int V, int T, int nU, size_
     A.kidx = m->kidx.p;
     A.kvert = m->kvert.p;
     A.members = m->urow_vertex.p;
+    A.ulist = m->ulist.p;
     A.rowcomp = m->rowcomp.p;
     A.blk_list = m->blk_list.p;
     A.warp_list = m->warp_list.p;

@@ -294,6 +294,8 @@ struct fem_mesh {
     fem::DArr<float> dinv32;        // nU inverse diagonal
     fem::DArr<double> dinv64;
     fem::DArr<int> urow_vertex;     // nU: vertex of each U row (rows numbered by component)
+    fem::DArr<int> ulist;           // nU: the unknown vertices in ascending id (system build)
+    fem::DArr<int> gcnt;            // new-vertex numbering of large bitmaps: marks per group of words, prefixes
     // components of the unknown-vertex graph (components.cu)
     fem::DArr<int> cc_parent, cc_root, cc_size, cc_fill, cc_cstart;
     fem::DArr<int> rowcomp;     // nU: rows of the component starting at this row, else 0

@@ -529,7 +529,7 @@ fem_status fem_mesh_destroy(fem_mesh* m) {
     release(m->flags, s); release(m->fscan, s); release(m->wcnt, s); release(m->topk_hist, s);
     release(m->uidx, s); release(m->kidx, s); release(m->nbr, s); release(m->coefA, s); release(m->diagA, s);
     release(m->ucol, s); release(m->uval32, s); release(m->uval64, s); release(m->udiag, s); release(m->ucnt, s); release(m->dinv32, s); release(m->dinv64, s);
-    release(m->urow_vertex, s); release(m->kvert, s);
+    release(m->urow_vertex, s); release(m->kvert, s); release(m->ulist, s); release(m->gcnt, s);
     release(m->cc_parent, s); release(m->cc_root, s); release(m->cc_size, s); release(m->cc_fill, s);
     release(m->cc_cstart, s); release(m->rowcomp, s); release(m->blk_list, s); release(m->warp_list, s);
     release(m->ccount, s);

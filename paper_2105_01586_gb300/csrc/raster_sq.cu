@@ -595,54 +595,41 @@ struct SqInc {
 // one record per covered node (coarse ones).  With I.vchg the kernel also
 // classifies every triangle dirty or clean (above), marks the squares of the
 // dirty fine ones, and takes the old bins of the counted dirty ones out of
-// the histograms (one atomic per distinct bin and warp).  The loop is
-// warp-uniform, so the whole warp takes part in the bin matching.
+// the histograms (a few per cent of the triangles, spread over the bins, so
+// plain atomics).
 __global__ void k_sq_records(const int* __restrict__ order, const int4* __restrict__ tri, const int2* __restrict__ vxy,
                              const double* __restrict__ uv, const float2* __restrict__ uvf,
                              const int* __restrict__ nodeof, int T, int N, SqRec* __restrict__ rec, SqInc I) {
     pdl_wait();
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int stride = gridDim.x * blockDim.x;
-    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < T; i0 += stride) {
-        const int i = i0 + lane;
-        unsigned blo = 0xffffffffu, bhi = 0xffffffffu;
-        if (i < T) {
-            const int t = order[i];
-            const int4 tr = tri[t];
-            const TriGeom g = tri_geom(tr, vxy, N);
-            ff uc, gx, gy;
-            tri_plane(g, tr, uv, uvf, uc, gx, gy);
-            SqRec r;
-            r.ax = (unsigned short)g.ax; r.ay = (unsigned short)g.ay;
-            r.bx = (unsigned short)g.bx; r.by = (unsigned short)g.by;
-            r.cx = (unsigned short)g.cx; r.cy = (unsigned short)g.cy;
-            r.t = t;
-            r.ucf = __fadd_rn(uc.hi, uc.lo);
-            r.gxf = __fadd_rn(gx.hi, gx.lo);
-            r.gyf = __fadd_rn(gy.hi, gy.lo);
-            r.pad = 0.f;
-            rec[i] = r;
-            if (I.vchg) {
-                const bool d = t >= I.Tk || I.tchg[t] || I.vchg[tr.x] || I.vchg[tr.y] || I.vchg[tr.z];
-                I.tdirty[t] = d ? 1 : 0;
-                if (d) {
-                    const int nd = nodeof[i];
-                    if (nd >= 0) I.dmark[nd >> 1] = 1;
-                    if (t < I.Tk && I.hcnt[t]) {
-                        blo = fast_bin(I.lo[t]);
-                        bhi = fast_bin(I.hi[t]);
-                    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
+        const int t = order[i];
+        const int4 tr = tri[t];
+        const TriGeom g = tri_geom(tr, vxy, N);
+        ff uc, gx, gy;
+        tri_plane(g, tr, uv, uvf, uc, gx, gy);
+        SqRec r;
+        r.ax = (unsigned short)g.ax; r.ay = (unsigned short)g.ay;
+        r.bx = (unsigned short)g.bx; r.by = (unsigned short)g.by;
+        r.cx = (unsigned short)g.cx; r.cy = (unsigned short)g.cy;
+        r.t = t;
+        r.ucf = __fadd_rn(uc.hi, uc.lo);
+        r.gxf = __fadd_rn(gx.hi, gx.lo);
+        r.gyf = __fadd_rn(gy.hi, gy.lo);
+        r.pad = 0.f;
+        rec[i] = r;
+        if (I.vchg) {
+            const bool d = t >= I.Tk || I.tchg[t] || I.vchg[tr.x] || I.vchg[tr.y] || I.vchg[tr.z];
+            I.tdirty[t] = d ? 1 : 0;
+            if (d) {
+                const int nd = nodeof[i];
+                if (nd >= 0) I.dmark[nd >> 1] = 1;
+                if (t < I.Tk && I.hcnt[t]) {
+                    atomicSub(I.hlo + fast_bin(I.lo[t]), 1u);
+                    atomicSub(I.hhi + fast_bin(I.hi[t]), 1u);
                 }
             }
-            if (I.tchg) I.tchg[t] = 0;
         }
-        if (I.vchg) {
-            unsigned peers = __match_any_sync(FULL, blo);
-            if (blo != 0xffffffffu && (__ffs(peers) - 1) == lane) atomicSub(I.hlo + blo, (unsigned)__popc(peers));
-            peers = __match_any_sync(FULL, bhi);
-            if (bhi != 0xffffffffu && (__ffs(peers) - 1) == lane) atomicSub(I.hhi + bhi, (unsigned)__popc(peers));
-        }
+        if (I.tchg) I.tchg[t] = 0;
     }
 }
 

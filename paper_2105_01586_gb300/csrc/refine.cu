@@ -612,11 +612,15 @@ __device__ __forceinline__ int midpoint_id(const unsigned* __restrict__ bm, cons
     return V0 + wpre[p >> 5] + __popc(below);
 }
 
-// New vertices as one fused scan over the bitmap words: the input is the
-// number of marked midpoints in word w (and clears word w of the other
-// round's bitmaps: the edge bitmaps alternate between two buffers), the
-// output numbers them V0 + (marks before them) and writes their positions
-// and mask flags.
+// New vertices, numbered V0 + (marks before them) in ascending pixel order,
+// with their positions and mask flags, and wpre[w] = the marks before word w
+// (read by midpoint_id, which asks only for words with a mark).  The edge
+// bitmaps alternate between two buffers by round, and the same pass clears
+// the other round's words.  Up to kScanSmallN words (images up to about
+// 2049^2) one fused scan runs over the words.  Larger bitmaps go through
+// groups of 32 words (1024 pixels), a warp per group with a lane per word
+// (coalesced): the groups' counts, a scan over them (1/32 of the length),
+// and the numbering within each group that holds a mark (most hold none).
 struct WordIn {
     const unsigned* bmM;
     unsigned* clearM;
@@ -637,9 +641,11 @@ struct NewVertexOut {
     int2* vxy;
     unsigned char* mask;
     int* n_new_mask;
-    __device__ __forceinline__ void operator()(long long w, int pre, int) const {
+    // the marks of word w, numbered from V0 + pre; returns the new mask vertices
+    __device__ __forceinline__ int word(long long w, int pre) const {
         wpre[w] = pre;
-        unsigned bits = bmM[w], sbits = bmS[w];
+        unsigned bits = bmM[w];
+        const unsigned sbits = bmS[w];
         int id = V0 + pre, nm = 0;
         while (bits) {
             int b = __ffs(bits) - 1;
@@ -652,9 +658,57 @@ struct NewVertexOut {
             nm += mk;
             id++;
         }
+        return nm;
+    }
+    __device__ __forceinline__ void operator()(long long w, int pre, int cnt) const {
+        if (cnt == 0) return;
+        const int nm = word(w, pre);
         if (nm) atomicAdd(n_new_mask, nm);
     }
 };
+
+constexpr int kWordGroup = 32;
+
+// a warp per group of 32 words: the group's marks, and the other round's
+// words cleared
+__global__ void k_group_count(const unsigned* __restrict__ bmM, unsigned* __restrict__ clearM,
+                              unsigned* __restrict__ clearS, long long nw, int ngroups, int* __restrict__ gcnt) {
+    pdl_wait();
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = (int)(gt >> 5), lane = threadIdx.x & 31;
+    if (g >= ngroups) return;  // the same for the whole warp
+    const long long w = (long long)g * kWordGroup + lane;
+    int c = 0;
+    if (w < nw) {
+        c = __popc(bmM[w]);
+        clearM[w] = 0u;
+        clearS[w] = 0u;
+    }
+    c = warp_sum(c);
+    if (lane == 0) gcnt[g] = c;
+}
+
+// a warp per group that holds a mark: each word's marks before it (the
+// group's prefix plus a warp scan), then the word's new vertices
+__global__ void k_group_number(NewVertexOut O, long long nw, int ngroups, const int* __restrict__ gcnt,
+                               const int* __restrict__ gpre) {
+    pdl_wait();
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = (int)(gt >> 5), lane = threadIdx.x & 31;
+    if (g >= ngroups || gcnt[g] == 0) return;  // the same for the whole warp
+    const long long w = (long long)g * kWordGroup + lane;
+    const unsigned bits = w < nw ? O.bmM[w] : 0u;
+    const int c = __popc(bits);
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    int nm = bits ? O.word(w, gpre[g] + inc - c) : 0;
+    nm = warp_sum(nm);
+    if (lane == 0 && nm) atomicAdd(O.n_new_mask, nm);
+}
 
 // Bisection flags [gen 1 | gen 2 of the kept child | gen 2 of the new
 // child] as the input of one fused scan (the scan numbers the new
@@ -926,11 +980,22 @@ fem_status refine_round(fem_mesh* m, const float* f, double frac, long long vsta
         int grid = T <= kClosureOneBlockT ? 1 : coop_grid((const void*)k_closure, 256, T, m->num_sms);
         FEM_TRY(launch_coop(F_REFINE, (const void*)k_closure, grid, 256, 0, s, args, "k_closure"));
     }
-    int Wi = (int)W;
     int* stage_dev = m->host_stage_dev ? (int*)m->host_stage_dev + kRoundStageInts : nullptr;
-    FEM_TRY(scan_fused(m, WordIn{bmM, bmM_other, bmS_other},
-                       NewVertexOut{bmM, bmS, (int*)m->wpre.p, N, V, m->W, m->H, m->vxy.p, m->mask.p, nmask_new}, Wi, s, nnew,
-                       F_REFINE));
+    const NewVertexOut nvo{bmM, bmS, (int*)m->wpre.p, N, V, m->W, m->H, m->vxy.p, m->mask.p, nmask_new};
+    if (W <= kScanSmallN) {
+        FEM_TRY(scan_fused(m, WordIn{bmM, bmM_other, bmS_other}, nvo, (int)W, s, nnew, F_REFINE));
+    } else {
+        const int groups = (int)((W + kWordGroup - 1) / kWordGroup);
+        FEM_TRY(ensure(m->gcnt, (size_t)2 * groups, s));
+        int* gcnt = m->gcnt.p;
+        int* gpre = m->gcnt.p + groups;
+        const int gb = (int)(((long long)groups * 32 + 255) / 256);
+        FEM_LAUNCH(F_REFINE, s, k_group_count, gb, 256, 0, (const unsigned*)bmM, bmM_other, bmS_other, (long long)W,
+                   groups, gcnt);
+        FEM_TRY(scan_fused(m, ScanLoad{gcnt}, ScanStoreTo{gpre}, groups, s, nnew, F_REFINE));
+        FEM_LAUNCH(F_REFINE, s, k_group_number, gb, 256, 0, nvo, (long long)W, groups, (const int*)gcnt,
+                   (const int*)gpre);
+    }
     m->bm_parity ^= 1;
     FEM_TRY(scan_fused(m, BisectFlagIn{m->tri.p, m->vxy.p, bmM, T, N, m->flags.p}, ScanStore{m->fscan.p}, 3 * T, s,
                        ntri, F_REFINE));
