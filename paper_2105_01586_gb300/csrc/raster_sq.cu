@@ -618,8 +618,12 @@ __global__ void k_sq_records(const int* __restrict__ order, const int4* __restri
         r.pad = 0.f;
         rec[i] = r;
         if (I.vchg) {
-            const bool d = t >= I.Tk || I.tchg[t] || I.vchg[tr.x] || I.vchg[tr.y] || I.vchg[tr.z];
-            I.tdirty[t] = d ? 1 : 0;
+            // flags are written only where they change: a few per cent of
+            // the triangles, instead of scattered byte stores for all
+            const unsigned char tc = t < I.Tk ? I.tchg[t] : 1;  // a new id's flag is not yet cleared
+            const bool d = tc || I.vchg[tr.x] || I.vchg[tr.y] || I.vchg[tr.z];
+            if (tc) I.tchg[t] = 0;
+            if (I.tdirty[t] != (unsigned char)d) I.tdirty[t] = d ? 1 : 0;
             if (d) {
                 const int nd = nodeof[i];
                 if (nd >= 0) I.dmark[nd >> 1] = 1;
@@ -628,8 +632,9 @@ __global__ void k_sq_records(const int* __restrict__ order, const int4* __restri
                     atomicSub(I.hhi + fast_bin(I.hi[t]), 1u);
                 }
             }
+        } else if (I.tchg) {
+            I.tchg[t] = 0;
         }
-        if (I.tchg) I.tchg[t] = 0;
     }
 }
 
@@ -1345,7 +1350,7 @@ fem_status sq_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, FastOu
     I.tchg = m->tchg.p;
     if (inc) {
         FEM_TRY(ensure(m->vchg, (size_t)V, s));
-        FEM_TRY(ensure(m->tdirty, (size_t)T, s));
+        FEM_TRY(ensure(m->tdirty, (size_t)T, s, (size_t)m->inc_T));
         FEM_TRY(ensure(m->sq_dlist, (size_t)nsq + 1, s));
         if (!m->sq_dmark.p || m->sq_dmark.n < (size_t)nsq) {
             FEM_TRY(ensure(m->sq_dmark, (size_t)nsq, s));
@@ -1387,6 +1392,10 @@ fem_status sq_keys_fast(fem_mesh* m, const double* uv, const float2* uvf, FastOu
     FEM_LAUNCH(F_RASTER, s, k_sq_final<SQ_FAST>, m->num_sms * 8, 256, 0, A, (const int*)m->sq_coarse.p,
                (const int*)(m->sq_ctr.p + 1));
     if (!inc) {
+        // the incremental passes that follow read and write only changes of
+        // the dirty flags: they start from all clean
+        FEM_TRY(ensure(m->tdirty, (size_t)T, s));
+        FEM_CUDA(cudaMemsetAsync(m->tdirty.p, 0, (size_t)T, s));
         FEM_CUDA(cudaMemcpyAsync(m->uvk.p, uv, sizeof(double) * V, cudaMemcpyDeviceToDevice, s));
         if (uvf) FEM_CUDA(cudaMemcpyAsync(m->uvfk.p, uvf, sizeof(float2) * V, cudaMemcpyDeviceToDevice, s));
     }
