@@ -768,9 +768,12 @@ def run_serving(a, world, rank):
         lat = np.array([r["t_end"] - r["t_submit"] for r in res]) * 1e3
         span = max(r["t_end"] for r in res) - min(r["t_submit"] for r in res)
         bad = sum(1 for r in res if r["status"] not in (0, 4))
+        ratio = np.array([r["mem_measured"] / r["mem_estimate"] for r in res if r["mem_estimate"] > 0])
         return {"requests": R, "makespan_s": round(span, 3), "mpixel_per_s": round(mpx / span, 3),
                 "requests_per_s": round(R / span, 3), "p50_ms": round(float(np.percentile(lat, 50)), 2),
-                "p99_ms": round(float(np.percentile(lat, 99)), 2), "failed": bad}
+                "p99_ms": round(float(np.percentile(lat, 99)), 2), "failed": bad,
+                "mem_measured_over_estimate": {"median": round(float(np.median(ratio)), 4),
+                                               "max": round(float(ratio.max()), 4)} if ratio.size else None}
 
     # warm-up: one request of each size
     with Server(slots=4) as sv:

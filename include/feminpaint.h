@@ -298,9 +298,13 @@ FEM_API fem_status fem_tonal_loss(fem_mesh *m, const float *g_dev, const float *
  * 5 of the benchmarks; the paper has no serving layer).  A server owns
  * `slots` worker threads, each with its own CUDA stream on the current
  * device.  Requests wait in a FIFO queue; the head request is admitted when a
- * slot is free and its estimated device memory fits next to the running
- * requests within `mem_budget_bytes` (0 = half of the free device memory; a
- * request larger than the budget runs alone).  An admitted request runs the
+ * slot is free and its device memory fits next to the running requests
+ * within `mem_budget_bytes` (0 = half of the free device memory; a request
+ * larger than the budget runs alone).  A request's memory is a static
+ * estimate scaled by 1.25 times the largest ratio of measured peak to
+ * estimate among the requests that have finished (the static estimate
+ * alone before any has); the library counts every device allocation on the
+ * stream it was made on.  An admitted request runs the
  * whole path on its slot's stream: fem_mesh_create, fem_spatial_refine,
  * fem_gather_mask, fem_tonal_opt and the result read-back.  Requests in
  * different slots overlap on the device; each computes exactly what it
@@ -324,9 +328,10 @@ FEM_API fem_status fem_server_wait(fem_server *sv, long long id, double timeout_
 /* Results of a finished request (host buffers, any may be NULL):
  * sizes[4] = V, T, nmask, width; xy (2V), tri (3T), is_mask (V) as in
  * fem_mesh_export; g (nmask float32, the tonally optimised values);
- * times[8] = submit, start and end time (seconds, steady clock), spatial
+ * times[9] = submit, start and end time (seconds, steady clock), spatial
  * rounds, spatial CG iterations, tonal iterations, tonal relative residual,
- * estimated device bytes.  Query the sizes first with NULL arrays.  Returns
+ * the static estimate of its device bytes, the peak device bytes it held
+ * (measured).  Query the sizes first with NULL arrays.  Returns
  * the request's own status (FEM_E_NOT_CONVERGED if the tonal cap was hit). */
 FEM_API fem_status fem_server_result(fem_server *sv, long long id, int *sizes, int *xy, int *tri,
                                      unsigned char *is_mask, float *g, double *times);

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "fem_internal.cuh"
@@ -154,6 +155,51 @@ static std::atomic<long long> g_alloc_calls{0};
 static std::atomic<long long> g_alloc_fail_at{-1};
 static std::atomic<cudaMemPool_t> g_pool{nullptr};
 
+// Device bytes held per stream (the stream an allocation was made on), live
+// and at their peak since the last stream_alloc_peak_take: the serving loop
+// runs each request on its own stream and admits by what they measured.
+// Allocations happen only when arrays grow, so a mutex is cheap here.
+// The tables are never destroyed, so a mesh released during process exit
+// still finds them.
+struct AllocAcct {
+    std::mutex mu;
+    std::unordered_map<void*, std::pair<size_t, cudaStream_t>> ptr;
+    std::unordered_map<cudaStream_t, std::pair<size_t, size_t>> stream;  // live, peak
+};
+static AllocAcct& acct() {
+    static AllocAcct* a = new AllocAcct;
+    return *a;
+}
+
+static void acct_alloc(void* p, size_t bytes, cudaStream_t s) {
+    AllocAcct& A = acct();
+    std::lock_guard<std::mutex> lk(A.mu);
+    A.ptr[p] = {bytes, s};
+    auto& a = A.stream[s];
+    a.first += bytes;
+    if (a.first > a.second) a.second = a.first;
+}
+
+static void acct_free(void* p) {
+    AllocAcct& A = acct();
+    std::lock_guard<std::mutex> lk(A.mu);
+    auto it = A.ptr.find(p);
+    if (it == A.ptr.end()) return;
+    auto& a = A.stream[it->second.second];
+    a.first -= std::min(a.first, it->second.first);
+    A.ptr.erase(it);
+}
+
+size_t stream_alloc_peak_take(cudaStream_t s) {
+    AllocAcct& A = acct();
+    std::lock_guard<std::mutex> lk(A.mu);
+    auto it = A.stream.find(s);
+    if (it == A.stream.end()) return 0;
+    const size_t peak = it->second.second;
+    it->second.second = it->second.first;  // the next peak starts from what is live now
+    return peak;
+}
+
 fem_status dalloc_raw(void** p, size_t bytes, cudaStream_t s) {
     if (bytes == 0) bytes = 16;
     long long k = g_alloc_calls.fetch_add(1);
@@ -170,11 +216,15 @@ fem_status dalloc_raw(void** p, size_t bytes, cudaStream_t s) {
         set_error("device allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
         return FEM_E_OOM;
     }
+    acct_alloc(*p, bytes, s);
     return FEM_OK;
 }
 
 void dfree_raw(void* p, cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
+    if (p) {
+        acct_free(p);
+        cudaFreeAsync(p, s);
+    }
 }
 
 int sm_count() {

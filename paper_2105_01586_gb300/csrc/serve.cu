@@ -2,8 +2,11 @@
 //
 // A server owns `slots` worker threads, each with its own CUDA stream.  A
 // request (an image, a vertex density and parameters) waits in a FIFO queue
-// until a slot is free and its estimated device memory fits the budget next
-// to the requests already running; it is then admitted and runs the whole
+// until a slot is free and its device memory fits the budget next to the
+// requests already running.  That memory is a static upper estimate scaled
+// by the largest ratio of measured peak to estimate among the requests that
+// have finished (each request's allocations are counted on its slot's
+// stream).  It is then admitted and runs the whole
 // path on its slot's stream: mesh creation, spatial optimisation (Sec. 3),
 // g = f at the mask vertices and tonal optimisation (Sec. 4).  Requests on
 // different slots overlap on the device: most kernels of one request occupy
@@ -11,8 +14,10 @@
 // the GPU.  Every request computes exactly what it would compute alone: the
 // kernels are deterministic and share no state across meshes.  Results (the
 // mesh, g and timings) stay in host memory until the caller releases them.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -23,6 +28,11 @@
 #include <vector>
 
 #include "fem_internal.cuh"
+
+namespace fem {
+// peak device bytes allocated on stream s since the last call (mesh.cu)
+size_t stream_alloc_peak_take(cudaStream_t s);
+}  // namespace fem
 
 namespace fem {
 namespace {
@@ -39,7 +49,9 @@ struct Request {
     double density = 0.0;
     fem_params params{};
     std::vector<float> f;  // host copy of the image
-    size_t mem_estimate = 0;
+    size_t mem_estimate = 0;   // static upper estimate (estimate_bytes)
+    size_t mem_reserved = 0;   // what admission reserved: the estimate scaled by the measured ratio
+    size_t mem_measured = 0;   // peak device bytes the request's stream held (after it ran)
     double t_submit = 0, t_start = 0, t_end = 0;
     fem_status status = FEM_OK;
     std::string error;
@@ -61,6 +73,11 @@ struct fem_server {
     int slots = 0;
     size_t budget = 0;
     size_t in_use = 0;
+    // largest measured peak / static estimate over the finished requests,
+    // with a margin (1 until a request has finished): admission reserves
+    // the estimate scaled by it
+    double mem_scale = 1.0;
+    bool measured_any = false;
     int dev = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -86,6 +103,10 @@ size_t estimate_bytes(int width, double density) {
     double T = 2.0 * V;
     return (size_t)(4.0 * P + 0.5 * P + 2.0 * (260.0 * V + 220.0 * T + 140.0 * V) + (64 << 20));
 }
+
+// Margin on the measured ratio: requests of other sizes and densities may
+// hold a little more per estimated byte than those measured so far.
+constexpr double kMeasuredMargin = 1.25;
 
 fem_status run_request(Request& r, cudaStream_t s) {
     fem_mesh* m = nullptr;
@@ -144,24 +165,36 @@ void worker_main(fem_server* sv) {
             // FIFO admission: the head request starts when its memory fits
             // next to the running ones (a request larger than the whole
             // budget runs alone)
+            auto need_of = [&](const Request& q) {
+                return (size_t)std::ceil(sv->mem_scale * (double)q.mem_estimate);
+            };
             sv->cv_work.wait(lk, [&] {
                 if (sv->stopping) return true;
                 if (sv->queue.empty()) return false;
-                size_t need = sv->queue.front()->mem_estimate;
+                size_t need = need_of(*sv->queue.front());
                 return sv->in_use + need <= sv->budget || sv->running == 0;
             });
             if (sv->stopping && sv->queue.empty()) break;
             if (sv->stopping) break;
             r = sv->queue.front();
             sv->queue.pop_front();
-            sv->in_use += r->mem_estimate;
+            r->mem_reserved = need_of(*r);
+            sv->in_use += r->mem_reserved;
             sv->running++;
             r->running = true;
             r->t_start = now_s();
         }
+        stream_alloc_peak_take(s);  // the peak from here on is this request's
         fem_status st = run_request(*r, s);
+        const size_t measured = stream_alloc_peak_take(s);
         {
             std::lock_guard<std::mutex> lk(sv->mu);
+            r->mem_measured = measured;
+            if (st == FEM_OK && r->mem_estimate > 0) {
+                const double ratio = kMeasuredMargin * (double)measured / (double)r->mem_estimate;
+                sv->mem_scale = sv->measured_any ? std::max(sv->mem_scale, ratio) : ratio;
+                sv->measured_any = true;
+            }
             r->status = st;
             if (st != FEM_OK) r->error = fem_last_error();
             r->t_end = now_s();
@@ -169,7 +202,7 @@ void worker_main(fem_server* sv) {
             r->running = false;
             r->f.clear();
             r->f.shrink_to_fit();
-            sv->in_use -= r->mem_estimate;
+            sv->in_use -= r->mem_reserved;
             sv->running--;
         }
         sv->cv_done.notify_all();
@@ -282,6 +315,7 @@ fem_status fem_server_result(fem_server* sv, long long id, int* sizes, int* xy, 
         times[5] = r->tonal.tonal_iters;
         times[6] = r->tonal.tonal_relres;
         times[7] = (double)r->mem_estimate;
+        times[8] = (double)r->mem_measured;
     }
     if (r->status != FEM_OK && r->status != FEM_E_NOT_CONVERGED) set_error(r->error);
     return r->status;

@@ -40,13 +40,13 @@ class Server:
         tri = np.zeros((T, 3), np.int32)
         mk = np.zeros(V, np.uint8)
         g = np.zeros(K, np.float32)
-        times = np.zeros(8, np.float64)
+        times = np.zeros(9, np.float64)
         st = _lib.fem_server_result(self.h, rid, sizes.ctypes.data, xy.ctypes.data, tri.ctypes.data, mk.ctypes.data,
                                     g.ctypes.data, times.ctypes.data)
         return {"status": int(st), "width": width, "xy": xy, "tri": tri, "mask": mk, "g": g,
                 "t_submit": times[0], "t_start": times[1], "t_end": times[2], "rounds": int(times[3]),
                 "cg_iters": int(times[4]), "tonal_iters": int(times[5]), "tonal_relres": float(times[6]),
-                "mem_estimate": int(times[7])}
+                "mem_estimate": int(times[7]), "mem_measured": int(times[8])}
 
     def state(self, rid: int) -> str:
         """"queued", "running" or "finished" (fem_server_state)."""

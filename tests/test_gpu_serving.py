@@ -66,6 +66,20 @@ def test_admission_by_memory_serialises_when_the_budget_is_small(fem):
         assert s1 >= e0 - 1e-6
 
 
+def test_measured_peak_is_within_the_static_estimate(fem):
+    """Each request's device allocations are counted on its slot's stream:
+    the measured peak holds at least the request's image copy and stays
+    below the static upper estimate that admission is scaled from."""
+    from paper_2105_01586_gb300.serving import Server
+    jobs = _jobs()[:6]
+    with Server(slots=2) as sv:
+        ids = [sv.submit(f, d) for f, d in jobs]
+        res = [sv.result(rid) if sv.wait(rid, 600.0) else None for rid in ids]
+    for (f, _), r in zip(jobs, res):
+        assert r is not None and r["status"] == 0
+        assert 4 * f.size <= r["mem_measured"] <= r["mem_estimate"]
+
+
 def test_serving_matches_the_direct_api(fem):
     """A served request returns the same mesh and g as calling the library
     directly on one stream."""
