@@ -55,6 +55,14 @@
  *      term restricted to the image, and the padding holds no unknowns
  *      (with no data there, they would form large badly conditioned
  *      blocks).  With W = H = N everything reduces to the square case.
+ *  R10 Colour (Sec. 5 says only that colour is straightforward): C <= 4
+ *      channels share the mesh, the mask set and A_UU; each channel has its
+ *      own mask values and solve, and a triangle's error is the sum of its
+ *      channels' errors (channel 0 first).  C = 1 is the grey case.
+ *  R11 The L1 data term of Sec. 5: min_g sum_p |(B g)_p - f_p| by
+ *      iteratively reweighted least squares, weights 1 / max(|B g - f|, eps)
+ *      from the current g, each step a weighted least-squares solve; with
+ *      eps each step is a majorise-minimise step of the Huber function.
  *
  * Threads.  Compiled with -fopenmp (the multi-core CPU baseline), two loops
  * share their iterations among threads: the per-triangle raster loop and the
