@@ -407,6 +407,19 @@ static fem_status check_mesh(const fem_mesh* m) {
     return FEM_OK;
 }
 
+namespace fem {
+// the triangles' (a, b, c) without the padding word of the int4 rows
+__global__ void k_pack_tri(const int4* __restrict__ tri, int T, int* __restrict__ out) {
+    pdl_wait();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        const int4 v = tri[t];
+        out[3 * (size_t)t] = v.x;
+        out[3 * (size_t)t + 1] = v.y;
+        out[3 * (size_t)t + 2] = v.z;
+    }
+}
+}  // namespace fem
+
 extern "C" {
 
 void fem_params_default(fem_params* p) {
@@ -639,18 +652,21 @@ fem_status fem_mesh_stats(const fem_mesh* m, fem_stats* out) {
 fem_status fem_mesh_export(fem_mesh* m, int* xy, int* tri, unsigned char* is_mask) {
     FEM_TRY(check_mesh(m));
     cudaStream_t s = m->last_stream;
+    if (tri && m->T > 0) {
+        // (a, b, c) packed from the int4 rows on the device, then one copy
+        // straight into the caller's array
+        int* t3 = nullptr;
+        FEM_TRY(dalloc_raw((void**)&t3, sizeof(int) * 3 * (size_t)m->T, s));
+        const int grid = (int)std::min<long long>(((long long)m->T + 255) / 256, (long long)m->num_sms * 16);
+        FEM_LAUNCH(F_OTHER, s, k_pack_tri, grid, 256, 0, (const int4*)m->tri.p, m->T, t3);
+        cudaError_t e = cudaMemcpyAsync(tri, t3, sizeof(int) * 3 * (size_t)m->T, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        dfree_raw(t3, s);
+        if (e != cudaSuccess) return cuda_fail(e, "fem_mesh_export: triangles");
+    }
     FEM_CUDA(cudaStreamSynchronize(s));
     if (xy) FEM_CUDA(cudaMemcpy(xy, m->vxy.p, sizeof(int2) * m->V, cudaMemcpyDeviceToHost));
     if (is_mask) FEM_CUDA(cudaMemcpy(is_mask, m->mask.p, m->V, cudaMemcpyDeviceToHost));
-    if (tri) {
-        std::vector<int4> t4(m->T);
-        FEM_CUDA(cudaMemcpy(t4.data(), m->tri.p, sizeof(int4) * m->T, cudaMemcpyDeviceToHost));
-        for (int t = 0; t < m->T; ++t) {
-            tri[3 * t] = t4[t].x;
-            tri[3 * t + 1] = t4[t].y;
-            tri[3 * t + 2] = t4[t].z;
-        }
-    }
     return FEM_OK;
 }
 
